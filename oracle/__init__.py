@@ -1,0 +1,136 @@
+"""CPU ORACLE -- test infrastructure, not part of the product path.
+
+Python loader for the plain single-threaded C evaluator in ``wh_oracle.c``.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package; the CUDA library never does, and this
+package imports nothing from it.
+
+Functions and the independent checks that pin them (all in ``tests/``):
+
+* ``dist``           -- grid distance; pinned by Dijkstra (scipy) on the
+                        explicit aisle/cross-aisle graph, all pairs, several
+                        layouts (the paper names Dijkstra, Sec. 5).
+* ``sshape``         -- S-shape walk; pinned by the closed form
+                        2*x_r + (m even ? m*Y : (m-1)*Y + 2*d_r) and by
+                        hand-drawn tours.
+* ``heldkarp`` / ``permutation`` -- exact optimum on small tours; pinned
+                        against each other and against a pure-Python
+                        enumeration over scipy shortest paths.
+* ``rr``             -- Ratliff-Rosenthal DP; pinned by Held-Karp on
+                        thousands of random tours of <= 10 picks and by the
+                        route invariants (opt <= S-shape, lower bound, even,
+                        monotone in the pick set, ...).
+* ``eval_plans``     -- plan sums; pinned by summing per-tour calls over
+                        hand-assembled pick lists.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, portable C99) into liboracle.so."""
+    srcs = [os.path.join(_HERE, f) for f in ("wh_oracle.c", "wh_oracle.h")]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp,
+                               os.path.join(_HERE, "wh_oracle.c")])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class OrLayout(ctypes.Structure):
+    _fields_ = [("n_aisles", ctypes.c_int32), ("slots_per_side", ctypes.c_int32),
+                ("aisle_pitch", ctypes.c_int32), ("slot_pitch", ctypes.c_int32),
+                ("cross_aisle_width", ctypes.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            lp = ctypes.POINTER(OrLayout)
+            lib.or_dist.restype = ctypes.c_int64
+            lib.or_dist.argtypes = [lp] + [ctypes.c_int32] * 4
+            for name in ("or_sshape_tour", "or_rr_tour", "or_heldkarp_tour", "or_permutation_tour"):
+                f = getattr(lib, name)
+                f.restype = ctypes.c_int64
+                f.argtypes = [lp, i32p, ctypes.c_int32]
+            lib.or_eval_plans.restype = ctypes.c_int
+            lib.or_eval_plans.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
+                                          ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, i64p, i64p]
+            _lib = lib
+    return _lib
+
+
+def _layout(lay) -> OrLayout:
+    return OrLayout(lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _ptr(a, t=ctypes.c_int32):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def dist(lay, a1: int, y1: int, a2: int, y2: int) -> int:
+    return int(_load().or_dist(ctypes.byref(_layout(lay)), a1, y1, a2, y2))
+
+
+def _tour(fn, lay, locs) -> int:
+    arr = _i32(locs)
+    v = int(fn(ctypes.byref(_layout(lay)), _ptr(arr), arr.shape[0]))
+    if v < 0:
+        raise ValueError(f"oracle error {v}")
+    return v
+
+
+def sshape(lay, locs) -> int:
+    return _tour(_load().or_sshape_tour, lay, locs)
+
+
+def rr(lay, locs) -> int:
+    return _tour(_load().or_rr_tour, lay, locs)
+
+
+def heldkarp(lay, locs) -> int:
+    return _tour(_load().or_heldkarp_tour, lay, locs)
+
+
+def permutation(lay, locs) -> int:
+    return _tour(_load().or_permutation_tour, lay, locs)
+
+
+def eval_plans(inst, slot_map=None, slot_map_stride: int = 0):
+    """Per-tour and per-plan S-shape and optimal costs of an Instance:
+    (tour_s int32, tour_rr int32, plan_s int64, plan_rr int64)."""
+    lib = _load()
+    smap = _i32(inst.slot_map if slot_map is None else slot_map)
+    off, lines = _i32(inst.order_off), _i32(inst.line_sku)
+    pto, to, seq = _i32(inst.plan_tour_off), _i32(inst.tour_off), _i32(inst.order_seq)
+    nt, npl = to.shape[0] - 1, pto.shape[0] - 1
+    ts, tr = np.zeros(max(nt, 1), np.int32), np.zeros(max(nt, 1), np.int32)
+    ps, pr = np.zeros(max(npl, 1), np.int64), np.zeros(max(npl, 1), np.int64)
+    rc = lib.or_eval_plans(ctypes.byref(_layout(inst.layout)), off.shape[0] - 1, _ptr(off), _ptr(lines),
+                           inst.n_sku, _ptr(smap), slot_map_stride, npl, _ptr(pto), _ptr(to), _ptr(seq),
+                           _ptr(ts), _ptr(tr), _ptr(ps, ctypes.c_int64), _ptr(pr, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError(f"or_eval_plans error {rc}")
+    return ts[:nt], tr[:nt], ps[:npl], pr[:npl]

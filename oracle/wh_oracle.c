@@ -1,0 +1,445 @@
+/*
+ * CPU ORACLE for the warehouse plan evaluator -- TEST INFRASTRUCTURE ONLY.
+ * Plain single-threaded C99; see wh_oracle.h for what it follows and who may
+ * use it.  Nothing here is tuned: clarity first, one obvious step at a time.
+ */
+#include "wh_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+#define INF64 ((int64_t)1 << 60)
+
+typedef struct { int32_t a; int64_t y; } pick_t;
+
+/* ---------------------------------------------------------------- geometry */
+
+/* back cross-aisle centre depth: Y = W + (L-1)*S */
+static int64_t depth_back(const or_layout *g) {
+    return (int64_t)g->cross_aisle_width + (int64_t)(g->slots_per_side - 1) * g->slot_pitch;
+}
+
+/* Reading of the layout: positive sizes, even cross-aisle width, and the
+ * longest S-shape tour 2*x_{A-1} + A*Y below 2^30 so every tour cost fits an
+ * int32 with room to spare. */
+static int layout_check(const or_layout *g) {
+    if (!g || g->n_aisles < 1 || g->slots_per_side < 1 || g->aisle_pitch < 1 ||
+        g->slot_pitch < 1 || g->cross_aisle_width < 2 || (g->cross_aisle_width & 1))
+        return OR_EINVAL;
+    int64_t worst = 2 * (int64_t)(g->n_aisles - 1) * g->aisle_pitch + (int64_t)g->n_aisles * depth_back(g);
+    if (worst >= ((int64_t)1 << 30)) return OR_ERANGE;
+    return OR_OK;
+}
+
+/* location id -> (aisle, depth); loc = (a*2 + side)*L + k, depth = W/2 + k*S */
+static int loc_to_pick(const or_layout *g, int32_t loc, pick_t *out) {
+    int64_t n_loc = (int64_t)g->n_aisles * 2 * g->slots_per_side;
+    if (loc < 0 || loc >= n_loc) return OR_ERANGE;
+    int32_t a = loc / (2 * g->slots_per_side);
+    int32_t k = loc % g->slots_per_side;
+    out->a = a;
+    out->y = g->cross_aisle_width / 2 + (int64_t)k * g->slot_pitch;
+    return OR_OK;
+}
+
+int64_t or_dist(const or_layout *g, int32_t a1, int32_t y1, int32_t a2, int32_t y2) {
+    int64_t Y = depth_back(g);
+    if (a1 == a2) return y1 > y2 ? (int64_t)y1 - y2 : (int64_t)y2 - y1;
+    int64_t dx = (int64_t)(a1 > a2 ? a1 - a2 : a2 - a1) * g->aisle_pitch;
+    int64_t via_front = (int64_t)y1 + y2;
+    int64_t via_back = 2 * Y - y1 - y2;
+    return dx + (via_front < via_back ? via_front : via_back);
+}
+
+static int cmp_pick(const void *p, const void *q) {
+    const pick_t *u = (const pick_t *)p, *v = (const pick_t *)q;
+    if (u->a != v->a) return u->a < v->a ? -1 : 1;
+    return u->y < v->y ? -1 : (u->y > v->y);
+}
+
+/* The tour's pick set: decode, sort by (aisle, depth), drop duplicates.
+ * Returns the number of distinct picks or an error. */
+static int32_t pick_set(const or_layout *g, const int32_t *locs, int32_t n, pick_t **out) {
+    *out = NULL;
+    if (n < 0) return OR_EINVAL;
+    if (n == 0) return 0;
+    pick_t *p = (pick_t *)malloc(sizeof(pick_t) * (size_t)n);
+    if (!p) return OR_ENOMEM;
+    for (int32_t i = 0; i < n; ++i) {
+        if (loc_to_pick(g, locs[i], &p[i]) != OR_OK) { free(p); return OR_ERANGE; }
+    }
+    qsort(p, (size_t)n, sizeof(pick_t), cmp_pick);
+    int32_t m = 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (m == 0 || p[i].a != p[m - 1].a || p[i].y != p[m - 1].y) p[m++] = p[i];
+    *out = p;
+    return m;
+}
+
+/* ----------------------------------------------------------------- S-shape */
+
+/* S-shape route, simulated as a walk (routing rule: the S-shape heuristic).
+ * The picker leaves the depot along the front cross-aisle, enters the pick
+ * aisles from left to right and traverses each one completely, alternately
+ * front-to-back and back-to-front, moving between consecutive pick aisles along
+ * whichever cross-aisle it stands on.  When the number of pick aisles is odd,
+ * the last one is entered from the front, walked up to its deepest pick and
+ * left again at the front.  The picker then walks back to the depot along the
+ * front cross-aisle.  Aisles without picks are never entered. */
+int64_t or_sshape_tour(const or_layout *g, const int32_t *locs, int32_t n) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    pick_t *p;
+    int32_t m = pick_set(g, locs, n, &p);
+    if (m < 0) return m;
+    if (m == 0) return 0;
+    int64_t Y = depth_back(g);
+    /* the pick aisles, left to right, with the deepest pick of each */
+    int32_t *aisle = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    int64_t *deep = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    int32_t na = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        if (na == 0 || aisle[na - 1] != p[i].a) { aisle[na] = p[i].a; deep[na] = p[i].y; ++na; }
+        else if (p[i].y > deep[na - 1]) deep[na - 1] = p[i].y;
+    }
+    int64_t walked = 0;
+    int64_t x = 0;       /* horizontal position of the picker */
+    int64_t depth = 0;   /* 0 = on the front cross-aisle, Y = on the back one */
+    for (int32_t q = 0; q < na; ++q) {
+        int64_t xa = (int64_t)aisle[q] * g->aisle_pitch;
+        walked += xa > x ? xa - x : x - xa;  /* along the current cross-aisle */
+        x = xa;
+        if (q == na - 1 && (na % 2) == 1) {
+            /* odd number of pick aisles: the picker is at the front here */
+            walked += 2 * deep[q];
+        } else {
+            walked += Y;                     /* full traversal of the aisle */
+            depth = (depth == 0) ? Y : 0;
+        }
+    }
+    walked += x;                             /* back along the front to the depot */
+    free(aisle);
+    free(deep);
+    free(p);
+    (void)depth;
+    return walked;
+}
+
+/* ----------------------------------------------------- Ratliff-Rosenthal DP */
+
+/* Degree label of an aisle end vertex in a partial tour subgraph. */
+enum { D0 = 0, DE = 1, DU = 2 }; /* not in the subgraph / even degree / odd degree */
+
+/* The seven equivalence classes (deg a_j, deg b_j, number of components):
+ * (U,U,1C) (0,E,1C) (E,0,1C) (E,E,1C) (E,E,2C) (0,0,0C) (0,0,1C). */
+typedef struct { int da, db, nc; } cls_t;
+static const cls_t CLASSES[7] = {
+    {DU, DU, 1}, {D0, DE, 1}, {DE, D0, 1}, {DE, DE, 1}, {DE, DE, 2}, {D0, D0, 0}, {D0, D0, 1}};
+enum { C_UU1 = 0, C_0E1, C_E01, C_EE1, C_EE2, C_000, C_001 };
+
+/* A component of a partial subgraph, described by which of the two current
+ * aisle ends it contains.  A component containing neither is closed. */
+typedef struct { int has_a, has_b; } comp_t;
+
+typedef struct {
+    int in_a, in_b;     /* vertex belongs to the subgraph */
+    int odd_a, odd_b;   /* degree parity */
+    int n;              /* number of components */
+    comp_t c[4];
+} graph_state_t;
+
+static graph_state_t state_of_class(int k) {
+    graph_state_t s;
+    memset(&s, 0, sizeof(s));
+    cls_t c = CLASSES[k];
+    s.in_a = c.da != D0; s.odd_a = c.da == DU;
+    s.in_b = c.db != D0; s.odd_b = c.db == DU;
+    if (c.nc == 0) { s.n = 0; }
+    else if (c.nc == 2) { s.n = 2; s.c[0].has_a = 1; s.c[1].has_b = 1; }
+    else { s.n = 1; s.c[0].has_a = s.in_a; s.c[0].has_b = s.in_b; }
+    return s;
+}
+
+/* merge components that share an aisle end */
+static void merge_components(graph_state_t *s) {
+    int changed = 1;
+    while (changed) {
+        changed = 0;
+        for (int i = 0; i < s->n && !changed; ++i)
+            for (int j = i + 1; j < s->n && !changed; ++j)
+                if ((s->c[i].has_a && s->c[j].has_a) || (s->c[i].has_b && s->c[j].has_b)) {
+                    s->c[i].has_a |= s->c[j].has_a;
+                    s->c[i].has_b |= s->c[j].has_b;
+                    s->c[j] = s->c[s->n - 1];
+                    --s->n;
+                    changed = 1;
+                }
+    }
+}
+
+/* Classify a state; -1 when it is not one of the seven classes (for instance
+ * a closed component beside an open one, which can never become one tour). */
+static int class_of_state(const graph_state_t *s) {
+    int open = 0, closed = 0;
+    for (int i = 0; i < s->n; ++i) {
+        if (s->c[i].has_a || s->c[i].has_b) ++open; else ++closed;
+    }
+    if (closed > 0 && (open > 0 || closed > 1)) return -1;
+    int da = s->in_a ? (s->odd_a ? DU : DE) : D0;
+    int db = s->in_b ? (s->odd_b ? DU : DE) : D0;
+    int nc = s->n;
+    if (closed == 1) { da = D0; db = D0; }
+    for (int k = 0; k < 7; ++k) {
+        if (CLASSES[k].da != da || CLASSES[k].db != db || CLASSES[k].nc != nc) continue;
+        if (k == C_EE1 || k == C_UU1) {
+            if (!(s->c[0].has_a && s->c[0].has_b)) return -1;
+        }
+        return k;
+    }
+    return -1;
+}
+
+/* Vertical configurations of one aisle (its picks p_1 <= ... <= p_k):
+ *   full traverse        cost Y,         +1 at a_j and b_j, one piece a..b
+ *   double traverse      cost 2Y,        +2 / +2, one piece a..b
+ *   largest gap left out cost 2(Y-g),    +2 / +2, a piece at a and one at b
+ *   from the back only   cost 2(Y-p_1),  0 / +2, a piece at b
+ *   from the front only  cost 2 p_k,     +2 / 0, a piece at a
+ *   none                 cost 0          (only when the aisle has no pick)
+ * with g the largest gap between consecutive members of {0, p_1..p_k, Y}. */
+typedef struct { int64_t cost; int da, db; int npieces; comp_t piece[2]; } vopt_t;
+
+static int vertical_options(const int64_t *p, int32_t k, int64_t Y, vopt_t *o) {
+    if (k == 0) {
+        o[0].cost = 0; o[0].da = 0; o[0].db = 0; o[0].npieces = 0;
+        return 1;
+    }
+    int64_t g = p[0];
+    for (int32_t i = 1; i < k; ++i) if (p[i] - p[i - 1] > g) g = p[i] - p[i - 1];
+    if (Y - p[k - 1] > g) g = Y - p[k - 1];
+    comp_t ab = {1, 1}, a = {1, 0}, b = {0, 1};
+    o[0] = (vopt_t){Y, 1, 1, 1, {ab, ab}};
+    o[1] = (vopt_t){2 * Y, 2, 2, 1, {ab, ab}};
+    o[2] = (vopt_t){2 * (Y - g), 2, 2, 2, {a, b}};
+    o[3] = (vopt_t){2 * (Y - p[0]), 0, 2, 1, {b, b}};
+    o[4] = (vopt_t){2 * p[k - 1], 2, 0, 1, {a, a}};
+    return 5;
+}
+
+static int apply_vertical(int cls, const vopt_t *v) {
+    graph_state_t s = state_of_class(cls);
+    if (v->npieces == 0) return cls;
+    for (int i = 0; i < v->npieces; ++i) s.c[s.n++] = v->piece[i];
+    if (v->da) { s.in_a = 1; s.odd_a ^= (v->da & 1); }
+    if (v->db) { s.in_b = 1; s.odd_b ^= (v->db & 1); }
+    merge_components(&s);
+    return class_of_state(&s);
+}
+
+/* Horizontal edges between aisle j-1 and j: xa copies of a_{j-1}a_j and xb of
+ * b_{j-1}b_j, from the five combinations (1,1) (2,0) (0,2) (2,2) (0,0).  After
+ * this step a_{j-1} and b_{j-1} get no more edges, so their degrees must be
+ * even; a vertex outside the subgraph gets no edge. */
+static int apply_horizontal(int cls, int xa, int xb) {
+    graph_state_t s = state_of_class(cls);
+    if ((s.odd_a + xa) % 2 != 0 || (s.odd_b + xb) % 2 != 0) return -1;
+    if ((!s.in_a && xa > 0) || (!s.in_b && xb > 0)) return -1;
+    graph_state_t t;
+    memset(&t, 0, sizeof(t));
+    t.in_a = xa > 0; t.odd_a = xa & 1;
+    t.in_b = xb > 0; t.odd_b = xb & 1;
+    t.n = s.n;
+    for (int i = 0; i < s.n; ++i) {
+        t.c[i].has_a = s.c[i].has_a && xa > 0;
+        t.c[i].has_b = s.c[i].has_b && xb > 0;
+    }
+    return class_of_state(&t);
+}
+
+/* Optimal tour length by the Ratliff-Rosenthal dynamic programme over the
+ * aisles 0..r (r = rightmost aisle with a pick).  The depot is a required
+ * pick at depth 0 of aisle 0, so aisle 0 always has a pick; the DP starts in
+ * class (0,0,0C) and the answer is the cheapest class after aisle r that is a
+ * single component with all degrees even. */
+int64_t or_rr_tour(const or_layout *g, const int32_t *locs, int32_t n) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    pick_t *p;
+    int32_t m = pick_set(g, locs, n, &p);
+    if (m < 0) return m;
+    if (m == 0) return 0;
+    int64_t Y = depth_back(g);
+    int32_t r = p[m - 1].a;
+    int64_t *depths = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    int64_t cost[7], next[7];
+    for (int k = 0; k < 7; ++k) cost[k] = INF64;
+    cost[C_000] = 0;
+    static const int HX[5][2] = {{1, 1}, {2, 0}, {0, 2}, {2, 2}, {0, 0}};
+    int32_t i = 0;
+    for (int32_t j = 0; j <= r; ++j) {
+        if (j > 0) {
+            for (int k = 0; k < 7; ++k) next[k] = INF64;
+            for (int k = 0; k < 7; ++k) {
+                if (cost[k] >= INF64) continue;
+                for (int h = 0; h < 5; ++h) {
+                    int t = apply_horizontal(k, HX[h][0], HX[h][1]);
+                    if (t < 0) continue;
+                    int64_t c = cost[k] + (int64_t)(HX[h][0] + HX[h][1]) * g->aisle_pitch;
+                    if (c < next[t]) next[t] = c;
+                }
+            }
+            memcpy(cost, next, sizeof(cost));
+        }
+        /* the picks of aisle j, ascending (the depot counts as one in aisle 0) */
+        int32_t k = 0;
+        if (j == 0) depths[k++] = 0;
+        while (i < m && p[i].a == j) depths[k++] = p[i++].y;
+        vopt_t opt[5];
+        int no = vertical_options(depths, k, Y, opt);
+        for (int q = 0; q < 7; ++q) next[q] = INF64;
+        for (int q = 0; q < 7; ++q) {
+            if (cost[q] >= INF64) continue;
+            for (int v = 0; v < no; ++v) {
+                int t = apply_vertical(q, &opt[v]);
+                if (t < 0) continue;
+                int64_t c = cost[q] + opt[v].cost;
+                if (c < next[t]) next[t] = c;
+            }
+        }
+        memcpy(cost, next, sizeof(cost));
+    }
+    int64_t best = INF64;
+    const int finals[4] = {C_EE1, C_E01, C_0E1, C_001};
+    for (int f = 0; f < 4; ++f) if (cost[finals[f]] < best) best = cost[finals[f]];
+    free(depths);
+    free(p);
+    return best;
+}
+
+/* ------------------------------------------------------ exact small tours */
+
+/* Held-Karp over {depot} + distinct picks with the grid distance. */
+int64_t or_heldkarp_tour(const or_layout *g, const int32_t *locs, int32_t n) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    pick_t *p;
+    int32_t m = pick_set(g, locs, n, &p);
+    if (m < 0) return m;
+    if (m == 0) return 0;
+    if (m > 16) { free(p); return OR_ERANGE; }
+    int64_t d0[16], d[16][16];
+    for (int i = 0; i < m; ++i) {
+        d0[i] = or_dist(g, 0, 0, p[i].a, (int32_t)p[i].y);
+        for (int j = 0; j < m; ++j) d[i][j] = or_dist(g, p[i].a, (int32_t)p[i].y, p[j].a, (int32_t)p[j].y);
+    }
+    size_t nsub = (size_t)1 << m;
+    int64_t *best = (int64_t *)malloc(sizeof(int64_t) * nsub * (size_t)m);
+    if (!best) { free(p); return OR_ENOMEM; }
+    for (size_t s = 0; s < nsub * (size_t)m; ++s) best[s] = INF64;
+    /* best[S][last]: shortest path from the depot through exactly S ending at last */
+    for (int i = 0; i < m; ++i) best[((size_t)1 << i) * m + i] = d0[i];
+    for (size_t s = 1; s < nsub; ++s)
+        for (int last = 0; last < m; ++last) {
+            int64_t b = best[s * m + last];
+            if (!(s >> last & 1) || b >= INF64) continue;
+            for (int nx = 0; nx < m; ++nx) {
+                if (s >> nx & 1) continue;
+                size_t t = s | ((size_t)1 << nx);
+                int64_t c = b + d[last][nx];
+                if (c < best[t * m + nx]) best[t * m + nx] = c;
+            }
+        }
+    int64_t ans = INF64;
+    for (int last = 0; last < m; ++last) {
+        int64_t c = best[(nsub - 1) * m + last] + d0[last];
+        if (c < ans) ans = c;
+    }
+    free(best);
+    free(p);
+    return ans;
+}
+
+/* Every permutation of the picking sequence (the paper's own statement of how
+ * the minimum route is found), lexicographic enumeration. */
+int64_t or_permutation_tour(const or_layout *g, const int32_t *locs, int32_t n) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    pick_t *p;
+    int32_t m = pick_set(g, locs, n, &p);
+    if (m < 0) return m;
+    if (m == 0) return 0;
+    if (m > 10) { free(p); return OR_ERANGE; }
+    int idx[10];
+    for (int i = 0; i < m; ++i) idx[i] = i;
+    int64_t ans = INF64;
+    for (;;) {
+        int64_t c = or_dist(g, 0, 0, p[idx[0]].a, (int32_t)p[idx[0]].y);
+        for (int i = 0; i + 1 < m; ++i)
+            c += or_dist(g, p[idx[i]].a, (int32_t)p[idx[i]].y, p[idx[i + 1]].a, (int32_t)p[idx[i + 1]].y);
+        c += or_dist(g, p[idx[m - 1]].a, (int32_t)p[idx[m - 1]].y, 0, 0);
+        if (c < ans) ans = c;
+        /* next permutation */
+        int i = m - 2;
+        while (i >= 0 && idx[i] > idx[i + 1]) --i;
+        if (i < 0) break;
+        int j = m - 1;
+        while (idx[j] < idx[i]) --j;
+        int t = idx[i]; idx[i] = idx[j]; idx[j] = t;
+        for (int a = i + 1, b = m - 1; a < b; ++a, --b) { t = idx[a]; idx[a] = idx[b]; idx[b] = t; }
+    }
+    free(p);
+    return ans;
+}
+
+/* ------------------------------------------------------------------- plans */
+
+/* Plan cost = sum over the plan's tours of the tour length (Eq. 2, sum d_i),
+ * per routing rule, in int64.  A tour's picks are the locations of the SKUs of
+ * all lines of all its orders. */
+int or_eval_plans(const or_layout *g, int32_t n_orders, const int32_t *order_off,
+                  const int32_t *line_sku, int32_t n_sku, const int32_t *slot_map,
+                  int64_t slot_map_stride, int32_t n_plans, const int32_t *plan_tour_off,
+                  const int32_t *tour_off, const int32_t *order_seq, int32_t *tour_s,
+                  int32_t *tour_rr, int64_t *plan_s, int64_t *plan_rr) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    if (n_orders < 0 || n_plans < 0 || n_sku < 0 || slot_map_stride < 0) return OR_EINVAL;
+    int64_t cap = 64;
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    if (!buf) return OR_ENOMEM;
+    for (int32_t pl = 0; pl < n_plans; ++pl) {
+        const int32_t *smap = slot_map + (int64_t)pl * slot_map_stride;
+        int64_t sum_s = 0, sum_rr = 0;
+        if (plan_tour_off[pl + 1] < plan_tour_off[pl]) { free(buf); return OR_EINVAL; }
+        for (int32_t t = plan_tour_off[pl]; t < plan_tour_off[pl + 1]; ++t) {
+            if (tour_off[t + 1] < tour_off[t]) { free(buf); return OR_EINVAL; }
+            int64_t nl = 0;
+            for (int32_t q = tour_off[t]; q < tour_off[t + 1]; ++q) {
+                int32_t o = order_seq[q];
+                if (o < 0 || o >= n_orders) { free(buf); return OR_ERANGE; }
+                for (int32_t l = order_off[o]; l < order_off[o + 1]; ++l) {
+                    int32_t sku = line_sku[l];
+                    if (sku < 0 || sku >= n_sku) { free(buf); return OR_ERANGE; }
+                    if (nl == cap) {
+                        cap *= 2;
+                        int32_t *nb = (int32_t *)realloc(buf, sizeof(int32_t) * (size_t)cap);
+                        if (!nb) { free(buf); return OR_ENOMEM; }
+                        buf = nb;
+                    }
+                    buf[nl++] = smap[sku];
+                }
+            }
+            int64_t cs = or_sshape_tour(g, buf, (int32_t)nl);
+            int64_t cr = or_rr_tour(g, buf, (int32_t)nl);
+            if (cs < 0 || cr < 0) { free(buf); return (int)(cs < 0 ? cs : cr); }
+            if (tour_s) tour_s[t] = (int32_t)cs;
+            if (tour_rr) tour_rr[t] = (int32_t)cr;
+            sum_s += cs;
+            sum_rr += cr;
+        }
+        if (plan_s) plan_s[pl] = sum_s;
+        if (plan_rr) plan_rr[pl] = sum_rr;
+    }
+    free(buf);
+    return OR_OK;
+}

@@ -1,0 +1,77 @@
+/*
+ * CPU ORACLE for the warehouse plan evaluator -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded C evaluator of order-picking tour lengths,
+ * written to be checked against the paper by eye.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it; the product
+ * path (the CUDA library) never links, calls or includes anything here, and
+ * this file includes nothing of the product path.
+ *
+ * What it follows:
+ *   Sec. 5, Eq. (2): subproblem 2 minimises the picking route sum d_i; the
+ *     distance between two picking positions is a shortest path (the paper
+ *     names Dijkstra) and the route is the best permutation of the picking
+ *     sequence.  The oracle computes, per tour,
+ *       - the S-shape route length (a fixed routing rule, simulated walk),
+ *       - the optimal route length by the Ratliff-Rosenthal aisle-by-aisle
+ *         dynamic programme (Ratliff & Rosenthal, Oper. Res. 31(3), 1983),
+ *       - for small tours, the optimum by Held-Karp and by enumerating
+ *         permutations of the picking sequence (the paper's own wording).
+ *   Sec. 5: a plan = product positions x (slot map) + picking lists (which
+ *     orders are picked together); its cost is the sum of its tours' lengths.
+ *   Sec. 5, subroutine 4 / picking list: a move changes one plan; its delta
+ *     is the plan cost after the move minus before (plain re-evaluation).
+ *
+ * Geometry (the paper gives none; reading used throughout): aisle a has its
+ * centreline at x_a = a*P; slot k (either side) is at depth y_k = W/2 + k*S;
+ * the front cross-aisle centre is depth 0, the back one Y = W + (L-1)*S; the
+ * depot is at (0, 0).  W must be even.  Location id loc = (a*2+side)*L + k.
+ *
+ * Parity pins: see the module docstring of oracle/__init__.py; every function
+ * here is pinned by at least one independent check in tests/.
+ */
+#ifndef WH_ORACLE_H
+#define WH_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t n_aisles;          /* A */
+    int32_t slots_per_side;    /* L */
+    int32_t aisle_pitch;       /* P */
+    int32_t slot_pitch;        /* S */
+    int32_t cross_aisle_width; /* W (even) */
+} or_layout;
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ERANGE (-2)
+#define OR_ENOMEM (-3)
+
+/* Grid distance between (a1,y1) and (a2,y2): same aisle |y1-y2|, otherwise
+ * P*|a1-a2| + min(y1+y2, 2Y-y1-y2). */
+int64_t or_dist(const or_layout *g, int32_t a1, int32_t y1, int32_t a2, int32_t y2);
+
+/* Tour lengths for a multiset of location ids (duplicates collapse).  A
+ * negative return is an error code. */
+int64_t or_sshape_tour(const or_layout *g, const int32_t *locs, int32_t n);
+int64_t or_rr_tour(const or_layout *g, const int32_t *locs, int32_t n);
+int64_t or_heldkarp_tour(const or_layout *g, const int32_t *locs, int32_t n);   /* <= 20 distinct */
+int64_t or_permutation_tour(const or_layout *g, const int32_t *locs, int32_t n); /* <= 10 distinct */
+
+/* Plan evaluation: tours of orders, orders of lines (SKUs), SKUs to
+ * locations by slot_map + p*slot_map_stride (stride 0: one shared slotting).
+ * Outputs may be NULL.  Returns OR_OK or an error. */
+int or_eval_plans(const or_layout *g, int32_t n_orders, const int32_t *order_off,
+                  const int32_t *line_sku, int32_t n_sku, const int32_t *slot_map,
+                  int64_t slot_map_stride, int32_t n_plans, const int32_t *plan_tour_off,
+                  const int32_t *tour_off, const int32_t *order_seq, int32_t *tour_s,
+                  int32_t *tour_rr, int64_t *plan_s, int64_t *plan_rr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
