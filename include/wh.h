@@ -1,0 +1,176 @@
+/*
+ * wh.h -- C ABI of the GB300 warehouse order-picking plan evaluator.
+ *
+ * The library scores candidate order-picking plans for a single-block
+ * rectangular warehouse: parallel aisles, a front and a back cross-aisle, and
+ * the depot at the front end of aisle 0.  A plan is a SKU-to-location slotting
+ * (product position x, Sec. 5, subproblem 3) plus a partition of the day's
+ * orders (order history o, Sec. 5) into picker tours (the picking list,
+ * Sec. 5, subroutine 5).  A tour's length is the picker's travel distance
+ * (Sec. 5, subproblem 2, Eq. (2): min sum d_i), under two routing rules:
+ *   - S-shape: every aisle holding a pick is traversed completely, alternating
+ *     direction; with an odd number of such aisles the last one is entered and
+ *     left from the front;
+ *   - optimal: the shortest closed walk from the depot through all picks (the
+ *     paper's Dijkstra distances and best picking sequence), computed exactly
+ *     by the Ratliff-Rosenthal aisle-by-aisle dynamic programme.
+ * A plan's cost is the int64 sum of its tours' int32 lengths (Eq. (2)).
+ *
+ * Geometry in integer units: aisle a has its centreline at x = a*aisle_pitch;
+ * slot k (0 <= k < slots_per_side, either side of the aisle) lies at depth
+ * cross_aisle_width/2 + k*slot_pitch; the front cross-aisle centre is depth 0,
+ * the back one depth Y = cross_aisle_width + (slots_per_side-1)*slot_pitch.
+ * Location ids: loc = (aisle*2 + side)*slots_per_side + k.
+ *
+ * Conventions shared by every call:
+ *   - Return value: WH_OK (0) or a negative WH_E* code.  No exception or
+ *     abort crosses the ABI.  Argument checks that need no device data run
+ *     on the host before anything is launched; a failing call launches nothing.
+ *   - Device pointers are CUDA device (or managed) addresses on the device
+ *     that was current when the call was made.  Inputs and outputs are owned by
+ *     the caller; the library owns only the layout handle and its scratch.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) and runs asynchronously.  Errors found on the
+ *     device (an id out of range, a malformed offset array, a tour longer than
+ *     WH_MAX_TOUR_LINES) set bits in a device status word that
+ *     wh_get_last_status reads; the affected tours get cost -1 and are left out
+ *     of their plan's sum.
+ *   - One handle may be used from one host thread at a time; calls on the
+ *     same handle from different streams must not overlap on the device.
+ */
+#ifndef WH_H
+#define WH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WH_OK 0
+#define WH_EINVAL (-1)   /* bad argument: NULL pointer, negative size, bad mask */
+#define WH_ERANGE (-2)   /* size beyond a documented limit, or an id out of range */
+#define WH_ENOMEM (-3)   /* scratch allocation failed */
+#define WH_ECUDA (-4)    /* a CUDA runtime call or launch failed */
+#define WH_ETIMEOUT (-5) /* a bounded device-side wait gave up */
+
+/* routing_mask bits */
+#define WH_ROUTE_SSHAPE 1u
+#define WH_ROUTE_OPTIMAL 2u
+
+/* device status word bits (wh_get_last_status) */
+#define WH_STATUS_BAD_ORDER 1u    /* order id outside [0, n_orders) */
+#define WH_STATUS_BAD_SKU 2u      /* SKU id outside [0, n_sku) */
+#define WH_STATUS_BAD_LOC 4u      /* slot_map entry outside [0, n_locations) */
+#define WH_STATUS_BAD_OFFSET 8u   /* offsets decreasing or past the end of their array */
+#define WH_STATUS_TOUR_TOO_LONG 16u
+
+/* Limits of this implementation. */
+#define WH_MAX_AISLES 65534
+#define WH_MAX_SLOTS_PER_SIDE 65535
+#define WH_MAX_TOUR_LINES 2048
+/* 2*x_{A-1} + A*Y (the longest S-shape tour) must stay below this bound so the
+ * device DP has int32 headroom for its partial costs. */
+#define WH_MAX_TOUR_SPAN (1 << 27)
+
+/* Warehouse geometry (Sec. 5: the design variable a, distance between racks,
+ * is the aisle pitch here).  cross_aisle_width must be even and >= 2; all
+ * other fields >= 1. */
+typedef struct wh_layout_desc {
+    int32_t n_aisles;
+    int32_t slots_per_side;
+    int32_t aisle_pitch;
+    int32_t slot_pitch;
+    int32_t cross_aisle_width;
+} wh_layout_desc;
+
+/* Opaque handle: the geometry plus the library's device scratch. */
+typedef struct wh_layout wh_layout;
+
+/* The day's order book (order history o, Sec. 5) in CSR form, device memory:
+ * order o holds lines order_off[o] .. order_off[o+1]-1, line l asks for SKU
+ * line_sku[l] in [0, n_sku).  order_off[0] must be 0 and order_off[n_orders]
+ * equal n_lines. */
+typedef struct wh_orders {
+    int32_t n_orders;
+    int32_t n_lines;
+    int32_t n_sku;
+    const int32_t *order_off; /* [n_orders + 1] */
+    const int32_t *line_sku;  /* [n_lines] */
+} wh_orders;
+
+/* Candidate plans, device memory.  Slotting (product position x, Sec. 5):
+ * SKU s of plan p sits at location slot_map[p*slot_map_stride + s];
+ * slot_map_stride = 0 shares one slotting among all plans, otherwise it must be
+ * >= n_sku.  Batching (picking lists, Sec. 5): plan p owns tours
+ * plan_tour_off[p] .. plan_tour_off[p+1]-1 (global tour ids, plan_tour_off[0]
+ * = 0, plan_tour_off[n_plans] = n_tours); tour t picks the orders
+ * order_seq[tour_off[t] .. tour_off[t+1]-1] (tour_off[n_tours] <= n_seq).  A
+ * tour's pick set is the set of locations of all lines of its orders
+ * (repeats collapse); an empty tour costs 0. */
+typedef struct wh_plans {
+    int32_t n_plans;
+    int32_t n_tours;
+    int64_t n_seq;
+    const int32_t *slot_map;
+    int64_t slot_map_stride;
+    const int32_t *plan_tour_off; /* [n_plans + 1] */
+    const int32_t *tour_off;      /* [n_tours + 1] */
+    const int32_t *order_seq;     /* [n_seq] */
+} wh_plans;
+
+/* Outputs, caller-owned device memory; any pointer may be NULL to skip it.
+ * tour_* are per tour [n_tours] (int32), plan_* per plan [n_plans] (int64). */
+typedef struct wh_costs {
+    int32_t *tour_s;
+    int32_t *tour_rr;
+    int64_t *plan_s;
+    int64_t *plan_rr;
+} wh_costs;
+
+/* Create a layout handle for the geometry `desc` (Sec. 5, Eq. (1)'s design
+ * variable a and the rack layout of subsystem 1).  Host only: allocates the
+ * handle, no device memory yet.  Returns WH_EINVAL for a NULL argument or a
+ * non-positive / odd field, WH_ERANGE beyond WH_MAX_AISLES,
+ * WH_MAX_SLOTS_PER_SIDE or WH_MAX_TOUR_SPAN.  *out is set only on success and
+ * must be released with wh_destroy. */
+int wh_create_layout(const wh_layout_desc *desc, wh_layout **out);
+
+/* Score every tour and plan (Sec. 5, Eq. (2): sum over tours of d_i) under
+ * the routing rules in routing_mask (WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL, at
+ * least one).  Costs are exact integers: int32 per tour, int64 per plan.
+ * The first call on a device (or one with more lines / tours than any before)
+ * allocates scratch with cudaMalloc, which synchronises; later calls allocate
+ * nothing.  Returns WH_EINVAL (NULL handle/struct/pointer needed by the mask,
+ * negative count, bad mask or stride), WH_ENOMEM, WH_ECUDA, or WH_OK once the
+ * work is enqueued on `stream`. */
+int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *plans,
+                  uint32_t routing_mask, const wh_costs *out, void *stream);
+
+/* Read and clear the device status word of `layout` (WH_STATUS_* bits of all
+ * calls since the last read).  Synchronises `stream`.  Returns WH_OK,
+ * WH_EINVAL or WH_ECUDA. */
+int wh_get_last_status(wh_layout *layout, void *stream, uint32_t *status);
+
+/* Kernel timing (tracing aid; no counterpart in the paper).  While enabled,
+ * every kernel this handle launches is bracketed by two CUDA events recorded
+ * on the launch's stream; wh_get_timing synchronises on those events and
+ * reports, per kernel name, the number of launches and their summed device
+ * time since timing was enabled.  Enabling resets the totals.  Returns WH_OK,
+ * WH_EINVAL or WH_ENOMEM. */
+int wh_set_timing(wh_layout *layout, int enable);
+
+/* Fill up to `cap` entries: names[i] (static strings owned by the library),
+ * launches[i], total_ms[i]; *n_kernels receives the number of kernel kinds.
+ * Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_get_timing(wh_layout *layout, int32_t *n_kernels, const char **names, int32_t *launches,
+                  double *total_ms, int32_t cap);
+
+/* Release the handle and its device scratch.  The caller must make sure no
+ * work that uses the handle is still running.  NULL is a no-op. */
+void wh_destroy(wh_layout *layout);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,269 @@
+"""GB300 warehouse order-picking plan evaluator -- Python binding.
+
+A thin ctypes layer over ``libwh.so`` whose C ABI is ``include/wh.h``.  The
+functions named ``wh_*`` mirror the C entry points one to one and only
+marshal arguments; every step of the evaluation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libwh.so")
+_lib = None
+
+WH_OK, WH_EINVAL, WH_ERANGE, WH_ENOMEM, WH_ECUDA, WH_ETIMEOUT = 0, -1, -2, -3, -4, -5
+WH_ROUTE_SSHAPE, WH_ROUTE_OPTIMAL = 1, 2
+WH_STATUS_BAD_ORDER, WH_STATUS_BAD_SKU, WH_STATUS_BAD_LOC = 1, 2, 4
+WH_STATUS_BAD_OFFSET, WH_STATUS_TOUR_TOO_LONG = 8, 16
+ERRORS = {WH_EINVAL: "WH_EINVAL", WH_ERANGE: "WH_ERANGE", WH_ENOMEM: "WH_ENOMEM",
+          WH_ECUDA: "WH_ECUDA", WH_ETIMEOUT: "WH_ETIMEOUT"}
+
+
+class WhError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+class wh_layout_desc(ctypes.Structure):
+    _fields_ = [("n_aisles", ctypes.c_int32), ("slots_per_side", ctypes.c_int32),
+                ("aisle_pitch", ctypes.c_int32), ("slot_pitch", ctypes.c_int32),
+                ("cross_aisle_width", ctypes.c_int32)]
+
+
+class wh_orders(ctypes.Structure):
+    _fields_ = [("n_orders", ctypes.c_int32), ("n_lines", ctypes.c_int32), ("n_sku", ctypes.c_int32),
+                ("order_off", ctypes.c_void_p), ("line_sku", ctypes.c_void_p)]
+
+
+class wh_plans(ctypes.Structure):
+    _fields_ = [("n_plans", ctypes.c_int32), ("n_tours", ctypes.c_int32), ("n_seq", ctypes.c_int64),
+                ("slot_map", ctypes.c_void_p), ("slot_map_stride", ctypes.c_int64),
+                ("plan_tour_off", ctypes.c_void_p), ("tour_off", ctypes.c_void_p),
+                ("order_seq", ctypes.c_void_p)]
+
+
+class wh_costs(ctypes.Structure):
+    _fields_ = [("tour_s", ctypes.c_void_p), ("tour_rr", ctypes.c_void_p),
+                ("plan_s", ctypes.c_void_p), ("plan_rr", ctypes.c_void_p)]
+
+
+# every symbol include/wh.h declares, with its ctypes signature
+SIGNATURES = {
+    "wh_create_layout": (ctypes.c_int, [ctypes.POINTER(wh_layout_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "wh_eval_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
+                                     ctypes.c_uint32, ctypes.POINTER(wh_costs), ctypes.c_void_p]),
+    "wh_get_last_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "wh_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
+    "wh_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load():
+    """Load libwh.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise RuntimeError(f"CUDA library {_SO} is missing: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(_SO)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != WH_OK:
+        raise WhError(rc, what)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+# ------------------------------------------------------------- C entry points
+
+def wh_create_layout(n_aisles: int, slots_per_side: int, aisle_pitch: int = 3, slot_pitch: int = 1,
+                     cross_aisle_width: int = 2) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    desc = wh_layout_desc(n_aisles, slots_per_side, aisle_pitch, slot_pitch, cross_aisle_width)
+    _check(load().wh_create_layout(ctypes.byref(desc), ctypes.byref(h)), "wh_create_layout")
+    return h
+
+
+def wh_eval_plans(layout, orders: wh_orders, plans: wh_plans, routing_mask: int, out: wh_costs,
+                  stream=None) -> None:
+    _check(load().wh_eval_plans(layout, ctypes.byref(orders), ctypes.byref(plans), routing_mask,
+                                ctypes.byref(out), _stream_ptr(stream)), "wh_eval_plans")
+
+
+def wh_get_last_status(layout, stream=None) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load().wh_get_last_status(layout, _stream_ptr(stream), ctypes.byref(v)), "wh_get_last_status")
+    return int(v.value)
+
+
+def wh_set_timing(layout, enable: bool) -> None:
+    _check(load().wh_set_timing(layout, 1 if enable else 0), "wh_set_timing")
+
+
+def wh_get_timing(layout) -> dict:
+    """{kernel name: (launches, total ms)} since timing was enabled."""
+    cap = 16
+    n = ctypes.c_int32(0)
+    names = (ctypes.c_char_p * cap)()
+    launches = (ctypes.c_int32 * cap)()
+    ms = (ctypes.c_double * cap)()
+    _check(load().wh_get_timing(layout, ctypes.byref(n), names, launches, ms, cap), "wh_get_timing")
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n.value, cap))}
+
+
+def wh_destroy(layout) -> None:
+    load().wh_destroy(layout)
+
+
+# ------------------------------------------------------ tensor-level helpers
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+@dataclass
+class DeviceProblem:
+    """Orders and plans resident on one device (int32 tensors) plus the
+    ctypes views the C calls take.  Keeps the tensors alive."""
+    order_off: object
+    line_sku: object
+    slot_map: object
+    plan_tour_off: object
+    tour_off: object
+    order_seq: object
+    n_sku: int
+    slot_map_stride: int = 0
+
+    @property
+    def n_plans(self) -> int:
+        return int(self.plan_tour_off.shape[0] - 1)
+
+    @property
+    def n_tours(self) -> int:
+        return int(self.tour_off.shape[0] - 1)
+
+    def orders(self) -> wh_orders:
+        return wh_orders(int(self.order_off.shape[0] - 1), int(self.line_sku.shape[0]), self.n_sku,
+                         _ptr(self.order_off), _ptr(self.line_sku))
+
+    def plans(self) -> wh_plans:
+        return wh_plans(self.n_plans, self.n_tours, int(self.order_seq.shape[0]), _ptr(self.slot_map),
+                        self.slot_map_stride, _ptr(self.plan_tour_off), _ptr(self.tour_off),
+                        _ptr(self.order_seq))
+
+
+def to_device(inst, device="cuda", slot_map=None, slot_map_stride: int = 0) -> DeviceProblem:
+    """Copy a generated instance (numpy CSR arrays) to `device`."""
+    import torch
+
+    def t(a):
+        return torch.as_tensor(a, dtype=torch.int32).to(device).contiguous()
+
+    smap = inst.slot_map if slot_map is None else slot_map
+    return DeviceProblem(t(inst.order_off), t(inst.line_sku), t(smap), t(inst.plan_tour_off),
+                         t(inst.tour_off), t(inst.order_seq), int(inst.n_sku), int(slot_map_stride))
+
+
+@dataclass
+class Costs:
+    tour_s: object
+    tour_rr: object
+    plan_s: object
+    plan_rr: object
+
+    def c(self) -> wh_costs:
+        return wh_costs(_ptr(self.tour_s), _ptr(self.tour_rr), _ptr(self.plan_s), _ptr(self.plan_rr))
+
+
+def alloc_costs(n_tours: int, n_plans: int, device="cuda", tours: bool = True) -> Costs:
+    import torch
+    ti = (lambda: torch.empty(max(n_tours, 1), dtype=torch.int32, device=device)) if tours else (lambda: None)
+    return Costs(ti(), ti(), torch.empty(max(n_plans, 1), dtype=torch.int64, device=device),
+                 torch.empty(max(n_plans, 1), dtype=torch.int64, device=device))
+
+
+class Layout:
+    """Owning wrapper of a ``wh_layout`` handle."""
+
+    def __init__(self, n_aisles, slots_per_side, aisle_pitch=3, slot_pitch=1, cross_aisle_width=2):
+        self.desc = (n_aisles, slots_per_side, aisle_pitch, slot_pitch, cross_aisle_width)
+        self.handle = wh_create_layout(*self.desc)
+
+    @classmethod
+    def of(cls, lay) -> "Layout":
+        return cls(lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width)
+
+    def eval_plans(self, prob: DeviceProblem, costs: Costs, mask: int = 3, stream=None) -> Costs:
+        wh_eval_plans(self.handle, prob.orders(), prob.plans(), mask, costs.c(), stream)
+        return costs
+
+    def status(self, stream=None) -> int:
+        return wh_get_last_status(self.handle, stream)
+
+    def set_timing(self, enable: bool) -> None:
+        wh_set_timing(self.handle, enable)
+
+    def timing(self) -> dict:
+        return wh_get_timing(self.handle)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            wh_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def evaluate(layout: Layout, prob: DeviceProblem, mask: int = 3, tours: bool = True, stream=None) -> Costs:
+    """Allocate outputs and score every tour and plan of `prob`."""
+    costs = alloc_costs(prob.n_tours, prob.n_plans, prob.order_off.device, tours)
+    return layout.eval_plans(prob, costs, mask, stream)
+
+
+def evaluate_host(layout: Layout, host: DeviceProblem, dev: DeviceProblem, costs: Costs,
+                  host_plan_out, mask: int = 3, stream=None):
+    """End-to-end call from host memory: copy the pinned host inputs of `host`
+    into the device buffers of `dev` (same shapes), evaluate, and copy the
+    per-plan costs back into the pinned `host_plan_out` ([2, n_plans] int64).
+    Returns (bytes host->device, bytes device->host)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    h2d = 0
+    with torch.cuda.stream(s):
+        for name in ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off", "order_seq"):
+            src, dst = getattr(host, name), getattr(dev, name)
+            dst.copy_(src, non_blocking=True)
+            h2d += src.numel() * src.element_size()
+        layout.eval_plans(dev, costs, mask, s)
+        host_plan_out[0].copy_(costs.plan_s[:dev.n_plans], non_blocking=True)
+        host_plan_out[1].copy_(costs.plan_rr[:dev.n_plans], non_blocking=True)
+    d2h = 2 * dev.n_plans * 8
+    return h2d, d2h

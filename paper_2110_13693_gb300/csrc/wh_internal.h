@@ -1,0 +1,62 @@
+// Internal declarations shared by the C-ABI host code and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/wh.h"
+
+namespace wh {
+
+// packed pick key: aisle in the high 16 bits, slot index k in the low 16;
+// ascending key order = ascending (aisle, depth)
+constexpr uint32_t KEY_NONE = 0xFFFFFFFFu;
+constexpr int SHORT_MAX = 64;   // tours up to this many lines run one per thread
+
+struct Geo {
+    int32_t A, L, P, S, W;
+    int32_t h;      // W/2: depth of slot 0
+    int32_t Y;      // back cross-aisle depth
+    int32_t n_loc;  // A*2*L
+};
+
+struct EvalArgs {
+    Geo g;
+    int32_t n_orders, n_lines, n_sku;
+    const int32_t* order_off;
+    const int32_t* line_sku;
+    const uint32_t* line_key;   // shared slotting: key of every line (scratch)
+    const int32_t* slot_map;
+    int64_t slot_stride;        // 0: shared slotting
+    int32_t n_plans, n_tours;
+    int64_t n_seq;
+    const int32_t* plan_tour_off;
+    const int32_t* tour_off;
+    const int32_t* order_seq;
+    int32_t* tour_s;
+    int32_t* tour_rr;
+    int64_t* plan_s;
+    int64_t* plan_rr;
+    uint32_t mask;
+    int32_t plans_per_item;     // candidates per CTA work item
+    int32_t n_items;
+    int32_t max_rec;            // record slots per thread = min(SHORT_MAX, A)
+    int32_t smem_tables;        // stage order_off + line_key in shared memory
+    uint32_t* status;           // device status word
+    int32_t* long_list;         // tours deferred to the long-tour kernel
+    int32_t* long_count;
+};
+
+struct Tuning {
+    int threads;          // CTA size (tours in flight per CTA)
+    int plans_per_item;
+    int smem_tables;
+};
+
+// launch wrappers (k_eval.cu)
+cudaError_t launch_line_keys(const EvalArgs& a, uint32_t* line_key, cudaStream_t s);
+cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s,
+                              int* grid_out);
+cudaError_t launch_eval_long(const EvalArgs& a, int num_sms, cudaStream_t s);
+size_t eval_short_smem_bytes(const EvalArgs& a, const Tuning& t);
+
+}  // namespace wh
