@@ -147,6 +147,34 @@ int wh_create_layout(const wh_layout_desc *desc, wh_layout **out);
 int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *plans,
                   uint32_t routing_mask, const wh_costs *out, void *stream);
 
+/* Sizes accepted by wh_eval_plans_noalloc. */
+#define WH_NOALLOC_MAX_LINES (1 << 20)
+#define WH_NOALLOC_MAX_TOURS (1 << 20)
+
+/* wh_eval_plans for callers that cannot allocate device memory (the paper has
+ * no counterpart; this is an interface for embedding).  Some callers must not
+ * let a library call cudaMalloc or cudaFree: a serving process whose device
+ * memory is fully reserved up front by its own pool, where one more cudaMalloc
+ * would fail or upset its memory plan, or a loop that cannot afford the
+ * device-wide synchronisation that cudaMalloc / cudaFree may cause.  This call
+ * takes the geometry directly (no handle) and computes exactly what
+ * wh_eval_plans computes, with the same kernels, but its scratch lives in one
+ * fixed device array inside the library (about 12 MiB, held on every GPU that
+ * loads the library until the process exits); it allocates nothing.
+ *   - Limits: orders->n_lines <= WH_NOALLOC_MAX_LINES and
+ *     plans->n_tours <= WH_NOALLOC_MAX_TOURS, else WH_ERANGE before any work.
+ *   - status: optional caller-owned device word; the call zeroes it on
+ *     `stream` and the kernels OR WH_STATUS_* bits into it.  NULL: no status.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array: calls that may overlap on the GPU (on
+ *     different streams, or from different threads) race and corrupt each
+ *     other's results.  Serialise them.
+ * Returns as wh_eval_plans (WH_EINVAL for a bad desc or argument). */
+int wh_eval_plans_noalloc(const wh_layout_desc *desc, const wh_orders *orders, const wh_plans *plans,
+                          uint32_t routing_mask, const wh_costs *out, uint32_t *status, void *stream);
+
 /* Read and clear the device status word of `layout` (WH_STATUS_* bits of all
  * calls since the last read).  Synchronises `stream`.  Returns WH_OK,
  * WH_EINVAL or WH_ECUDA. */

@@ -20,6 +20,7 @@ WH_OK, WH_EINVAL, WH_ERANGE, WH_ENOMEM, WH_ECUDA, WH_ETIMEOUT = 0, -1, -2, -3, -
 WH_ROUTE_SSHAPE, WH_ROUTE_OPTIMAL = 1, 2
 WH_STATUS_BAD_ORDER, WH_STATUS_BAD_SKU, WH_STATUS_BAD_LOC = 1, 2, 4
 WH_STATUS_BAD_OFFSET, WH_STATUS_TOUR_TOO_LONG = 8, 16
+WH_NOALLOC_MAX_LINES, WH_NOALLOC_MAX_TOURS = 1 << 20, 1 << 20
 ERRORS = {WH_EINVAL: "WH_EINVAL", WH_ERANGE: "WH_ERANGE", WH_ENOMEM: "WH_ENOMEM",
           WH_ECUDA: "WH_ECUDA", WH_ETIMEOUT: "WH_ETIMEOUT"}
 
@@ -59,6 +60,9 @@ SIGNATURES = {
     "wh_eval_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                      ctypes.c_uint32, ctypes.POINTER(wh_costs), ctypes.c_void_p]),
     "wh_get_last_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_eval_plans_noalloc": (ctypes.c_int, [ctypes.POINTER(wh_layout_desc), ctypes.POINTER(wh_orders),
+                                             ctypes.POINTER(wh_plans), ctypes.c_uint32,
+                                             ctypes.POINTER(wh_costs), ctypes.c_void_p, ctypes.c_void_p]),
     "wh_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "wh_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int32),
@@ -112,6 +116,16 @@ def wh_eval_plans(layout, orders: wh_orders, plans: wh_plans, routing_mask: int,
                   stream=None) -> None:
     _check(load().wh_eval_plans(layout, ctypes.byref(orders), ctypes.byref(plans), routing_mask,
                                 ctypes.byref(out), _stream_ptr(stream)), "wh_eval_plans")
+
+
+def wh_eval_plans_noalloc(desc: wh_layout_desc, orders: wh_orders, plans: wh_plans, routing_mask: int,
+                          out: wh_costs, status_ptr: int = 0, stream=None) -> None:
+    """Same results as wh_eval_plans, for callers that cannot allocate device
+    memory: scratch comes from a fixed array inside the library (limits
+    WH_NOALLOC_MAX_LINES / WH_NOALLOC_MAX_TOURS); concurrent calls race."""
+    _check(load().wh_eval_plans_noalloc(ctypes.byref(desc), ctypes.byref(orders), ctypes.byref(plans),
+                                        routing_mask, ctypes.byref(out), ctypes.c_void_p(status_ptr or None),
+                                        _stream_ptr(stream)), "wh_eval_plans_noalloc")
 
 
 def wh_get_last_status(layout, stream=None) -> int:
