@@ -4,17 +4,22 @@
 // S-shape route and of the optimal route through its picks, and for every
 // plan the int64 sum of its tours' lengths.
 //
-// Design (one GPU, integer work, no tensor-core shape):
-//   k_line_keys   -- layout/slot-map build: one packed key (aisle<<16 | slot)
-//                    per order line under the shared slotting.
-//   k_eval_short  -- one tour per thread for tours of <= 64 lines: keys are
-//                    gathered into registers, sorted by a bitonic network
-//                    fully unrolled over registers, reduced to per-aisle
-//                    records (aisle, shallowest and deepest pick, largest
-//                    gap between consecutive picks) kept in shared memory,
-//                    then the S-shape closed form and the optimal-route DP
-//                    run over the records.  Per-plan int64 sums are
-//                    accumulated in shared memory and stored once per plan.
+// Design (one GPU, integer work; nothing here is a dense contraction):
+//   k_prep        -- layout / slot-map build: one packed key (aisle<<16 | slot)
+//                    per order line under the shared slotting; zeroes the
+//                    per-plan sums and the long-tour counter.
+//   k_eval_short  -- one tour per thread for tours of <= 64 lines.  A warp
+//                    owns 32 consecutive tours; keys are gathered from the
+//                    shared-memory order book into registers and sorted by a
+//                    fully unrolled bitonic network (two 16-bit keys per
+//                    register when the layout allows, so one min/max pair
+//                    serves two comparators), reduced to per-aisle records
+//                    (aisle, shallowest and deepest pick, largest gap between
+//                    consecutive picks) in shared memory, then the S-shape
+//                    closed form and the optimal-route DP run over the
+//                    records.  Plan sums: a segmented warp reduction and one
+//                    int64 atomic per (warp, plan) segment; no CTA barrier
+//                    after the table staging.
 //   k_eval_long   -- one warp per tour for longer tours: shared-memory
 //                    bitonic sort, then one lane runs the record scan and DP.
 //
@@ -32,9 +37,10 @@ namespace {
 
 constexpr int INF = 1 << 29;
 constexpr uint32_t KEY_BAD = 0xFFFFFFFEu;   // a line whose SKU or slot is invalid
+constexpr uint32_t KEY16_NONE = 0xFFFFu;
+constexpr uint32_t KEY16_BAD = 0xFFFEu;
 constexpr int LONG_WARPS = 4;
 constexpr int LONG_MAXL = WH_MAX_TOUR_LINES;
-constexpr int SHORT_THREADS_MAX = 256;
 
 __device__ __forceinline__ void flag(uint32_t* status, uint32_t bit) { atomicOr(status, bit); }
 
@@ -44,6 +50,12 @@ __device__ __forceinline__ uint32_t loc_key(const Geo& g, int loc) {
     const int r = loc - a * two_l;          // side*L + k
     const int k = r >= g.L ? r - g.L : r;
     return ((uint32_t)a << 16) | (uint32_t)k;
+}
+
+// 32-bit key -> 16-bit key (aisle<<8 | slot); valid when A <= 255, L <= 256
+__device__ __forceinline__ uint32_t key16_of(uint32_t k32) {
+    if (k32 == KEY_BAD) return KEY16_BAD;
+    return ((k32 >> 8) & 0xFF00u) | (k32 & 0xFFu);
 }
 
 // ---------------------------------------------------------------- DP state
@@ -95,7 +107,7 @@ __device__ __forceinline__ int sshape_cost(const Geo& g, int m, int last_a, int 
     return 2 * last_a * g.P + ((m & 1) ? (m - 1) * g.Y + 2 * d_r : m * g.Y);
 }
 
-// ---------------------------------------------------------- register sort
+// ------------------------------------------------------ 32-bit key network
 template <int N>
 __device__ __forceinline__ void bitonic_sort(uint32_t (&x)[N]) {
 #pragma unroll
@@ -116,11 +128,60 @@ __device__ __forceinline__ void bitonic_sort(uint32_t (&x)[N]) {
     }
 }
 
-// Sorted keys -> per-aisle records (written to rec[j*stride], at most cap of
-// them), plus the S-shape inputs.
+// ------------------------------------------------------ 16-bit key network
+// 2R positions in R registers: position p lives in register p % R, in the low
+// half when p < R and the high half otherwise.  All-ascending bitonic sorter:
+// each merge of block size k starts by comparing p with p ^ (k-1) (the
+// mirrored partner), then half-cleans with p ^ j for j = k/4 .. 1.  For
+// k <= R both halves run the same register pairs, so one 16x2 min/max pair
+// serves two comparators; the final mirror step pairs halves across
+// registers and needs a half swap.
+template <int R>
+__device__ __forceinline__ void sort16x2(uint32_t (&x)[R]) {
+    constexpr int N = 2 * R;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+        if (k == N) {
+#pragma unroll
+            for (int r = 0; r < R / 2; ++r) {
+                const uint32_t A = x[r], B = x[R - 1 - r];
+                const uint32_t Bs = __byte_perm(B, 0, 0x1032);
+                const uint32_t mn = __vminu2(A, Bs), mx = __vmaxu2(A, Bs);
+                x[r] = __byte_perm(mn, mx, 0x7610);
+                x[R - 1 - r] = __byte_perm(mn, mx, 0x5432);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = r ^ (k - 1);
+                if (l > r) {
+                    const uint32_t a = x[r], b = x[l];
+                    x[r] = __vminu2(a, b);
+                    x[l] = __vmaxu2(a, b);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = r ^ j;
+                if (l > r) {
+                    const uint32_t a = x[r], b = x[l];
+                    x[r] = __vminu2(a, b);
+                    x[l] = __vmaxu2(a, b);
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------- record scans
+// Sorted keys -> per-aisle records (rec[j*stride], at most cap of them) and
+// the S-shape inputs (pick-aisle count, rightmost aisle, its deepest slot).
 template <int N>
-__device__ __forceinline__ void scan_records(const uint32_t (&x)[N], uint2* rec, int stride, int cap,
-                                             bool write, int& m, int& last_a, int& last_hi) {
+__device__ __forceinline__ void scan32(const uint32_t (&x)[N], uint2* rec, int stride, int cap, bool write,
+                                       int& m, int& last_a, int& last_hi) {
     int lo = 0, prev = 0, gi = 0;
     m = 0; last_a = 0; last_hi = 0;
 #pragma unroll
@@ -142,7 +203,37 @@ __device__ __forceinline__ void scan_records(const uint32_t (&x)[N], uint2* rec,
     }
 }
 
-__device__ __forceinline__ int rr_records(const Geo& g, const uint2* rec, int stride, int m) {
+template <int R>
+__device__ __forceinline__ uint32_t key16_at(const uint32_t (&x)[R], int p) {
+    return p < R ? (x[p] & 0xFFFFu) : (x[p - R] >> 16);
+}
+
+template <int R>
+__device__ __forceinline__ void scan16(const uint32_t (&x)[R], uint32_t* rec, int stride, int cap, bool write,
+                                       int& m, int& last_a, int& last_hi) {
+    constexpr int N = 2 * R;
+    int lo = 0, prev = 0, gi = 0;
+    m = 0; last_a = 0; last_hi = 0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        const uint32_t key = key16_at<R>(x, p);
+        const uint32_t a = key >> 8;
+        const int k = (int)(key & 0xFFu);
+        const bool first = (p == 0) || ((key16_at<R>(x, p - 1) >> 8) != a);
+        const bool last = (p == N - 1) || ((key16_at<R>(x, p + 1) >> 8) != a);
+        gi = first ? 0 : max(gi, k - prev);
+        lo = first ? k : lo;
+        prev = k;
+        if (key != KEY16_NONE && last) {
+            if (write && m < cap) rec[m * stride] = (a << 24) | ((uint32_t)lo << 16) | ((uint32_t)k << 8) | (uint32_t)gi;
+            ++m;
+            last_a = (int)a;
+            last_hi = k;
+        }
+    }
+}
+
+__device__ __forceinline__ int rr_records32(const Geo& g, const uint2* rec, int stride, int m) {
     DP5 v;
     dp_init(v);
     int pa = 0;
@@ -155,156 +246,267 @@ __device__ __forceinline__ int rr_records(const Geo& g, const uint2* rec, int st
     return dp_final(v);
 }
 
-// key of line l for the tour's slotting
-template <bool SHARED_MAP>
-__device__ __forceinline__ uint32_t key_of(const EvalArgs& a, const uint32_t* keys, const int32_t* skus,
-                                           const int32_t* map, int l) {
+__device__ __forceinline__ int rr_records16(const Geo& g, const uint32_t* rec, int stride, int m) {
+    DP5 v;
+    dp_init(v);
+    int pa = 0;
+    for (int j = 0; j < m; ++j) {
+        const uint32_t r = rec[j * stride];
+        const int a = (int)(r >> 24);
+        dp_aisle(v, g, a - pa, (int)((r >> 16) & 0xFFu), (int)((r >> 8) & 0xFFu), (int)(r & 0xFFu));
+        pa = a;
+    }
+    return dp_final(v);
+}
+
+// ------------------------------------------------------------ tour bodies
+// Key source: with a shared slotting, keys come from the per-line table
+// (16-bit or 32-bit entries); with per-plan slottings, from the plan's slot
+// map via the line's SKU.
+struct KeySrc {
+    const int32_t* off;     // order offsets
+    const void* keys;       // per-line keys (shared slotting)
+    const int32_t* skus;    // per-line SKUs (per-plan slotting)
+    const int32_t* map;     // this plan's slot map (per-plan slotting)
+};
+
+template <bool KEY16, bool SHARED_MAP>
+__device__ __forceinline__ uint32_t key_of(const EvalArgs& a, const KeySrc& s, int l) {
     if constexpr (SHARED_MAP) {
-        return keys[l];
+        if constexpr (KEY16) return static_cast<const uint16_t*>(s.keys)[l];
+        else return static_cast<const uint32_t*>(s.keys)[l];
     } else {
-        const int sku = skus[l];
-        if ((unsigned)sku >= (unsigned)a.n_sku) { flag(a.status, WH_STATUS_BAD_SKU); return KEY_BAD; }
-        const int loc = map[sku];
-        if ((unsigned)loc >= (unsigned)a.g.n_loc) { flag(a.status, WH_STATUS_BAD_LOC); return KEY_BAD; }
-        return loc_key(a.g, loc);
+        const int sku = s.skus[l];
+        uint32_t k32 = KEY_BAD;
+        if ((unsigned)sku >= (unsigned)a.n_sku) {
+            flag(a.status, WH_STATUS_BAD_SKU);
+        } else {
+            const int loc = s.map[sku];
+            if ((unsigned)loc >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
+            else k32 = loc_key(a.g, loc);
+        }
+        if constexpr (KEY16) return key16_of(k32);
+        else return k32;
     }
 }
 
 template <int N, bool SHARED_MAP>
-__device__ __forceinline__ void short_tour(const EvalArgs& a, const int32_t* off, const uint32_t* keys,
-                                           const int32_t* skus, const int32_t* map, int q0, int q1,
-                                           uint2* rec, bool need_rr, int& cs, int& cr, bool& bad) {
+__device__ __forceinline__ void short_tour32(const EvalArgs& a, const KeySrc& s, int q0, int q1, uint2* rec,
+                                             int stride, bool need_rr, int& cs, int& cr, bool& bad) {
     uint32_t x[N];
     int q = q0, l = 0, le = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         while (l >= le && q < q1) {
             const int o = a.order_seq[q++];
-            l = off[o];
-            le = off[o + 1];
+            l = s.off[o];
+            le = s.off[o + 1];
         }
         uint32_t k = KEY_NONE;
-        if (l < le) { k = key_of<SHARED_MAP>(a, keys, skus, map, l); ++l; }
+        if (l < le) { k = key_of<false, SHARED_MAP>(a, s, l); ++l; }
         bad |= (k == KEY_BAD);
         x[i] = k;
     }
     bitonic_sort<N>(x);
     int m, last_a, last_hi;
-    scan_records<N>(x, rec, blockDim.x, a.max_rec, need_rr, m, last_a, last_hi);
+    scan32<N>(x, rec, stride, a.max_rec, need_rr, m, last_a, last_hi);
     cs = sshape_cost(a.g, m, last_a, last_hi);
-    cr = need_rr ? rr_records(a.g, rec, blockDim.x, min(m, a.max_rec)) : 0;
+    cr = need_rr ? rr_records32(a.g, rec, stride, min(m, a.max_rec)) : 0;
+}
+
+template <int R, bool SHARED_MAP>
+__device__ __forceinline__ void short_tour16(const EvalArgs& a, const KeySrc& s, int q0, int q1, uint32_t* rec,
+                                             int stride, bool need_rr, int& cs, int& cr, bool& bad) {
+    uint32_t x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = 0xFFFFFFFFu;
+    int q = q0, l = 0, le = 0;
+#pragma unroll
+    for (int p = 0; p < 2 * R; ++p) {
+        while (l >= le && q < q1) {
+            const int o = a.order_seq[q++];
+            l = s.off[o];
+            le = s.off[o + 1];
+        }
+        uint32_t k = KEY16_NONE;
+        if (l < le) { k = key_of<true, SHARED_MAP>(a, s, l); ++l; }
+        bad |= (k == KEY16_BAD);
+        if (p < R) x[p] = __byte_perm(x[p], k, 0x3254);
+        else x[p - R] = __byte_perm(x[p - R], k, 0x5410);
+    }
+    sort16x2<R>(x);
+    int m, last_a, last_hi;
+    scan16<R>(x, rec, stride, a.max_rec, need_rr, m, last_a, last_hi);
+    cs = sshape_cost(a.g, m, last_a, last_hi);
+    cr = need_rr ? rr_records16(a.g, rec, stride, min(m, a.max_rec)) : 0;
+}
+
+// Segmented sum over the lanes of a warp whose `key` (plan id, non-decreasing
+// with the lane) is equal; the first lane of each segment ends up with the
+// segment's total.
+__device__ __forceinline__ long long segmented_sum(long long v, int key, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long ov = __shfl_down_sync(0xffffffffu, v, o);
+        const int ok = __shfl_down_sync(0xffffffffu, key, o);
+        if (lane + o < 32 && ok == key) v += ov;
+    }
+    return v;
 }
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void k_line_keys(EvalArgs a, uint32_t* line_key) {
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < a.n_lines; l += gridDim.x * blockDim.x) {
-        const int sku = a.line_sku[l];
-        uint32_t key = KEY_BAD;
-        if ((unsigned)sku >= (unsigned)a.n_sku) {
-            flag(a.status, WH_STATUS_BAD_SKU);
-        } else {
-            const int loc = a.slot_map[sku];
-            if ((unsigned)loc >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
-            else key = loc_key(a.g, loc);
+__global__ void k_prep(EvalArgs a, uint32_t* line_key) {
+    const int stride = gridDim.x * blockDim.x;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) *a.long_count = 0;
+    if (line_key) {
+        for (int l = i0; l < a.n_lines; l += stride) {
+            const int sku = a.line_sku[l];
+            uint32_t key = KEY_BAD;
+            if ((unsigned)sku >= (unsigned)a.n_sku) {
+                flag(a.status, WH_STATUS_BAD_SKU);
+            } else {
+                const int loc = a.slot_map[sku];
+                if ((unsigned)loc >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
+                else key = loc_key(a.g, loc);
+            }
+            line_key[l] = key;
         }
-        line_key[l] = key;
+    }
+    const bool zs = a.plan_s && (a.mask & WH_ROUTE_SSHAPE);
+    const bool zr = a.plan_rr && (a.mask & WH_ROUTE_OPTIMAL);
+    for (int p = i0; p < a.n_plans; p += stride) {
+        if (zs) a.plan_s[p] = 0;
+        if (zr) a.plan_rr[p] = 0;
+        const int t0 = a.plan_tour_off[p], t1 = a.plan_tour_off[p + 1];
+        if (t0 < 0 || t1 < t0 || t1 > a.n_tours || (p == 0 && t0 != 0) || (p == a.n_plans - 1 && t1 != a.n_tours))
+            flag(a.status, WH_STATUS_BAD_OFFSET);
     }
 }
 
-template <bool SMEM_TABLES, bool SHARED_MAP>
-__global__ void __launch_bounds__(128, 4) k_eval_short(EvalArgs a) {
+template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
+__global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int T = blockDim.x, tid = threadIdx.x;
-    const int K = a.plans_per_item;
-    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);   // [2K]
-    uint2* rec_all = reinterpret_cast<uint2*>(acc + 2 * K);                   // [max_rec][T]
-    int32_t* s_off = reinterpret_cast<int32_t*>(rec_all + (size_t)a.max_rec * T);
-    int32_t* s_tab = s_off + a.n_orders + 1;  // line keys (shared map) or SKUs
-    uint2* rec = rec_all + tid;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    size_t off_b = 0;
+    int32_t* s_off = reinterpret_cast<int32_t*>(smem);
+    off_b += sizeof(int32_t) * ((size_t)a.n_orders + 1);
+    void* s_tab = smem + off_b;
+    if (SMEM_TABLES) off_b += (SHARED_MAP ? (KEY16 ? 2 : 4) : 4) * (size_t)a.n_lines;
+    else off_b = 0;
+    off_b = (off_b + 15) & ~(size_t)15;
+    unsigned char* rec_base = smem + off_b;
 
-    const int32_t* off = a.order_off;
-    const uint32_t* keys = a.line_key;
-    const int32_t* skus = a.line_sku;
+    KeySrc src;
+    src.off = a.order_off;
+    src.keys = a.line_key;
+    src.skus = a.line_sku;
+    src.map = nullptr;
     if constexpr (SMEM_TABLES) {
         for (int i = tid; i <= a.n_orders; i += T) s_off[i] = a.order_off[i];
         if constexpr (SHARED_MAP) {
-            for (int i = tid; i < a.n_lines; i += T) s_tab[i] = (int32_t)a.line_key[i];
-            keys = reinterpret_cast<const uint32_t*>(s_tab);
+            if constexpr (KEY16) {
+                uint16_t* k16 = static_cast<uint16_t*>(s_tab);
+                for (int i = tid; i < a.n_lines; i += T) k16[i] = (uint16_t)key16_of(a.line_key[i]);
+            } else {
+                uint32_t* k32 = static_cast<uint32_t*>(s_tab);
+                for (int i = tid; i < a.n_lines; i += T) k32[i] = a.line_key[i];
+            }
+            src.keys = s_tab;
         } else {
-            for (int i = tid; i < a.n_lines; i += T) s_tab[i] = a.line_sku[i];
-            skus = s_tab;
+            int32_t* sk = static_cast<int32_t*>(s_tab);
+            for (int i = tid; i < a.n_lines; i += T) sk[i] = a.line_sku[i];
+            src.skus = sk;
         }
-        off = s_off;
+        src.off = s_off;
         __syncthreads();
     }
     const bool need_rr = (a.mask & WH_ROUTE_OPTIMAL) != 0;
+    const bool want_s = (a.mask & WH_ROUTE_SSHAPE) != 0;
 
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-        const int p0 = item * K;
-        const int p1 = min(p0 + K, a.n_plans);
-        int T0 = a.plan_tour_off[p0];
-        int T1 = a.plan_tour_off[p1];
-        if (T0 < 0 || T1 < T0 || T1 > a.n_tours) {
-            if (tid == 0) flag(a.status, WH_STATUS_BAD_OFFSET);
-            T1 = T0 = 0;
+    // this warp's contiguous range of 32-tour chunks
+    const int warps = gridDim.x * (T >> 5);
+    const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
+    const int n_chunks = (a.n_tours + 31) >> 5;
+    const int per = (n_chunks + warps - 1) / warps;
+    const int c_begin = gw * per;
+    const int c_end = min(c_begin + per, n_chunks);
+    if (c_begin >= c_end) return;
+
+    // plan of the first tour: largest p with plan_tour_off[p] <= t
+    int plan = 0;
+    {
+        const int t0 = c_begin * 32;
+        int lo = 0, hi = a.n_plans - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.plan_tour_off[mid] <= t0) lo = mid; else hi = mid - 1;
         }
-        for (int i = tid; i < 2 * K; i += T) acc[i] = 0ull;
-        __syncthreads();
-        for (int c = T0; c < T1; c += T) {
-            const int t = c + tid;
-            const bool active = t < T1;
-            int plan = p0;
-            int q0 = 0, q1 = 0, n = 0;
-            bool bad = false;
-            if (active) {
-                while (plan + 1 < p1 && a.plan_tour_off[plan + 1] <= t) ++plan;
-                q0 = a.tour_off[t];
-                q1 = a.tour_off[t + 1];
-                if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
-                    flag(a.status, WH_STATUS_BAD_OFFSET);
-                    bad = true;
-                } else {
-                    for (int q = q0; q < q1; ++q) {
-                        const int o = a.order_seq[q];
-                        if ((unsigned)o >= (unsigned)a.n_orders) { flag(a.status, WH_STATUS_BAD_ORDER); bad = true; break; }
-                        const int lb = off[o], le = off[o + 1];
-                        if (lb < 0 || le < lb || le > a.n_lines) { flag(a.status, WH_STATUS_BAD_OFFSET); bad = true; break; }
-                        n += le - lb;
-                    }
+        plan = lo;
+    }
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const int t = c * 32 + lane;
+        const bool active = t < a.n_tours;
+        while (plan + 1 < a.n_plans && a.plan_tour_off[plan + 1] <= t) ++plan;
+        int q0 = 0, q1 = 0, n = 0;
+        bool bad = false;
+        if (active) {
+            q0 = a.tour_off[t];
+            q1 = a.tour_off[t + 1];
+            if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
+                flag(a.status, WH_STATUS_BAD_OFFSET);
+                bad = true;
+            } else {
+                for (int q = q0; q < q1; ++q) {
+                    const int o = a.order_seq[q];
+                    if ((unsigned)o >= (unsigned)a.n_orders) { flag(a.status, WH_STATUS_BAD_ORDER); bad = true; break; }
+                    const int lb = src.off[o], le = src.off[o + 1];
+                    if (lb < 0 || le < lb || le > a.n_lines) { flag(a.status, WH_STATUS_BAD_OFFSET); bad = true; break; }
+                    n += le - lb;
                 }
             }
-            const bool is_long = active && !bad && n > SHORT_MAX;
-            if (is_long) {
-                const int slot = atomicAdd(a.long_count, 1);
-                a.long_list[2 * slot] = t;
-                a.long_list[2 * slot + 1] = plan;
-            }
-            const bool run = active && !bad && !is_long;
-            if (!run) q1 = q0;   // gather nothing
-            const int nmax = __reduce_max_sync(0xffffffffu, run ? n : 0);
-            const int32_t* map = SHARED_MAP ? nullptr : a.slot_map + (int64_t)plan * a.slot_stride;
-            int cs = 0, cr = 0;
-            bool kbad = false;
-            if (nmax <= 16) short_tour<16, SHARED_MAP>(a, off, keys, skus, map, q0, q1, rec, need_rr, cs, cr, kbad);
-            else if (nmax <= 32) short_tour<32, SHARED_MAP>(a, off, keys, skus, map, q0, q1, rec, need_rr, cs, cr, kbad);
-            else short_tour<64, SHARED_MAP>(a, off, keys, skus, map, q0, q1, rec, need_rr, cs, cr, kbad);
-            if (active && (bad || kbad)) {
-                if (a.tour_s) a.tour_s[t] = -1;
-                if (a.tour_rr) a.tour_rr[t] = -1;
-            } else if (run) {
-                if (a.tour_s && (a.mask & WH_ROUTE_SSHAPE)) a.tour_s[t] = cs;
-                if (a.tour_rr && need_rr) a.tour_rr[t] = cr;
-                atomicAdd(&acc[2 * (plan - p0)], (unsigned long long)cs);
-                atomicAdd(&acc[2 * (plan - p0) + 1], (unsigned long long)cr);
-            }
         }
-        __syncthreads();
-        for (int q = tid; q < p1 - p0; q += T) {
-            if (a.plan_s && (a.mask & WH_ROUTE_SSHAPE)) a.plan_s[p0 + q] = (int64_t)acc[2 * q];
-            if (a.plan_rr && need_rr) a.plan_rr[p0 + q] = (int64_t)acc[2 * q + 1];
+        const bool is_long = active && !bad && n > SHORT_MAX;
+        if (is_long) {
+            const int slot = atomicAdd(a.long_count, 1);
+            a.long_list[2 * slot] = t;
+            a.long_list[2 * slot + 1] = plan;
         }
-        __syncthreads();
+        const bool run = active && !bad && !is_long;
+        if (!run) q1 = q0;   // gather nothing
+        const int nmax = __reduce_max_sync(0xffffffffu, run ? n : 0);
+        if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
+        int cs = 0, cr = 0;
+        bool kbad = false;
+        if constexpr (KEY16) {
+            uint32_t* rec = reinterpret_cast<uint32_t*>(rec_base) + tid;
+            if (nmax <= 16) short_tour16<8, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+            else if (nmax <= 32) short_tour16<16, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+            else short_tour16<32, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+        } else {
+            uint2* rec = reinterpret_cast<uint2*>(rec_base) + tid;
+            if (nmax <= 16) short_tour32<16, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+            else if (nmax <= 32) short_tour32<32, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+            else short_tour32<64, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+        }
+        const bool ok = run && !kbad;
+        if (active && (bad || kbad)) {
+            if (a.tour_s) a.tour_s[t] = -1;
+            if (a.tour_rr) a.tour_rr[t] = -1;
+        } else if (ok) {
+            if (a.tour_s && want_s) a.tour_s[t] = cs;
+            if (a.tour_rr && need_rr) a.tour_rr[t] = cr;
+        }
+        const int key = active ? plan : -1;
+        const long long ss = segmented_sum(ok ? cs : 0, key, lane);
+        const long long sr = segmented_sum(ok ? cr : 0, key, lane);
+        const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+        if (active && (lane == 0 || prev_key != key)) {
+            if (a.plan_s && want_s && ss) atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)ss);
+            if (a.plan_rr && need_rr && sr) atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_rr[plan]), (unsigned long long)sr);
+        }
     }
 }
 
@@ -325,10 +527,16 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
     const int count = *a.long_count;
     uint32_t* kb = buf[warp];
     const bool need_rr = (a.mask & WH_ROUTE_OPTIMAL) != 0;
+    const bool want_s = (a.mask & WH_ROUTE_SSHAPE) != 0;
+    KeySrc src;
+    src.off = a.order_off;
+    src.keys = a.line_key;
+    src.skus = a.line_sku;
+    src.map = nullptr;
     for (int w = blockIdx.x * LONG_WARPS + warp; w < count; w += gridDim.x * LONG_WARPS) {
         const int t = a.long_list[2 * w], plan = a.long_list[2 * w + 1];
         const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];   // checked by k_eval_short
-        const int32_t* map = SHARED_MAP ? nullptr : a.slot_map + (int64_t)plan * a.slot_stride;
+        if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
         int n = 0;
         bool bad = false;
         for (int qb = q0; qb < q1; qb += 32) {
@@ -343,7 +551,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
             const int incl = warp_inclusive_scan(cnt);
             int pos = n + incl - cnt;
             for (int l = lb; l < le; ++l, ++pos) {
-                const uint32_t k = key_of<SHARED_MAP>(a, a.line_key, a.line_sku, map, l);
+                const uint32_t k = key_of<false, SHARED_MAP>(a, src, l);
                 bad |= (k == KEY_BAD);
                 if (pos < LONG_MAXL) kb[pos] = k;
             }
@@ -398,9 +606,9 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
             }
             const int cs = sshape_cost(a.g, m, last_a, last_hi);
             const int cr = need_rr ? dp_final(v) : 0;
-            if (a.tour_s && (a.mask & WH_ROUTE_SSHAPE)) a.tour_s[t] = cs;
+            if (a.tour_s && want_s) a.tour_s[t] = cs;
             if (a.tour_rr && need_rr) a.tour_rr[t] = cr;
-            if (a.plan_s && (a.mask & WH_ROUTE_SSHAPE))
+            if (a.plan_s && want_s)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)cs);
             if (a.plan_rr && need_rr)
                 atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_rr[plan]), (unsigned long long)cr);
@@ -409,55 +617,67 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
     }
 }
 
-template <bool SM, bool SH>
-cudaError_t set_smem(size_t bytes) {
-    return cudaFuncSetAttribute(k_eval_short<SM, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <bool SM, bool SH>
+template <bool K16, bool SH, bool SM>
 cudaError_t launch_short_t(const EvalArgs& a, const Tuning& t, size_t smem, int num_sms, cudaStream_t s,
                            int* grid_out) {
-    cudaError_t e = set_smem<SM, SH>(smem);
+    auto kern = k_eval_short<K16, SH, SM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_short<SM, SH>, t.threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t.threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int warps_needed = (a.n_tours + 31) / 32;
     int grid = per_sm * num_sms;
-    if (grid > a.n_items) grid = a.n_items;
+    const int max_grid = (warps_needed + t.threads / 32 - 1) / (t.threads / 32);
+    if (grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = grid;
-    k_eval_short<SM, SH><<<grid, t.threads, smem, s>>>(a);
+    kern<<<grid, t.threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+bool key16_ok(const Geo& g) { return g.A <= 255 && g.L <= 256; }
+
 size_t eval_short_smem_bytes(const EvalArgs& a, const Tuning& t) {
-    size_t b = sizeof(unsigned long long) * 2 * (size_t)t.plans_per_item;
-    b += sizeof(uint2) * (size_t)a.max_rec * (size_t)t.threads;
-    if (t.smem_tables) b += sizeof(int32_t) * ((size_t)a.n_orders + 1 + (size_t)a.n_lines);
+    const bool k16 = t.key16 && key16_ok(a.g);
+    size_t b = 0;
+    if (t.smem_tables) {
+        b += sizeof(int32_t) * ((size_t)a.n_orders + 1);
+        b += (a.slot_stride == 0 ? (k16 ? 2 : 4) : 4) * (size_t)a.n_lines;
+        b = (b + 15) & ~(size_t)15;
+    }
+    b += (k16 ? sizeof(uint32_t) : sizeof(uint2)) * (size_t)a.max_rec * (size_t)t.threads;
     return b;
 }
 
-cudaError_t launch_line_keys(const EvalArgs& a, uint32_t* line_key, cudaStream_t s) {
-    if (a.n_lines <= 0) return cudaSuccess;
-    int grid = (a.n_lines + 255) / 256;
+cudaError_t launch_prep(const EvalArgs& a, uint32_t* line_key, cudaStream_t s) {
+    int work = a.n_plans;
+    if (line_key && a.n_lines > work) work = a.n_lines;
+    int grid = (work + 255) / 256;
     if (grid > 4096) grid = 4096;
-    k_line_keys<<<grid, 256, 0, s>>>(a, line_key);
+    if (grid < 1) grid = 1;
+    k_prep<<<grid, 256, 0, s>>>(a, line_key);
     return cudaGetLastError();
 }
 
 cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s, int* grid_out) {
-    if (t.threads % 32 != 0 || t.threads > SHORT_THREADS_MAX || t.threads < 32) return cudaErrorInvalidValue;
+    if (t.threads % 32 != 0 || t.threads > 256 || t.threads < 32) return cudaErrorInvalidValue;
+    if (a.n_tours == 0) return cudaSuccess;
     const size_t smem = eval_short_smem_bytes(a, t);
     const bool shared_map = a.slot_stride == 0;
-    if (t.smem_tables) {
-        return shared_map ? launch_short_t<true, true>(a, t, smem, num_sms, s, grid_out)
-                          : launch_short_t<true, false>(a, t, smem, num_sms, s, grid_out);
+    const bool k16 = t.key16 && key16_ok(a.g);
+    const bool sm = t.smem_tables != 0;
+#define WH_LAUNCH(K, H, M) launch_short_t<K, H, M>(a, t, smem, num_sms, s, grid_out)
+    if (k16) {
+        if (shared_map) return sm ? WH_LAUNCH(true, true, true) : WH_LAUNCH(true, true, false);
+        return sm ? WH_LAUNCH(true, false, true) : WH_LAUNCH(true, false, false);
     }
-    return shared_map ? launch_short_t<false, true>(a, t, smem, num_sms, s, grid_out)
-                      : launch_short_t<false, false>(a, t, smem, num_sms, s, grid_out);
+    if (shared_map) return sm ? WH_LAUNCH(false, true, true) : WH_LAUNCH(false, true, false);
+    return sm ? WH_LAUNCH(false, false, true) : WH_LAUNCH(false, false, false);
+#undef WH_LAUNCH
 }
 
 cudaError_t launch_eval_long(const EvalArgs& a, int num_sms, cudaStream_t s) {

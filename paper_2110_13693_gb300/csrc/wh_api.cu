@@ -22,8 +22,8 @@ struct wh_layout {
 };
 
 namespace {
-enum KernelId { K_LINE_KEYS = 0, K_EVAL_SHORT = 1, K_EVAL_LONG = 2, K_COUNT = 3 };
-const char* const kKernelNames[K_COUNT] = {"k_line_keys", "k_eval_short", "k_eval_long"};
+enum KernelId { K_PREP = 0, K_EVAL_SHORT = 1, K_EVAL_LONG = 2, K_COUNT = 3 };
+const char* const kKernelNames[K_COUNT] = {"k_prep", "k_eval_short", "k_eval_long"};
 
 // Brackets one launch with events when timing is on.
 class LaunchTimer {
@@ -115,10 +115,11 @@ int reserve_scratch(wh_layout* h, size_t bytes) {
 
 wh::Tuning default_tuning(const wh::EvalArgs& a) {
     wh::Tuning t;
-    t.threads = 128;
-    t.plans_per_item = 2;
-    const size_t tables = sizeof(int32_t) * ((size_t)a.n_orders + 1 + (size_t)a.n_lines);
-    t.smem_tables = tables <= 64 * 1024 ? 1 : 0;
+    t.threads = 256;
+    t.key16 = 1;
+    t.smem_tables = 1;
+    // keep two 256-thread CTAs per SM; larger order books stay in global memory
+    if (wh::eval_short_smem_bytes(a, t) > 112 * 1024) t.smem_tables = 0;
     return t;
 }
 
@@ -197,9 +198,6 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     a.long_count = reinterpret_cast<int32_t*>(h->meta + 1);
 
     const wh::Tuning t = default_tuning(a);
-    a.plans_per_item = t.plans_per_item;
-    a.n_items = (p.n_plans + t.plans_per_item - 1) / t.plans_per_item;
-    a.smem_tables = t.smem_tables;
 
     const bool shared_map = p.slot_map_stride == 0;
     const size_t key_bytes = shared_map ? align_up(sizeof(uint32_t) * (size_t)o.n_lines) : 0;
@@ -207,14 +205,13 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     rc = reserve_scratch(h, key_bytes + list_bytes);
     if (rc != WH_OK) return rc;
     char* base = static_cast<char*>(h->scratch);
-    uint32_t* line_key = shared_map ? reinterpret_cast<uint32_t*>(base) : nullptr;
+    uint32_t* line_key = shared_map && o.n_lines > 0 ? reinterpret_cast<uint32_t*>(base) : nullptr;
     a.line_key = line_key;
     a.long_list = reinterpret_cast<int32_t*>(base + key_bytes);
 
-    if (cudaMemsetAsync(a.long_count, 0, sizeof(int32_t), s) != cudaSuccess) return WH_ECUDA;
-    if (shared_map && a.n_lines > 0) {
-        LaunchTimer lt(h, K_LINE_KEYS, s);
-        if (!lt.ok() || wh::launch_line_keys(a, line_key, s) != cudaSuccess) return WH_ECUDA;
+    {
+        LaunchTimer lt(h, K_PREP, s);
+        if (!lt.ok() || wh::launch_prep(a, line_key, s) != cudaSuccess) return WH_ECUDA;
     }
     {
         LaunchTimer lt(h, K_EVAL_SHORT, s);

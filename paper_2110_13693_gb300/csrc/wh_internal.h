@@ -37,23 +37,23 @@ struct EvalArgs {
     int64_t* plan_s;
     int64_t* plan_rr;
     uint32_t mask;
-    int32_t plans_per_item;     // candidates per CTA work item
-    int32_t n_items;
     int32_t max_rec;            // record slots per thread = min(SHORT_MAX, A)
-    int32_t smem_tables;        // stage order_off + line_key in shared memory
     uint32_t* status;           // device status word
     int32_t* long_list;         // tours deferred to the long-tour kernel
     int32_t* long_count;
 };
 
 struct Tuning {
-    int threads;          // CTA size (tours in flight per CTA)
-    int plans_per_item;
-    int smem_tables;
+    int threads;          // CTA size: 32 tours in flight per warp
+    int smem_tables;      // stage the order book (offsets + line keys) in shared memory
+    int key16;            // 16-bit keys, two per register, when the layout allows
 };
 
 // launch wrappers (k_eval.cu)
-cudaError_t launch_line_keys(const EvalArgs& a, uint32_t* line_key, cudaStream_t s);
+bool key16_ok(const Geo& g);   // A <= 255 and L <= 256
+// line keys (shared slotting; line_key may be NULL), zeroed plan sums and
+// long-tour counter, plan offset checks
+cudaError_t launch_prep(const EvalArgs& a, uint32_t* line_key, cudaStream_t s);
 cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s,
                               int* grid_out);
 cudaError_t launch_eval_long(const EvalArgs& a, int num_sms, cudaStream_t s);

@@ -125,12 +125,10 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
     a.long_count = reinterpret_cast<int32_t*>(base) + 1;
 
     wh::Tuning t;
-    t.threads = 128;
-    t.plans_per_item = 2;
-    t.smem_tables = sizeof(int32_t) * ((size_t)o.n_orders + 1 + (size_t)o.n_lines) <= 64 * 1024 ? 1 : 0;
-    a.plans_per_item = t.plans_per_item;
-    a.n_items = (p.n_plans + t.plans_per_item - 1) / t.plans_per_item;
-    a.smem_tables = t.smem_tables;
+    t.threads = 256;
+    t.key16 = 1;
+    t.smem_tables = 1;
+    if (wh::eval_short_smem_bytes(a, t) > 112 * 1024) t.smem_tables = 0;
 
     const bool shared_map = p.slot_map_stride == 0;
     uint32_t* line_key = reinterpret_cast<uint32_t*>(base + kHeaderBytes);
@@ -138,9 +136,9 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
     a.long_list = reinterpret_cast<int32_t*>(base + kHeaderBytes + kKeyBytes);
 
     // the array keeps the previous call's contents: zero what must start at 0
-    if (cudaMemsetAsync(base, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return WH_ECUDA;
+    // (the caller's status word here; the long-tour counter in k_prep)
     if (status && cudaMemsetAsync(status, 0, sizeof(uint32_t), s) != cudaSuccess) return WH_ECUDA;
-    if (shared_map && a.n_lines > 0 && wh::launch_line_keys(a, line_key, s) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_prep(a, shared_map ? line_key : nullptr, s) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_eval_short(a, t, num_sms, s, nullptr) != cudaSuccess) return WH_ECUDA;
     if (p.n_tours > 0 && wh::launch_eval_long(a, num_sms, s) != cudaSuccess) return WH_ECUDA;
     return WH_OK;
