@@ -74,10 +74,17 @@ __device__ __forceinline__ void dp_init(DP5& v) {
 // One aisle holding picks, reached d >= 0 aisles to the right of the previous
 // one.  lo / hi: slot index of its shallowest / deepest pick; gi: largest gap
 // between consecutive picks in slot units.
+//
+// No value is clamped at INF: every state value is min over partial tours of
+// (start value 0 or INF) + that partial tour's length, and a partial tour is
+// at most 4*x_{A-1} (horizontal) + 2*A*Y (vertical) < 2^28 by the layout
+// bound 2*x_{A-1} + A*Y < 2^27, so values stay below INF + 2^28 + 2^28 = 2^30.
+// __viaddmin_s32(a, b, c) = min(a + b, c) and __vimin3_s32 are the fused
+// min-plus forms of those steps.
 __device__ __forceinline__ void dp_aisle(DP5& v, const Geo& g, int d, int lo, int hi, int gi) {
     // cross the d aisle gaps: (1,1) for UU; (2,0) / (0,2) for E0 / OE, which
     // EE may also switch to; (2,2) for EE and E2
-    const int h2 = 2 * g.P * d, h4 = 2 * h2;
+    const int h2 = 2 * g.P * d, h4 = h2 + h2;
     const int huu = v.uu + h2;
     const int he0 = min(v.e0, v.ee) + h2;
     const int hoe = min(v.oe, v.ee) + h2;
@@ -86,15 +93,15 @@ __device__ __forceinline__ void dp_aisle(DP5& v, const Geo& g, int d, int lo, in
     // vertical options of this aisle: traverse Y, double traverse 2Y, leave
     // out the largest gap 2(Y-g), from the back 2(Y-y_lo), from the front 2*y_hi
     const int ylo = g.h + lo * g.S, yhi = g.h + hi * g.S;
-    const int gap = max(max(ylo, gi * g.S), g.Y - yhi);
+    const int gap = __vimax3_s32(ylo, gi * g.S, g.Y - yhi);
     const int cG = 2 * (g.Y - gap), cB = 2 * (g.Y - ylo), cF = 2 * yhi;
     const int cT = g.Y, cD = 2 * g.Y;
-    const int m3 = min(min(he0, hoe), he2);
-    v.uu = min(min(huu + cG, min(m3, hee) + cT), INF);
-    v.ee = min(min(min(huu + cT, m3 + cD), hee + cG), INF);
-    v.e0 = min(he0 + cF, INF);
-    v.oe = min(hoe + cB, INF);
-    v.e2 = min(m3 + cG, INF);
+    const int m3 = __vimin3_s32(he0, hoe, he2);
+    v.uu = __viaddmin_s32(huu, cG, min(m3, hee) + cT);
+    v.ee = __viaddmin_s32(huu, cT, __viaddmin_s32(m3, cD, hee + cG));
+    v.e0 = he0 + cF;
+    v.oe = hoe + cB;
+    v.e2 = m3 + cG;
 }
 
 __device__ __forceinline__ int dp_final(const DP5& v) { return min(min(v.ee, v.e0), v.oe); }
@@ -259,12 +266,12 @@ __device__ __forceinline__ int rr_records16(const Geo& g, const uint32_t* rec, i
     return dp_final(v);
 }
 
-// ------------------------------------------------------------ tour bodies
 // Key source: with a shared slotting, keys come from the per-line table
 // (16-bit or 32-bit entries); with per-plan slottings, from the plan's slot
 // map via the line's SKU.
 struct KeySrc {
-    const int32_t* off;     // order offsets
+    const int32_t* off;     // order offsets (global order book)
+    const uint32_t* desc;   // per-order (first line << 8 | line count), shared memory
     const void* keys;       // per-line keys (shared slotting)
     const int32_t* skus;    // per-line SKUs (per-plan slotting)
     const int32_t* map;     // this plan's slot map (per-plan slotting)
@@ -290,55 +297,55 @@ __device__ __forceinline__ uint32_t key_of(const EvalArgs& a, const KeySrc& s, i
     }
 }
 
-template <int N, bool SHARED_MAP>
-__device__ __forceinline__ void short_tour32(const EvalArgs& a, const KeySrc& s, int q0, int q1, uint2* rec,
-                                             int stride, bool need_rr, int& cs, int& cr, bool& bad) {
-    uint32_t x[N];
-    int q = q0, l = 0, le = 0;
+// ------------------------------------------------------------ tour bodies
+// Each thread owns a column of slots in a shared-memory buffer: slot j of
+// thread tid sits at [j*T + tid], one slot = two keys = one per-aisle record
+// (4 bytes with 16-bit keys, 8 bytes with 32-bit keys), so columns of
+// different threads never overlap.  A tour's keys are first staged in the
+// column (key p in slot p/2, half p%2), loaded into registers with static
+// indices for the sort, and the column is then reused for the records.  The
+// gather itself is a plain loop over the tour's orders and their lines.
+template <int N>
+__device__ __forceinline__ void load32(const uint2* col, int T, int n, uint32_t (&x)[N]) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        while (l >= le && q < q1) {
-            const int o = a.order_seq[q++];
-            l = s.off[o];
-            le = s.off[o + 1];
-        }
-        uint32_t k = KEY_NONE;
-        if (l < le) { k = key_of<false, SHARED_MAP>(a, s, l); ++l; }
-        bad |= (k == KEY_BAD);
-        x[i] = k;
+    for (int p = 0; p < N; ++p) {
+        const uint2 w = col[(p >> 1) * T];
+        x[p] = p < n ? ((p & 1) ? w.y : w.x) : KEY_NONE;
     }
-    bitonic_sort<N>(x);
-    int m, last_a, last_hi;
-    scan32<N>(x, rec, stride, a.max_rec, need_rr, m, last_a, last_hi);
-    cs = sshape_cost(a.g, m, last_a, last_hi);
-    cr = need_rr ? rr_records32(a.g, rec, stride, min(m, a.max_rec)) : 0;
 }
 
-template <int R, bool SHARED_MAP>
-__device__ __forceinline__ void short_tour16(const EvalArgs& a, const KeySrc& s, int q0, int q1, uint32_t* rec,
-                                             int stride, bool need_rr, int& cs, int& cr, bool& bad) {
-    uint32_t x[R];
+template <int R>
+__device__ __forceinline__ void load16(const uint32_t* col, int T, int n, uint32_t (&x)[R]) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = 0xFFFFFFFFu;
-    int q = q0, l = 0, le = 0;
-#pragma unroll
-    for (int p = 0; p < 2 * R; ++p) {
-        while (l >= le && q < q1) {
-            const int o = a.order_seq[q++];
-            l = s.off[o];
-            le = s.off[o + 1];
-        }
-        uint32_t k = KEY16_NONE;
-        if (l < le) { k = key_of<true, SHARED_MAP>(a, s, l); ++l; }
-        bad |= (k == KEY16_BAD);
-        if (p < R) x[p] = __byte_perm(x[p], k, 0x3254);
-        else x[p - R] = __byte_perm(x[p - R], k, 0x5410);
+    for (int r = 0; r < R; ++r) {
+        const uint32_t wl = col[(r >> 1) * T], wh = col[((r + R) >> 1) * T];
+        x[r] = __byte_perm(wl, wh, (r & 1) ? 0x7632 : 0x5410) | (r < n ? 0u : 0xFFFFu) |
+               (r + R < n ? 0u : 0xFFFF0000u);
     }
+}
+
+template <int N>
+__device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int n, bool need_rr, int& cs,
+                                       int& cr) {
+    uint32_t x[N];
+    load32<N>(col, T, n, x);
+    bitonic_sort<N>(x);
+    int m, last_a, last_hi;
+    scan32<N>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
+    cs = sshape_cost(a.g, m, last_a, last_hi);
+    cr = need_rr ? rr_records32(a.g, col, T, min(m, a.max_rec)) : 0;
+}
+
+template <int R>
+__device__ __forceinline__ void tour16(const EvalArgs& a, uint32_t* col, int T, int n, bool need_rr, int& cs,
+                                       int& cr) {
+    uint32_t x[R];
+    load16<R>(col, T, n, x);
     sort16x2<R>(x);
     int m, last_a, last_hi;
-    scan16<R>(x, rec, stride, a.max_rec, need_rr, m, last_a, last_hi);
+    scan16<R>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
     cs = sshape_cost(a.g, m, last_a, last_hi);
-    cr = need_rr ? rr_records16(a.g, rec, stride, min(m, a.max_rec)) : 0;
+    cr = need_rr ? rr_records16(a.g, col, T, min(m, a.max_rec)) : 0;
 }
 
 // Segmented sum over the lanes of a warp whose `key` (plan id, non-decreasing
@@ -390,21 +397,29 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     size_t off_b = 0;
-    int32_t* s_off = reinterpret_cast<int32_t*>(smem);
-    off_b += sizeof(int32_t) * ((size_t)a.n_orders + 1);
+    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);
+    off_b += sizeof(uint32_t) * (size_t)a.n_orders;
     void* s_tab = smem + off_b;
     if (SMEM_TABLES) off_b += (SHARED_MAP ? (KEY16 ? 2 : 4) : 4) * (size_t)a.n_lines;
     else off_b = 0;
     off_b = (off_b + 15) & ~(size_t)15;
-    unsigned char* rec_base = smem + off_b;
+    // this thread's buffer column: elements at buf + p*T*(element size)
+    unsigned char* buf_base = smem + off_b;
 
     KeySrc src;
     src.off = a.order_off;
+    src.desc = nullptr;
     src.keys = a.line_key;
     src.skus = a.line_sku;
     src.map = nullptr;
     if constexpr (SMEM_TABLES) {
-        for (int i = tid; i <= a.n_orders; i += T) s_off[i] = a.order_off[i];
+        // descriptor per order; malformed or >= 255-line orders get count
+        // 255, which sends their tours to the long-tour kernel (it checks them)
+        for (int o = tid; o < a.n_orders; o += T) {
+            const int lb = a.order_off[o], le = a.order_off[o + 1];
+            const bool ok = lb >= 0 && le >= lb && le <= a.n_lines && le - lb < 255 && lb < (1 << 24);
+            s_desc[o] = ok ? ((uint32_t)lb << 8) | (uint32_t)(le - lb) : 0xFFu;
+        }
         if constexpr (SHARED_MAP) {
             if constexpr (KEY16) {
                 uint16_t* k16 = static_cast<uint16_t*>(s_tab);
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
             for (int i = tid; i < a.n_lines; i += T) sk[i] = a.line_sku[i];
             src.skus = sk;
         }
-        src.off = s_off;
+        src.desc = s_desc;
         __syncthreads();
     }
     const bool need_rr = (a.mask & WH_ROUTE_OPTIMAL) != 0;
@@ -433,6 +448,8 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
     const int c_begin = gw * per;
     const int c_end = min(c_begin + per, n_chunks);
     if (c_begin >= c_end) return;
+    uint32_t* col16 = reinterpret_cast<uint32_t*>(buf_base) + tid;   // used when KEY16
+    uint2* col32 = reinterpret_cast<uint2*>(buf_base) + tid;         // used otherwise
 
     // plan of the first tour: largest p with plan_tour_off[p] <= t
     int plan = 0;
@@ -450,21 +467,54 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
         const int t = c * 32 + lane;
         const bool active = t < a.n_tours;
         while (plan + 1 < a.n_plans && a.plan_tour_off[plan + 1] <= t) ++plan;
-        int q0 = 0, q1 = 0, n = 0;
-        bool bad = false;
+        if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
+        // one pass over the tour's orders: check them, count the lines and
+        // stage the first SHORT_MAX keys in this thread's buffer column
+        int n = 0;
+        bool bad = false, kbad = false;
         if (active) {
-            q0 = a.tour_off[t];
-            q1 = a.tour_off[t + 1];
+            const int q0 = __ldg(a.tour_off + t), q1 = __ldg(a.tour_off + t + 1);
             if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
                 flag(a.status, WH_STATUS_BAD_OFFSET);
                 bad = true;
             } else {
+                // software-pipelined: order ids two ahead, descriptors one ahead
+                int o2 = q0 + 1 < q1 ? __ldg(a.order_seq + q0 + 1) : 0;
+                uint32_t d1 = 0;
+                int o1 = 0;
+                if (q0 < q1) {
+                    o1 = __ldg(a.order_seq + q0);
+                    if constexpr (SMEM_TABLES) d1 = (unsigned)o1 < (unsigned)a.n_orders ? src.desc[o1] : 0xFFFFFFFFu;
+                }
                 for (int q = q0; q < q1; ++q) {
-                    const int o = a.order_seq[q];
+                    const int o = o1;
+                    const uint32_t d = d1;
+                    o1 = o2;
+                    if constexpr (SMEM_TABLES)
+                        d1 = (q + 1 < q1 && (unsigned)o1 < (unsigned)a.n_orders) ? src.desc[o1] : 0xFFFFFFFFu;
+                    o2 = q + 2 < q1 ? __ldg(a.order_seq + q + 2) : 0;
                     if ((unsigned)o >= (unsigned)a.n_orders) { flag(a.status, WH_STATUS_BAD_ORDER); bad = true; break; }
-                    const int lb = src.off[o], le = src.off[o + 1];
-                    if (lb < 0 || le < lb || le > a.n_lines) { flag(a.status, WH_STATUS_BAD_OFFSET); bad = true; break; }
-                    n += le - lb;
+                    int lb, le;
+                    if constexpr (SMEM_TABLES) {
+                        lb = (int)(d >> 8);
+                        le = lb + (int)(d & 0xFFu);
+                        if ((d & 0xFFu) == 0xFFu) { n = SHORT_MAX + 1; break; }   // long-tour kernel checks it
+                    } else {
+                        lb = src.off[o];
+                        le = src.off[o + 1];
+                        if (lb < 0 || le < lb || le > a.n_lines) { flag(a.status, WH_STATUS_BAD_OFFSET); bad = true; break; }
+                    }
+                    if (n + (le - lb) > SHORT_MAX) { n += le - lb; break; }
+                    for (int l = lb; l < le; ++l, ++n) {
+                        const uint32_t k = key_of<KEY16, SHARED_MAP>(a, src, l);
+                        if constexpr (KEY16) {
+                            kbad |= k == KEY16_BAD;
+                            reinterpret_cast<uint16_t*>(col16 + (n >> 1) * T)[n & 1] = (uint16_t)k;
+                        } else {
+                            kbad |= k == KEY_BAD;
+                            reinterpret_cast<uint32_t*>(col32 + (n >> 1) * T)[n & 1] = k;
+                        }
+                    }
                 }
             }
         }
@@ -475,21 +525,17 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
             a.long_list[2 * slot + 1] = plan;
         }
         const bool run = active && !bad && !is_long;
-        if (!run) q1 = q0;   // gather nothing
-        const int nmax = __reduce_max_sync(0xffffffffu, run ? n : 0);
-        if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
+        const int nr = run ? n : 0;
+        const int nmax = __reduce_max_sync(0xffffffffu, nr);
         int cs = 0, cr = 0;
-        bool kbad = false;
         if constexpr (KEY16) {
-            uint32_t* rec = reinterpret_cast<uint32_t*>(rec_base) + tid;
-            if (nmax <= 16) short_tour16<8, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
-            else if (nmax <= 32) short_tour16<16, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
-            else short_tour16<32, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+            if (nmax <= 16) tour16<8>(a, col16, T, nr, need_rr, cs, cr);
+            else if (nmax <= 32) tour16<16>(a, col16, T, nr, need_rr, cs, cr);
+            else tour16<32>(a, col16, T, nr, need_rr, cs, cr);
         } else {
-            uint2* rec = reinterpret_cast<uint2*>(rec_base) + tid;
-            if (nmax <= 16) short_tour32<16, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
-            else if (nmax <= 32) short_tour32<32, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
-            else short_tour32<64, SHARED_MAP>(a, src, q0, q1, rec, T, need_rr, cs, cr, kbad);
+            if (nmax <= 16) tour32<16>(a, col32, T, nr, need_rr, cs, cr);
+            else if (nmax <= 32) tour32<32>(a, col32, T, nr, need_rr, cs, cr);
+            else tour32<64>(a, col32, T, nr, need_rr, cs, cr);
         }
         const bool ok = run && !kbad;
         if (active && (bad || kbad)) {
@@ -530,6 +576,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
     const bool want_s = (a.mask & WH_ROUTE_SSHAPE) != 0;
     KeySrc src;
     src.off = a.order_off;
+    src.desc = nullptr;
     src.keys = a.line_key;
     src.skus = a.line_sku;
     src.map = nullptr;
@@ -543,9 +590,14 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
             const int q = qb + lane;
             int lb = 0, le = 0;
             if (q < q1) {
-                const int o = a.order_seq[q];
+                const int o = a.order_seq[q];   // in range: checked by k_eval_short
                 lb = a.order_off[o];
                 le = a.order_off[o + 1];
+                if (lb < 0 || le < lb || le > a.n_lines) {
+                    flag(a.status, WH_STATUS_BAD_OFFSET);
+                    bad = true;
+                    lb = le = 0;
+                }
             }
             const int cnt = le - lb;
             const int incl = warp_inclusive_scan(cnt);
@@ -645,11 +697,12 @@ size_t eval_short_smem_bytes(const EvalArgs& a, const Tuning& t) {
     const bool k16 = t.key16 && key16_ok(a.g);
     size_t b = 0;
     if (t.smem_tables) {
-        b += sizeof(int32_t) * ((size_t)a.n_orders + 1);
+        b += sizeof(uint32_t) * (size_t)a.n_orders;
         b += (a.slot_stride == 0 ? (k16 ? 2 : 4) : 4) * (size_t)a.n_lines;
         b = (b + 15) & ~(size_t)15;
     }
-    b += (k16 ? sizeof(uint32_t) : sizeof(uint2)) * (size_t)a.max_rec * (size_t)t.threads;
+    const size_t slots = a.max_rec > SHORT_MAX / 2 ? (size_t)a.max_rec : (size_t)(SHORT_MAX / 2);
+    b += (k16 ? sizeof(uint32_t) : sizeof(uint2)) * slots * (size_t)t.threads;
     return b;
 }
 
