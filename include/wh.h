@@ -64,6 +64,7 @@ extern "C" {
 #define WH_STATUS_BAD_LOC 4u      /* slot_map entry outside [0, n_locations) */
 #define WH_STATUS_BAD_OFFSET 8u   /* offsets decreasing or past the end of their array */
 #define WH_STATUS_TOUR_TOO_LONG 16u
+#define WH_STATUS_LONG_OVERFLOW 32u /* more long tours in one call than the deferral list holds */
 
 /* Limits of this implementation. */
 #define WH_MAX_AISLES 65534
@@ -159,7 +160,7 @@ int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * device-wide synchronisation that cudaMalloc / cudaFree may cause.  This call
  * takes the geometry directly (no handle) and computes exactly what
  * wh_eval_plans computes, with the same kernels, but its scratch lives in one
- * fixed device array inside the library (about 12 MiB, held on every GPU that
+ * fixed device array inside the library (about 16 MiB, held on every GPU that
  * loads the library until the process exits); it allocates nothing.
  *   - Limits: orders->n_lines <= WH_NOALLOC_MAX_LINES and
  *     plans->n_tours <= WH_NOALLOC_MAX_TOURS, else WH_ERANGE before any work.
@@ -174,6 +175,65 @@ int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * Returns as wh_eval_plans (WH_EINVAL for a bad desc or argument). */
 int wh_eval_plans_noalloc(const wh_layout_desc *desc, const wh_orders *orders, const wh_plans *plans,
                           uint32_t routing_mask, const wh_costs *out, uint32_t *status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched evaluation: many independent warehouse instances of uneven size
+ * (each its own geometry, order book, shared slotting and plans) scored in
+ * one persistent launch.  This is the paper's subsystem evaluation run for
+ * many candidate designs at once (Sec. 4: subsystem work distributed to GPU
+ * nodes; Sec. 5, Eq. (2) per instance).  The launch takes (instance, chunk
+ * range) work items from a device queue ordered largest first; it can be
+ * replayed as a CUDA graph.
+ */
+typedef struct wh_instance {
+    wh_layout_desc layout;
+    wh_orders orders;
+    wh_plans plans;   /* slot_map_stride must be 0 (one slotting per instance) */
+    wh_costs out;
+} wh_instance;
+
+typedef struct wh_batch wh_batch;
+
+/* Validate n >= 1 instance descriptors (host array; the data they point to
+ * is device memory, which must stay valid and unchanged in size while the
+ * batch lives), copy them to the device and build the work queue.
+ * Allocates device memory (synchronises).  Returns WH_OK, WH_EINVAL (an
+ * instance fails the checks of wh_create_layout / wh_eval_plans, or uses
+ * per-plan slottings), WH_ERANGE, WH_ENOMEM or WH_ECUDA. */
+int wh_batch_create(const wh_instance *insts, int32_t n, wh_batch **out);
+
+/* Launch shape: CTA size (32..256, multiple of 32), 32-tour chunks per work
+ * item (>= 1) and whether order books are staged in shared memory (0/1; it
+ * is turned off when the largest order book does not fit).  Rebuilds the
+ * work queue and drops captured graphs.  Returns WH_OK or WH_EINVAL. */
+int wh_batch_set_tuning(wh_batch *b, int32_t threads, int32_t chunks_per_item, int32_t smem_tables);
+
+/* Read the launch shape in use. */
+int wh_batch_get_tuning(wh_batch *b, int32_t *threads, int32_t *chunks_per_item, int32_t *smem_tables);
+
+/* Score every tour and plan of every instance (as wh_eval_plans does for
+ * one), enqueued on `stream`.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_batch_eval(wh_batch *b, uint32_t routing_mask, void *stream);
+
+/* Same work, replayed from a CUDA graph that the first call for a given
+ * routing_mask captures (on a private stream) and instantiates. */
+int wh_batch_eval_graph(wh_batch *b, uint32_t routing_mask, void *stream);
+
+/* Autotuner: time candidate launch shapes (CTA size x chunks per item) on
+ * this batch with the given mask, keep the fastest and report it.  When
+ * cache_path is not NULL the choice is looked up first, and stored after, in
+ * that JSON file under a key built from the batch's size bucket (key width,
+ * instance count, total tours, largest order book, mask).  Synchronises
+ * `stream`.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_batch_autotune(wh_batch *b, uint32_t routing_mask, const char *cache_path, void *stream,
+                      int32_t *threads, int32_t *chunks_per_item, int32_t *from_cache);
+
+/* Read and clear the batch's device status word (WH_STATUS_* bits).
+ * Synchronises `stream`. */
+int wh_batch_get_status(wh_batch *b, void *stream, uint32_t *status);
+
+/* Release the batch (device memory and graphs).  NULL is a no-op. */
+void wh_batch_destroy(wh_batch *b);
 
 /* Read and clear the device status word of `layout` (WH_STATUS_* bits of all
  * calls since the last read).  Synchronises `stream`.  Returns WH_OK,

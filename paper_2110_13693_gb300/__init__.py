@@ -19,7 +19,7 @@ _lib = None
 WH_OK, WH_EINVAL, WH_ERANGE, WH_ENOMEM, WH_ECUDA, WH_ETIMEOUT = 0, -1, -2, -3, -4, -5
 WH_ROUTE_SSHAPE, WH_ROUTE_OPTIMAL = 1, 2
 WH_STATUS_BAD_ORDER, WH_STATUS_BAD_SKU, WH_STATUS_BAD_LOC = 1, 2, 4
-WH_STATUS_BAD_OFFSET, WH_STATUS_TOUR_TOO_LONG = 8, 16
+WH_STATUS_BAD_OFFSET, WH_STATUS_TOUR_TOO_LONG, WH_STATUS_LONG_OVERFLOW = 8, 16, 32
 WH_NOALLOC_MAX_LINES, WH_NOALLOC_MAX_TOURS = 1 << 20, 1 << 20
 ERRORS = {WH_EINVAL: "WH_EINVAL", WH_ERANGE: "WH_ERANGE", WH_ENOMEM: "WH_ENOMEM",
           WH_ECUDA: "WH_ECUDA", WH_ETIMEOUT: "WH_ETIMEOUT"}
@@ -54,6 +54,10 @@ class wh_costs(ctypes.Structure):
                 ("plan_s", ctypes.c_void_p), ("plan_rr", ctypes.c_void_p)]
 
 
+class wh_instance(ctypes.Structure):
+    _fields_ = [("layout", wh_layout_desc), ("orders", wh_orders), ("plans", wh_plans), ("out", wh_costs)]
+
+
 # every symbol include/wh.h declares, with its ctypes signature
 SIGNATURES = {
     "wh_create_layout": (ctypes.c_int, [ctypes.POINTER(wh_layout_desc), ctypes.POINTER(ctypes.c_void_p)]),
@@ -68,6 +72,15 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "wh_destroy": (None, [ctypes.c_void_p]),
+    "wh_batch_create": (ctypes.c_int, [ctypes.POINTER(wh_instance), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "wh_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "wh_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int32)] * 3),
+    "wh_batch_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "wh_batch_eval_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "wh_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_char_p, ctypes.c_void_p]
+                          + [ctypes.POINTER(ctypes.c_int32)] * 3),
+    "wh_batch_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_batch_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -151,6 +164,50 @@ def wh_get_timing(layout) -> dict:
 
 def wh_destroy(layout) -> None:
     load().wh_destroy(layout)
+
+
+def wh_batch_create(instances) -> ctypes.c_void_p:
+    arr = (wh_instance * len(instances))(*instances)
+    h = ctypes.c_void_p()
+    _check(load().wh_batch_create(arr, len(instances), ctypes.byref(h)), "wh_batch_create")
+    return h
+
+
+def wh_batch_set_tuning(batch, threads: int, chunks_per_item: int, smem_tables: int = 1) -> None:
+    _check(load().wh_batch_set_tuning(batch, threads, chunks_per_item, smem_tables), "wh_batch_set_tuning")
+
+
+def wh_batch_get_tuning(batch):
+    v = [ctypes.c_int32() for _ in range(3)]
+    _check(load().wh_batch_get_tuning(batch, *[ctypes.byref(x) for x in v]), "wh_batch_get_tuning")
+    return tuple(int(x.value) for x in v)
+
+
+def wh_batch_eval(batch, routing_mask: int, stream=None) -> None:
+    _check(load().wh_batch_eval(batch, routing_mask, _stream_ptr(stream)), "wh_batch_eval")
+
+
+def wh_batch_eval_graph(batch, routing_mask: int, stream=None) -> None:
+    _check(load().wh_batch_eval_graph(batch, routing_mask, _stream_ptr(stream)), "wh_batch_eval_graph")
+
+
+def wh_batch_autotune(batch, routing_mask: int, cache_path=None, stream=None):
+    """Returns (threads, chunks_per_item, from_cache)."""
+    v = [ctypes.c_int32() for _ in range(3)]
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().wh_batch_autotune(batch, routing_mask, path, _stream_ptr(stream), *[ctypes.byref(x) for x in v]),
+           "wh_batch_autotune")
+    return tuple(int(x.value) for x in v)
+
+
+def wh_batch_get_status(batch, stream=None) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load().wh_batch_get_status(batch, _stream_ptr(stream), ctypes.byref(v)), "wh_batch_get_status")
+    return int(v.value)
+
+
+def wh_batch_destroy(batch) -> None:
+    load().wh_batch_destroy(batch)
 
 
 # ------------------------------------------------------ tensor-level helpers
@@ -281,3 +338,41 @@ def evaluate_host(layout: Layout, host: DeviceProblem, dev: DeviceProblem, costs
         host_plan_out[1].copy_(costs.plan_rr[:dev.n_plans], non_blocking=True)
     d2h = 2 * dev.n_plans * 8
     return h2d, d2h
+
+
+class Batch:
+    """Owning wrapper of a ``wh_batch``: many instances (each a Layout
+    geometry tuple, a DeviceProblem and its Costs) scored in one launch."""
+
+    def __init__(self, items):
+        self._keep = list(items)
+        insts = []
+        for desc, prob, costs in self._keep:
+            insts.append(wh_instance(wh_layout_desc(*desc), prob.orders(), prob.plans(), costs.c()))
+        self.handle = wh_batch_create(insts)
+
+    def eval(self, mask: int = 3, stream=None, graph: bool = False) -> None:
+        (wh_batch_eval_graph if graph else wh_batch_eval)(self.handle, mask, stream)
+
+    def set_tuning(self, threads: int, chunks_per_item: int, smem_tables: int = 1) -> None:
+        wh_batch_set_tuning(self.handle, threads, chunks_per_item, smem_tables)
+
+    def tuning(self):
+        return wh_batch_get_tuning(self.handle)
+
+    def autotune(self, mask: int = 3, cache_path=None, stream=None):
+        return wh_batch_autotune(self.handle, mask, cache_path, stream)
+
+    def status(self, stream=None) -> int:
+        return wh_batch_get_status(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            wh_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

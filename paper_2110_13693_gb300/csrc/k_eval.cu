@@ -277,10 +277,13 @@ struct KeySrc {
     const int32_t* map;     // this plan's slot map (per-plan slotting)
 };
 
-template <bool KEY16, bool SHARED_MAP>
+// STAGED: the shared-slotting key table is the shared-memory copy (16-bit
+// entries when KEY16); otherwise it is the 32-bit table in global memory.
+template <bool KEY16, bool SHARED_MAP, bool STAGED>
 __device__ __forceinline__ uint32_t key_of(const EvalArgs& a, const KeySrc& s, int l) {
     if constexpr (SHARED_MAP) {
-        if constexpr (KEY16) return static_cast<const uint16_t*>(s.keys)[l];
+        if constexpr (KEY16 && STAGED) return static_cast<const uint16_t*>(s.keys)[l];
+        else if constexpr (KEY16) return key16_of(static_cast<const uint32_t*>(s.keys)[l]);
         else return static_cast<const uint32_t*>(s.keys)[l];
     } else {
         const int sku = s.skus[l];
@@ -363,94 +366,65 @@ __device__ __forceinline__ long long segmented_sum(long long v, int key, int lan
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void k_prep(EvalArgs a, uint32_t* line_key) {
-    const int stride = gridDim.x * blockDim.x;
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i0 == 0) *a.long_count = 0;
-    if (line_key) {
-        for (int l = i0; l < a.n_lines; l += stride) {
-            const int sku = a.line_sku[l];
-            uint32_t key = KEY_BAD;
-            if ((unsigned)sku >= (unsigned)a.n_sku) {
-                flag(a.status, WH_STATUS_BAD_SKU);
-            } else {
-                const int loc = a.slot_map[sku];
-                if ((unsigned)loc >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
-                else key = loc_key(a.g, loc);
-            }
-            line_key[l] = key;
+// Per-instance staging of the order book into shared memory: one descriptor
+// per order (first line << 8 | line count; count 255 marks an order that the
+// short path does not take: malformed, or 255 lines or more, so its tours go
+// to the long-tour kernel, which checks them) and one key (or SKU) per line.
+template <bool KEY16, bool SHARED_MAP>
+__device__ __forceinline__ void stage_tables(const EvalArgs& a, uint32_t* s_desc, void* s_tab, KeySrc& src,
+                                             int tid, int T) {
+    for (int o = tid; o < a.n_orders; o += T) {
+        const int lb = a.order_off[o], le = a.order_off[o + 1];
+        const bool ok = lb >= 0 && le >= lb && le <= a.n_lines && le - lb < 255 && lb < (1 << 24);
+        s_desc[o] = ok ? ((uint32_t)lb << 8) | (uint32_t)(le - lb) : 0xFFu;
+    }
+    if constexpr (SHARED_MAP) {
+        if constexpr (KEY16) {
+            uint16_t* k16 = static_cast<uint16_t*>(s_tab);
+            for (int i = tid; i < a.n_lines; i += T) k16[i] = (uint16_t)key16_of(a.line_key[i]);
+        } else {
+            uint32_t* k32 = static_cast<uint32_t*>(s_tab);
+            for (int i = tid; i < a.n_lines; i += T) k32[i] = a.line_key[i];
         }
+        src.keys = s_tab;
+    } else {
+        int32_t* sk = static_cast<int32_t*>(s_tab);
+        for (int i = tid; i < a.n_lines; i += T) sk[i] = a.line_sku[i];
+        src.skus = sk;
     }
-    const bool zs = a.plan_s && (a.mask & WH_ROUTE_SSHAPE);
-    const bool zr = a.plan_rr && (a.mask & WH_ROUTE_OPTIMAL);
-    for (int p = i0; p < a.n_plans; p += stride) {
-        if (zs) a.plan_s[p] = 0;
-        if (zr) a.plan_rr[p] = 0;
-        const int t0 = a.plan_tour_off[p], t1 = a.plan_tour_off[p + 1];
-        if (t0 < 0 || t1 < t0 || t1 > a.n_tours || (p == 0 && t0 != 0) || (p == a.n_plans - 1 && t1 != a.n_tours))
-            flag(a.status, WH_STATUS_BAD_OFFSET);
-    }
+    src.desc = s_desc;
 }
 
-template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
-__global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
-    size_t off_b = 0;
-    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);
-    off_b += sizeof(uint32_t) * (size_t)a.n_orders;
-    void* s_tab = smem + off_b;
-    if (SMEM_TABLES) off_b += (SHARED_MAP ? (KEY16 ? 2 : 4) : 4) * (size_t)a.n_lines;
-    else off_b = 0;
-    off_b = (off_b + 15) & ~(size_t)15;
-    // this thread's buffer column: elements at buf + p*T*(element size)
-    unsigned char* buf_base = smem + off_b;
-
+__device__ __forceinline__ KeySrc global_src(const EvalArgs& a) {
     KeySrc src;
     src.off = a.order_off;
     src.desc = nullptr;
     src.keys = a.line_key;
     src.skus = a.line_sku;
     src.map = nullptr;
-    if constexpr (SMEM_TABLES) {
-        // descriptor per order; malformed or >= 255-line orders get count
-        // 255, which sends their tours to the long-tour kernel (it checks them)
-        for (int o = tid; o < a.n_orders; o += T) {
-            const int lb = a.order_off[o], le = a.order_off[o + 1];
-            const bool ok = lb >= 0 && le >= lb && le <= a.n_lines && le - lb < 255 && lb < (1 << 24);
-            s_desc[o] = ok ? ((uint32_t)lb << 8) | (uint32_t)(le - lb) : 0xFFu;
-        }
-        if constexpr (SHARED_MAP) {
-            if constexpr (KEY16) {
-                uint16_t* k16 = static_cast<uint16_t*>(s_tab);
-                for (int i = tid; i < a.n_lines; i += T) k16[i] = (uint16_t)key16_of(a.line_key[i]);
-            } else {
-                uint32_t* k32 = static_cast<uint32_t*>(s_tab);
-                for (int i = tid; i < a.n_lines; i += T) k32[i] = a.line_key[i];
-            }
-            src.keys = s_tab;
-        } else {
-            int32_t* sk = static_cast<int32_t*>(s_tab);
-            for (int i = tid; i < a.n_lines; i += T) sk[i] = a.line_sku[i];
-            src.skus = sk;
-        }
-        src.desc = s_desc;
-        __syncthreads();
+    return src;
+}
+
+// Defer tour t of plan `plan` (instance `inst`) to the long-tour kernel.
+__device__ __forceinline__ bool defer_long(const EvalArgs& a, int inst, int t, int plan) {
+    const int slot = atomicAdd(a.long_count, 1);
+    if (slot >= a.long_cap) {
+        flag(a.status, WH_STATUS_LONG_OVERFLOW);
+        return false;
     }
-    const bool need_rr = (a.mask & WH_ROUTE_OPTIMAL) != 0;
-    const bool want_s = (a.mask & WH_ROUTE_SSHAPE) != 0;
+    a.long_list[3 * slot] = inst;
+    a.long_list[3 * slot + 1] = t;
+    a.long_list[3 * slot + 2] = plan;
+    return true;
+}
 
-    // this warp's contiguous range of 32-tour chunks
-    const int warps = gridDim.x * (T >> 5);
-    const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
-    const int n_chunks = (a.n_tours + 31) >> 5;
-    const int per = (n_chunks + warps - 1) / warps;
-    const int c_begin = gw * per;
-    const int c_end = min(c_begin + per, n_chunks);
-    if (c_begin >= c_end) return;
-    uint32_t* col16 = reinterpret_cast<uint32_t*>(buf_base) + tid;   // used when KEY16
-    uint2* col32 = reinterpret_cast<uint2*>(buf_base) + tid;         // used otherwise
-
+// One warp scores the 32-tour chunks [c_begin, c_end) of instance `a`, one
+// tour per lane, and adds its plans' sums with one atomic per plan segment.
+template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
+__device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint32_t mask, int inst, int c_begin,
+                                            int c_end, uint32_t* col16, uint2* col32, int T, int lane) {
+    const bool need_rr = (mask & WH_ROUTE_OPTIMAL) != 0;
+    const bool want_s = (mask & WH_ROUTE_SSHAPE) != 0;
     // plan of the first tour: largest p with plan_tour_off[p] <= t
     int plan = 0;
     {
@@ -462,7 +436,6 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
         }
         plan = lo;
     }
-
     for (int c = c_begin; c < c_end; ++c) {
         const int t = c * 32 + lane;
         const bool active = t < a.n_tours;
@@ -506,7 +479,7 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
                     }
                     if (n + (le - lb) > SHORT_MAX) { n += le - lb; break; }
                     for (int l = lb; l < le; ++l, ++n) {
-                        const uint32_t k = key_of<KEY16, SHARED_MAP>(a, src, l);
+                        const uint32_t k = key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
                         if constexpr (KEY16) {
                             kbad |= k == KEY16_BAD;
                             reinterpret_cast<uint16_t*>(col16 + (n >> 1) * T)[n & 1] = (uint16_t)k;
@@ -518,12 +491,8 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
                 }
             }
         }
-        const bool is_long = active && !bad && n > SHORT_MAX;
-        if (is_long) {
-            const int slot = atomicAdd(a.long_count, 1);
-            a.long_list[2 * slot] = t;
-            a.long_list[2 * slot + 1] = plan;
-        }
+        bool is_long = active && !bad && n > SHORT_MAX;
+        if (is_long && !defer_long(a, inst, t, plan)) { is_long = false; bad = true; }
         const bool run = active && !bad && !is_long;
         const int nr = run ? n : 0;
         const int nmax = __reduce_max_sync(0xffffffffu, nr);
@@ -556,6 +525,126 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
     }
 }
 
+// line keys of one instance, zeroed plan sums, plan offset checks
+__device__ __forceinline__ void prep_instance(const EvalArgs& a, uint32_t mask, int i0, int stride) {
+    if (a.line_key) {
+        uint32_t* line_key = const_cast<uint32_t*>(a.line_key);
+        for (int l = i0; l < a.n_lines; l += stride) {
+            const int sku = a.line_sku[l];
+            uint32_t key = KEY_BAD;
+            if ((unsigned)sku >= (unsigned)a.n_sku) {
+                flag(a.status, WH_STATUS_BAD_SKU);
+            } else {
+                const int loc = a.slot_map[sku];
+                if ((unsigned)loc >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
+                else key = loc_key(a.g, loc);
+            }
+            line_key[l] = key;
+        }
+    }
+    const bool zs = a.plan_s && (mask & WH_ROUTE_SSHAPE);
+    const bool zr = a.plan_rr && (mask & WH_ROUTE_OPTIMAL);
+    for (int p = i0; p < a.n_plans; p += stride) {
+        if (zs) a.plan_s[p] = 0;
+        if (zr) a.plan_rr[p] = 0;
+        const int t0 = a.plan_tour_off[p], t1 = a.plan_tour_off[p + 1];
+        if (t0 < 0 || t1 < t0 || t1 > a.n_tours || (p == 0 && t0 != 0) || (p == a.n_plans - 1 && t1 != a.n_tours))
+            flag(a.status, WH_STATUS_BAD_OFFSET);
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_prep(EvalArgs a) {
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) *a.long_count = 0;
+    prep_instance(a, a.mask, i0, gridDim.x * blockDim.x);
+}
+
+// one block row per instance (blockIdx.y); block (0,0) resets the counters
+__global__ void k_prep_batch(BatchArgs b) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        *b.queue = 0;
+        *b.long_count = 0;
+    }
+    for (int i = blockIdx.y; i < b.n_inst; i += gridDim.y)
+        prep_instance(b.insts[i], b.mask, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
+__global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);
+    void* s_tab = smem + sizeof(uint32_t) * (size_t)a.n_orders;
+    size_t off_b = 0;
+    if (SMEM_TABLES)
+        off_b = (sizeof(uint32_t) * (size_t)a.n_orders + (SHARED_MAP ? (KEY16 ? 2 : 4) : 4) * (size_t)a.n_lines + 15) &
+                ~(size_t)15;
+    unsigned char* buf_base = smem + off_b;
+
+    KeySrc src = global_src(a);
+    if constexpr (SMEM_TABLES) {
+        stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T);
+        __syncthreads();
+    }
+    // this warp's contiguous range of 32-tour chunks
+    const int warps = gridDim.x * (T >> 5);
+    const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
+    const int n_chunks = (a.n_tours + 31) >> 5;
+    const int per = (n_chunks + warps - 1) / warps;
+    const int c_begin = gw * per;
+    const int c_end = min(c_begin + per, n_chunks);
+    if (c_begin >= c_end) return;
+    eval_chunks<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, a.mask, 0, c_begin, c_end,
+                                                reinterpret_cast<uint32_t*>(buf_base) + tid,
+                                                reinterpret_cast<uint2*>(buf_base) + tid, T, lane);
+}
+
+// Persistent batch kernel: CTAs pop work items (instance, chunk range) from
+// a queue ordered largest first, stage that instance's order book once, and
+// split the item's chunks among their warps.
+template <bool KEY16, bool SMEM_TABLES>
+__global__ void __launch_bounds__(256, 2) k_eval_batch(BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    __shared__ __align__(16) EvalArgs s_a;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);
+    void* s_tab = smem + sizeof(uint32_t) * (size_t)b.max_orders;
+    size_t off_b = 0;
+    if (SMEM_TABLES)
+        off_b = (sizeof(uint32_t) * (size_t)b.max_orders + (KEY16 ? 2 : 4) * (size_t)b.max_lines + 15) & ~(size_t)15;
+    unsigned char* buf_base = smem + off_b;
+    uint32_t* col16 = reinterpret_cast<uint32_t*>(buf_base) + tid;
+    uint2* col32 = reinterpret_cast<uint2*>(buf_base) + tid;
+    int staged = -1;
+    KeySrc src;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(b.queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= b.n_items) break;
+        const WorkItem w = b.items[it];
+        if (w.inst != staged) {
+            const int* srcw = reinterpret_cast<const int*>(b.insts + w.inst);
+            int* dstw = reinterpret_cast<int*>(&s_a);
+            for (int i = tid; i < (int)(sizeof(EvalArgs) / sizeof(int)); i += T) dstw[i] = srcw[i];
+            __syncthreads();
+            src = global_src(s_a);
+            if constexpr (SMEM_TABLES) stage_tables<KEY16, true>(s_a, s_desc, s_tab, src, tid, T);
+            staged = w.inst;
+        }
+        __syncthreads();
+        const int n = w.chunk_end - w.chunk_begin;
+        const int per = (n + nw - 1) / nw;
+        const int cb = w.chunk_begin + warp * per;
+        const int ce = min(cb + per, w.chunk_end);
+        if (cb < ce) eval_chunks<KEY16, true, SMEM_TABLES>(s_a, src, b.mask, w.inst, cb, ce, col16, col32, T, lane);
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ int warp_inclusive_scan(int v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -566,23 +655,22 @@ __device__ __forceinline__ int warp_inclusive_scan(int v) {
     return v;
 }
 
+// One warp per deferred tour (more than SHORT_MAX lines): keys gathered into
+// a per-warp shared-memory buffer, bitonic-sorted there, then one lane runs
+// the record scan and the DP.
 template <bool SHARED_MAP>
-__global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
+__global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
     __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int count = *a.long_count;
+    const int count = min(*L.count, L.cap);
     uint32_t* kb = buf[warp];
-    const bool need_rr = (a.mask & WH_ROUTE_OPTIMAL) != 0;
-    const bool want_s = (a.mask & WH_ROUTE_SSHAPE) != 0;
-    KeySrc src;
-    src.off = a.order_off;
-    src.desc = nullptr;
-    src.keys = a.line_key;
-    src.skus = a.line_sku;
-    src.map = nullptr;
+    const bool need_rr = (L.mask & WH_ROUTE_OPTIMAL) != 0;
+    const bool want_s = (L.mask & WH_ROUTE_SSHAPE) != 0;
     for (int w = blockIdx.x * LONG_WARPS + warp; w < count; w += gridDim.x * LONG_WARPS) {
-        const int t = a.long_list[2 * w], plan = a.long_list[2 * w + 1];
-        const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];   // checked by k_eval_short
+        const int inst = L.list[3 * w], t = L.list[3 * w + 1], plan = L.list[3 * w + 2];
+        const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
+        KeySrc src = global_src(a);
+        const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];   // checked by the short kernel
         if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
         int n = 0;
         bool bad = false;
@@ -590,7 +678,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
             const int q = qb + lane;
             int lb = 0, le = 0;
             if (q < q1) {
-                const int o = a.order_seq[q];   // in range: checked by k_eval_short
+                const int o = a.order_seq[q];   // in range: checked by the short kernel
                 lb = a.order_off[o];
                 le = a.order_off[o + 1];
                 if (lb < 0 || le < lb || le > a.n_lines) {
@@ -603,7 +691,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
             const int incl = warp_inclusive_scan(cnt);
             int pos = n + incl - cnt;
             for (int l = lb; l < le; ++l, ++pos) {
-                const uint32_t k = key_of<false, SHARED_MAP>(a, src, l);
+                const uint32_t k = key_of<false, SHARED_MAP, false>(a, src, l);
                 bad |= (k == KEY_BAD);
                 if (pos < LONG_MAXL) kb[pos] = k;
             }
@@ -669,23 +757,41 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(EvalArgs a) {
     }
 }
 
+template <typename K>
+cudaError_t grid_for(K kern, int threads, size_t smem, int num_sms, int want, int* grid) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int g = per_sm * num_sms;
+    if (g > want) g = want;
+    if (g < 1) g = 1;
+    *grid = g;
+    return cudaSuccess;
+}
+
 template <bool K16, bool SH, bool SM>
 cudaError_t launch_short_t(const EvalArgs& a, const Tuning& t, size_t smem, int num_sms, cudaStream_t s,
                            int* grid_out) {
     auto kern = k_eval_short<K16, SH, SM>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t.threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int warps_needed = (a.n_tours + 31) / 32;
-    int grid = per_sm * num_sms;
-    const int max_grid = (warps_needed + t.threads / 32 - 1) / (t.threads / 32);
-    if (grid > max_grid) grid = max_grid;
-    if (grid < 1) grid = 1;
+    int grid = 0;
+    cudaError_t e = grid_for(kern, t.threads, smem, num_sms, (warps_needed + t.threads / 32 - 1) / (t.threads / 32), &grid);
+    if (e != cudaSuccess) return e;
     if (grid_out) *grid_out = grid;
     kern<<<grid, t.threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool K16, bool SM>
+cudaError_t launch_batch_t(const BatchArgs& b, const Tuning& t, size_t smem, int num_sms, cudaStream_t s) {
+    auto kern = k_eval_batch<K16, SM>;
+    int grid = 0;
+    cudaError_t e = grid_for(kern, t.threads, smem, num_sms, b.n_items, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, t.threads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -693,26 +799,44 @@ cudaError_t launch_short_t(const EvalArgs& a, const Tuning& t, size_t smem, int 
 
 bool key16_ok(const Geo& g) { return g.A <= 255 && g.L <= 256; }
 
-size_t eval_short_smem_bytes(const EvalArgs& a, const Tuning& t) {
-    const bool k16 = t.key16 && key16_ok(a.g);
-    size_t b = 0;
-    if (t.smem_tables) {
-        b += sizeof(uint32_t) * (size_t)a.n_orders;
-        b += (a.slot_stride == 0 ? (k16 ? 2 : 4) : 4) * (size_t)a.n_lines;
-        b = (b + 15) & ~(size_t)15;
-    }
-    const size_t slots = a.max_rec > SHORT_MAX / 2 ? (size_t)a.max_rec : (size_t)(SHORT_MAX / 2);
-    b += (k16 ? sizeof(uint32_t) : sizeof(uint2)) * slots * (size_t)t.threads;
-    return b;
+
+static size_t buffer_bytes(bool k16, int max_rec, int threads) {
+    const size_t slots = max_rec > SHORT_MAX / 2 ? (size_t)max_rec : (size_t)(SHORT_MAX / 2);
+    return (k16 ? sizeof(uint32_t) : sizeof(uint2)) * slots * (size_t)threads;
 }
 
-cudaError_t launch_prep(const EvalArgs& a, uint32_t* line_key, cudaStream_t s) {
+static size_t table_bytes(bool k16, bool shared_map, int64_t n_orders, int64_t n_lines) {
+    const size_t b = sizeof(uint32_t) * (size_t)n_orders + (shared_map ? (k16 ? 2 : 4) : 4) * (size_t)n_lines;
+    return (b + 15) & ~(size_t)15;
+}
+
+size_t eval_short_smem_bytes(const EvalArgs& a, const Tuning& t) {
+    const bool k16 = t.key16 && key16_ok(a.g);
+    size_t b = t.smem_tables ? table_bytes(k16, a.slot_stride == 0, a.n_orders, a.n_lines) : 0;
+    return b + buffer_bytes(k16, a.max_rec, t.threads);
+}
+
+size_t eval_batch_smem_bytes(const BatchArgs& b, const Tuning& t, bool k16) {
+    size_t s = t.smem_tables ? table_bytes(k16, true, b.max_orders, b.max_lines) : 0;
+    return s + buffer_bytes(k16, b.max_rec, t.threads);
+}
+
+cudaError_t launch_prep(const EvalArgs& a, cudaStream_t s) {
     int work = a.n_plans;
-    if (line_key && a.n_lines > work) work = a.n_lines;
+    if (a.line_key && a.n_lines > work) work = a.n_lines;
     int grid = (work + 255) / 256;
     if (grid > 4096) grid = 4096;
     if (grid < 1) grid = 1;
-    k_prep<<<grid, 256, 0, s>>>(a, line_key);
+    k_prep<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(const BatchArgs& b, int max_work, cudaStream_t s) {
+    int gx = (max_work + 255) / 256;
+    if (gx > 16) gx = 16;
+    if (gx < 1) gx = 1;
+    const int gy = b.n_inst < 65535 ? b.n_inst : 65535;
+    k_prep_batch<<<dim3(gx, gy), 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -733,10 +857,19 @@ cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, c
 #undef WH_LAUNCH
 }
 
-cudaError_t launch_eval_long(const EvalArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int num_sms, cudaStream_t s) {
+    if (t.threads % 32 != 0 || t.threads > 256 || t.threads < 32) return cudaErrorInvalidValue;
+    if (b.n_items == 0) return cudaSuccess;
+    const size_t smem = eval_batch_smem_bytes(b, t, k16);
+    const bool sm = t.smem_tables != 0;
+    if (k16) return sm ? launch_batch_t<true, true>(b, t, smem, num_sms, s) : launch_batch_t<true, false>(b, t, smem, num_sms, s);
+    return sm ? launch_batch_t<false, true>(b, t, smem, num_sms, s) : launch_batch_t<false, false>(b, t, smem, num_sms, s);
+}
+
+cudaError_t launch_eval_long(const LongArgs& L, bool shared_map, int num_sms, cudaStream_t s) {
     const int grid = num_sms * 2;
-    if (a.slot_stride == 0) k_eval_long<true><<<grid, LONG_WARPS * 32, 0, s>>>(a);
-    else k_eval_long<false><<<grid, LONG_WARPS * 32, 0, s>>>(a);
+    if (shared_map) k_eval_long<true><<<grid, LONG_WARPS * 32, 0, s>>>(L);
+    else k_eval_long<false><<<grid, LONG_WARPS * 32, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,14 @@
 // C-ABI entry points (declared in include/wh.h): argument checks, the layout
-// handle and its device scratch, and the launch sequence of a plan evaluation.
+// handle and its device scratch, the launch sequence of a plan evaluation, the
+// batched persistent launch with CUDA-graph replay, and its autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "wh_internal.h"
@@ -19,6 +26,27 @@ struct wh_layout {
     std::vector<cudaEvent_t> events;       // pool, reused across sessions
     std::vector<int> event_kernel;         // kernel id of each recorded pair
     size_t n_recorded = 0;                 // pairs recorded this session
+};
+
+struct wh_batch {
+    int device = -1;
+    int num_sms = 0;
+    int32_t n_inst = 0;
+    std::vector<wh::EvalArgs> args;        // host copy of the per-instance descriptors
+    wh::EvalArgs* d_args = nullptr;
+    wh::WorkItem* d_items = nullptr;
+    int32_t n_items = 0;
+    size_t items_cap = 0;
+    uint32_t* meta = nullptr;              // [0] status, [1] long count, [2] queue
+    void* scratch = nullptr;               // line keys of all instances + long list
+    bool key16 = true;
+    int32_t max_orders = 0, max_lines = 0, max_rec = 0, max_work = 0;
+    int64_t total_tours = 0;
+    int32_t long_cap = 0;
+    wh::Tuning tune{};
+    int32_t chunks_per_item = 16;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};   // per routing mask
 };
 
 namespace {
@@ -53,11 +81,9 @@ class LaunchTimer {
     bool ok_ = true;
     bool armed_ = false;
 };
-}  // namespace
-
-namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int32_t kBatchLongCap = 1 << 22;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -76,6 +102,70 @@ class DeviceGuard {
     int prev_ = -1;
     bool switched_ = false;
 };
+
+int check_desc(const wh_layout_desc& d, wh::Geo* g) {
+    if (d.n_aisles < 1 || d.slots_per_side < 1 || d.aisle_pitch < 1 || d.slot_pitch < 1 ||
+        d.cross_aisle_width < 2 || (d.cross_aisle_width & 1))
+        return WH_EINVAL;
+    if (d.n_aisles > WH_MAX_AISLES || d.slots_per_side > WH_MAX_SLOTS_PER_SIDE) return WH_ERANGE;
+    const int64_t Y = (int64_t)d.cross_aisle_width + (int64_t)(d.slots_per_side - 1) * d.slot_pitch;
+    const int64_t span = 2 * (int64_t)(d.n_aisles - 1) * d.aisle_pitch + (int64_t)d.n_aisles * Y;
+    if (span >= WH_MAX_TOUR_SPAN) return WH_ERANGE;
+    if ((int64_t)d.n_aisles * 2 * d.slots_per_side > 0x7fffffff) return WH_ERANGE;
+    g->A = d.n_aisles;
+    g->L = d.slots_per_side;
+    g->P = d.aisle_pitch;
+    g->S = d.slot_pitch;
+    g->W = d.cross_aisle_width;
+    g->h = d.cross_aisle_width / 2;
+    g->Y = (int32_t)Y;
+    g->n_loc = d.n_aisles * 2 * d.slots_per_side;
+    return WH_OK;
+}
+
+int check_problem(const wh_orders& o, const wh_plans& p) {
+    if (o.n_orders < 0 || o.n_lines < 0 || o.n_sku < 0 || p.n_plans < 0 || p.n_tours < 0 || p.n_seq < 0)
+        return WH_EINVAL;
+    if (p.n_seq > 0x7fffffff) return WH_ERANGE;
+    if (!o.order_off || (o.n_lines > 0 && !o.line_sku)) return WH_EINVAL;
+    if (p.n_plans > 0 && !p.plan_tour_off) return WH_EINVAL;
+    if (p.n_tours > 0 && !p.tour_off) return WH_EINVAL;
+    if (p.n_seq > 0 && !p.order_seq) return WH_EINVAL;
+    if (o.n_lines > 0 && !p.slot_map) return WH_EINVAL;
+    if (p.slot_map_stride < 0 || (p.slot_map_stride != 0 && p.slot_map_stride < o.n_sku)) return WH_EINVAL;
+    return WH_OK;
+}
+
+void fill_args(wh::EvalArgs& a, const wh::Geo& g, const wh_orders& o, const wh_plans& p, const wh_costs& out,
+               uint32_t mask) {
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.n_orders = o.n_orders;
+    a.n_lines = o.n_lines;
+    a.n_sku = o.n_sku;
+    a.order_off = o.order_off;
+    a.line_sku = o.line_sku;
+    a.slot_map = p.slot_map;
+    a.slot_stride = p.slot_map_stride;
+    a.n_plans = p.n_plans;
+    a.n_tours = p.n_tours;
+    a.n_seq = p.n_seq;
+    a.plan_tour_off = p.plan_tour_off;
+    a.tour_off = p.tour_off;
+    a.order_seq = p.order_seq;
+    a.tour_s = out.tour_s;
+    a.tour_rr = out.tour_rr;
+    a.plan_s = out.plan_s;
+    a.plan_rr = out.plan_rr;
+    a.mask = mask;
+    a.max_rec = g.A < wh::SHORT_MAX ? g.A : wh::SHORT_MAX;
+}
+
+int device_info(int* dev, int* sms) {
+    if (cudaGetDevice(dev) != cudaSuccess) return WH_ECUDA;
+    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *dev) != cudaSuccess) return WH_ECUDA;
+    return WH_OK;
+}
 
 // Bind the handle to the current device on first use; later calls must run on
 // the same device.
@@ -127,26 +217,13 @@ wh::Tuning default_tuning(const wh::EvalArgs& a) {
 
 extern "C" int wh_create_layout(const wh_layout_desc* desc, wh_layout** out) {
     if (!desc || !out) return WH_EINVAL;
-    const wh_layout_desc d = *desc;
-    if (d.n_aisles < 1 || d.slots_per_side < 1 || d.aisle_pitch < 1 || d.slot_pitch < 1 ||
-        d.cross_aisle_width < 2 || (d.cross_aisle_width & 1))
-        return WH_EINVAL;
-    if (d.n_aisles > WH_MAX_AISLES || d.slots_per_side > WH_MAX_SLOTS_PER_SIDE) return WH_ERANGE;
-    const int64_t Y = (int64_t)d.cross_aisle_width + (int64_t)(d.slots_per_side - 1) * d.slot_pitch;
-    const int64_t span = 2 * (int64_t)(d.n_aisles - 1) * d.aisle_pitch + (int64_t)d.n_aisles * Y;
-    if (span >= WH_MAX_TOUR_SPAN) return WH_ERANGE;
-    if ((int64_t)d.n_aisles * 2 * d.slots_per_side > 0x7fffffff) return WH_ERANGE;
+    wh::Geo g;
+    const int rc = check_desc(*desc, &g);
+    if (rc != WH_OK) return rc;
     wh_layout* h = new (std::nothrow) wh_layout;
     if (!h) return WH_ENOMEM;
-    h->d = d;
-    h->g.A = d.n_aisles;
-    h->g.L = d.slots_per_side;
-    h->g.P = d.aisle_pitch;
-    h->g.S = d.slot_pitch;
-    h->g.W = d.cross_aisle_width;
-    h->g.h = d.cross_aisle_width / 2;
-    h->g.Y = (int32_t)Y;
-    h->g.n_loc = d.n_aisles * 2 * d.slots_per_side;
+    h->d = *desc;
+    h->g = g;
     *out = h;
     return WH_OK;
 }
@@ -157,61 +234,33 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     if (routing_mask == 0 || (routing_mask & ~(WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL))) return WH_EINVAL;
     const wh_orders o = *orders;
     const wh_plans p = *plans;
-    if (o.n_orders < 0 || o.n_lines < 0 || o.n_sku < 0 || p.n_plans < 0 || p.n_tours < 0 || p.n_seq < 0)
-        return WH_EINVAL;
-    if (p.n_seq > 0x7fffffff) return WH_ERANGE;
-    if (!o.order_off || (o.n_lines > 0 && !o.line_sku)) return WH_EINVAL;
-    if (p.n_plans > 0 && !p.plan_tour_off) return WH_EINVAL;
-    if (p.n_tours > 0 && !p.tour_off) return WH_EINVAL;
-    if (p.n_seq > 0 && !p.order_seq) return WH_EINVAL;
-    if (o.n_lines > 0 && !p.slot_map) return WH_EINVAL;
-    if (p.slot_map_stride < 0 || (p.slot_map_stride != 0 && p.slot_map_stride < o.n_sku)) return WH_EINVAL;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
     if (p.n_plans == 0) return WH_OK;
 
-    int rc = bind_device(h);
+    rc = bind_device(h);
     if (rc != WH_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     wh::EvalArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.g = h->g;
-    a.n_orders = o.n_orders;
-    a.n_lines = o.n_lines;
-    a.n_sku = o.n_sku;
-    a.order_off = o.order_off;
-    a.line_sku = o.line_sku;
-    a.slot_map = p.slot_map;
-    a.slot_stride = p.slot_map_stride;
-    a.n_plans = p.n_plans;
-    a.n_tours = p.n_tours;
-    a.n_seq = p.n_seq;
-    a.plan_tour_off = p.plan_tour_off;
-    a.tour_off = p.tour_off;
-    a.order_seq = p.order_seq;
-    a.tour_s = out->tour_s;
-    a.tour_rr = out->tour_rr;
-    a.plan_s = out->plan_s;
-    a.plan_rr = out->plan_rr;
-    a.mask = routing_mask;
-    a.max_rec = h->g.A < wh::SHORT_MAX ? h->g.A : wh::SHORT_MAX;
+    fill_args(a, h->g, o, p, *out, routing_mask);
     a.status = h->meta;
     a.long_count = reinterpret_cast<int32_t*>(h->meta + 1);
-
+    a.long_cap = p.n_tours;
     const wh::Tuning t = default_tuning(a);
 
     const bool shared_map = p.slot_map_stride == 0;
     const size_t key_bytes = shared_map ? align_up(sizeof(uint32_t) * (size_t)o.n_lines) : 0;
-    const size_t list_bytes = align_up(sizeof(int32_t) * 2 * ((size_t)p.n_tours + 1));
+    const size_t list_bytes = align_up(sizeof(int32_t) * 3 * ((size_t)p.n_tours + 1));
     rc = reserve_scratch(h, key_bytes + list_bytes);
     if (rc != WH_OK) return rc;
     char* base = static_cast<char*>(h->scratch);
-    uint32_t* line_key = shared_map && o.n_lines > 0 ? reinterpret_cast<uint32_t*>(base) : nullptr;
-    a.line_key = line_key;
+    a.line_key = shared_map && o.n_lines > 0 ? reinterpret_cast<uint32_t*>(base) : nullptr;
     a.long_list = reinterpret_cast<int32_t*>(base + key_bytes);
 
     {
         LaunchTimer lt(h, K_PREP, s);
-        if (!lt.ok() || wh::launch_prep(a, line_key, s) != cudaSuccess) return WH_ECUDA;
+        if (!lt.ok() || wh::launch_prep(a, s) != cudaSuccess) return WH_ECUDA;
     }
     {
         LaunchTimer lt(h, K_EVAL_SHORT, s);
@@ -219,7 +268,14 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     }
     if (p.n_tours > 0) {
         LaunchTimer lt(h, K_EVAL_LONG, s);
-        if (!lt.ok() || wh::launch_eval_long(a, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+        wh::LongArgs L;
+        L.single = a;
+        L.insts = nullptr;
+        L.list = a.long_list;
+        L.count = a.long_count;
+        L.cap = a.long_cap;
+        L.mask = routing_mask;
+        if (!lt.ok() || wh::launch_eval_long(L, shared_map, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
     }
     return WH_OK;
 }
@@ -280,4 +336,385 @@ extern "C" void wh_destroy(wh_layout* h) {
         if (h->meta) cudaFree(h->meta);
     }
     delete h;
+}
+
+// ---------------------------------------------------------------- batches
+
+namespace {
+
+void drop_graphs(wh_batch* b) {
+    for (auto& g : b->graphs) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// Work items: each instance's 32-tour chunks cut into runs of
+// chunks_per_item, ordered by estimated cost (chunks x orders per tour),
+// largest first; ties keep instance order, so the order is deterministic.
+int build_items(wh_batch* b) {
+    std::vector<wh::WorkItem> items;
+    for (int32_t i = 0; i < b->n_inst; ++i) {
+        const wh::EvalArgs& a = b->args[i];
+        const int32_t chunks = (a.n_tours + 31) / 32;
+        const int64_t per_chunk = a.n_tours > 0 ? std::max<int64_t>(1, a.n_seq / std::max(1, a.n_tours)) : 1;
+        for (int32_t c = 0; c < chunks; c += b->chunks_per_item) {
+            wh::WorkItem w;
+            w.inst = i;
+            w.chunk_begin = c;
+            w.chunk_end = std::min(chunks, c + b->chunks_per_item);
+            w.cost = (int32_t)std::min<int64_t>(0x7fffffff, (int64_t)(w.chunk_end - w.chunk_begin) * per_chunk);
+            items.push_back(w);
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const wh::WorkItem& x, const wh::WorkItem& y) { return x.cost > y.cost; });
+    if (items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = 0;
+        if (cudaMalloc(&b->d_items, sizeof(wh::WorkItem) * std::max<size_t>(items.size(), 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return WH_ENOMEM;
+        }
+        b->items_cap = items.size();
+    }
+    if (!items.empty() &&
+        cudaMemcpy(b->d_items, items.data(), sizeof(wh::WorkItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return WH_ECUDA;
+    b->n_items = (int32_t)items.size();
+    drop_graphs(b);
+    return WH_OK;
+}
+
+wh::BatchArgs batch_args(const wh_batch* b, uint32_t mask) {
+    wh::BatchArgs B;
+    B.insts = b->d_args;
+    B.n_inst = b->n_inst;
+    B.items = b->d_items;
+    B.n_items = b->n_items;
+    B.queue = reinterpret_cast<int32_t*>(b->meta + 2);
+    B.long_count = reinterpret_cast<int32_t*>(b->meta + 1);
+    B.mask = mask;
+    B.max_orders = b->max_orders;
+    B.max_lines = b->max_lines;
+    B.max_rec = b->max_rec;
+    return B;
+}
+
+int launch_batch(wh_batch* b, uint32_t mask, cudaStream_t s) {
+    const wh::BatchArgs B = batch_args(b, mask);
+    if (wh::launch_prep_batch(B, b->max_work, s) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_eval_batch(B, b->tune, b->key16, b->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    wh::LongArgs L;
+    std::memset(&L, 0, sizeof(L));
+    L.insts = b->d_args;
+    L.list = b->args.empty() ? nullptr : b->args[0].long_list;
+    L.count = B.long_count;
+    L.cap = b->long_cap;
+    L.mask = mask;
+    if (wh::launch_eval_long(L, true, b->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    return WH_OK;
+}
+
+bool valid_mask(uint32_t m) { return m != 0 && !(m & ~(WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL)); }
+
+}  // namespace
+
+extern "C" int wh_batch_create(const wh_instance* insts, int32_t n, wh_batch** out) {
+    if (!insts || n < 1 || !out) return WH_EINVAL;
+    wh_batch* b = new (std::nothrow) wh_batch;
+    if (!b) return WH_ENOMEM;
+    int rc = device_info(&b->device, &b->num_sms);
+    if (rc != WH_OK) {
+        b->device = -1;
+        delete b;
+        return rc;
+    }
+    b->n_inst = n;
+    b->args.resize(n);
+    size_t key_bytes = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        wh::Geo g;
+        rc = check_desc(insts[i].layout, &g);
+        if (rc == WH_OK) rc = check_problem(insts[i].orders, insts[i].plans);
+        if (rc == WH_OK && (insts[i].plans.slot_map_stride != 0 || insts[i].plans.n_plans < 1)) rc = WH_EINVAL;
+        if (rc != WH_OK) {
+            b->device = -1;
+            delete b;
+            return rc;
+        }
+        fill_args(b->args[i], g, insts[i].orders, insts[i].plans, insts[i].out, WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL);
+        b->key16 = b->key16 && wh::key16_ok(g);
+        b->max_orders = std::max(b->max_orders, insts[i].orders.n_orders);
+        b->max_lines = std::max(b->max_lines, insts[i].orders.n_lines);
+        b->max_rec = std::max(b->max_rec, b->args[i].max_rec);
+        b->max_work = std::max(b->max_work, std::max(insts[i].orders.n_lines, insts[i].plans.n_plans));
+        b->total_tours += insts[i].plans.n_tours;
+        key_bytes += align_up(sizeof(uint32_t) * (size_t)insts[i].orders.n_lines);
+    }
+    b->long_cap = (int32_t)std::min<int64_t>(kBatchLongCap, b->total_tours + 1);
+    const size_t list_bytes = align_up(sizeof(int32_t) * 3 * (size_t)b->long_cap);
+    if (cudaMalloc(&b->meta, kAlign) != cudaSuccess || cudaMemset(b->meta, 0, kAlign) != cudaSuccess ||
+        cudaMalloc(&b->scratch, key_bytes + list_bytes) != cudaSuccess ||
+        cudaMalloc(&b->d_args, sizeof(wh::EvalArgs) * n) != cudaSuccess) {
+        cudaGetLastError();
+        wh_batch_destroy(b);
+        return WH_ENOMEM;
+    }
+    char* base = static_cast<char*>(b->scratch);
+    int32_t* list = reinterpret_cast<int32_t*>(base + key_bytes);
+    size_t off = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        wh::EvalArgs& a = b->args[i];
+        a.line_key = a.n_lines > 0 ? reinterpret_cast<uint32_t*>(base + off) : nullptr;
+        off += align_up(sizeof(uint32_t) * (size_t)a.n_lines);
+        a.status = b->meta;
+        a.long_count = reinterpret_cast<int32_t*>(b->meta + 1);
+        a.long_list = list;
+        a.long_cap = b->long_cap;
+    }
+    if (cudaMemcpy(b->d_args, b->args.data(), sizeof(wh::EvalArgs) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        wh_batch_destroy(b);
+        return WH_ECUDA;
+    }
+    b->tune.threads = 256;
+    b->tune.key16 = b->key16 ? 1 : 0;
+    b->tune.smem_tables = 1;
+    if (wh::eval_batch_smem_bytes(batch_args(b, 3), b->tune, b->key16) > 112 * 1024) b->tune.smem_tables = 0;
+    b->chunks_per_item = 16;
+    rc = build_items(b);
+    if (rc != WH_OK) {
+        wh_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return WH_OK;
+}
+
+extern "C" int wh_batch_set_tuning(wh_batch* b, int32_t threads, int32_t chunks_per_item, int32_t smem_tables) {
+    if (!b || threads < 32 || threads > 256 || (threads % 32) || chunks_per_item < 1 || smem_tables < 0 ||
+        smem_tables > 1)
+        return WH_EINVAL;
+    DeviceGuard guard(b->device);
+    wh::Tuning t = b->tune;
+    t.threads = threads;
+    t.smem_tables = smem_tables;
+    if (t.smem_tables && wh::eval_batch_smem_bytes(batch_args(b, 3), t, b->key16) > 200 * 1024) t.smem_tables = 0;
+    b->tune = t;
+    if (chunks_per_item != b->chunks_per_item) {
+        b->chunks_per_item = chunks_per_item;
+        return build_items(b);
+    }
+    drop_graphs(b);
+    return WH_OK;
+}
+
+extern "C" int wh_batch_get_tuning(wh_batch* b, int32_t* threads, int32_t* chunks_per_item, int32_t* smem_tables) {
+    if (!b || !threads || !chunks_per_item || !smem_tables) return WH_EINVAL;
+    *threads = b->tune.threads;
+    *chunks_per_item = b->chunks_per_item;
+    *smem_tables = b->tune.smem_tables;
+    return WH_OK;
+}
+
+extern "C" int wh_batch_eval(wh_batch* b, uint32_t routing_mask, void* stream) {
+    if (!b || !valid_mask(routing_mask)) return WH_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WH_ECUDA;
+    if (dev != b->device) return WH_EINVAL;
+    return launch_batch(b, routing_mask, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int wh_batch_eval_graph(wh_batch* b, uint32_t routing_mask, void* stream) {
+    if (!b || !valid_mask(routing_mask)) return WH_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WH_ECUDA;
+    if (dev != b->device) return WH_EINVAL;
+    cudaGraphExec_t& exec = b->graphs[routing_mask];
+    if (!exec) {
+        if (!b->capture && cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) return WH_ECUDA;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WH_ECUDA;
+        const int rc = launch_batch(b, routing_mask, b->capture);
+        const cudaError_t ec = cudaStreamEndCapture(b->capture, &graph);
+        if (rc != WH_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc != WH_OK ? rc : WH_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            exec = nullptr;
+            return WH_ECUDA;
+        }
+    }
+    return cudaGraphLaunch(exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
+namespace {
+
+// The autotune cache is a flat JSON object, one entry per size bucket:
+//   {"<bucket>": {"threads": T, "chunks_per_item": C, "ms": X}, ...}
+struct TuneEntry {
+    int threads = 0, chunks = 0;
+    double ms = 0;
+};
+
+std::map<std::string, TuneEntry> read_cache(const char* path) {
+    std::map<std::string, TuneEntry> m;
+    FILE* f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return m;
+    std::string text;
+    char buf[4096];
+    size_t k;
+    while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+    std::fclose(f);
+    size_t pos = 0;
+    while ((pos = text.find('"', pos)) != std::string::npos) {
+        const size_t end = text.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = text.substr(pos + 1, end - pos - 1);
+        const size_t brace = text.find('{', end);
+        const size_t close = text.find('}', end);
+        if (brace == std::string::npos || close == std::string::npos || brace > close) {
+            pos = end + 1;
+            continue;
+        }
+        const std::string body = text.substr(brace, close - brace + 1);
+        TuneEntry e;
+        const size_t ti = body.find("\"threads\"");
+        const size_t ci = body.find("\"chunks_per_item\"");
+        const size_t mi = body.find("\"ms\"");
+        if (ti != std::string::npos && ci != std::string::npos) {
+            e.threads = std::atoi(body.c_str() + body.find(':', ti) + 1);
+            e.chunks = std::atoi(body.c_str() + body.find(':', ci) + 1);
+            if (mi != std::string::npos) e.ms = std::atof(body.c_str() + body.find(':', mi) + 1);
+            m[key] = e;
+        }
+        pos = close + 1;
+    }
+    return m;
+}
+
+bool write_cache(const char* path, const std::map<std::string, TuneEntry>& m) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    std::fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto& kv : m) {
+        std::fprintf(f, "  \"%s\": {\"threads\": %d, \"chunks_per_item\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(),
+                     kv.second.threads, kv.second.chunks, kv.second.ms, ++i < m.size() ? "," : "");
+    }
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+std::string bucket_key(const wh_batch* b, uint32_t mask) {
+    char k[160];
+    std::snprintf(k, sizeof(k), "key%d_inst2^%d_tours2^%d_orders2^%d_mask%u", b->key16 ? 16 : 32, ilog2(b->n_inst),
+                  ilog2(std::max<int64_t>(1, b->total_tours)), ilog2(std::max(1, b->max_orders)), mask);
+    return k;
+}
+
+}  // namespace
+
+extern "C" int wh_batch_autotune(wh_batch* b, uint32_t routing_mask, const char* cache_path, void* stream,
+                                 int32_t* threads, int32_t* chunks_per_item, int32_t* from_cache) {
+    if (!b || !valid_mask(routing_mask)) return WH_EINVAL;
+    DeviceGuard guard(b->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const std::string key = bucket_key(b, routing_mask);
+    std::map<std::string, TuneEntry> cache = read_cache(cache_path);
+    auto it = cache.find(key);
+    int rc = WH_OK;
+    if (it != cache.end() && it->second.threads > 0 && it->second.chunks > 0) {
+        rc = wh_batch_set_tuning(b, it->second.threads, it->second.chunks, b->tune.smem_tables);
+        if (from_cache) *from_cache = 1;
+    } else {
+        if (from_cache) *from_cache = 0;
+        const int32_t smem = b->tune.smem_tables;
+        const int thread_opts[] = {128, 256};
+        const int chunk_opts[] = {2, 4, 8, 16, 32, 64};
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return WH_ECUDA;
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return WH_ECUDA;
+        }
+        TuneEntry best;
+        best.ms = 1e30;
+        for (int th : thread_opts) {
+            for (int ch : chunk_opts) {
+                rc = wh_batch_set_tuning(b, th, ch, smem);
+                if (rc != WH_OK) break;
+                rc = launch_batch(b, routing_mask, s);   // warm-up
+                if (rc != WH_OK) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && rc == WH_OK; ++r) rc = launch_batch(b, routing_mask, s);
+                cudaEventRecord(e1, s);
+                if (rc != WH_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = rc != WH_OK ? rc : WH_ECUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / 3 < best.ms) {
+                    best.ms = ms / 3;
+                    best.threads = th;
+                    best.chunks = ch;
+                }
+            }
+            if (rc != WH_OK) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc != WH_OK) return rc;
+        rc = wh_batch_set_tuning(b, best.threads, best.chunks, smem);
+        if (rc == WH_OK && cache_path) {
+            cache[key] = best;
+            write_cache(cache_path, cache);
+        }
+    }
+    if (threads) *threads = b->tune.threads;
+    if (chunks_per_item) *chunks_per_item = b->chunks_per_item;
+    return rc;
+}
+
+extern "C" int wh_batch_get_status(wh_batch* b, void* stream, uint32_t* status) {
+    if (!b || !status) return WH_EINVAL;
+    DeviceGuard guard(b->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, b->meta, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return WH_ECUDA;
+    if (cudaMemsetAsync(b->meta, 0, sizeof(uint32_t), s) != cudaSuccess) return WH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return WH_ECUDA;
+    *status = v;
+    return WH_OK;
+}
+
+extern "C" void wh_batch_destroy(wh_batch* b) {
+    if (!b) return;
+    if (b->device >= 0) {
+        DeviceGuard guard(b->device);
+        drop_graphs(b);
+        if (b->capture) cudaStreamDestroy(b->capture);
+        if (b->d_items) cudaFree(b->d_items);
+        if (b->d_args) cudaFree(b->d_args);
+        if (b->scratch) cudaFree(b->scratch);
+        if (b->meta) cudaFree(b->meta);
+    }
+    delete b;
 }

@@ -39,8 +39,38 @@ struct EvalArgs {
     uint32_t mask;
     int32_t max_rec;            // record slots per thread = min(SHORT_MAX, A)
     uint32_t* status;           // device status word
-    int32_t* long_list;         // tours deferred to the long-tour kernel
+    int32_t* long_list;         // tours deferred to the long-tour kernel: (inst, tour, plan)
     int32_t* long_count;
+    int32_t long_cap;           // capacity of long_list in entries
+};
+
+// A work item of the batched launch: 32-tour chunks [chunk_begin, chunk_end)
+// of instance `inst`.
+struct WorkItem {
+    int32_t inst;
+    int32_t chunk_begin;
+    int32_t chunk_end;
+    int32_t cost;               // estimated work, for the largest-first order
+};
+
+struct BatchArgs {
+    const EvalArgs* insts;      // device array, one per instance
+    int32_t n_inst;
+    const WorkItem* items;      // device array, largest first
+    int32_t n_items;
+    int32_t* queue;             // next item to take (zeroed by the batch prep kernel)
+    int32_t* long_count;
+    uint32_t mask;
+    int32_t max_orders, max_lines, max_rec;
+};
+
+struct LongArgs {
+    EvalArgs single;            // the instance when insts is NULL
+    const EvalArgs* insts;      // batched instances (device), else NULL
+    const int32_t* list;
+    const int32_t* count;
+    int32_t cap;
+    uint32_t mask;
 };
 
 struct Tuning {
@@ -51,12 +81,15 @@ struct Tuning {
 
 // launch wrappers (k_eval.cu)
 bool key16_ok(const Geo& g);   // A <= 255 and L <= 256
-// line keys (shared slotting; line_key may be NULL), zeroed plan sums and
+// line keys (shared slotting, when a.line_key is set), zeroed plan sums and
 // long-tour counter, plan offset checks
-cudaError_t launch_prep(const EvalArgs& a, uint32_t* line_key, cudaStream_t s);
+cudaError_t launch_prep(const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_prep_batch(const BatchArgs& b, int max_work, cudaStream_t s);
 cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s,
                               int* grid_out);
-cudaError_t launch_eval_long(const EvalArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int num_sms, cudaStream_t s);
+cudaError_t launch_eval_long(const LongArgs& L, bool shared_map, int num_sms, cudaStream_t s);
 size_t eval_short_smem_bytes(const EvalArgs& a, const Tuning& t);
+size_t eval_batch_smem_bytes(const BatchArgs& b, const Tuning& t, bool k16);
 
 }  // namespace wh

@@ -11,7 +11,7 @@
 // handle's cudaMalloc'd buffers.  It needs no handle at all.
 //
 // The array is part of the library image: every GPU that loads the library
-// holds it (about 12 MiB) until the process exits.
+// holds it (about 16 MiB) until the process exits.
 #include <cstring>
 #include <mutex>
 
@@ -21,7 +21,7 @@ namespace {
 
 constexpr size_t kHeaderBytes = 256;  // [0] status word, [1] long-tour count
 constexpr size_t kKeyBytes = sizeof(uint32_t) * (size_t)WH_NOALLOC_MAX_LINES;
-constexpr size_t kListBytes = sizeof(int32_t) * 2 * ((size_t)WH_NOALLOC_MAX_TOURS + 1);
+constexpr size_t kListBytes = sizeof(int32_t) * 3 * ((size_t)WH_NOALLOC_MAX_TOURS + 1);
 constexpr size_t kScratchBytes = kHeaderBytes + kKeyBytes + kListBytes;
 
 // The shared scratch.  Host code must not use this name as a device address:
@@ -123,6 +123,7 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
     // status bits go to the caller's word when given, else to the array's own
     a.status = status ? status : reinterpret_cast<uint32_t*>(base);
     a.long_count = reinterpret_cast<int32_t*>(base) + 1;
+    a.long_cap = p.n_tours;
 
     wh::Tuning t;
     t.threads = 256;
@@ -132,14 +133,23 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
 
     const bool shared_map = p.slot_map_stride == 0;
     uint32_t* line_key = reinterpret_cast<uint32_t*>(base + kHeaderBytes);
-    a.line_key = shared_map ? line_key : nullptr;
+    a.line_key = shared_map && o.n_lines > 0 ? line_key : nullptr;
     a.long_list = reinterpret_cast<int32_t*>(base + kHeaderBytes + kKeyBytes);
 
     // the array keeps the previous call's contents: zero what must start at 0
     // (the caller's status word here; the long-tour counter in k_prep)
     if (status && cudaMemsetAsync(status, 0, sizeof(uint32_t), s) != cudaSuccess) return WH_ECUDA;
-    if (wh::launch_prep(a, shared_map ? line_key : nullptr, s) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_prep(a, s) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_eval_short(a, t, num_sms, s, nullptr) != cudaSuccess) return WH_ECUDA;
-    if (p.n_tours > 0 && wh::launch_eval_long(a, num_sms, s) != cudaSuccess) return WH_ECUDA;
+    if (p.n_tours > 0) {
+        wh::LongArgs L;
+        L.single = a;
+        L.insts = nullptr;
+        L.list = a.long_list;
+        L.count = a.long_count;
+        L.cap = a.long_cap;
+        L.mask = routing_mask;
+        if (wh::launch_eval_long(L, shared_map, num_sms, s) != cudaSuccess) return WH_ECUDA;
+    }
     return WH_OK;
 }

@@ -1,0 +1,176 @@
+"""Batched persistent launch: many uneven instances in one call, eager and
+replayed from a CUDA graph, under several launch shapes and the autotuner;
+bit-exact against the CPU oracle and against one-instance calls."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import wh_gen
+
+pytestmark = pytest.mark.gpu
+
+
+def build_batch(wh, insts, dev="cuda"):
+    items = []
+    for inst in insts:
+        lay = inst.layout
+        desc = (lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width)
+        prob = wh.to_device(inst, dev)
+        costs = wh.alloc_costs(prob.n_tours, prob.n_plans, dev)
+        for t in (costs.tour_s, costs.tour_rr, costs.plan_s, costs.plan_rr):
+            t.fill_(-99)
+        items.append((desc, prob, costs))
+    return wh.Batch(items), items
+
+
+def results(items, i):
+    _, prob, c = items[i]
+    return (c.tour_s[:prob.n_tours].cpu().numpy(), c.tour_rr[:prob.n_tours].cpu().numpy(),
+            c.plan_s[:prob.n_plans].cpu().numpy(), c.plan_rr[:prob.n_plans].cpu().numpy())
+
+
+def assert_same(got, want, tag):
+    for name, g, w in zip(("tour_s", "tour_rr", "plan_s", "plan_rr"), got, want):
+        assert np.array_equal(g, w), f"{tag}: {name} differs"
+
+
+def test_batch_matches_oracle_eager_and_graph(gpu_lib):
+    import torch
+    insts = [wh_gen.batched_instance(9, i, n_plans=6) for i in range(24)]
+    want = [oracle.eval_plans(inst) for inst in insts]
+    batch, items = build_batch(gpu_lib, insts)
+    batch.eval(3)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for i in range(len(insts)):
+        assert_same(results(items, i), want[i], f"eager instance {i}")
+    for rep in range(2):
+        for _, _, c in items:
+            for t in (c.tour_s, c.tour_rr, c.plan_s, c.plan_rr):
+                t.fill_(-99)
+        batch.eval(3, graph=True)
+        torch.cuda.synchronize()
+        assert batch.status() == 0
+        for i in range(len(insts)):
+            assert_same(results(items, i), want[i], f"graph replay {rep} instance {i}")
+    batch.close()
+
+
+@pytest.mark.parametrize("shape", [(256, 16, 1), (128, 2, 1), (256, 64, 1), (64, 1, 0), (256, 7, 0)])
+def test_batch_launch_shapes_agree(gpu_lib, shape):
+    import torch
+    insts = [wh_gen.batched_instance(5, i, n_plans=12) for i in range(40)]
+    batch, items = build_batch(gpu_lib, insts)
+    batch.set_tuning(*shape)
+    batch.eval(3)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    rng = np.random.default_rng(shape[1])
+    for i in rng.choice(len(insts), 6, replace=False):
+        assert_same(results(items, i), oracle.eval_plans(insts[i]), f"shape {shape} instance {i}")
+    batch.close()
+
+
+def test_batch_equals_single_calls(gpu_lib):
+    """The batch and one wh_eval_plans call per instance give identical results."""
+    import torch
+    wh = gpu_lib
+    insts = [wh_gen.batched_instance(7, i, n_plans=64) for i in range(32)]
+    batch, items = build_batch(wh, insts)
+    batch.eval(3, graph=True)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for i, inst in enumerate(insts):
+        lay = wh.Layout.of(inst.layout)
+        prob = items[i][1]
+        costs = wh.evaluate(lay, prob)
+        torch.cuda.synchronize()
+        single = (costs.tour_s[:prob.n_tours].cpu().numpy(), costs.tour_rr[:prob.n_tours].cpu().numpy(),
+                  costs.plan_s[:prob.n_plans].cpu().numpy(), costs.plan_rr[:prob.n_plans].cpu().numpy())
+        assert_same(results(items, i), single, f"instance {i}")
+        lay.close()
+    batch.close()
+
+
+def test_batch_routing_masks(gpu_lib):
+    import torch
+    insts = [wh_gen.batched_instance(2, i, n_plans=4) for i in range(8)]
+    want = [oracle.eval_plans(inst) for inst in insts]
+    batch, items = build_batch(gpu_lib, insts)
+    batch.eval(1, graph=True)
+    torch.cuda.synchronize()
+    for i in range(len(insts)):
+        got = results(items, i)
+        assert np.array_equal(got[0], want[i][0]) and np.array_equal(got[2], want[i][2])
+        assert (got[1] == -99).all() and (got[3] == -99).all()
+    batch.eval(2)
+    torch.cuda.synchronize()
+    for i in range(len(insts)):
+        got = results(items, i)
+        assert np.array_equal(got[1], want[i][1]) and np.array_equal(got[3], want[i][3])
+    batch.close()
+
+
+def test_batch_with_long_tours_and_mixed_layouts(gpu_lib):
+    """Instances whose layout needs 32-bit keys and tours beyond 64 lines go
+    through the long-tour kernel inside the batch."""
+    import torch
+    insts = [wh_gen.paperscale(seed=8, n_plans=3), wh_gen.tiny(seed=2, n_plans=5),
+             wh_gen.batched_instance(4, 0, n_plans=3)]
+    want = [oracle.eval_plans(inst) for inst in insts]
+    batch, items = build_batch(gpu_lib, insts)
+    batch.eval(3, graph=True)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for i in range(len(insts)):
+        assert_same(results(items, i), want[i], f"instance {i}")
+    batch.close()
+
+
+def test_autotune_and_cache(gpu_lib, tmp_path):
+    import torch
+    insts = [wh_gen.batched_instance(11, i, n_plans=16) for i in range(48)]
+    batch, items = build_batch(gpu_lib, insts)
+    cache = tmp_path / "tune.json"
+    th, ch, hit = batch.autotune(3, str(cache))
+    assert hit == 0 and th in (128, 256) and ch >= 1
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 1 and list(entries.values())[0]["threads"] == th
+    assert batch.tuning()[:2] == (th, ch)
+    batch.set_tuning(64, 3, 1)
+    th2, ch2, hit2 = batch.autotune(3, str(cache))
+    assert hit2 == 1 and (th2, ch2) == (th, ch)
+    batch.eval(3, graph=True)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    for i in (0, 17, 47):
+        assert_same(results(items, i), oracle.eval_plans(insts[i]), f"tuned instance {i}")
+    batch.close()
+
+
+def test_batched_full_size_sampled(gpu_lib):
+    """1,024 instances x 256 plans in one graph-replayed launch; 12 sampled
+    plans from 6 sampled instances re-scored by the oracle, size-independent
+    properties on every output of those instances."""
+    import torch
+    insts = [wh_gen.batched_instance(3, i, n_plans=256) for i in range(1024)]
+    batch, items = build_batch(gpu_lib, insts)
+    batch.eval(3, graph=True)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    rng = np.random.default_rng(1)
+    for i in rng.choice(1024, 6, replace=False):
+        inst = insts[i]
+        ts, tr, ps, pr = results(items, i)
+        assert (tr >= 0).all() and (tr <= ts).all() and (tr % 2 == 0).all()
+        seg = inst.plan_tour_off
+        assert np.array_equal(pr, np.add.reduceat(tr.astype(np.int64), seg[:-1]))
+        plans = np.sort(rng.choice(inst.n_plans, 2, replace=False))
+        sub = oracle.eval_plans(inst.subset_plans(plans))
+        idx = np.concatenate([np.arange(seg[p], seg[p + 1]) for p in plans])
+        assert np.array_equal(tr[idx], sub[1]) and np.array_equal(ts[idx], sub[0])
+        assert np.array_equal(pr[plans], sub[3]) and np.array_equal(ps[plans], sub[2])
+    batch.close()

@@ -240,3 +240,17 @@ def test_repeatable(gpu_lib):
     b = gpu_eval(gpu_lib, inst)
     for x, y in zip(a[:4], b[:4]):
         assert np.array_equal(x, y)
+
+
+def test_large_order_book_global_tables(gpu_lib):
+    """An order book too large for shared memory (the kernel reads offsets
+    and 32-bit keys from global memory) on a layout that uses 16-bit keys."""
+    lay = wh_gen.Layout(60, 150)
+    off, lines = wh_gen.gen_orders(21, 24000, 18000, 12, 0.4, 1.1)
+    slot = wh_gen.gen_slot_abc(21, lay, 18000, 0.1)
+    pto, to, seq = wh_gen.gen_plans(21, 1, off, 3, 20, 60)
+    inst = wh_gen.Instance(lay, 18000, off, lines, slot, pto, to, seq)
+    assert 4 * (inst.n_orders + inst.n_lines) > 112 * 1024
+    got = gpu_eval(gpu_lib, inst)
+    assert got[4] == 0
+    assert_exact(got, oracle.eval_plans(inst))
