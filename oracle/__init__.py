@@ -22,6 +22,10 @@ Functions and the independent checks that pin them (all in ``tests/``):
                         monotone in the pick set, ...).
 * ``eval_plans``     -- plan sums; pinned by summing per-tour calls over
                         hand-assembled pick lists.
+* ``eval_moves``     -- move deltas by applying each move to a copy and
+                        re-scoring the plan; pinned by building the moved
+                        plans explicitly in Python and differencing two
+                        ``eval_plans`` results, and by status special cases.
 """
 from __future__ import annotations
 
@@ -74,6 +78,10 @@ def _load():
             lib.or_eval_plans.restype = ctypes.c_int
             lib.or_eval_plans.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
                                           ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, i64p, i64p]
+            lib.or_eval_moves.restype = ctypes.c_int
+            lib.or_eval_moves.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
+                                          ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, i64p, i32p]
             _lib = lib
     return _lib
 
@@ -134,3 +142,21 @@ def eval_plans(inst, slot_map=None, slot_map_stride: int = 0):
     if rc != 0:
         raise ValueError(f"or_eval_plans error {rc}")
     return ts[:nt], tr[:nt], ps[:npl], pr[:npl]
+
+
+def eval_moves(inst, moves, max_orders: int = 0, max_lines: int = 0, slot_map=None, slot_map_stride: int = 0):
+    """Deltas [n, 2] (S-shape, optimal) and status [n] of moves {type, a, b, plan}."""
+    lib = _load()
+    smap = _i32(inst.slot_map if slot_map is None else slot_map)
+    off, lines = _i32(inst.order_off), _i32(inst.line_sku)
+    pto, to, seq = _i32(inst.plan_tour_off), _i32(inst.tour_off), _i32(inst.order_seq)
+    mv = _i32(np.asarray(moves).reshape(-1, 4))
+    n = mv.shape[0]
+    delta = np.zeros((max(n, 1), 2), np.int64)
+    status = np.zeros(max(n, 1), np.int32)
+    rc = lib.or_eval_moves(ctypes.byref(_layout(inst.layout)), off.shape[0] - 1, _ptr(off), _ptr(lines), inst.n_sku,
+                           _ptr(smap), slot_map_stride, pto.shape[0] - 1, _ptr(pto), _ptr(to), _ptr(seq), _ptr(mv), n,
+                           max_orders, max_lines, _ptr(delta, ctypes.c_int64), _ptr(status))
+    if rc != 0:
+        raise ValueError(f"or_eval_moves error {rc}")
+    return delta[:n], status[:n]

@@ -443,3 +443,162 @@ int or_eval_plans(const or_layout *g, int32_t n_orders, const int32_t *order_off
     free(buf);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------- moves */
+
+/* One plan held as separate order lists per tour, so a move can be applied
+ * to a copy by editing lists. */
+typedef struct {
+    int32_t n_tours;
+    int32_t *len;      /* orders per tour */
+    int32_t *cap;      /* capacity of each list */
+    int32_t **orders;  /* order ids per tour */
+} plan_copy_t;
+
+static void plan_free(plan_copy_t *c) {
+    for (int32_t t = 0; t < c->n_tours; ++t) free(c->orders[t]);
+    free(c->orders);
+    free(c->len);
+    free(c->cap);
+}
+
+static int plan_load(plan_copy_t *c, int32_t p, const int32_t *plan_tour_off, const int32_t *tour_off,
+                     const int32_t *order_seq) {
+    int32_t t0 = plan_tour_off[p], t1 = plan_tour_off[p + 1];
+    c->n_tours = t1 - t0;
+    c->len = (int32_t *)calloc((size_t)c->n_tours + 1, sizeof(int32_t));
+    c->cap = (int32_t *)calloc((size_t)c->n_tours + 1, sizeof(int32_t));
+    c->orders = (int32_t **)calloc((size_t)c->n_tours + 1, sizeof(int32_t *));
+    if (!c->len || !c->cap || !c->orders) return OR_ENOMEM;
+    for (int32_t t = 0; t < c->n_tours; ++t) {
+        int32_t q0 = tour_off[t0 + t], q1 = tour_off[t0 + t + 1];
+        c->len[t] = q1 - q0;
+        c->cap[t] = q1 - q0 + 1;
+        c->orders[t] = (int32_t *)malloc(sizeof(int32_t) * (size_t)c->cap[t]);
+        if (!c->orders[t]) return OR_ENOMEM;
+        memcpy(c->orders[t], order_seq + q0, sizeof(int32_t) * (size_t)(q1 - q0));
+    }
+    return OR_OK;
+}
+
+/* index of the tour holding order o, or -1 */
+static int32_t plan_find(const plan_copy_t *c, int32_t o, int32_t *pos) {
+    for (int32_t t = 0; t < c->n_tours; ++t)
+        for (int32_t i = 0; i < c->len[t]; ++i)
+            if (c->orders[t][i] == o) { *pos = i; return t; }
+    return -1;
+}
+
+static int32_t tour_line_count(const plan_copy_t *c, int32_t t, const int32_t *order_off) {
+    int32_t n = 0;
+    for (int32_t i = 0; i < c->len[t]; ++i) n += order_off[c->orders[t][i] + 1] - order_off[c->orders[t][i]];
+    return n;
+}
+
+/* Sum of both rules over every tour of the plan copy under slotting smap. */
+static int plan_cost(const or_layout *g, const plan_copy_t *c, const int32_t *order_off, const int32_t *line_sku,
+                     const int32_t *smap, int64_t *sum_s, int64_t *sum_rr) {
+    *sum_s = 0;
+    *sum_rr = 0;
+    for (int32_t t = 0; t < c->n_tours; ++t) {
+        int32_t n = tour_line_count(c, t, order_off);
+        int32_t *locs = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+        if (!locs) return OR_ENOMEM;
+        int32_t k = 0;
+        for (int32_t i = 0; i < c->len[t]; ++i) {
+            int32_t o = c->orders[t][i];
+            for (int32_t l = order_off[o]; l < order_off[o + 1]; ++l) locs[k++] = smap[line_sku[l]];
+        }
+        int64_t cs = or_sshape_tour(g, locs, n), cr = or_rr_tour(g, locs, n);
+        free(locs);
+        if (cs < 0 || cr < 0) return (int)(cs < 0 ? cs : cr);
+        *sum_s += cs;
+        *sum_rr += cr;
+    }
+    return OR_OK;
+}
+
+int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+                  int32_t n_sku, const int32_t *slot_map, int64_t slot_map_stride, int32_t n_plans,
+                  const int32_t *plan_tour_off, const int32_t *tour_off, const int32_t *order_seq,
+                  const int32_t *moves, int32_t n_moves, int32_t max_orders, int32_t max_lines, int64_t *delta,
+                  int32_t *status) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    int32_t *smap_copy = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_sku > 0 ? n_sku : 1));
+    if (!smap_copy) return OR_ENOMEM;
+    for (int32_t m = 0; m < n_moves; ++m) {
+        const int32_t type = moves[4 * m], a = moves[4 * m + 1], b = moves[4 * m + 2], p = moves[4 * m + 3];
+        delta[2 * m] = delta[2 * m + 1] = 0;
+        status[m] = 3;
+        if (p < 0 || p >= n_plans) continue;
+        const int32_t *smap = slot_map + (int64_t)p * slot_map_stride;
+        plan_copy_t c;
+        memset(&c, 0, sizeof(c));
+        rc = plan_load(&c, p, plan_tour_off, tour_off, order_seq);
+        if (rc != OR_OK) { plan_free(&c); free(smap_copy); return rc; }
+        int64_t before_s, before_rr;
+        rc = plan_cost(g, &c, order_off, line_sku, smap, &before_s, &before_rr);
+        if (rc != OR_OK) { plan_free(&c); free(smap_copy); return rc; }
+        const int32_t *after_map = smap;
+        int32_t st = 0;
+        if (type == 0 || type == 1) {
+            int32_t ia = 0, ib = 0;
+            int32_t ta = (a >= 0 && a < n_orders) ? plan_find(&c, a, &ia) : -1;
+            if (ta < 0) st = 3;
+            else if (type == 0) {
+                int32_t tb = (b >= 0 && b < n_orders) ? plan_find(&c, b, &ib) : -1;
+                if (tb < 0) st = 3;
+                else if (ta == tb) st = 2;
+                else {
+                    c.orders[ta][ia] = b;
+                    c.orders[tb][ib] = a;
+                    if (max_lines > 0 && (tour_line_count(&c, ta, order_off) > max_lines ||
+                                          tour_line_count(&c, tb, order_off) > max_lines))
+                        st = 1;
+                }
+            } else {
+                if (b < 0 || b >= c.n_tours) st = 3;
+                else if (b == ta) st = 2;
+                else {
+                    /* remove a from ta, append to b */
+                    for (int32_t i = ia; i + 1 < c.len[ta]; ++i) c.orders[ta][i] = c.orders[ta][i + 1];
+                    --c.len[ta];
+                    if (c.len[b] == c.cap[b]) {
+                        int32_t *nb = (int32_t *)realloc(c.orders[b], sizeof(int32_t) * (size_t)(c.cap[b] + 1));
+                        if (!nb) { plan_free(&c); free(smap_copy); return OR_ENOMEM; }
+                        c.orders[b] = nb;
+                        ++c.cap[b];
+                    }
+                    c.orders[b][c.len[b]++] = a;
+                    if ((max_orders > 0 && c.len[b] > max_orders) ||
+                        (max_lines > 0 && tour_line_count(&c, b, order_off) > max_lines))
+                        st = 1;
+                }
+            }
+        } else if (type == 2) {
+            if (slot_map_stride == 0 || a < 0 || a >= n_sku || b < 0 || b >= n_sku) st = 3;
+            else if (a == b) st = 2;
+            else {
+                memcpy(smap_copy, smap, sizeof(int32_t) * (size_t)n_sku);
+                int32_t tmp = smap_copy[a];
+                smap_copy[a] = smap_copy[b];
+                smap_copy[b] = tmp;
+                after_map = smap_copy;
+            }
+        } else {
+            st = 3;
+        }
+        status[m] = st;
+        if (st == 0) {
+            int64_t after_s, after_rr;
+            rc = plan_cost(g, &c, order_off, line_sku, after_map, &after_s, &after_rr);
+            if (rc != OR_OK) { plan_free(&c); free(smap_copy); return rc; }
+            delta[2 * m] = after_s - before_s;
+            delta[2 * m + 1] = after_rr - before_rr;
+        }
+        plan_free(&c);
+    }
+    free(smap_copy);
+    return OR_OK;
+}

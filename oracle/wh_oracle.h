@@ -71,6 +71,27 @@ int or_eval_plans(const or_layout *g, int32_t n_orders, const int32_t *order_off
                   const int32_t *tour_off, const int32_t *order_seq, int32_t *tour_s,
                   int32_t *tour_rr, int64_t *plan_s, int64_t *plan_rr);
 
+/* Neighbourhood moves (Sec. 5: subroutine 4 evaluates a change in product
+ * position; the picking list decides which orders are picked together).
+ * moves[4*m .. 4*m+3] = {type, a, b, plan}:
+ *   type 0: swap orders a and b between their tours of `plan`,
+ *   type 1: relocate order a into tour b of `plan` (b local to the plan),
+ *   type 2: swap the locations of SKUs a and b in `plan`'s slotting
+ *           (per-plan slottings only, slot_map_stride > 0).
+ * Each move is applied to a copy of its plan, the whole plan is evaluated
+ * before and after, and delta[2m], delta[2m+1] = (after - before) for the
+ * S-shape and optimal rule.  status[m]: 0 applied, 1 infeasible (a changed
+ * tour would exceed max_orders orders or max_lines lines; 0 = no cap),
+ * 2 no-op (same tour or same SKU), 3 invalid (id out of range, order not in
+ * the plan, SKU swap under a shared slotting).  Deltas are 0 unless the
+ * status is 0. */
+int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off,
+                  const int32_t *line_sku, int32_t n_sku, const int32_t *slot_map,
+                  int64_t slot_map_stride, int32_t n_plans, const int32_t *plan_tour_off,
+                  const int32_t *tour_off, const int32_t *order_seq, const int32_t *moves,
+                  int32_t n_moves, int32_t max_orders, int32_t max_lines, int64_t *delta,
+                  int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif
