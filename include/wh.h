@@ -148,6 +148,29 @@ int wh_create_layout(const wh_layout_desc *desc, wh_layout **out);
 int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *plans,
                   uint32_t routing_mask, const wh_costs *out, void *stream);
 
+/* Neighbourhood moves for plan-level local search (Sec. 5: subroutine 4
+ * evaluates a change in product position; the picking list decides which
+ * orders are picked together).  moves[4*m .. 4*m+3] = {type, a, b, plan}:
+ *   type 0: swap orders a and b between their tours of `plan`;
+ *   type 1: relocate order a into tour b of `plan` (b counted from the
+ *           plan's first tour);
+ *   type 2: swap the locations of SKUs a and b in `plan`'s slotting (only
+ *           with per-plan slottings, slot_map_stride > 0).
+ * delta[2m], delta[2m+1] receive (after - before) of the plan's S-shape and
+ * optimal cost; only the tours the move changes are re-costed, against their
+ * current costs tour_s / tour_rr (the wh_eval_plans output for `plans`).
+ * status[m]: 0 evaluated, 1 infeasible (a changed tour would exceed
+ * max_orders_per_tour orders or max_lines_per_tour lines; 0 = no cap), 2 no-op
+ * (same tour, same SKU), 3 invalid (id out of range, order not in the plan,
+ * SKU swap under a shared slotting, or a malformed tour); deltas are 0 unless
+ * the status is 0.  Each plan must hold every order at most once.
+ * All arrays are device memory.  The call synchronises `stream` once (to size
+ * its task list) and may allocate scratch.  Returns WH_OK, WH_EINVAL, WH_ENOMEM
+ * or WH_ECUDA. */
+int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *tour_s,
+                  const int32_t *tour_rr, const int32_t *moves, int32_t n_moves, int32_t max_orders_per_tour,
+                  int32_t max_lines_per_tour, int64_t *delta, int32_t *status, void *stream);
+
 /* Sizes accepted by wh_eval_plans_noalloc. */
 #define WH_NOALLOC_MAX_LINES (1 << 20)
 #define WH_NOALLOC_MAX_TOURS (1 << 20)

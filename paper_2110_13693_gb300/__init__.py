@@ -64,6 +64,10 @@ SIGNATURES = {
     "wh_eval_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                      ctypes.c_uint32, ctypes.POINTER(wh_costs), ctypes.c_void_p]),
     "wh_get_last_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_eval_moves": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
     "wh_eval_plans_noalloc": (ctypes.c_int, [ctypes.POINTER(wh_layout_desc), ctypes.POINTER(wh_orders),
                                              ctypes.POINTER(wh_plans), ctypes.c_uint32,
                                              ctypes.POINTER(wh_costs), ctypes.c_void_p, ctypes.c_void_p]),
@@ -139,6 +143,15 @@ def wh_eval_plans_noalloc(desc: wh_layout_desc, orders: wh_orders, plans: wh_pla
     _check(load().wh_eval_plans_noalloc(ctypes.byref(desc), ctypes.byref(orders), ctypes.byref(plans),
                                         routing_mask, ctypes.byref(out), ctypes.c_void_p(status_ptr or None),
                                         _stream_ptr(stream)), "wh_eval_plans_noalloc")
+
+
+def wh_eval_moves(layout, orders: wh_orders, plans: wh_plans, tour_s, tour_rr, moves, n_moves: int,
+                  max_orders: int, max_lines: int, delta, status, stream=None) -> None:
+    """Pointers (ints) for tour_s, tour_rr, moves, delta and status."""
+    _check(load().wh_eval_moves(layout, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(tour_s),
+                                ctypes.c_void_p(tour_rr), ctypes.c_void_p(moves), n_moves, max_orders, max_lines,
+                                ctypes.c_void_p(delta), ctypes.c_void_p(status), _stream_ptr(stream)),
+           "wh_eval_moves")
 
 
 def wh_get_last_status(layout, stream=None) -> int:
@@ -294,6 +307,19 @@ class Layout:
 
     def status(self, stream=None) -> int:
         return wh_get_last_status(self.handle, stream)
+
+    def eval_moves(self, prob: DeviceProblem, costs: Costs, moves, max_orders: int = 0, max_lines: int = 0,
+                   stream=None):
+        """Deltas [n, 2] int64 and status [n] int32 (device tensors) of moves
+        ([n, 4] int32 device tensor) against the current costs `costs`."""
+        import torch
+        mv = moves.reshape(-1, 4).contiguous()
+        n = int(mv.shape[0])
+        delta = torch.empty((max(n, 1), 2), dtype=torch.int64, device=mv.device)
+        status = torch.empty(max(n, 1), dtype=torch.int32, device=mv.device)
+        wh_eval_moves(self.handle, prob.orders(), prob.plans(), _ptr(costs.tour_s), _ptr(costs.tour_rr),
+                      _ptr(mv), n, max_orders, max_lines, _ptr(delta), _ptr(status), stream)
+        return delta[:n], status[:n]
 
     def set_timing(self, enable: bool) -> None:
         wh_set_timing(self.handle, enable)

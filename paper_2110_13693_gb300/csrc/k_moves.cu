@@ -1,0 +1,542 @@
+// Move-delta kernels for sm_103a: the change of a plan's S-shape and optimal
+// costs under a neighbourhood move (Sec. 5: subroutine 4 evaluates a change of
+// product position; the picking list decides which orders share a tour).
+//
+// Only the tours a move changes are re-costed:
+//   order swap (o1, o2)     -> the two tours holding them, each with one order
+//                              exchanged;
+//   relocate (o, tour)      -> the source tour without o, the target with o;
+//   SKU-slot swap (s1, s2)  -> every tour holding an order with s1 or s2,
+//                              under the plan's slotting with the two
+//                              locations exchanged.
+// Pipeline: per-tour line counts and the plan's order -> tour map; the SKU ->
+// orders index of the order book; per move a check, a status and a task count;
+// an exclusive scan of the counts; the task list; one task per thread (tasks
+// over SHORT_MAX lines: one warp each) re-costing one changed tour and adding
+// (new - old) into the move's two int64 deltas.  A SKU-swap move lists one task
+// per (order with s1 or s2); of the tasks that land in the same tour only the
+// one of the smallest such order counts, so no de-duplication pass is needed.
+#include "tour_core.cuh"
+
+namespace wh {
+
+namespace {
+
+constexpr int MV_THREADS = 128;
+
+__device__ __forceinline__ int order_lines_checked(const EvalArgs& a, int o, int& lb, int& le) {
+    if ((unsigned)o >= (unsigned)a.n_orders) return -1;
+    lb = a.order_off[o];
+    le = a.order_off[o + 1];
+    if (lb < 0 || le < lb || le > a.n_lines) return -1;
+    return le - lb;
+}
+
+// plan of global tour t: largest p with plan_tour_off[p] <= t
+__device__ __forceinline__ int plan_of_tour(const EvalArgs& a, int t) {
+    int lo = 0, hi = a.n_plans - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.plan_tour_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_mv_tours(MoveArgs M) {
+    const EvalArgs& a = M.a;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n_tours; t += gridDim.x * blockDim.x) {
+        const int p = plan_of_tour(a, t);
+        const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];
+        int lines = 0;
+        if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
+            flag(a.status, WH_STATUS_BAD_OFFSET);
+            lines = -1;
+        } else {
+            for (int q = q0; q < q1; ++q) {
+                const int o = a.order_seq[q];
+                int lb, le;
+                const int c = order_lines_checked(a, o, lb, le);
+                if (c < 0) {
+                    flag(a.status, WH_STATUS_BAD_ORDER);
+                    lines = -1;
+                    break;
+                }
+                lines += c;
+                M.order_tour[(int64_t)p * a.n_orders + o] = t;
+            }
+        }
+        M.tour_lines[t] = lines;
+    }
+}
+
+__global__ void k_mv_sku_count(MoveArgs M) {
+    const EvalArgs& a = M.a;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < a.n_lines; l += gridDim.x * blockDim.x) {
+        const int s = a.line_sku[l];
+        if ((unsigned)s < (unsigned)a.n_sku) atomicAdd(&M.sku_cur[s], 1);
+    }
+}
+
+// one block: exclusive scan of the per-SKU counts into sku_off, cursors reset
+__global__ void k_mv_sku_scan(MoveArgs M) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int n = M.a.n_sku, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        const int v = i < n ? M.sku_cur[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int y = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += u;
+            }
+            warp_tot[lane] = y;
+        }
+        __syncthreads();
+        const int excl = carry + (w ? warp_tot[w - 1] : 0) + x - v;
+        if (i < n) {
+            M.sku_off[i] = excl;
+            M.sku_cur[i] = 0;
+        }
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (tid == 0) M.sku_off[n] = carry;
+}
+
+__global__ void k_mv_sku_fill(MoveArgs M) {
+    const EvalArgs& a = M.a;
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_orders; o += gridDim.x * blockDim.x) {
+        int lb, le;
+        if (order_lines_checked(a, o, lb, le) < 0) continue;
+        for (int l = lb; l < le; ++l) {
+            const int s = a.line_sku[l];
+            if ((unsigned)s >= (unsigned)a.n_sku) continue;
+            const int k = atomicAdd(&M.sku_cur[s], 1);
+            M.sku_orders[M.sku_off[s] + k] = o;
+        }
+    }
+}
+
+// status and task count of every move; deltas zeroed
+__global__ void k_mv_count(MoveArgs M) {
+    const EvalArgs& a = M.a;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M.n_moves; m += gridDim.x * blockDim.x) {
+        const int4 mv = M.moves[m];
+        M.delta[2 * m] = 0;
+        M.delta[2 * m + 1] = 0;
+        int st = 3, cnt = 0;
+        const int p = mv.w;
+        if (p >= 0 && p < a.n_plans) {
+            const int64_t row = (int64_t)p * a.n_orders;
+            if (mv.x == 0 || mv.x == 1) {
+                int lb, le;
+                const int la = order_lines_checked(a, mv.y, lb, le);
+                const int ta = la >= 0 ? M.order_tour[row + mv.y] : -1;
+                if (ta >= 0 && M.tour_lines[ta] >= 0) {
+                    if (mv.x == 0) {
+                        const int lbb = order_lines_checked(a, mv.z, lb, le);
+                        const int tb = lbb >= 0 ? M.order_tour[row + mv.z] : -1;
+                        if (tb >= 0 && M.tour_lines[tb] >= 0) {
+                            if (ta == tb) st = 2;
+                            else if (M.max_lines > 0 && (M.tour_lines[ta] - la + lbb > M.max_lines ||
+                                                         M.tour_lines[tb] - lbb + la > M.max_lines)) st = 1;
+                            else { st = 0; cnt = 2; }
+                        }
+                    } else {
+                        const int n_t = a.plan_tour_off[p + 1] - a.plan_tour_off[p];
+                        if (mv.z >= 0 && mv.z < n_t) {
+                            const int tb = a.plan_tour_off[p] + mv.z;
+                            if (tb == ta) st = 2;
+                            else if (M.tour_lines[tb] < 0) st = 3;
+                            else if ((M.max_orders > 0 && a.tour_off[tb + 1] - a.tour_off[tb] + 1 > M.max_orders) ||
+                                     (M.max_lines > 0 && M.tour_lines[tb] + la > M.max_lines)) st = 1;
+                            else { st = 0; cnt = 2; }
+                        }
+                    }
+                }
+            } else if (mv.x == 2) {
+                if (a.slot_stride > 0 && (unsigned)mv.y < (unsigned)a.n_sku && (unsigned)mv.z < (unsigned)a.n_sku) {
+                    if (mv.y == mv.z) st = 2;
+                    else {
+                        st = 0;
+                        cnt = (M.sku_off[mv.y + 1] - M.sku_off[mv.y]) + (M.sku_off[mv.z + 1] - M.sku_off[mv.z]);
+                    }
+                }
+            }
+        }
+        M.mstatus[m] = st;
+        M.task_off[m] = cnt;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        M.task_off[M.n_moves] = 0;
+        *M.long_count = 0;
+    }
+}
+
+// ---- exclusive scan of int64 counts in place (n+1 entries): block scans,
+// a scan of the block totals, then the carries added
+constexpr int SCAN_T = 1024;
+
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* warp_tot, long long& total) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long y = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += u;
+        }
+        warp_tot[lane] = y;
+    }
+    __syncthreads();
+    total = warp_tot[(blockDim.x >> 5) - 1];
+    const long long r = (w ? warp_tot[w - 1] : 0) + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_blocks(int64_t* v, int64_t n, int64_t* block_tot) {
+    __shared__ long long wt[32];
+    const int64_t i = (int64_t)blockIdx.x * SCAN_T + threadIdx.x;
+    const long long x = i < n ? v[i] : 0;
+    long long tot;
+    const long long e = block_excl_scan(x, wt, tot);
+    if (i < n) v[i] = e;
+    if (threadIdx.x == 0) block_tot[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int64_t* block_tot, int nb) {
+    __shared__ long long wt[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += SCAN_T) {
+        const int i = base + threadIdx.x;
+        const long long x = i < nb ? block_tot[i] : 0;
+        long long tot;
+        const long long e = block_excl_scan(x, wt, tot);
+        const long long c = carry;
+        if (i < nb) block_tot[i] = c + e;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int64_t* v, int64_t n, const int64_t* block_tot) {
+    const int64_t i = (int64_t)blockIdx.x * SCAN_T + threadIdx.x;
+    if (i < n) v[i] += block_tot[blockIdx.x];
+}
+
+// task = {move, tour, order, tag}: tag >= 0 or -1: order moves (tag = order
+// removed, order = order added, -1 = none); tag -2 / -3: SKU swap, `order` is
+// the order of s1's / s2's list the task came from
+__global__ void k_mv_fill(MoveArgs M) {
+    const EvalArgs& a = M.a;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M.n_moves; m += gridDim.x * blockDim.x) {
+        if (M.mstatus[m] != 0) continue;
+        const int4 mv = M.moves[m];
+        const int64_t row = (int64_t)mv.w * a.n_orders;
+        int4* out = M.tasks + M.task_off[m];
+        if (mv.x == 0) {
+            const int ta = M.order_tour[row + mv.y], tb = M.order_tour[row + mv.z];
+            out[0] = make_int4(m, ta, mv.z, mv.y);
+            out[1] = make_int4(m, tb, mv.y, mv.z);
+        } else if (mv.x == 1) {
+            const int ta = M.order_tour[row + mv.y], tb = a.plan_tour_off[mv.w] + mv.z;
+            out[0] = make_int4(m, ta, -1, mv.y);
+            out[1] = make_int4(m, tb, mv.y, -1);
+        } else {
+            int k = 0;
+            for (int side = 0; side < 2; ++side) {
+                const int s = side ? mv.z : mv.y;
+                for (int i = M.sku_off[s]; i < M.sku_off[s + 1]; ++i) {
+                    const int o = M.sku_orders[i];
+                    out[k++] = make_int4(m, M.order_tour[row + o], o, side ? -3 : -2);
+                }
+            }
+        }
+    }
+}
+
+// Location of SKU s under the task's slotting (swapped pair for SKU swaps).
+__device__ __forceinline__ int task_loc(const int32_t* map, int s, bool swap, int s1, int s2) {
+    if (swap) s = s == s1 ? s2 : (s == s2 ? s1 : s);
+    return map[s];
+}
+
+// Walk the changed tour of task `tk`: calls emit(key) for every line, in
+// order; returns false on an invalid id.  For SKU-swap tasks also reports
+// whether the task is the counted one of its tour.
+template <typename Emit>
+__device__ __forceinline__ bool walk_task(const MoveArgs& M, const int4 tk, const int4 mv, bool& primary,
+                                          Emit emit) {
+    const EvalArgs& a = M.a;
+    const bool swap = mv.x == 2;
+    const int32_t* map = a.slot_map + (int64_t)mv.w * a.slot_stride;
+    const int q0 = a.tour_off[tk.y], q1 = a.tour_off[tk.y + 1];
+    const int add = (!swap && tk.z >= 0) ? tk.z : -1;
+    const int rem = (!swap && tk.w >= 0) ? tk.w : -1;
+    int hit_min = 0x7fffffff;
+    bool own_has_s1 = false;
+    bool ok = q0 >= 0 && q1 >= q0 && (int64_t)q1 <= a.n_seq;
+    for (int q = q0; ok && q <= q1; ++q) {
+        int o;
+        if (q < q1) {
+            o = a.order_seq[q];
+            if (o == rem) continue;
+        } else {
+            if (add < 0) break;
+            o = add;
+        }
+        int lb, le;
+        if (order_lines_checked(a, o, lb, le) < 0) { ok = false; break; }
+        for (int l = lb; l < le; ++l) {
+            const int s = a.line_sku[l];
+            if ((unsigned)s >= (unsigned)a.n_sku) { ok = false; break; }
+            if (swap && (s == mv.y || s == mv.z)) {
+                hit_min = min(hit_min, o);
+                if (o == tk.z && s == mv.y) own_has_s1 = true;
+            }
+            const int loc = task_loc(map, s, swap, mv.y, mv.z);
+            if ((unsigned)loc >= (unsigned)a.g.n_loc) { ok = false; break; }
+            emit(loc_key(a.g, loc));
+        }
+    }
+    primary = !swap || (hit_min == tk.z && (tk.w == -2 || !own_has_s1));
+    return ok;
+}
+
+template <bool KEY16>
+__global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    uint32_t* col16 = reinterpret_cast<uint32_t*>(smem) + tid;
+    uint2* col32 = reinterpret_cast<uint2*>(smem) + tid;
+    const EvalArgs& a = M.a;
+    const int64_t n_tasks = M.n_tasks;
+    const int64_t warps = (int64_t)gridDim.x * (T >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (T >> 5) + (tid >> 5)) * 32; base < n_tasks; base += warps * 32) {
+        const int64_t i = base + lane;
+        const bool active = i < n_tasks;
+        int4 tk = make_int4(-1, -1, -1, -1), mv = make_int4(0, 0, 0, 0);
+        int n = 0;
+        bool ok = false, primary = false;
+        if (active) {
+            tk = M.tasks[i];
+            mv = M.moves[tk.x];
+            if (tk.y >= 0 && tk.y < a.n_tours) {
+                ok = walk_task(M, tk, mv, primary, [&](uint32_t k) {
+                    if (n < SHORT_MAX) {
+                        if constexpr (KEY16) reinterpret_cast<uint16_t*>(col16 + (n >> 1) * T)[n & 1] = (uint16_t)key16_of(k);
+                        else reinterpret_cast<uint32_t*>(col32 + (n >> 1) * T)[n & 1] = k;
+                    }
+                    ++n;
+                });
+            } else {
+                primary = false;   // an order of the SKU lists outside the plan
+                ok = true;
+            }
+            if (!ok) {
+                flag(a.status, WH_STATUS_BAD_ORDER);
+                M.mstatus[tk.x] = 3;
+            }
+        }
+        bool run = active && ok && primary;
+        if (run && n > SHORT_MAX) {
+            const int slot = atomicAdd(M.long_count, 1);
+            if (slot < M.long_cap) M.long_list[slot] = (int32_t)i;
+            else { flag(a.status, WH_STATUS_LONG_OVERFLOW); M.mstatus[tk.x] = 3; }
+            run = false;
+        }
+        const int nr = run ? n : 0;
+        const int nmax = __reduce_max_sync(0xffffffffu, nr);
+        int cs = 0, cr = 0;
+        if constexpr (KEY16) {
+            if (nmax <= 16) tour16<8>(a, col16, T, nr, true, cs, cr);
+            else if (nmax <= 32) tour16<16>(a, col16, T, nr, true, cs, cr);
+            else tour16<32>(a, col16, T, nr, true, cs, cr);
+        } else {
+            if (nmax <= 16) tour32<16>(a, col32, T, nr, true, cs, cr);
+            else if (nmax <= 32) tour32<32>(a, col32, T, nr, true, cs, cr);
+            else tour32<64>(a, col32, T, nr, true, cs, cr);
+        }
+        long long ds = 0, dr = 0;
+        if (run) {
+            ds = (long long)cs - M.tour_s_old[tk.y];
+            dr = (long long)cr - M.tour_rr_old[tk.y];
+        }
+        const int key = active ? tk.x : -1;
+        const long long ss = segmented_sum(ds, key, lane);
+        const long long sr = segmented_sum(dr, key, lane);
+        const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+        if (active && (lane == 0 || prev_key != key) && (ss || sr)) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x]), (unsigned long long)ss);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x + 1]), (unsigned long long)sr);
+        }
+    }
+}
+
+// one warp per task of more than SHORT_MAX lines
+__global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
+    __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int count = min(*M.long_count, M.long_cap);
+    uint32_t* kb = buf[warp];
+    const EvalArgs& a = M.a;
+    for (int w = blockIdx.x * LONG_WARPS + warp; w < count; w += gridDim.x * LONG_WARPS) {
+        const int64_t i = M.long_list[w];
+        const int4 tk = M.tasks[i];
+        const int4 mv = M.moves[tk.x];
+        int n = 0;
+        bool primary = false, ok = true;
+        if (lane == 0) {
+            ok = walk_task(M, tk, mv, primary, [&](uint32_t k) {
+                if (n < LONG_MAXL) kb[n] = k;
+                ++n;
+            });
+        }
+        n = __shfl_sync(0xffffffffu, n, 0);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+        if (!ok || n > LONG_MAXL) {
+            if (lane == 0) {
+                flag(a.status, n > LONG_MAXL ? WH_STATUS_TOUR_TOO_LONG : WH_STATUS_BAD_ORDER);
+                M.mstatus[tk.x] = 3;
+            }
+            __syncwarp();
+            continue;
+        }
+        int p2 = 64;
+        while (p2 < n) p2 <<= 1;
+        for (int j = n + lane; j < p2; j += 32) kb[j] = KEY_NONE;
+        __syncwarp();
+        for (int k = 2; k <= p2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int x = lane; x < p2; x += 32) {
+                    const int l = x ^ j;
+                    if (l > x) {
+                        const uint32_t u = kb[x], v = kb[l];
+                        const bool up = (x & k) == 0;
+                        if ((u > v) == up) { kb[x] = v; kb[l] = u; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            DP5 v;
+            dp_init(v);
+            int m = 0, pa = 0, lo = 0, prev = 0, gi = 0, last_a = 0, last_hi = 0;
+            for (int x = 0; x < n; ++x) {
+                const uint32_t key = kb[x];
+                const int ai = (int)(key >> 16), k = (int)(key & 0xFFFFu);
+                const bool first = (x == 0) || ((int)(kb[x - 1] >> 16) != ai);
+                const bool last = (x == n - 1) || ((int)(kb[x + 1] >> 16) != ai);
+                gi = first ? 0 : max(gi, k - prev);
+                lo = first ? k : lo;
+                prev = k;
+                if (last) {
+                    dp_aisle(v, a.g, ai - pa, lo, k, gi);
+                    pa = ai;
+                    ++m;
+                    last_a = ai;
+                    last_hi = k;
+                }
+            }
+            const long long ds = (long long)sshape_cost(a.g, m, last_a, last_hi) - M.tour_s_old[tk.y];
+            const long long dr = (long long)dp_final(v) - M.tour_rr_old[tk.y];
+            atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x]), (unsigned long long)ds);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x + 1]), (unsigned long long)dr);
+        }
+        __syncwarp();
+    }
+}
+
+// moves that ended with a non-zero status report zero deltas
+__global__ void k_mv_finish(MoveArgs M) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M.n_moves; m += gridDim.x * blockDim.x) {
+        if (M.mstatus[m] != 0) {
+            M.delta[2 * m] = 0;
+            M.delta[2 * m + 1] = 0;
+        }
+    }
+}
+
+int grid_of(int64_t n, int threads, int cap = 8192) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s) {
+    const EvalArgs& a = M.a;
+    if (cudaMemsetAsync(M.order_tour, 0xFF, sizeof(int32_t) * (size_t)a.n_plans * (size_t)a.n_orders, s) != cudaSuccess)
+        return cudaGetLastError();
+    if (cudaMemsetAsync(M.sku_cur, 0, sizeof(int32_t) * ((size_t)a.n_sku + 1), s) != cudaSuccess)
+        return cudaGetLastError();
+    if (a.n_tours > 0) k_mv_tours<<<grid_of(a.n_tours, 256), 256, 0, s>>>(M);
+    if (a.n_lines > 0) k_mv_sku_count<<<grid_of(a.n_lines, 256), 256, 0, s>>>(M);
+    k_mv_sku_scan<<<1, 1024, 0, s>>>(M);
+    if (a.n_orders > 0) k_mv_sku_fill<<<grid_of(a.n_orders, 256), 256, 0, s>>>(M);
+    k_mv_count<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
+    // exclusive scan of n_moves + 1 task counts
+    const int64_t n = (int64_t)M.n_moves + 1;
+    const int nb = (int)((n + SCAN_T - 1) / SCAN_T);
+    k_scan_blocks<<<nb, SCAN_T, 0, s>>>(M.task_off, n, M.scan_aux);
+    k_scan_top<<<1, SCAN_T, 0, s>>>(M.scan_aux, nb);
+    k_scan_add<<<nb, SCAN_T, 0, s>>>(M.task_off, n, M.scan_aux);
+    return cudaGetLastError();
+}
+
+size_t moves_eval_smem_bytes(bool k16, int max_rec) {
+    const size_t slots = max_rec > SHORT_MAX / 2 ? (size_t)max_rec : (size_t)(SHORT_MAX / 2);
+    return (k16 ? sizeof(uint32_t) : sizeof(uint2)) * slots * MV_THREADS;
+}
+
+cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s) {
+    if (M.n_moves > 0) k_mv_fill<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
+    if (M.n_tasks > 0) {
+        const size_t smem = moves_eval_smem_bytes(k16, M.a.max_rec);
+        auto kern = k16 ? k_mv_eval<true> : k_mv_eval<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MV_THREADS, smem);
+        if (e != cudaSuccess) return e;
+        int64_t want = (M.n_tasks + MV_THREADS - 1) / MV_THREADS;
+        int grid = per_sm * num_sms;
+        if (grid > want) grid = (int)want;
+        if (grid < 1) grid = 1;
+        kern<<<grid, MV_THREADS, smem, s>>>(M);
+        k_mv_long<<<num_sms * 2, LONG_WARPS * 32, 0, s>>>(M);
+    }
+    if (M.n_moves > 0) k_mv_finish<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
+    return cudaGetLastError();
+}
+
+}  // namespace wh

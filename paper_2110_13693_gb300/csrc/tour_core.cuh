@@ -1,0 +1,344 @@
+// Device building blocks of a tour's cost, shared by the plan-evaluation and
+// move-evaluation kernels: pick keys, the sorting networks, the per-aisle
+// record scan, the S-shape closed form and the Ratliff-Rosenthal DP (Sec. 5,
+// Eq. (2)).  Included by each kernel translation unit; everything lives in an
+// unnamed namespace, so each unit gets its own copy.
+#pragma once
+#include "wh_internal.h"
+
+namespace wh {
+namespace {
+
+constexpr int INF = 1 << 29;
+constexpr uint32_t KEY_BAD = 0xFFFFFFFEu;   // a line whose SKU or slot is invalid
+constexpr uint32_t KEY16_NONE = 0xFFFFu;
+constexpr uint32_t KEY16_BAD = 0xFFFEu;
+constexpr int LONG_WARPS = 4;
+constexpr int LONG_MAXL = WH_MAX_TOUR_LINES;
+
+__device__ __forceinline__ void flag(uint32_t* status, uint32_t bit) { atomicOr(status, bit); }
+
+__device__ __forceinline__ uint32_t loc_key(const Geo& g, int loc) {
+    const int two_l = 2 * g.L;
+    const int a = loc / two_l;
+    const int r = loc - a * two_l;          // side*L + k
+    const int k = r >= g.L ? r - g.L : r;
+    return ((uint32_t)a << 16) | (uint32_t)k;
+}
+
+// 32-bit key -> 16-bit key (aisle<<8 | slot); valid when A <= 255, L <= 256
+__device__ __forceinline__ uint32_t key16_of(uint32_t k32) {
+    if (k32 == KEY_BAD) return KEY16_BAD;
+    return ((k32 >> 8) & 0xFF00u) | (k32 & 0xFFu);
+}
+
+// ---------------------------------------------------------------- DP state
+// Five classes of a partial tour subgraph after an aisle, named by the degree
+// of the aisle's front end a_j and back end b_j (0: not in the subgraph, E:
+// even, U: odd) and the number of components: UU = (U,U,1C), E0 = (E,0,1C),
+// OE = (0,E,1C), EE = (E,E,1C), E2 = (E,E,2C).
+struct DP5 {
+    int uu, e0, oe, ee, e2;
+};
+
+__device__ __forceinline__ void dp_init(DP5& v) {
+    v.uu = INF; v.e0 = 0; v.oe = INF; v.ee = INF; v.e2 = INF;
+}
+
+// One aisle holding picks, reached d >= 0 aisles to the right of the previous
+// one.  lo / hi: slot index of its shallowest / deepest pick; gi: largest gap
+// between consecutive picks in slot units.
+//
+// No value is clamped at INF: every state value is min over partial tours of
+// (start value 0 or INF) + that partial tour's length, and a partial tour is
+// at most 4*x_{A-1} (horizontal) + 2*A*Y (vertical) < 2^28 by the layout
+// bound 2*x_{A-1} + A*Y < 2^27, so values stay below INF + 2^28 + 2^28 = 2^30.
+// __viaddmin_s32(a, b, c) = min(a + b, c) and __vimin3_s32 are the fused
+// min-plus forms of those steps.
+__device__ __forceinline__ void dp_aisle(DP5& v, const Geo& g, int d, int lo, int hi, int gi) {
+    // cross the d aisle gaps: (1,1) for UU; (2,0) / (0,2) for E0 / OE, which
+    // EE may also switch to; (2,2) for EE and E2
+    const int h2 = 2 * g.P * d, h4 = h2 + h2;
+    const int huu = v.uu + h2;
+    const int he0 = min(v.e0, v.ee) + h2;
+    const int hoe = min(v.oe, v.ee) + h2;
+    const int hee = v.ee + h4;
+    const int he2 = v.e2 + h4;
+    // vertical options of this aisle: traverse Y, double traverse 2Y, leave
+    // out the largest gap 2(Y-g), from the back 2(Y-y_lo), from the front 2*y_hi
+    const int ylo = g.h + lo * g.S, yhi = g.h + hi * g.S;
+    const int gap = __vimax3_s32(ylo, gi * g.S, g.Y - yhi);
+    const int cG = 2 * (g.Y - gap), cB = 2 * (g.Y - ylo), cF = 2 * yhi;
+    const int cT = g.Y, cD = 2 * g.Y;
+    const int m3 = __vimin3_s32(he0, hoe, he2);
+    v.uu = __viaddmin_s32(huu, cG, min(m3, hee) + cT);
+    v.ee = __viaddmin_s32(huu, cT, __viaddmin_s32(m3, cD, hee + cG));
+    v.e0 = he0 + cF;
+    v.oe = hoe + cB;
+    v.e2 = m3 + cG;
+}
+
+__device__ __forceinline__ int dp_final(const DP5& v) { return min(min(v.ee, v.e0), v.oe); }
+
+// S-shape closed form from the number of pick aisles m, the rightmost pick
+// aisle and its deepest slot.
+__device__ __forceinline__ int sshape_cost(const Geo& g, int m, int last_a, int last_hi) {
+    if (m == 0) return 0;
+    const int d_r = g.h + last_hi * g.S;
+    return 2 * last_a * g.P + ((m & 1) ? (m - 1) * g.Y + 2 * d_r : m * g.Y);
+}
+
+// ------------------------------------------------------ 32-bit key network
+template <int N>
+__device__ __forceinline__ void bitonic_sort(uint32_t (&x)[N]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t a = x[i], b = x[l];
+                    const uint32_t lo = min(a, b), hi = max(a, b);
+                    if ((i & k) == 0) { x[i] = lo; x[l] = hi; }
+                    else { x[i] = hi; x[l] = lo; }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------ 16-bit key network
+// 2R positions in R registers: position p lives in register p % R, in the low
+// half when p < R and the high half otherwise.  All-ascending bitonic sorter:
+// each merge of block size k starts by comparing p with p ^ (k-1) (the
+// mirrored partner), then half-cleans with p ^ j for j = k/4 .. 1.  For
+// k <= R both halves run the same register pairs, so one 16x2 min/max pair
+// serves two comparators; the final mirror step pairs halves across
+// registers and needs a half swap.
+template <int R>
+__device__ __forceinline__ void sort16x2(uint32_t (&x)[R]) {
+    constexpr int N = 2 * R;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+        if (k == N) {
+#pragma unroll
+            for (int r = 0; r < R / 2; ++r) {
+                const uint32_t A = x[r], B = x[R - 1 - r];
+                const uint32_t Bs = __byte_perm(B, 0, 0x1032);
+                const uint32_t mn = __vminu2(A, Bs), mx = __vmaxu2(A, Bs);
+                x[r] = __byte_perm(mn, mx, 0x7610);
+                x[R - 1 - r] = __byte_perm(mn, mx, 0x5432);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = r ^ (k - 1);
+                if (l > r) {
+                    const uint32_t a = x[r], b = x[l];
+                    x[r] = __vminu2(a, b);
+                    x[l] = __vmaxu2(a, b);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = r ^ j;
+                if (l > r) {
+                    const uint32_t a = x[r], b = x[l];
+                    x[r] = __vminu2(a, b);
+                    x[l] = __vmaxu2(a, b);
+                }
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------- record scans
+// Sorted keys -> per-aisle records (rec[j*stride], at most cap of them) and
+// the S-shape inputs (pick-aisle count, rightmost aisle, its deepest slot).
+template <int N>
+__device__ __forceinline__ void scan32(const uint32_t (&x)[N], uint2* rec, int stride, int cap, bool write,
+                                       int& m, int& last_a, int& last_hi) {
+    int lo = 0, prev = 0, gi = 0;
+    m = 0; last_a = 0; last_hi = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const uint32_t key = x[i];
+        const uint32_t a = key >> 16;
+        const int k = (int)(key & 0xFFFFu);
+        const bool first = (i == 0) || ((x[i - 1] >> 16) != a);
+        const bool last = (i == N - 1) || ((x[i + 1] >> 16) != a);
+        gi = first ? 0 : max(gi, k - prev);
+        lo = first ? k : lo;
+        prev = k;
+        if (key != KEY_NONE && last) {
+            if (write && m < cap) rec[m * stride] = make_uint2((a << 16) | (uint32_t)lo, ((uint32_t)k << 16) | (uint32_t)gi);
+            ++m;
+            last_a = (int)a;
+            last_hi = k;
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t key16_at(const uint32_t (&x)[R], int p) {
+    return p < R ? (x[p] & 0xFFFFu) : (x[p - R] >> 16);
+}
+
+template <int R>
+__device__ __forceinline__ void scan16(const uint32_t (&x)[R], uint32_t* rec, int stride, int cap, bool write,
+                                       int& m, int& last_a, int& last_hi) {
+    constexpr int N = 2 * R;
+    int lo = 0, prev = 0, gi = 0;
+    m = 0; last_a = 0; last_hi = 0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        const uint32_t key = key16_at<R>(x, p);
+        const uint32_t a = key >> 8;
+        const int k = (int)(key & 0xFFu);
+        const bool first = (p == 0) || ((key16_at<R>(x, p - 1) >> 8) != a);
+        const bool last = (p == N - 1) || ((key16_at<R>(x, p + 1) >> 8) != a);
+        gi = first ? 0 : max(gi, k - prev);
+        lo = first ? k : lo;
+        prev = k;
+        if (key != KEY16_NONE && last) {
+            if (write && m < cap) rec[m * stride] = (a << 24) | ((uint32_t)lo << 16) | ((uint32_t)k << 8) | (uint32_t)gi;
+            ++m;
+            last_a = (int)a;
+            last_hi = k;
+        }
+    }
+}
+
+__device__ __forceinline__ int rr_records32(const Geo& g, const uint2* rec, int stride, int m) {
+    DP5 v;
+    dp_init(v);
+    int pa = 0;
+    for (int j = 0; j < m; ++j) {
+        const uint2 r = rec[j * stride];
+        const int a = (int)(r.x >> 16);
+        dp_aisle(v, g, a - pa, (int)(r.x & 0xFFFFu), (int)(r.y >> 16), (int)(r.y & 0xFFFFu));
+        pa = a;
+    }
+    return dp_final(v);
+}
+
+__device__ __forceinline__ int rr_records16(const Geo& g, const uint32_t* rec, int stride, int m) {
+    DP5 v;
+    dp_init(v);
+    int pa = 0;
+    for (int j = 0; j < m; ++j) {
+        const uint32_t r = rec[j * stride];
+        const int a = (int)(r >> 24);
+        dp_aisle(v, g, a - pa, (int)((r >> 16) & 0xFFu), (int)((r >> 8) & 0xFFu), (int)(r & 0xFFu));
+        pa = a;
+    }
+    return dp_final(v);
+}
+
+// Key source: with a shared slotting, keys come from the per-line table
+// (16-bit or 32-bit entries); with per-plan slottings, from the plan's slot
+// map via the line's SKU.
+struct KeySrc {
+    const int32_t* off;     // order offsets (global order book)
+    const uint32_t* desc;   // per-order (first line << 8 | line count), shared memory
+    const void* keys;       // per-line keys (shared slotting)
+    const int32_t* skus;    // per-line SKUs (per-plan slotting)
+    const int32_t* map;     // this plan's slot map (per-plan slotting)
+};
+
+// STAGED: the shared-slotting key table is the shared-memory copy (16-bit
+// entries when KEY16); otherwise it is the 32-bit table in global memory.
+template <bool KEY16, bool SHARED_MAP, bool STAGED>
+__device__ __forceinline__ uint32_t key_of(const EvalArgs& a, const KeySrc& s, int l) {
+    if constexpr (SHARED_MAP) {
+        if constexpr (KEY16 && STAGED) return static_cast<const uint16_t*>(s.keys)[l];
+        else if constexpr (KEY16) return key16_of(static_cast<const uint32_t*>(s.keys)[l]);
+        else return static_cast<const uint32_t*>(s.keys)[l];
+    } else {
+        const int sku = s.skus[l];
+        uint32_t k32 = KEY_BAD;
+        if ((unsigned)sku >= (unsigned)a.n_sku) {
+            flag(a.status, WH_STATUS_BAD_SKU);
+        } else {
+            const int loc = s.map[sku];
+            if ((unsigned)loc >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
+            else k32 = loc_key(a.g, loc);
+        }
+        if constexpr (KEY16) return key16_of(k32);
+        else return k32;
+    }
+}
+
+// ------------------------------------------------------------ tour bodies
+// Each thread owns a column of slots in a shared-memory buffer: slot j of
+// thread tid sits at [j*T + tid], one slot = two keys = one per-aisle record
+// (4 bytes with 16-bit keys, 8 bytes with 32-bit keys), so columns of
+// different threads never overlap.  A tour's keys are first staged in the
+// column (key p in slot p/2, half p%2), loaded into registers with static
+// indices for the sort, and the column is then reused for the records.  The
+// gather itself is a plain loop over the tour's orders and their lines.
+template <int N>
+__device__ __forceinline__ void load32(const uint2* col, int T, int n, uint32_t (&x)[N]) {
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        const uint2 w = col[(p >> 1) * T];
+        x[p] = p < n ? ((p & 1) ? w.y : w.x) : KEY_NONE;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void load16(const uint32_t* col, int T, int n, uint32_t (&x)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t wl = col[(r >> 1) * T], wh = col[((r + R) >> 1) * T];
+        x[r] = __byte_perm(wl, wh, (r & 1) ? 0x7632 : 0x5410) | (r < n ? 0u : 0xFFFFu) |
+               (r + R < n ? 0u : 0xFFFF0000u);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int n, bool need_rr, int& cs,
+                                       int& cr) {
+    uint32_t x[N];
+    load32<N>(col, T, n, x);
+    bitonic_sort<N>(x);
+    int m, last_a, last_hi;
+    scan32<N>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
+    cs = sshape_cost(a.g, m, last_a, last_hi);
+    cr = need_rr ? rr_records32(a.g, col, T, min(m, a.max_rec)) : 0;
+}
+
+template <int R>
+__device__ __forceinline__ void tour16(const EvalArgs& a, uint32_t* col, int T, int n, bool need_rr, int& cs,
+                                       int& cr) {
+    uint32_t x[R];
+    load16<R>(col, T, n, x);
+    sort16x2<R>(x);
+    int m, last_a, last_hi;
+    scan16<R>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
+    cs = sshape_cost(a.g, m, last_a, last_hi);
+    cr = need_rr ? rr_records16(a.g, col, T, min(m, a.max_rec)) : 0;
+}
+
+// Segmented sum over the lanes of a warp whose `key` (plan id, non-decreasing
+// with the lane) is equal; the first lane of each segment ends up with the
+// segment's total.
+__device__ __forceinline__ long long segmented_sum(long long v, int key, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long ov = __shfl_down_sync(0xffffffffu, v, o);
+        const int ok = __shfl_down_sync(0xffffffffu, key, o);
+        if (lane + o < 32 && ok == key) v += ov;
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ kernels
+
+}  // namespace
+}  // namespace wh

@@ -21,6 +21,10 @@ struct wh_layout {
     uint32_t* meta = nullptr;     // device: [0] status word, [1] long-tour count
     void* scratch = nullptr;      // device: line keys + long-tour list
     size_t scratch_bytes = 0;
+    void* mv_scratch = nullptr;   // device: move-evaluation index structures
+    size_t mv_scratch_bytes = 0;
+    void* mv_tasks = nullptr;     // device: move tasks + long-task list
+    size_t mv_tasks_bytes = 0;
     // kernel timing (wh_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> events;       // pool, reused across sessions
@@ -186,22 +190,24 @@ int bind_device(wh_layout* h) {
     return WH_OK;
 }
 
-int reserve_scratch(wh_layout* h, size_t bytes) {
-    if (bytes <= h->scratch_bytes) return WH_OK;
-    if (h->scratch) {
-        cudaFree(h->scratch);  // synchronises the device before releasing
-        h->scratch = nullptr;
-        h->scratch_bytes = 0;
+int grow(void** buf, size_t* have, size_t bytes) {
+    if (bytes <= *have) return WH_OK;
+    if (*buf) {
+        cudaFree(*buf);  // synchronises the device before releasing
+        *buf = nullptr;
+        *have = 0;
     }
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return WH_ENOMEM;
     }
-    h->scratch = p;
-    h->scratch_bytes = bytes;
+    *buf = p;
+    *have = bytes;
     return WH_OK;
 }
+
+int reserve_scratch(wh_layout* h, size_t bytes) { return grow(&h->scratch, &h->scratch_bytes, bytes); }
 
 wh::Tuning default_tuning(const wh::EvalArgs& a) {
     wh::Tuning t;
@@ -280,6 +286,76 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     return WH_OK;
 }
 
+extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* tour_s,
+                             const int32_t* tour_rr, const int32_t* moves, int32_t n_moves, int32_t max_orders,
+                             int32_t max_lines, int64_t* delta, int32_t* status, void* stream) {
+    if (!h || !orders || !plans || n_moves < 0 || max_orders < 0 || max_lines < 0) return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
+    if (n_moves == 0) return WH_OK;
+    if (!moves || !delta || !status || !tour_s || !tour_rr || p.n_plans < 1) return WH_EINVAL;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    wh::MoveArgs M;
+    std::memset(&M, 0, sizeof(M));
+    wh_costs none;
+    std::memset(&none, 0, sizeof(none));
+    fill_args(M.a, h->g, o, p, none, WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL);
+    M.a.status = h->meta;
+    M.tour_s_old = tour_s;
+    M.tour_rr_old = tour_rr;
+    M.moves = reinterpret_cast<const int4*>(moves);
+    M.n_moves = n_moves;
+    M.max_orders = max_orders;
+    M.max_lines = max_lines;
+    M.delta = delta;
+    M.mstatus = status;
+    M.long_count = reinterpret_cast<int32_t*>(h->meta + 2);
+
+    const size_t n_ot = (size_t)p.n_plans * (size_t)o.n_orders;
+    const size_t nb = ((size_t)n_moves + 1 + 1023) / 1024;
+    size_t off[8], total = 0;
+    const size_t sizes[8] = {sizeof(int32_t) * n_ot, sizeof(int32_t) * ((size_t)p.n_tours + 1),
+                             sizeof(int32_t) * ((size_t)o.n_sku + 1), sizeof(int32_t) * ((size_t)o.n_sku + 1),
+                             sizeof(int32_t) * ((size_t)o.n_lines + 1), sizeof(int64_t) * ((size_t)n_moves + 1),
+                             sizeof(int64_t) * (nb + 1), 0};
+    for (int i = 0; i < 8; ++i) {
+        off[i] = total;
+        total += align_up(sizes[i]);
+    }
+    rc = grow(&h->mv_scratch, &h->mv_scratch_bytes, total);
+    if (rc != WH_OK) return rc;
+    char* base = static_cast<char*>(h->mv_scratch);
+    M.order_tour = reinterpret_cast<int32_t*>(base + off[0]);
+    M.tour_lines = reinterpret_cast<int32_t*>(base + off[1]);
+    M.sku_off = reinterpret_cast<int32_t*>(base + off[2]);
+    M.sku_cur = reinterpret_cast<int32_t*>(base + off[3]);
+    M.sku_orders = reinterpret_cast<int32_t*>(base + off[4]);
+    M.task_off = reinterpret_cast<int64_t*>(base + off[5]);
+    M.scan_aux = reinterpret_cast<int64_t*>(base + off[6]);
+
+    if (wh::launch_moves_prepare(M, s) != cudaSuccess) return WH_ECUDA;
+    int64_t n_tasks = 0;
+    if (cudaMemcpyAsync(&n_tasks, M.task_off + n_moves, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return WH_ECUDA;
+    if (n_tasks < 0 || n_tasks > ((int64_t)1 << 40)) return WH_ECUDA;
+    M.n_tasks = n_tasks;
+    M.long_cap = (int32_t)std::min<int64_t>(n_tasks + 1, 0x7fffffff);
+    const size_t task_bytes = align_up(sizeof(int4) * (size_t)(n_tasks + 1));
+    rc = grow(&h->mv_tasks, &h->mv_tasks_bytes, task_bytes + align_up(sizeof(int32_t) * (size_t)M.long_cap));
+    if (rc != WH_OK) return rc;
+    M.tasks = static_cast<int4*>(h->mv_tasks);
+    M.long_list = reinterpret_cast<int32_t*>(static_cast<char*>(h->mv_tasks) + task_bytes);
+    const bool k16 = wh::key16_ok(h->g);
+    if (wh::launch_moves_eval(M, k16, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    return WH_OK;
+}
+
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {
     if (!h || !status) return WH_EINVAL;
     if (h->device < 0) {
@@ -332,6 +408,8 @@ extern "C" void wh_destroy(wh_layout* h) {
     if (h->device >= 0) {
         DeviceGuard guard(h->device);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+        if (h->mv_scratch) cudaFree(h->mv_scratch);
+        if (h->mv_tasks) cudaFree(h->mv_tasks);
         if (h->scratch) cudaFree(h->scratch);
         if (h->meta) cudaFree(h->meta);
     }

@@ -73,6 +73,34 @@ struct LongArgs {
     uint32_t mask;
 };
 
+// Move evaluation (k_moves.cu)
+struct MoveArgs {
+    EvalArgs a;                 // the plans the moves apply to
+    const int32_t* tour_s_old;  // current per-tour costs of those plans
+    const int32_t* tour_rr_old;
+    const int4* moves;          // {type, a, b, plan}
+    int32_t n_moves;
+    int32_t max_orders, max_lines;
+    int64_t* delta;             // [n_moves][2]
+    int32_t* mstatus;           // [n_moves]
+    // scratch
+    int32_t* order_tour;        // [n_plans][n_orders]: global tour holding the order, -1 if none
+    int32_t* tour_lines;        // [n_tours]: lines of the tour, -1 if malformed
+    int32_t* sku_off;           // [n_sku+1]: SKU -> orders index
+    int32_t* sku_cur;           // [n_sku+1]: counts, then fill cursors
+    int32_t* sku_orders;        // [n_lines]
+    int64_t* task_off;          // [n_moves+1]: exclusive scan of task counts
+    int64_t* scan_aux;          // block totals of that scan
+    int4* tasks;                // [n_tasks]
+    int64_t n_tasks;
+    int32_t* long_list;         // tasks over SHORT_MAX lines
+    int32_t* long_count;
+    int32_t long_cap;
+};
+
+cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s);
+cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s);
+
 struct Tuning {
     int threads;          // CTA size: 32 tours in flight per warp
     int smem_tables;      // stage the order book (offsets + line keys) in shared memory

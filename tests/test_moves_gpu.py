@@ -1,0 +1,103 @@
+"""wh_eval_moves against the oracle's apply-and-rescore deltas (exact int64)
+and status codes, on shared and per-plan slottings, short and long tours."""
+import numpy as np
+import pytest
+
+import oracle
+import wh_gen
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_moves(wh, inst, moves, max_orders=0, max_lines=0, maps=None):
+    import torch
+    lay = wh.Layout.of(inst.layout)
+    stride = inst.n_sku if maps is not None else 0
+    prob = wh.to_device(inst, slot_map=None if maps is None else maps.ravel(), slot_map_stride=stride)
+    costs = wh.evaluate(lay, prob)
+    mv = torch.as_tensor(np.ascontiguousarray(moves.reshape(-1, 4)), dtype=torch.int32).cuda()
+    delta, status = lay.eval_moves(prob, costs, mv, max_orders, max_lines)
+    torch.cuda.synchronize()
+    st = lay.status()
+    lay.close()
+    return delta.cpu().numpy(), status.cpu().numpy(), st
+
+
+def moves_for(inst, seed, per_plan):
+    mv = wh_gen.gen_moves(seed, 0, inst, per_plan)
+    mv[..., 3] = np.arange(inst.n_plans)[:, None]
+    return mv.reshape(-1, 4)
+
+
+def check(wh, inst, mv, max_orders=0, max_lines=0, maps=None):
+    d, s, st = gpu_moves(wh, inst, mv, max_orders, max_lines, maps)
+    kw = {} if maps is None else {"slot_map": maps.ravel(), "slot_map_stride": inst.n_sku}
+    wd, ws = oracle.eval_moves(inst, mv, max_orders, max_lines, **kw)
+    assert np.array_equal(s, ws), f"status differs at {np.nonzero(s != ws)[0][:5]}"
+    bad = np.nonzero((d != wd).any(axis=1))[0]
+    assert bad.size == 0, f"delta differs at {bad[:5]}: got {d[bad[:3]]} want {wd[bad[:3]]} moves {mv[bad[:3]]}"
+    return s, st
+
+
+def test_tiny_shared_slotting(gpu_lib):
+    inst = wh_gen.tiny(seed=3, n_plans=8)
+    s, st = check(gpu_lib, inst, moves_for(inst, 1, 64), max_orders=8)
+    assert st == 0 and (s == 0).sum() > 100 and (s == 3).sum() > 50
+
+
+def test_tiny_per_plan_slottings(gpu_lib):
+    inst = wh_gen.tiny(seed=4, n_plans=6)
+    rng = np.random.default_rng(0)
+    maps = np.stack([rng.permutation(inst.layout.n_loc)[: inst.n_sku] for _ in range(6)]).astype(np.int32)
+    s, st = check(gpu_lib, inst, moves_for(inst, 2, 64), max_orders=8, maps=maps)
+    assert st == 0 and (s == 0).sum() > 250
+
+
+def test_midsize_with_caps(gpu_lib):
+    inst = wh_gen.midsize(seed=5, n_plans=8)
+    maps = np.tile(inst.slot_map, (8, 1)).astype(np.int32)
+    s, st = check(gpu_lib, inst, moves_for(inst, 3, 48), max_orders=20, max_lines=60, maps=maps)
+    assert st == 0 and (s == 1).sum() > 0 and (s == 0).sum() > 200
+
+
+def test_paperscale_long_tours_and_popular_skus(gpu_lib):
+    """32-bit keys (500 aisles), tours beyond 64 lines, and SKU swaps of the
+    most popular SKUs, which touch most tours of a plan."""
+    inst = wh_gen.paperscale(seed=6, n_plans=3)
+    maps = np.tile(inst.slot_map, (3, 1)).astype(np.int32)
+    mv = moves_for(inst, 4, 24)
+    hot = np.asarray([[2, 0, 1, 0], [2, 1, 30000, 1], [2, 0, 49999, 2], [2, 2, 3, 0]], np.int32)
+    mv = np.concatenate([mv, hot])
+    s, st = check(gpu_lib, inst, mv, max_orders=24, maps=maps)
+    assert st == 0 and (s == 0).sum() > 40
+
+
+def test_status_cases(gpu_lib):
+    inst = wh_gen.tiny(seed=7, n_plans=2)
+    t0, t1 = inst.plan_tour_off[0], inst.plan_tour_off[1]
+    tours = [inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]].tolist() for t in range(t0, t1)]
+    big = max(range(len(tours)), key=lambda i: len(tours[i]))
+    a = tours[big][0]
+    same = tours[big][1] if len(tours[big]) > 1 else a
+    other = [t for i, t in enumerate(tours) if i != big][0][0]
+    mv = np.asarray([[0, a, same, 0], [1, a, big, 0], [0, a, 10_000, 0], [1, a, 10_000, 0], [2, 1, 2, 0],
+                     [9, 1, 2, 0], [0, a, other, 5], [1, other, big, 0], [0, a, other, 0], [1, a, -1, 1]],
+                    np.int32)
+    s, st = check(gpu_lib, inst, mv, max_orders=len(tours[big]))
+    assert s.tolist()[:8] == [2, 2, 3, 3, 3, 3, 3, 1]
+
+
+def test_repeat_and_empty(gpu_lib):
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.tiny(seed=9, n_plans=4)
+    mv = moves_for(inst, 5, 32)
+    a = gpu_moves(wh, inst, mv, 8)
+    b = gpu_moves(wh, inst, mv, 8)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    lay = wh.Layout.of(inst.layout)
+    prob = wh.to_device(inst)
+    costs = wh.evaluate(lay, prob)
+    d, s = lay.eval_moves(prob, costs, torch.zeros((0, 4), dtype=torch.int32, device="cuda"))
+    assert d.shape[0] == 0 and s.shape[0] == 0
+    lay.close()
