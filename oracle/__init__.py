@@ -22,6 +22,10 @@ Functions and the independent checks that pin them (all in ``tests/``):
                         monotone in the pick set, ...).
 * ``eval_plans``     -- plan sums; pinned by summing per-tour calls over
                         hand-assembled pick lists.
+* ``ls_step``        -- one best-improvement local-search step, editing the
+                        plans in place; pinned by checking the applied index
+                        against the argmin of ``eval_moves`` and the new plan
+                        cost against old cost + delta.
 * ``eval_moves``     -- move deltas by applying each move to a copy and
                         re-scoring the plan; pinned by building the moved
                         plans explicitly in Python and differencing two
@@ -82,6 +86,10 @@ def _load():
             lib.or_eval_moves.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
                                           ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, i64p, i32p]
+            lib.or_ls_step.restype = ctypes.c_int
+            lib.or_ls_step.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
+                                       ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, i32p]
             _lib = lib
     return _lib
 
@@ -160,3 +168,22 @@ def eval_moves(inst, moves, max_orders: int = 0, max_lines: int = 0, slot_map=No
     if rc != 0:
         raise ValueError(f"or_eval_moves error {rc}")
     return delta[:n], status[:n]
+
+
+def ls_step(inst, moves, moves_per_plan: int, max_orders: int = 0, max_lines: int = 0, slot_map=None,
+            slot_map_stride: int = 0):
+    """Apply one local-search step to copies of the plans: returns
+    (tour_off, order_seq, slot_map, applied) after the step."""
+    lib = _load()
+    smap = _i32(inst.slot_map if slot_map is None else slot_map).copy()
+    off, lines = _i32(inst.order_off), _i32(inst.line_sku)
+    pto, to, seq = _i32(inst.plan_tour_off), _i32(inst.tour_off).copy(), _i32(inst.order_seq).copy()
+    mv = _i32(np.asarray(moves).reshape(-1, 4))
+    npl = pto.shape[0] - 1
+    applied = np.zeros(max(npl, 1), np.int32)
+    rc = lib.or_ls_step(ctypes.byref(_layout(inst.layout)), off.shape[0] - 1, _ptr(off), _ptr(lines), inst.n_sku,
+                        _ptr(smap), slot_map_stride, npl, _ptr(pto), _ptr(to), _ptr(seq), _ptr(mv), moves_per_plan,
+                        max_orders, max_lines, _ptr(applied))
+    if rc != 0:
+        raise ValueError(f"or_ls_step error {rc}")
+    return to, seq, smap, applied[:npl]

@@ -602,3 +602,69 @@ int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off
     free(smap_copy);
     return OR_OK;
 }
+
+/* ---------------------------------------------------------- local search */
+
+int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+               int32_t n_sku, int32_t *slot_map, int64_t slot_map_stride, int32_t n_plans,
+               const int32_t *plan_tour_off, int32_t *tour_off, int32_t *order_seq, const int32_t *moves,
+               int32_t moves_per_plan, int32_t max_orders, int32_t max_lines, int32_t *applied) {
+    const int32_t M = moves_per_plan;
+    int64_t *delta = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(M > 0 ? M : 1));
+    int32_t *status = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+    if (!delta || !status) { free(delta); free(status); return OR_ENOMEM; }
+    for (int32_t p = 0; p < n_plans; ++p) {
+        applied[p] = -1;
+        const int32_t *mv = moves + (int64_t)p * M * 4;
+        /* every move of this plan is scored against the plan as it is now */
+        int rc = or_eval_moves(g, n_orders, order_off, line_sku, n_sku, slot_map, slot_map_stride, n_plans,
+                               plan_tour_off, tour_off, order_seq, mv, M, max_orders, max_lines, delta, status);
+        if (rc != OR_OK) { free(delta); free(status); return rc; }
+        int32_t best = -1;
+        for (int32_t k = 0; k < M; ++k) {
+            if (mv[4 * k + 3] != p || status[k] != 0 || delta[2 * k + 1] >= 0) continue;
+            if (best < 0 || delta[2 * k + 1] < delta[2 * best + 1]) best = k;
+        }
+        if (best < 0) continue;
+        applied[p] = best;
+        const int32_t type = mv[4 * best], a = mv[4 * best + 1], b = mv[4 * best + 2];
+        const int32_t t0 = plan_tour_off[p], t1 = plan_tour_off[p + 1];
+        const int32_t s0 = tour_off[t0], s1 = tour_off[t1];
+        if (type == 0) {
+            int32_t ia = -1, ib = -1;
+            for (int32_t q = s0; q < s1; ++q) {
+                if (order_seq[q] == a) ia = q;
+                if (order_seq[q] == b) ib = q;
+            }
+            order_seq[ia] = b;
+            order_seq[ib] = a;
+        } else if (type == 1) {
+            int32_t ia = -1, ta = -1;
+            for (int32_t t = t0; t < t1; ++t)
+                for (int32_t q = tour_off[t]; q < tour_off[t + 1]; ++q)
+                    if (order_seq[q] == a) { ia = q; ta = t; }
+            const int32_t tb = t0 + b;
+            if (tb > ta) {
+                /* entries after a up to the end of tour tb move one place left */
+                const int32_t end = tour_off[tb + 1];
+                for (int32_t q = ia; q + 1 < end; ++q) order_seq[q] = order_seq[q + 1];
+                order_seq[end - 1] = a;
+                for (int32_t t = ta + 1; t <= tb; ++t) tour_off[t] -= 1;
+            } else {
+                /* entries from the end of tour tb up to a move one place right */
+                const int32_t end = tour_off[tb + 1];
+                for (int32_t q = ia; q > end; --q) order_seq[q] = order_seq[q - 1];
+                order_seq[end] = a;
+                for (int32_t t = tb + 1; t <= ta; ++t) tour_off[t] += 1;
+            }
+        } else {
+            int32_t *smap = slot_map + (int64_t)p * slot_map_stride;
+            const int32_t tmp = smap[a];
+            smap[a] = smap[b];
+            smap[b] = tmp;
+        }
+    }
+    free(delta);
+    free(status);
+    return OR_OK;
+}

@@ -92,6 +92,19 @@ int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off
                   int32_t n_moves, int32_t max_orders, int32_t max_lines, int64_t *delta,
                   int32_t *status);
 
+/* One best-improvement local-search step on every plan: plan p owns moves
+ * [p*moves_per_plan, (p+1)*moves_per_plan) (their plan field must be p);
+ * among those with status 0 and a negative optimal-cost delta the most
+ * negative is applied, ties to the lowest index; applied[p] = that index
+ * within the plan or -1.  The plans are edited in place: an order swap
+ * exchanges the two entries of order_seq, a relocation removes the order from
+ * its tour and appends it to the end of the target tour (tour_off shifts
+ * between them), a SKU swap exchanges two entries of the plan's slotting. */
+int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+               int32_t n_sku, int32_t *slot_map, int64_t slot_map_stride, int32_t n_plans,
+               const int32_t *plan_tour_off, int32_t *tour_off, int32_t *order_seq, const int32_t *moves,
+               int32_t moves_per_plan, int32_t max_orders, int32_t max_lines, int32_t *applied);
+
 #ifdef __cplusplus
 }
 #endif
