@@ -171,6 +171,25 @@ int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
                   const int32_t *tour_rr, const int32_t *moves, int32_t n_moves, int32_t max_orders_per_tour,
                   int32_t max_lines_per_tour, int64_t *delta, int32_t *status, void *stream);
 
+/* One step of best-improvement local search on every plan (Sec. 5: the
+ * picking list and product positions are improved by evaluated moves).  Plan
+ * p owns moves [p*moves_per_plan, (p+1)*moves_per_plan) (plan field p,
+ * moves_per_plan <= 256) with their delta / status from wh_eval_moves; the
+ * move with the most negative optimal-cost delta among those of status 0 and
+ * negative delta is applied, ties to the lowest index; applied[p] receives its
+ * index within the plan or -1.  The plans are edited IN PLACE (the const
+ * pointers of `plans` are written): an order swap exchanges two entries of
+ * order_seq; a relocation removes the order from its tour and appends it to
+ * the end of the target tour, shifting order_seq and tour_off between them; a
+ * SKU swap exchanges two entries of the plan's slotting.  Tour costs are not
+ * refreshed: call wh_eval_plans afterwards.  Each plan's segment of order_seq
+ * may hold at most max(n_orders, 1) entries (WH_STATUS_BAD_OFFSET otherwise,
+ * and that plan is left unchanged).  Returns WH_OK, WH_EINVAL, WH_ERANGE
+ * (n_orders beyond 50,000: the staging buffer) or WH_ECUDA. */
+int wh_ls_apply(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *moves,
+                int32_t moves_per_plan, const int64_t *delta, const int32_t *status, int32_t *applied,
+                void *stream);
+
 /* Sizes accepted by wh_eval_plans_noalloc. */
 #define WH_NOALLOC_MAX_LINES (1 << 20)
 #define WH_NOALLOC_MAX_TOURS (1 << 20)

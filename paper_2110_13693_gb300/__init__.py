@@ -64,6 +64,9 @@ SIGNATURES = {
     "wh_eval_plans": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                      ctypes.c_uint32, ctypes.POINTER(wh_costs), ctypes.c_void_p]),
     "wh_get_last_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_ls_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
+                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
     "wh_eval_moves": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -152,6 +155,13 @@ def wh_eval_moves(layout, orders: wh_orders, plans: wh_plans, tour_s, tour_rr, m
                                 ctypes.c_void_p(tour_rr), ctypes.c_void_p(moves), n_moves, max_orders, max_lines,
                                 ctypes.c_void_p(delta), ctypes.c_void_p(status), _stream_ptr(stream)),
            "wh_eval_moves")
+
+
+def wh_ls_apply(layout, orders: wh_orders, plans: wh_plans, moves, moves_per_plan: int, delta, status, applied,
+                stream=None) -> None:
+    _check(load().wh_ls_apply(layout, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(moves),
+                              moves_per_plan, ctypes.c_void_p(delta), ctypes.c_void_p(status),
+                              ctypes.c_void_p(applied), _stream_ptr(stream)), "wh_ls_apply")
 
 
 def wh_get_last_status(layout, stream=None) -> int:
@@ -320,6 +330,19 @@ class Layout:
         wh_eval_moves(self.handle, prob.orders(), prob.plans(), _ptr(costs.tour_s), _ptr(costs.tour_rr),
                       _ptr(mv), n, max_orders, max_lines, _ptr(delta), _ptr(status), stream)
         return delta[:n], status[:n]
+
+    def ls_step(self, prob: DeviceProblem, costs: Costs, moves, moves_per_plan: int, max_orders: int = 0,
+                max_lines: int = 0, stream=None):
+        """One exact local-search step: score the moves, apply each plan's best
+        improving move in place, refresh the costs.  Returns applied [n_plans]."""
+        import torch
+        mv = moves.reshape(-1, 4).contiguous()
+        delta, status = self.eval_moves(prob, costs, mv, max_orders, max_lines, stream)
+        applied = torch.empty(max(prob.n_plans, 1), dtype=torch.int32, device=mv.device)
+        wh_ls_apply(self.handle, prob.orders(), prob.plans(), _ptr(mv), moves_per_plan, _ptr(delta), _ptr(status),
+                    _ptr(applied), stream)
+        self.eval_plans(prob, costs, 3, stream)
+        return applied[:prob.n_plans]
 
     def set_timing(self, enable: bool) -> None:
         wh_set_timing(self.handle, enable)

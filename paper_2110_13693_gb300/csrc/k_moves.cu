@@ -540,3 +540,105 @@ cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStre
 }
 
 }  // namespace wh
+
+// ---------------------------------------------------------- local search
+namespace wh {
+namespace {
+
+// One CTA per plan: the move with the most negative optimal-cost delta among
+// the plan's moves of status 0 (ties: lowest index) is applied in place.
+__global__ void k_ls_apply(LsArgs L) {
+    extern __shared__ int32_t seg[];
+    __shared__ long long s_best;
+    __shared__ int s_pos[2];
+    const EvalArgs& a = L.a;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int p = blockIdx.x; p < a.n_plans; p += gridDim.x) {
+        if (tid < 32) {
+            long long best = 0x7fffffffffffffffll;
+            for (int k = tid; k < L.moves_per_plan; k += 32) {
+                const int64_t m = (int64_t)p * L.moves_per_plan + k;
+                const long long d = L.delta[2 * m + 1];
+                if (L.status[m] == 0 && d < 0 && L.moves[m].w == p) best = min(best, d * 256 + k);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (tid == 0) {
+                s_best = best;
+                s_pos[0] = s_pos[1] = -1;
+            }
+        }
+        __syncthreads();
+        const long long best = s_best;
+        const int k = best == 0x7fffffffffffffffll ? -1 : (int)(((best % 256) + 256) % 256);
+        if (tid == 0) L.applied[p] = k;
+        if (k >= 0) {
+            const int4 mv = L.moves[(int64_t)p * L.moves_per_plan + k];
+            const int t0 = a.plan_tour_off[p], t1 = a.plan_tour_off[p + 1];
+            const int s0 = a.tour_off[t0], s1 = a.tour_off[t1];
+            int32_t* order_seq = const_cast<int32_t*>(a.order_seq);
+            int32_t* tour_off = const_cast<int32_t*>(a.tour_off);
+            if (mv.x == 0 || mv.x == 1) {
+                for (int q = s0 + tid; q < s1; q += T) {
+                    const int o = order_seq[q];
+                    if (o == mv.y) s_pos[0] = q;
+                    if (mv.x == 0 && o == mv.z) s_pos[1] = q;
+                }
+                __syncthreads();
+                const int ia = s_pos[0];
+                if (mv.x == 0) {
+                    if (tid == 0 && ia >= 0 && s_pos[1] >= 0) {
+                        order_seq[ia] = mv.z;
+                        order_seq[s_pos[1]] = mv.y;
+                    }
+                } else if (ia >= 0) {
+                    // tour holding position ia: largest t with tour_off[t] <= ia
+                    int lo = t0, hi = t1 - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (tour_off[mid] <= ia) lo = mid; else hi = mid - 1;
+                    }
+                    const int ta = lo, tb = t0 + mv.z;
+                    const int end = tour_off[tb + 1];
+                    const int r0 = tb > ta ? ia : end, r1 = tb > ta ? end : ia + 1;   // range that moves
+                    if (r1 - r0 <= L.seg_cap) {
+                        for (int q = r0 + tid; q < r1; q += T) seg[q - r0] = order_seq[q];
+                        __syncthreads();
+                        if (tb > ta) {
+                            for (int q = r0 + tid; q < r1 - 1; q += T) order_seq[q] = seg[q - r0 + 1];
+                            if (tid == 0) order_seq[r1 - 1] = mv.y;
+                            for (int t = ta + 1 + tid; t <= tb; t += T) tour_off[t] -= 1;
+                        } else {
+                            for (int q = r0 + 1 + tid; q < r1; q += T) order_seq[q] = seg[q - r0 - 1];
+                            if (tid == 0) order_seq[r0] = mv.y;
+                            for (int t = tb + 1 + tid; t <= ta; t += T) tour_off[t] += 1;
+                        }
+                    } else if (tid == 0) {
+                        flag(a.status, WH_STATUS_BAD_OFFSET);
+                        L.applied[p] = -1;
+                    }
+                }
+            } else if (mv.x == 2 && tid == 0) {
+                int32_t* smap = const_cast<int32_t*>(a.slot_map) + (int64_t)p * a.slot_stride;
+                const int32_t x = smap[mv.y];
+                smap[mv.y] = smap[mv.z];
+                smap[mv.z] = x;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s) {
+    const size_t smem = sizeof(int32_t) * (size_t)L.seg_cap;
+    cudaError_t e = cudaFuncSetAttribute(k_ls_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = L.a.n_plans < 65536 ? L.a.n_plans : 65536;
+    if (grid < 1) grid = 1;
+    k_ls_apply<<<grid, 256, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace wh

@@ -356,6 +356,34 @@ extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_pla
     return WH_OK;
 }
 
+extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* moves,
+                           int32_t moves_per_plan, const int64_t* delta, const int32_t* status, int32_t* applied,
+                           void* stream) {
+    if (!h || !orders || !plans || moves_per_plan < 1 || moves_per_plan > 256) return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
+    if (p.n_plans == 0) return WH_OK;
+    if (!moves || !delta || !status || !applied) return WH_EINVAL;
+    if (o.n_orders > 50000) return WH_ERANGE;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    wh::LsArgs L;
+    std::memset(&L, 0, sizeof(L));
+    wh_costs none;
+    std::memset(&none, 0, sizeof(none));
+    fill_args(L.a, h->g, o, p, none, WH_ROUTE_OPTIMAL);
+    L.a.status = h->meta;
+    L.moves = reinterpret_cast<const int4*>(moves);
+    L.moves_per_plan = moves_per_plan;
+    L.delta = delta;
+    L.status = status;
+    L.applied = applied;
+    L.seg_cap = std::max(o.n_orders, 1);
+    return wh::launch_ls_apply(L, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {
     if (!h || !status) return WH_EINVAL;
     if (h->device < 0) {

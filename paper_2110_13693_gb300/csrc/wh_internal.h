@@ -98,6 +98,17 @@ struct MoveArgs {
     int32_t long_cap;
 };
 
+struct LsArgs {
+    EvalArgs a;                 // plans edited in place (order_seq, tour_off, slot_map)
+    const int4* moves;          // plan p owns moves [p*moves_per_plan, (p+1)*moves_per_plan)
+    int32_t moves_per_plan;
+    const int64_t* delta;
+    const int32_t* status;
+    int32_t* applied;           // [n_plans]
+    int32_t seg_cap;            // shared-memory staging capacity (orders)
+};
+
+cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s);
 cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s);
 cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s);
 
