@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and move-delta measurements")
+    ap.add_argument("--extra-steps", type=int, default=20)
+    ap.add_argument("--case", choices=["batched-small", "moves-small"], default=None,
+                    help="run a small case of one kernel three times (for profiler captures) and exit")
     return ap.parse_args()
 
 
@@ -106,14 +110,14 @@ class ClockSampler:
 # ------------------------------------------------------------------ helpers
 
 def algorithmic_bytes(inst):
-    """HBM bytes one evaluation must move at least, counted once: the plans'
-    order sequences and tour offsets read, two int32 costs per tour and two
-    int64 sums per plan written, plan offsets read, and the order book with
-    its slotting read once."""
-    b = 4 * inst.order_seq.shape[0] + 4 * inst.tour_off.shape[0] + 4 * inst.plan_tour_off.shape[0]
-    b += 8 * inst.n_tours + 16 * inst.n_plans
-    b += 4 * inst.order_off.shape[0] + 8 * inst.n_lines
-    return b
+    """Algorithmic HBM bytes of one evaluation, per unit and counted once
+    (pick lists as if materialised, unpadded): 4 B per order line of every
+    tour read, 4 B per tour offset, 4 B per tour per routing rule written
+    (two rules), 8 B per plan per rule, and the slotting table (4 B per SKU)
+    once per instance.  The kernel itself reads order ids (4 B per order, not
+    per line), so its DRAM traffic is below this figure."""
+    lines = int(inst.tour_lines().sum())
+    return 4 * lines + 4 * (inst.n_tours + 1) + 8 * inst.n_tours + 16 * inst.n_plans + 4 * inst.n_sku
 
 
 def measured_peaks():
@@ -127,21 +131,22 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("k_eval.cu", "wh_internal.h"):
+    for name in ("k_eval.cu", "tour_core.cuh", "wh_internal.h"):
         with open(os.path.join(ROOT, "paper_2110_13693_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+def recorded_profile():
+    """The committed ncu summary of the dominant kernel (DRAM bytes per
+    launch, issue and pipe utilisation), only if it was taken on the current
+    kernel source."""
     path = os.path.join(ROOT, "profiles", "k_eval_short_midsize.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("kernel_source_sha") == kernel_source_hash():
-            return float(d["dram_bytes_per_launch"])
+            return d
     except Exception:
         pass
     return None
@@ -171,6 +176,89 @@ def cpu_oracle_rate(inst, seconds, plans_per_chunk=8):
         el = time.perf_counter() - t0
         if el >= seconds:
             return tours / el, tours, plans, el
+
+
+# ------------------------------------------------- other hot-path rows
+
+def run_batched(wh, dev, steps):
+    """1,024 uneven instances x 256 plans in one persistent launch replayed
+    as a CUDA graph, launch shape from the autotuner (JSON cache)."""
+    import torch
+    import wh_gen
+    insts = [wh_gen.batched_instance(3, i, n_plans=256) for i in range(1024)]
+    items = []
+    for inst in insts:
+        lay = inst.layout
+        prob = wh.to_device(inst, dev)
+        items.append(((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width),
+                      prob, wh.alloc_costs(prob.n_tours, prob.n_plans, dev)))
+    tours = sum(p.n_tours for _, p, _ in items)
+    batch = wh.Batch(items)
+    cache = os.path.join(ROOT, "paper_2110_13693_gb300", "autotune_cache.json")
+    th, ch, hit = batch.autotune(3, cache)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        batch.eval(3, stream, graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        batch.eval(3, stream, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert batch.status() == 0
+    batch.close()
+    return {"workload": "1,024 instances (aisles U[8,64], slots/side U[20,200], orders U[100,5000]) x 256 plans, "
+                        "one persistent launch replayed as a CUDA graph",
+            "tours_per_step": tours, "ms_per_step": ms, "tours_per_s": tours / (ms / 1e3), "steps": steps,
+            "tuning": {"threads": th, "chunks_per_item": ch, "from_cache": bool(hit)}}
+
+
+def run_moves(wh, dev, steps):
+    """Paper-scale local search: 500 aisles x 200 slots/side, 50,000 SKUs,
+    16,384 plans with their own slottings, 64 moves per plan per step."""
+    import numpy as np
+    import torch
+    import wh_gen
+    n_plans, M = 16384, 64
+    inst = wh_gen.paperscale(seed=4, n_plans=n_plans)
+    lay = wh.Layout.of(inst.layout)
+    base = wh.to_device(inst, dev)
+    smap = base.slot_map.repeat(n_plans)
+    prob = wh.DeviceProblem(base.order_off, base.line_sku, smap, base.plan_tour_off, base.tour_off,
+                            base.order_seq, inst.n_sku, inst.n_sku)
+    costs = wh.evaluate(lay, prob)
+    moves = []
+    for step in range(steps + 2):
+        mv = wh_gen.gen_moves(17, step, inst, M)
+        mv[..., 3] = np.arange(n_plans)[:, None]
+        moves.append(torch.as_tensor(mv.reshape(-1, 4)).to(dev))
+    for i in range(2):
+        lay.eval_moves(prob, costs, moves[i], 24)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        d, s = lay.eval_moves(prob, costs, moves[2 + i], 24)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    n_ok = int((s == 0).sum().item())
+    # full local-search steps (evaluate, apply, re-score) on the same population
+    t1 = time.perf_counter()
+    improved = 0
+    for i in range(steps):
+        applied = lay.ls_step(prob, costs, moves[2 + i], M, 24)
+        improved += int((applied >= 0).sum().item())
+    torch.cuda.synchronize()
+    el2 = time.perf_counter() - t1
+    assert lay.status() == 0
+    lay.close()
+    return {"workload": "paper scale: 500 aisles x 200 slots/side, 50,000 SKUs Zipf(1.0), 4,000 orders, "
+                        "16,384 plans x 64 moves per step (order swap / relocate / SKU-slot swap)",
+            "moves_per_step": n_plans * M, "ms_per_step": el * 1e3 / steps,
+            "move_deltas_per_s": n_plans * M * steps / el, "evaluated_fraction": n_ok / (n_plans * M),
+            "ls_step_ms": el2 * 1e3 / steps, "plans_improved_per_step": improved / steps, "steps": steps,
+            "timing": "wall clock around the calls (each call synchronises once)"}
 
 
 # -------------------------------------------------------------- our arm
@@ -290,8 +378,14 @@ def run_ours(args):
               for i, b in enumerate(batches)) / args.steps
     peak, peak_kind = measured_peaks()
     achieved = alg / per_launch_s / 1e9
-    traffic = recorded_traffic()
+    prof = recorded_profile()
+    traffic = float(prof["dram_bytes_per_launch"]) if prof else None
     launches = sum(v[0] for v in ktime.values())
+
+    extra = {}
+    if not args.no_extra and world == 1:
+        extra["batched"] = run_batched(wh, dev, args.extra_steps)
+        extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4))
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -319,9 +413,12 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_s * 1e3,
-                     "traffic": traffic},
+                     "traffic": traffic,
+                     "issue_active_frac": prof.get("issue_active_frac") if prof else None,
+                     "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None},
         "cpu_baseline": cpu,
     }
+    out.update(extra)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -363,8 +460,53 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_case(name):
+    """Small cases for profiler captures: 128 batched instances x 64 plans,
+    or paper-scale move deltas on 1,024 plans x 64 moves."""
+    import numpy as np
+    import torch
+    import paper_2110_13693_gb300 as wh
+    import wh_gen
+    from paper_2110_13693_gb300 import build as whbuild
+    whbuild.build()
+    wh.load()
+    if name == "batched-small":
+        items = []
+        for i in range(128):
+            inst = wh_gen.batched_instance(3, i, n_plans=64)
+            lay = inst.layout
+            prob = wh.to_device(inst)
+            items.append(((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width),
+                          prob, wh.alloc_costs(prob.n_tours, prob.n_plans)))
+        b = wh.Batch(items)
+        for _ in range(3):
+            b.eval(3)
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        b.close()
+    else:
+        n = 1024
+        inst = wh_gen.paperscale(seed=4, n_plans=n)
+        lay = wh.Layout.of(inst.layout)
+        base = wh.to_device(inst)
+        prob = wh.DeviceProblem(base.order_off, base.line_sku, base.slot_map.repeat(n), base.plan_tour_off,
+                                base.tour_off, base.order_seq, inst.n_sku, inst.n_sku)
+        costs = wh.evaluate(lay, prob)
+        for step in range(3):
+            mv = wh_gen.gen_moves(17, step, inst, 64)
+            mv[..., 3] = np.arange(n)[:, None]
+            lay.eval_moves(prob, costs, torch.as_tensor(mv.reshape(-1, 4)).cuda(), 24)
+        torch.cuda.synchronize()
+        assert lay.status() == 0
+        lay.close()
+    print(json.dumps({"case": name, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
