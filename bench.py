@@ -154,7 +154,8 @@ def recorded_profile():
 
 def make_batches(n_batches, rank):
     import wh_gen
-    return [wh_gen.midsize(seed=2, n_plans=PLANS_PER_STEP, plan_base=(rank * n_batches + b) * PLANS_PER_STEP)
+    from paper_2110_13693_gb300.shard import plan_base
+    return [wh_gen.midsize(seed=2, n_plans=PLANS_PER_STEP, plan_base=plan_base(rank, b, n_batches, PLANS_PER_STEP))
             for b in range(n_batches)]
 
 
@@ -320,14 +321,8 @@ def run_ours(args):
     lay.set_timing(False)
     assert lay.status() == 0
 
-    total_tours = n_tours
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        n = torch.tensor([n_tours], device=dev, dtype=torch.float64)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        total_tours = int(n.item())
+    from paper_2110_13693_gb300.shard import combine
+    elapsed_ms, total_tours = combine(elapsed_ms, n_tours, dev)
     value = total_tours / (elapsed_ms / 1e3)
 
     # ---- end to end through the public API from pinned host memory
@@ -357,13 +352,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-        n = torch.tensor([e_tours], device=dev, dtype=torch.float64)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        e_tours = int(n.item())
+    e2e_ms, e_tours = combine(e2e_ms, e_tours, dev)
     e2e_value = e_tours / (e2e_ms / 1e3)
 
     if rank != 0:
@@ -400,7 +389,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "plans_per_step": PLANS_PER_STEP,
                    "tours_per_step": round(sum(tours) / len(tours)), "routing": "S-shape + optimal",
                    "l2": f"inputs larger than L2: {len(batches)} plan batches rotated, "
-                         f"{sum(algorithmic_bytes(b) for b in batches) / 1e6:.0f} MB of step inputs (> 129 MB L2)",
+                         f"{sum(4 * (b.order_seq.size + b.tour_off.size) for b in batches) / 1e6:.0f} MB of "
+                         "plan arrays resident (> 129 MB L2)",
                    "parallelism": f"dp{world} (independent plan batches per GPU)"},
         "plans_per_s": world * PLANS_PER_STEP * args.steps / (elapsed_ms / 1e3),
         "clocks": clk,
