@@ -26,6 +26,13 @@ Functions and the independent checks that pin them (all in ``tests/``):
                         plans in place; pinned by checking the applied index
                         against the argmin of ``eval_moves`` and the new plan
                         cost against old cost + delta.
+* ``features``       -- the 192 surrogate features of a tour; pinned by a
+                        brute-force Python computation from the pick set.
+* ``mlp_forward`` / ``mlp_backward`` / ``adam`` -- the surrogate MLP;
+                        forward pinned by torch's float64 Linear + exact GELU
+                        with the same bf16 rounding points, backward by
+                        finite differences and by torch autograd, Adam by
+                        torch.optim.Adam.
 * ``eval_moves``     -- move deltas by applying each move to a copy and
                         re-scoring the plan; pinned by building the moved
                         plans explicitly in Python and differencing two
@@ -90,6 +97,19 @@ def _load():
             lib.or_ls_step.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
                                        ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, i32p]
+            f32p = ctypes.POINTER(ctypes.c_float)
+            f64p = ctypes.POINTER(ctypes.c_double)
+            lib.or_features.restype = ctypes.c_int
+            lib.or_features.argtypes = [lp, i32p, ctypes.c_int32, f32p]
+            lib.or_bf16.restype = ctypes.c_float
+            lib.or_bf16.argtypes = [ctypes.c_float]
+            lib.or_mlp_forward.restype = None
+            lib.or_mlp_forward.argtypes = [f32p] * 7 + [ctypes.c_int32, f64p]
+            lib.or_mlp_backward.restype = ctypes.c_double
+            lib.or_mlp_backward.argtypes = [f32p] * 7 + [f64p, ctypes.c_int32] + [f64p] * 6
+            lib.or_adam.restype = None
+            lib.or_adam.argtypes = [f64p, f64p, f64p, f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int32]
             _lib = lib
     return _lib
 
@@ -187,3 +207,61 @@ def ls_step(inst, moves, moves_per_plan: int, max_orders: int = 0, max_lines: in
     if rc != 0:
         raise ValueError(f"or_ls_step error {rc}")
     return to, seq, smap, applied[:npl]
+
+
+MLP_IN, MLP_H = 192, 256
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def features(lay, locs) -> np.ndarray:
+    """float32[192] features of one tour (before bf16 rounding)."""
+    arr = _i32(locs)
+    out = np.zeros(192, np.float32)
+    rc = _load().or_features(ctypes.byref(_layout(lay)), _ptr(arr), arr.shape[0], _ptr(out, ctypes.c_float))
+    if rc != 0:
+        raise ValueError(f"or_features error {rc}")
+    return out
+
+
+def bf16(x) -> np.ndarray:
+    """Round float32 values to bfloat16 (nearest even), returned as float32."""
+    f = _load().or_bf16
+    a = np.asarray(x, np.float32)
+    return np.vectorize(lambda v: f(float(v)), otypes=[np.float32])(a)
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    """params: dict w1 [192,256], b1, w2 [256,256], b2, w3 [256], b3 [1] (bf16 values)."""
+    X = _f32(X)
+    n = X.shape[0]
+    y = np.zeros(max(n, 1), np.float64)
+    ps = [_f32(params[k]) for k in ("w1", "b1", "w2", "b2", "w3", "b3")]
+    _load().or_mlp_forward(*[_ptr(p, ctypes.c_float) for p in ps], _ptr(X, ctypes.c_float), n,
+                           _ptr(y, ctypes.c_double))
+    return y[:n]
+
+
+def mlp_backward(params, X, t):
+    """(loss, grads dict) of 0.5 * mean((y - t)^2)."""
+    X = _f32(X)
+    t = np.ascontiguousarray(np.asarray(t, np.float64))
+    n = X.shape[0]
+    g = {"w1": np.zeros((MLP_IN, MLP_H)), "b1": np.zeros(MLP_H), "w2": np.zeros((MLP_H, MLP_H)),
+         "b2": np.zeros(MLP_H), "w3": np.zeros(MLP_H), "b3": np.zeros(1)}
+    ps = [_f32(params[k]) for k in ("w1", "b1", "w2", "b2", "w3", "b3")]
+    loss = _load().or_mlp_backward(*[_ptr(p, ctypes.c_float) for p in ps], _ptr(X, ctypes.c_float),
+                                   _ptr(t, ctypes.c_double), n,
+                                   *[_ptr(g[k], ctypes.c_double) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    return float(loss), g
+
+
+def adam(p, m, v, g, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    _load().or_adam(_ptr(p, ctypes.c_double), _ptr(m, ctypes.c_double), _ptr(v, ctypes.c_double),
+                    _ptr(g, ctypes.c_double), p.size, lr, b1, b2, eps, step)

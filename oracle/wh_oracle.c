@@ -5,6 +5,7 @@
  */
 #include "wh_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -667,4 +668,137 @@ int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, c
     free(delta);
     free(status);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------- surrogate */
+
+int or_features(const or_layout *g, const int32_t *locs, int32_t n, float *out) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    for (int i = 0; i < 192; ++i) out[i] = 0.0f;
+    const int32_t A = g->n_aisles, L = g->slots_per_side;
+    int32_t *kmin = (int32_t *)malloc(sizeof(int32_t) * (size_t)A);
+    int32_t *kmax = (int32_t *)malloc(sizeof(int32_t) * (size_t)A);
+    if (!kmin || !kmax) { free(kmin); free(kmax); return OR_ENOMEM; }
+    for (int32_t a = 0; a < A; ++a) { kmin[a] = -1; kmax[a] = -1; }
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t loc = locs[i];
+        if (loc < 0 || loc >= A * 2 * L) { free(kmin); free(kmax); return OR_ERANGE; }
+        const int32_t a = loc / (2 * L), k = loc % L;
+        if (kmin[a] < 0 || k < kmin[a]) kmin[a] = k;
+        if (k > kmax[a]) kmax[a] = k;
+    }
+    int32_t left = -1, right = -1, count = 0;
+    for (int32_t a = 0; a < A; ++a) {
+        if (kmax[a] < 0) continue;
+        if (left < 0) left = a;
+        right = a;
+        ++count;
+        out[(int64_t)kmax[a] * 64 / L] += 1.0f;
+        out[64 + (int64_t)kmin[a] * 64 / L] += 1.0f;
+        out[132 + (int64_t)a * 60 / A] += 1.0f;
+    }
+    const float inv_a = (float)(1.0 / (double)A);
+    if (count > 0) {
+        out[128] = (float)left * inv_a;
+        out[129] = (float)right * inv_a;
+    }
+    out[130] = (float)count * inv_a;
+    out[131] = (float)n * (1.0f / 64.0f);
+    free(kmin);
+    free(kmax);
+    return OR_OK;
+}
+
+float or_bf16(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;          /* inf / nan: keep */
+    const uint32_t lsb = (u >> 16) & 1u;
+    u = (u + 0x7fffu + lsb) & 0xffff0000u;                   /* round to nearest even */
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+static double gelu_grad(double x) {
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * 3.14159265358979323846);
+}
+
+#define MLP_IN 192
+#define MLP_H 256
+
+/* forward for one row; z1, z2 pre-activations (double), h1, h2 bf16-rounded activations */
+static double mlp_row(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                      const float *b3, const float *x, double *z1, double *h1, double *z2, double *h2) {
+    for (int j = 0; j < MLP_H; ++j) {
+        double s = b1[j];
+        for (int i = 0; i < MLP_IN; ++i) s += (double)x[i] * (double)w1[i * MLP_H + j];
+        z1[j] = s;
+        h1[j] = (double)or_bf16((float)gelu(s));
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        double s = b2[j];
+        for (int i = 0; i < MLP_H; ++i) s += h1[i] * (double)w2[i * MLP_H + j];
+        z2[j] = s;
+        h2[j] = (double)or_bf16((float)gelu(s));
+    }
+    double y = b3[0];
+    for (int i = 0; i < MLP_H; ++i) y += h2[i] * (double)w3[i];
+    return y;
+}
+
+void or_mlp_forward(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                    const float *b3, const float *X, int32_t n, double *y) {
+    double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H];
+    for (int32_t r = 0; r < n; ++r) y[r] = mlp_row(w1, b1, w2, b2, w3, b3, X + (int64_t)r * MLP_IN, z1, h1, z2, h2);
+}
+
+double or_mlp_backward(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                       const float *b3, const float *X, const double *t, int32_t n, double *g1, double *gb1,
+                       double *g2, double *gb2, double *g3, double *gb3) {
+    memset(g1, 0, sizeof(double) * MLP_IN * MLP_H);
+    memset(gb1, 0, sizeof(double) * MLP_H);
+    memset(g2, 0, sizeof(double) * MLP_H * MLP_H);
+    memset(gb2, 0, sizeof(double) * MLP_H);
+    memset(g3, 0, sizeof(double) * MLP_H);
+    gb3[0] = 0.0;
+    double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H], d2[MLP_H], d1[MLP_H];
+    double loss = 0.0;
+    for (int32_t r = 0; r < n; ++r) {
+        const float *x = X + (int64_t)r * MLP_IN;
+        const double y = mlp_row(w1, b1, w2, b2, w3, b3, x, z1, h1, z2, h2);
+        const double e = y - t[r];
+        loss += 0.5 * e * e;
+        const double dy = e / n;                  /* d loss / d y */
+        gb3[0] += dy;
+        for (int i = 0; i < MLP_H; ++i) {
+            g3[i] += dy * h2[i];
+            d2[i] = dy * (double)w3[i] * gelu_grad(z2[i]);   /* d loss / d z2 */
+        }
+        for (int j = 0; j < MLP_H; ++j) gb2[j] += d2[j];
+        for (int i = 0; i < MLP_H; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < MLP_H; ++j) {
+                g2[i * MLP_H + j] += h1[i] * d2[j];
+                s += (double)w2[i * MLP_H + j] * d2[j];
+            }
+            d1[i] = s * gelu_grad(z1[i]);                    /* d loss / d z1 */
+        }
+        for (int j = 0; j < MLP_H; ++j) gb1[j] += d1[j];
+        for (int i = 0; i < MLP_IN; ++i)
+            for (int j = 0; j < MLP_H; ++j) g1[i * MLP_H + j] += (double)x[i] * d1[j];
+    }
+    return loss / n;
+}
+
+void or_adam(double *p, double *m, double *v, const double *g, int64_t n, double lr, double b1, double b2,
+             double eps, int32_t step) {
+    const double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
 }

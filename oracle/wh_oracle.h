@@ -105,6 +105,46 @@ int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, c
                const int32_t *plan_tour_off, int32_t *tour_off, int32_t *order_seq, const int32_t *moves,
                int32_t moves_per_plan, int32_t max_orders, int32_t max_lines, int32_t *applied);
 
+/* ------------------------------------------------------------- surrogate
+ * Learned prescreen (the paper's machine-learning-in-the-loop idea, Sec. 1 and
+ * Fig. 1): a small MLP predicts a tour's normalised optimal length from a
+ * fixed feature vector of the tour.
+ *
+ * Features, 192 per tour (the readings are listed in the design notes):
+ *   [0, 64)    histogram over the visited aisles of their deepest pick,
+ *              bin = floor(k_max * 64 / L) of the slot index;
+ *   [64, 128)  the same for the shallowest pick (k_min);
+ *   [128]      leftmost visited aisle * inv_A, [129] rightmost * inv_A,
+ *   [130]      visited-aisle count * inv_A, [131] line count * (1/64);
+ *   [132, 192) histogram of the visited aisles, bin = floor(a * 60 / A).
+ * inv_A = (float)(1.0 / A).  Products are single-precision, as on the device;
+ * all values are then representable or rounded to bf16 by the caller. */
+int or_features(const or_layout *g, const int32_t *locs, int32_t n, float *out);
+
+/* round a float to bfloat16 (round to nearest even), returned as float */
+float or_bf16(float x);
+
+/* MLP 192 -> 256 -> GELU -> 256 -> GELU -> 1.  Weights are given as floats
+ * that are already bf16 values (w1[192*256] row-major [in][out], b1[256],
+ * w2[256*256], b2[256], w3[256], b3[1]).  X is [n][192] of bf16 values.
+ * Accumulation in double; each hidden activation is rounded to bf16 after
+ * bias + GELU (0.5 x (1 + erf(x / sqrt 2))), as the device stores it.
+ * y[n] receives the outputs (no rounding). */
+void or_mlp_forward(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                    const float *b3, const float *X, int32_t n, double *y);
+
+/* Loss 0.5 * mean((y - t)^2) and its gradient with respect to every
+ * parameter (double), by the chain rule through the same forward pass with
+ * the bf16 rounding points treated as identity. */
+double or_mlp_backward(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                       const float *b3, const float *X, const double *t, int32_t n, double *g1, double *gb1,
+                       double *g2, double *gb2, double *g3, double *gb3);
+
+/* One Adam step (Kingma & Ba 2015) on n parameters: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void or_adam(double *p, double *m, double *v, const double *g, int64_t n, double lr, double b1, double b2,
+             double eps, int32_t step);
+
 #ifdef __cplusplus
 }
 #endif
