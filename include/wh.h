@@ -190,6 +190,55 @@ int wh_ls_apply(wh_layout *layout, const wh_orders *orders, const wh_plans *plan
                 int32_t moves_per_plan, const int64_t *delta, const int32_t *status, int32_t *applied,
                 void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned prescreen (machine learning in the decision loop, Sec. 1 and
+ * Fig. 1): an MLP 192 -> 256 -> GELU -> 256 -> GELU -> 1 predicts a tour's
+ * optimal length divided by 2*x_{A-1} + A*Y from 192 tour features; bf16
+ * weights and activations, fp32 accumulation, trained on the device with
+ * Adam on fp32 master weights.  Parameters are one packed float vector of
+ * WH_MLP_NPARAM values: w1 [192][256], b1 [256], w2 [256][256], b2 [256],
+ * w3 [256], b3 [1] (row-major, [input][output]).
+ */
+#define WH_MLP_NPARAM 115457
+#define WH_FEATURES 192
+
+typedef struct wh_surrogate wh_surrogate;
+
+/* Features of every tour of `plans` into X (device, bf16 stored as uint16,
+ * [n_tours][192], rows 16-byte aligned): histograms over the tour's visited
+ * aisles of the deepest and the shallowest pick's slot bin floor(k*64/L)
+ * (features 0..63, 64..127), leftmost aisle / A, rightmost aisle / A,
+ * visited-aisle count / A, line count / 64 (128..131), and a 60-bin
+ * histogram of the visited aisles floor(a*60/A) (132..191).  Tours with more
+ * than 128 distinct aisles set WH_STATUS_TOUR_TOO_LONG.  Returns WH_OK,
+ * WH_EINVAL, WH_ERANGE (slots_per_side > 256), WH_ENOMEM or WH_ECUDA. */
+int wh_surrogate_features(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, uint16_t *X,
+                          void *stream);
+
+/* Create a surrogate on the current device: Xavier-uniform weights drawn
+ * from `seed` (SplitMix64), zero biases, zero Adam state.  Allocates and
+ * synchronises.  Returns WH_OK, WH_EINVAL, WH_ENOMEM or WH_ECUDA. */
+int wh_surrogate_create(uint64_t seed, wh_surrogate **out);
+
+/* Replace the parameters (host array of WH_MLP_NPARAM floats) and reset the
+ * Adam state.  Synchronises. */
+int wh_surrogate_set_params(wh_surrogate *s, const float *host_params);
+
+/* Copy the fp32 master parameters and / or the last step's gradients to host
+ * arrays of WH_MLP_NPARAM floats (either may be NULL).  Synchronises. */
+int wh_surrogate_get_params(wh_surrogate *s, float *host_params, float *host_grads);
+
+/* y[i] = MLP(X[i]) for n rows of bf16 features (device); fp32 outputs. */
+int wh_surrogate_predict(wh_surrogate *s, const uint16_t *X, int64_t n, float *y, void *stream);
+
+/* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared
+ * error 0.5*mean((y - target)^2) of n rows; *loss_out (device float, may be
+ * NULL) receives the loss before the step.  Allocates scratch when n grows. */
+int wh_surrogate_train_step(wh_surrogate *s, const uint16_t *X, const float *target, int32_t n, float lr,
+                            float *loss_out, void *stream);
+
+void wh_surrogate_destroy(wh_surrogate *s);
+
 /* Sizes accepted by wh_eval_plans_noalloc. */
 #define WH_NOALLOC_MAX_LINES (1 << 20)
 #define WH_NOALLOC_MAX_TOURS (1 << 20)

@@ -88,7 +88,19 @@ SIGNATURES = {
                           + [ctypes.POINTER(ctypes.c_int32)] * 3),
     "wh_batch_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "wh_batch_destroy": (None, [ctypes.c_void_p]),
+    "wh_surrogate_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_surrogate_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
+    "wh_surrogate_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "wh_surrogate_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_float)]),
+    "wh_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "wh_surrogate_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_surrogate_destroy": (None, [ctypes.c_void_p]),
 }
+WH_MLP_NPARAM, WH_FEATURES = 115457, 192
 
 
 def library_path() -> str:
@@ -425,3 +437,114 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- surrogate
+
+def wh_surrogate_features(layout, orders: wh_orders, plans: wh_plans, X, stream=None) -> None:
+    _check(load().wh_surrogate_features(layout, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(X),
+                                        _stream_ptr(stream)), "wh_surrogate_features")
+
+
+def wh_surrogate_create(seed: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().wh_surrogate_create(seed, ctypes.byref(h)), "wh_surrogate_create")
+    return h
+
+
+def wh_surrogate_set_params(s, params) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(np.asarray(params, np.float32))
+    assert p.size == WH_MLP_NPARAM
+    _check(load().wh_surrogate_set_params(s, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "wh_surrogate_set_params")
+
+
+def wh_surrogate_get_params(s):
+    """(params, grads) as float32 numpy arrays."""
+    import numpy as np
+    p = np.zeros(WH_MLP_NPARAM, np.float32)
+    g = np.zeros(WH_MLP_NPARAM, np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(load().wh_surrogate_get_params(s, p.ctypes.data_as(fp), g.ctypes.data_as(fp)), "wh_surrogate_get_params")
+    return p, g
+
+
+def wh_surrogate_predict(s, X, n: int, y, stream=None) -> None:
+    _check(load().wh_surrogate_predict(s, ctypes.c_void_p(X), n, ctypes.c_void_p(y), _stream_ptr(stream)),
+           "wh_surrogate_predict")
+
+
+def wh_surrogate_train_step(s, X, target, n: int, lr: float, loss=0, stream=None) -> None:
+    _check(load().wh_surrogate_train_step(s, ctypes.c_void_p(X), ctypes.c_void_p(target), n, lr,
+                                          ctypes.c_void_p(loss or None), _stream_ptr(stream)),
+           "wh_surrogate_train_step")
+
+
+def wh_surrogate_destroy(s) -> None:
+    load().wh_surrogate_destroy(s)
+
+
+def unpack_params(p):
+    """Packed parameter vector -> dict of arrays (w1 [192,256], b1, w2 [256,256], b2, w3, b3)."""
+    sizes = (("w1", (192, 256)), ("b1", (256,)), ("w2", (256, 256)), ("b2", (256,)), ("w3", (256,)), ("b3", (1,)))
+    out, off = {}, 0
+    for k, shape in sizes:
+        n = 1
+        for d in shape:
+            n *= d
+        out[k] = p[off:off + n].reshape(shape)
+        off += n
+    return out
+
+
+def pack_params(d):
+    import numpy as np
+    return np.concatenate([np.asarray(d[k], np.float32).reshape(-1) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+
+
+class Surrogate:
+    """Owning wrapper of a ``wh_surrogate``."""
+
+    def __init__(self, seed: int = 0):
+        self.handle = wh_surrogate_create(seed)
+
+    def set_params(self, packed):
+        wh_surrogate_set_params(self.handle, packed)
+
+    def params(self):
+        return wh_surrogate_get_params(self.handle)
+
+    def predict(self, X, stream=None):
+        import torch
+        n = int(X.shape[0])
+        y = torch.empty(max(n, 1), dtype=torch.float32, device=X.device)
+        wh_surrogate_predict(self.handle, X.data_ptr(), n, y.data_ptr(), stream)
+        return y[:n]
+
+    def train_step(self, X, target, lr: float, stream=None):
+        """Returns the loss (device tensor) before the step."""
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        wh_surrogate_train_step(self.handle, X.data_ptr(), target.data_ptr(), int(X.shape[0]), lr,
+                                loss.data_ptr(), stream)
+        return loss
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            wh_surrogate_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def features(layout: "Layout", prob: DeviceProblem, stream=None):
+    """bf16 [n_tours, 192] features of every tour of `prob`."""
+    import torch
+    X = torch.empty((max(prob.n_tours, 1), WH_FEATURES), dtype=torch.bfloat16, device=prob.order_off.device)
+    wh_surrogate_features(layout.handle, prob.orders(), prob.plans(), X.data_ptr(), stream)
+    return X[:prob.n_tours]

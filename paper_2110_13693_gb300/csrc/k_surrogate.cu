@@ -1,0 +1,357 @@
+// Surrogate kernels for sm_103a: tour features and a small MLP that predicts
+// a tour's normalised optimal length (the learned prescreen of local-search
+// moves; the paper puts machine learning in the decision loop, Sec. 1 and
+// Fig. 1).  MLP 192 -> 256 -> GELU -> 256 -> GELU -> 1, bf16 weights and
+// activations, fp32 accumulation; training by forward, backward and Adam on
+// fp32 master weights, all on the device.
+//
+// The GEMMs use the warp-level tensor-core instruction mma.sync m16n8k16
+// (bf16 in, fp32 accumulate) on 128x128x32 shared-memory tiles; operands may
+// be transposed, epilogues fuse bias + GELU (keeping the fp32
+// pre-activation), the GELU derivative, or write fp32.
+#include "tour_core.cuh"
+
+namespace wh {
+
+namespace {
+
+constexpr int FEAT_THREADS = 128;
+constexpr int G_BM = 128, G_BN = 128, G_BK = 32, G_PAD = 8, G_THREADS = 256;
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// --------------------------------------------------------------- features
+// One tour per thread: gather the tour's line keys, hash the visited aisles,
+// write the tour's 192 bf16 features.
+__global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst c, uint4* X) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    FeatThread f;
+    f.tab = reinterpret_cast<uint32_t*>(smem) + tid;
+    f.list = smem + sizeof(uint32_t) * FEAT_SLOTS * T + tid;
+    unsigned char* cnt_base = smem + (sizeof(uint32_t) + 1) * FEAT_SLOTS * T;
+    f.cnt = cnt_base + (size_t)tid * FEAT_CNT_STRIDE;
+    f.T = T;
+    f.n_aisles = 0;
+    f.n_lines = 0;
+    f.overflow = false;
+    for (int i = 0; i < FEAT_SLOTS; ++i) f.tab[i * T] = 0;
+    for (int i = 0; i < FEAT_CNT_STRIDE / 4; ++i) reinterpret_cast<uint32_t*>(f.cnt)[i] = 0;
+    const bool shared_map = a.slot_stride == 0;
+    for (int t = blockIdx.x * T + tid; t < a.n_tours; t += gridDim.x * T) {
+        int plan = 0;
+        if (!shared_map) {
+            int lo = 0, hi = a.n_plans - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.plan_tour_off[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            plan = lo;
+        }
+        const int32_t* map = a.slot_map + (int64_t)plan * a.slot_stride;
+        const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];
+        bool bad = q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq;
+        for (int q = q0; !bad && q < q1; ++q) {
+            const int o = a.order_seq[q];
+            if ((unsigned)o >= (unsigned)a.n_orders) { bad = true; break; }
+            const int lb = a.order_off[o], le = a.order_off[o + 1];
+            if (lb < 0 || le < lb || le > a.n_lines) { bad = true; break; }
+            for (int l = lb; l < le; ++l) {
+                uint32_t key;
+                if (shared_map) {
+                    key = a.line_key[l];
+                } else {
+                    const int s = a.line_sku[l];
+                    const int loc = (unsigned)s < (unsigned)a.n_sku ? map[s] : -1;
+                    key = (unsigned)loc < (unsigned)a.g.n_loc ? loc_key(a.g, loc) : KEY_BAD;
+                }
+                if (key == KEY_BAD) { bad = true; break; }
+                feat_insert(f, key);
+            }
+        }
+        if (bad || f.overflow) {
+            flag(a.status, bad ? WH_STATUS_BAD_ORDER : WH_STATUS_TOUR_TOO_LONG);
+            f.overflow = false;
+        }
+        feat_finish(f, c, X + (int64_t)t * 24);
+    }
+}
+
+// ------------------------------------------------------------------ GEMM
+enum { EPI_BIAS_GELU = 0, EPI_F32 = 1, EPI_GELU_GRAD = 2 };
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[M,N] = op(A)[M,K] op(B)[K,N]; A(m,k) = transA ? A[k*lda+m] : A[m*lda+k];
+// B(k,n) = transB ? B[n*ldb+k] : B[k*ldb+n].  8 warps, 2 x 4 warp grid of
+// 64 x 32 warp tiles; fragments per the m16n8k16 layout (row = lane/4,
+// k pair = 2*(lane%4)).
+template <int EPI>
+__global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 As[G_BM][G_BK + G_PAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[G_BN][G_BK + G_PAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int64_t m0 = (int64_t)blockIdx.y * G_BM;
+    const int n0 = blockIdx.x * G_BN;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int k0 = 0; k0 < g.K; k0 += G_BK) {
+#pragma unroll 4
+        for (int i = 0; i < (G_BM * G_BK) / G_THREADS; ++i) {
+            const int e = tid + i * G_THREADS;
+            int m, k;
+            if (g.transA) { m = e % G_BM; k = e / G_BM; } else { m = e / G_BK; k = e % G_BK; }
+            const int64_t gm = m0 + m;
+            const int gk = k0 + k;
+            __nv_bfloat16 v = zero;
+            if (gm < g.M && gk < g.K) v = g.transA ? g.A[(int64_t)gk * g.lda + gm] : g.A[gm * g.lda + gk];
+            As[m][k] = v;
+        }
+#pragma unroll 4
+        for (int i = 0; i < (G_BN * G_BK) / G_THREADS; ++i) {
+            const int e = tid + i * G_THREADS;
+            int n, k;
+            if (g.transB) { n = e / G_BK; k = e % G_BK; } else { n = e % G_BN; k = e / G_BN; }
+            const int gn = n0 + n, gk = k0 + k;
+            __nv_bfloat16 v = zero;
+            if (gn < g.N && gk < g.K) v = g.transB ? g.B[(int64_t)gn * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gn];
+            Bs[n][k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < G_BK; ks += 16) {
+            uint32_t af[4][4], bfr[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                const int r = wm * 64 + mt * 16 + gid;
+                af[mt][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
+                af[mt][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
+                af[mt][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
+                af[mt][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int cidx = wn * 32 + nt * 8 + gid;
+                bfr[nt][0] = *reinterpret_cast<const uint32_t*>(&Bs[cidx][ks + tig * 2]);
+                bfr[nt][1] = *reinterpret_cast<const uint32_t*>(&Bs[cidx][ks + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t m = m0 + wm * 64 + mt * 16 + gid + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn * 32 + nt * 8 + tig * 2 + (r & 1);
+                if (m >= g.M || n >= g.N) continue;
+                const float v = acc[mt][nt][r];
+                if constexpr (EPI == EPI_BIAS_GELU) {
+                    const float z = v + g.bias[n];
+                    if (g.Z) g.Z[m * g.ldz + n] = z;
+                    g.Cb[m * g.ldc + n] = __float2bfloat16_rn(gelu_f(z));
+                } else if constexpr (EPI == EPI_GELU_GRAD) {
+                    g.Cb[m * g.ldc + n] = __float2bfloat16_rn(v * gelu_grad_f(g.Z[m * g.ldz + n]));
+                } else {
+                    g.Cf[m * g.ldc + n] = v;
+                }
+            }
+        }
+    }
+}
+
+// y[m] = H[m,:] . w + b, one warp per row (256 bf16 = one 16-byte load per lane)
+__global__ void k_mlp_out(const __nv_bfloat16* H, const float* w, const float* b, int64_t M, float* y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += warps) {
+        const uint4 v = reinterpret_cast<const uint4*>(H + m * 256)[lane];
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(h[i]);
+            s += f.x * w[lane * 8 + 2 * i] + f.y * w[lane * 8 + 2 * i + 1];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) y[m] = s + b[0];
+    }
+}
+
+// dy = (y - t) / n; loss += 0.5 (y - t)^2 / n
+__global__ void k_loss(const float* y, const float* t, int n, float* dy, float* loss) {
+    float part = 0.0f;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        const float e = y[m] - t[m];
+        dy[m] = e / (float)n;
+        part += 0.5f * e * e / (float)n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part);
+}
+
+// dZ2[m,j] = dy[m] * w3[j] * gelu'(Z2[m,j])
+__global__ void k_dz2(const float* dy, const float* w3, const float* Z2, int64_t n, __nv_bfloat16* dZ2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * 256; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i >> 8;
+        const int j = (int)(i & 255);
+        dZ2[i] = __float2bfloat16_rn(dy[m] * w3[j] * gelu_grad_f(Z2[i]));
+    }
+}
+
+// out[j] = sum_m X[m, j] * (scale ? scale[m] : 1), X bf16 [n][cols]; one block per
+// 32 columns, threads stride over rows
+__global__ void k_colsum(const __nv_bfloat16* X, int64_t n, int cols, const float* scale, float* out) {
+    __shared__ float part[8][33];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int r0 = threadIdx.x >> 5;
+    float s = 0.0f;
+    if (c < cols)
+        for (int64_t m = r0; m < n; m += 8) s += __bfloat162float(X[m * cols + c]) * (scale ? scale[m] : 1.0f);
+    part[r0][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (r0 == 0 && c < cols) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += part[i][threadIdx.x & 31];
+        out[c] = t;
+    }
+}
+
+__global__ void k_sum(const float* v, int n, float* out) {
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += w[i];
+        *out = t;
+    }
+}
+
+// Adam on fp32 master parameters; refresh the bf16 copies of the GEMM weights
+__global__ void k_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2, __nv_bfloat16* w1b, __nv_bfloat16* w2b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (i < MLP_W1) w1b[i] = __float2bfloat16_rn(pi);
+        else if (i >= MLP_W2_OFF && i < MLP_W2_OFF + MLP_W2) w2b[i - MLP_W2_OFF] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void k_to_bf16(const float* p, int64_t n, __nv_bfloat16* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(p[i]);
+}
+
+int blocks_for(int64_t n, int t, int cap = 4096) {
+    int64_t b = (n + t - 1) / t;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+size_t features_smem_bytes() {
+    return (sizeof(uint32_t) + 1) * FEAT_SLOTS * FEAT_THREADS + (size_t)FEAT_CNT_STRIDE * FEAT_THREADS;
+}
+
+cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, int num_sms, cudaStream_t s) {
+    if (a.n_tours == 0) return cudaSuccess;
+    const size_t smem = features_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_features, FEAT_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    int grid = per_sm * num_sms;
+    const int want = (a.n_tours + FEAT_THREADS - 1) / FEAT_THREADS;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    k_features<<<grid, FEAT_THREADS, smem, s>>>(a, c, static_cast<uint4*>(X));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    const dim3 grid((g.N + G_BN - 1) / G_BN, (unsigned)((g.M + G_BM - 1) / G_BM));
+    if (grid.y > 65535u * 1024u) return cudaErrorInvalidValue;
+    if (epi == EPI_BIAS_GELU) k_gemm<EPI_BIAS_GELU><<<grid, G_THREADS, 0, s>>>(g);
+    else if (epi == EPI_GELU_GRAD) k_gemm<EPI_GELU_GRAD><<<grid, G_THREADS, 0, s>>>(g);
+    else k_gemm<EPI_F32><<<grid, G_THREADS, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    k_mlp_out<<<blocks_for(M * 32, 256, 8192), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(H), w, b, M, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, float* loss, const float* w3,
+                              const float* Z2, void* dZ2, cudaStream_t s) {
+    k_loss<<<blocks_for(n, 256, 1024), 256, 0, s>>>(y, t, n, dy, loss);
+    k_dz2<<<blocks_for((int64_t)n * 256, 256), 256, 0, s>>>(dy, w3, Z2, n, static_cast<__nv_bfloat16*>(dZ2));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s) {
+    k_colsum<<<(cols + 31) / 32, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(X), n, cols, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const float* v, int n, float* out, cudaStream_t s) {
+    k_sum<<<1, 1024, 0, s>>>(v, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr, int step, void* w1b,
+                        void* w2b, cudaStream_t s) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    k_adam<<<blocks_for(n, 256), 256, 0, s>>>(p, m, v, g, n, lr, b1, b2, 1e-8f, c1, c2,
+                                              static_cast<__nv_bfloat16*>(w1b), static_cast<__nv_bfloat16*>(w2b));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* p, int64_t n, void* out, cudaStream_t s) {
+    k_to_bf16<<<blocks_for(n, 256), 256, 0, s>>>(p, n, static_cast<__nv_bfloat16*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace wh

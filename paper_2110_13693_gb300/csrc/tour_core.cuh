@@ -4,6 +4,8 @@
 // Eq. (2)).  Included by each kernel translation unit; everything lives in an
 // unnamed namespace, so each unit gets its own copy.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "wh_internal.h"
 
 namespace wh {
@@ -339,6 +341,102 @@ __device__ __forceinline__ long long segmented_sum(long long v, int key, int lan
 }
 
 // ------------------------------------------------------------------ kernels
+
+// ------------------------------------------------------ surrogate features
+// 192 features of a tour (the surrogate's input): histograms over its
+// visited aisles of the deepest and shallowest pick's slot bin
+// floor(k*64/L), leftmost / rightmost aisle and aisle count times 1/A, line
+// count / 64, and a 60-bin histogram of the visited aisles floor(a*60/A).
+// Per-aisle extremes come from a per-thread open-addressing hash of the
+// visited aisles (no sort).  Bins use exact multiply-shift division:
+// floor(n/d) = (n * ceil(2^40/d)) >> 40 for n < 2^22 and d < 2^16.
+constexpr int FEAT_SLOTS = 128;        // hash slots per thread (distinct aisles per tour)
+constexpr int FEAT_CNT_STRIDE = 196;   // bytes per thread row of counters (49 words: no bank conflicts)
+
+struct FeatThread {
+    uint32_t* tab;      // [FEAT_SLOTS][T] entries ((a+1) << 16 | kmin << 8 | kmax), 0 = empty
+    uint8_t* list;      // [FEAT_SLOTS][T] occupied slot indices
+    uint8_t* cnt;       // this thread's FEAT_CNT_STRIDE counter bytes
+    int T;
+    int n_aisles;       // occupied slots
+    int n_lines;
+    bool overflow;
+};
+
+__device__ __forceinline__ void feat_insert(FeatThread& f, uint32_t key32) {
+    const uint32_t a = key32 >> 16, k = key32 & 0xFFu;
+    ++f.n_lines;
+    uint32_t h = (a * 2654435761u) >> 25;   // 7 bits
+    for (int probe = 0; probe < FEAT_SLOTS; ++probe) {
+        uint32_t* e = f.tab + h * f.T;
+        const uint32_t v = *e;
+        if (v == 0) {
+            *e = ((a + 1) << 16) | (k << 8) | k;
+            f.list[f.n_aisles * f.T] = (uint8_t)h;
+            ++f.n_aisles;
+            return;
+        }
+        if ((v >> 16) == a + 1) {
+            const uint32_t lo = min((v >> 8) & 0xFFu, k), hi = max(v & 0xFFu, k);
+            *e = ((a + 1) << 16) | (lo << 8) | hi;
+            return;
+        }
+        h = (h + 1) & (FEAT_SLOTS - 1);
+    }
+    f.overflow = true;
+}
+
+__device__ __forceinline__ uint32_t feat_div(uint32_t n, uint64_t magic) {
+    return (uint32_t)(((uint64_t)n * magic) >> 40);
+}
+
+// Write the tour's 192 bf16 features to row (16-byte aligned) and leave the
+// thread's hash table and counters zeroed for the next tour.
+__device__ __forceinline__ void feat_finish(FeatThread& f, const FeatConst& c, uint4* row) {
+    int amin = 0x7fffffff, amax = -1;
+    for (int j = 0; j < f.n_aisles; ++j) {
+        const uint32_t h = f.list[j * f.T];
+        uint32_t* e = f.tab + h * f.T;
+        const uint32_t v = *e;
+        *e = 0;
+        const int a = (int)(v >> 16) - 1;
+        const uint32_t lo = (v >> 8) & 0xFFu, hi = v & 0xFFu;
+        f.cnt[feat_div(hi * 64u, c.magic_l)] += 1;
+        f.cnt[64 + feat_div(lo * 64u, c.magic_l)] += 1;
+        f.cnt[132 + feat_div((uint32_t)a * 60u, c.magic_a)] += 1;
+        amin = min(amin, a);
+        amax = max(amax, a);
+    }
+    const float sc[4] = {f.n_aisles ? (float)amin * c.inv_a : 0.0f, f.n_aisles ? (float)amax * c.inv_a : 0.0f,
+                         (float)f.n_aisles * c.inv_a, (float)f.n_lines * (1.0f / 64.0f)};
+    uint32_t* words = reinterpret_cast<uint32_t*>(f.cnt);
+#pragma unroll 4
+    for (int q = 0; q < 24; ++q) {          // 8 features per 16-byte store
+        const uint32_t w0 = words[2 * q], w1 = words[2 * q + 1];
+        words[2 * q] = 0;
+        words[2 * q + 1] = 0;
+        float v[8];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            v[b] = (float)((w0 >> (8 * b)) & 0xFFu);
+            v[4 + b] = (float)((w1 >> (8 * b)) & 0xFFu);
+        }
+        if (q == 16) {                       // features 128..135: the four scalars, then counters
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v[b] = sc[b];
+        }
+        uint4 o;
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+        o.x = *reinterpret_cast<uint32_t*>(&p0);
+        o.y = *reinterpret_cast<uint32_t*>(&p1);
+        o.z = *reinterpret_cast<uint32_t*>(&p2);
+        o.w = *reinterpret_cast<uint32_t*>(&p3);
+        row[q] = o;
+    }
+    f.n_aisles = 0;
+    f.n_lines = 0;
+}
 
 }  // namespace
 }  // namespace wh

@@ -384,6 +384,41 @@ extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans
     return wh::launch_ls_apply(L, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
+extern "C" int wh_surrogate_features(wh_layout* h, const wh_orders* orders, const wh_plans* plans, uint16_t* X,
+                                     void* stream) {
+    if (!h || !orders || !plans) return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
+    if (h->g.L > 256) return WH_ERANGE;
+    if (p.n_plans == 0 || p.n_tours == 0) return WH_OK;
+    if (!X) return WH_EINVAL;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    wh::EvalArgs a;
+    wh_costs none;
+    std::memset(&none, 0, sizeof(none));
+    fill_args(a, h->g, o, p, none, WH_ROUTE_OPTIMAL);
+    a.status = h->meta;
+    a.long_count = reinterpret_cast<int32_t*>(h->meta + 1);
+    const bool shared_map = p.slot_map_stride == 0;
+    if (shared_map && o.n_lines > 0) {
+        rc = reserve_scratch(h, align_up(sizeof(uint32_t) * (size_t)o.n_lines) + kAlign);
+        if (rc != WH_OK) return rc;
+        a.line_key = static_cast<uint32_t*>(h->scratch);
+        if (wh::launch_prep(a, s) != cudaSuccess) return WH_ECUDA;
+    }
+    wh::FeatConst c;
+    c.A = h->g.A;
+    c.L = h->g.L;
+    c.magic_a = (((uint64_t)1 << 40) + (uint64_t)h->g.A - 1) / (uint64_t)h->g.A;
+    c.magic_l = (((uint64_t)1 << 40) + (uint64_t)h->g.L - 1) / (uint64_t)h->g.L;
+    c.inv_a = (float)(1.0 / (double)h->g.A);
+    return wh::launch_features(a, c, X, h->num_sms, s) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {
     if (!h || !status) return WH_EINVAL;
     if (h->device < 0) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the C-ABI host code and the kernels.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/wh.h"
@@ -111,6 +112,52 @@ struct LsArgs {
 cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s);
 cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s);
 cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s);
+
+// Surrogate (k_surrogate.cu).  Packed parameter vector: w1 [192][256],
+// b1 [256], w2 [256][256], b2 [256], w3 [256], b3 [1].
+constexpr int64_t MLP_W1 = 192 * 256;
+constexpr int64_t MLP_B1_OFF = MLP_W1;
+constexpr int64_t MLP_W2_OFF = MLP_B1_OFF + 256;
+constexpr int64_t MLP_W2 = 256 * 256;
+constexpr int64_t MLP_B2_OFF = MLP_W2_OFF + MLP_W2;
+constexpr int64_t MLP_W3_OFF = MLP_B2_OFF + 256;
+constexpr int64_t MLP_B3_OFF = MLP_W3_OFF + 256;
+constexpr int64_t MLP_NPARAM = MLP_B3_OFF + 1;
+
+struct GemmArgs {
+    int64_t M;
+    int N, K;
+    const __nv_bfloat16* A;
+    int64_t lda;
+    int transA;
+    const __nv_bfloat16* B;
+    int64_t ldb;
+    int transB;
+    const float* bias;
+    float* Z;
+    int64_t ldz;
+    __nv_bfloat16* Cb;
+    float* Cf;
+    int64_t ldc;
+};
+
+struct FeatConst {
+    int32_t A, L;
+    uint64_t magic_a;   // ceil(2^40 / A)
+    uint64_t magic_l;   // ceil(2^40 / L)
+    float inv_a;        // (float)(1.0 / A)
+};
+size_t features_smem_bytes();
+cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, int num_sms, cudaStream_t s);
+cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 0 bias+GELU, 1 fp32, 2 GELU grad
+cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s);
+cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, float* loss, const float* w3,
+                              const float* Z2, void* dZ2, cudaStream_t s);
+cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s);
+cudaError_t launch_sum(const float* v, int n, float* out, cudaStream_t s);
+cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr, int step, void* w1b,
+                        void* w2b, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* p, int64_t n, void* out, cudaStream_t s);
 
 struct Tuning {
     int threads;          // CTA size: 32 tours in flight per warp

@@ -1,0 +1,248 @@
+// C-ABI of the surrogate MLP (declared in include/wh.h): parameters, Adam
+// state and activation scratch on the device; prediction and training steps
+// enqueued on the caller's stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "wh_internal.h"
+
+struct wh_surrogate {
+    int device = -1;
+    float* P = nullptr;    // fp32 master parameters [MLP_NPARAM]
+    float* Mo = nullptr;   // Adam first moment
+    float* Ve = nullptr;   // Adam second moment
+    float* G = nullptr;    // last gradients
+    __nv_bfloat16* w1b = nullptr;
+    __nv_bfloat16* w2b = nullptr;
+    int step = 0;
+    int64_t cap = 0;       // rows of training scratch
+    float *Z1 = nullptr, *Z2 = nullptr, *y = nullptr, *dy = nullptr, *loss = nullptr;
+    __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    int64_t icap = 0;      // rows of inference scratch
+    __nv_bfloat16 *iH1 = nullptr, *iH2 = nullptr;
+};
+
+namespace {
+
+constexpr int64_t kInferChunk = 1 << 18;
+
+// SplitMix64 (Steele, Lea & Flood 2014)
+uint64_t sm64(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void free_all(wh_surrogate* s) {
+    void* ptrs[] = {s->P, s->Mo, s->Ve, s->G, s->w1b, s->w2b, s->Z1, s->Z2, s->y, s->dy, s->loss,
+                    s->H1, s->H2, s->dZ2, s->dZ1, s->iH1, s->iH2};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int upload_params(wh_surrogate* s, const float* host) {
+    if (cudaMemcpy(s->P, host, sizeof(float) * wh::MLP_NPARAM, cudaMemcpyHostToDevice) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_to_bf16(s->P, wh::MLP_W1, s->w1b, nullptr) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_to_bf16(s->P + wh::MLP_W2_OFF, wh::MLP_W2, s->w2b, nullptr) != cudaSuccess) return WH_ECUDA;
+    return cudaDeviceSynchronize() == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
+template <typename T>
+int dalloc(T** p, size_t n) {
+    if (cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return WH_ENOMEM;
+    }
+    return WH_OK;
+}
+
+int reserve_train(wh_surrogate* s, int64_t n) {
+    if (n <= s->cap) return WH_OK;
+    void* old[] = {s->Z1, s->Z2, s->y, s->dy, s->H1, s->H2, s->dZ2, s->dZ1};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    s->cap = 0;
+    const size_t r = (size_t)n;
+    if (dalloc(&s->Z1, r * 256) || dalloc(&s->Z2, r * 256) || dalloc(&s->y, r) || dalloc(&s->dy, r) ||
+        dalloc(&s->H1, r * 256) || dalloc(&s->H2, r * 256) || dalloc(&s->dZ2, r * 256) || dalloc(&s->dZ1, r * 256))
+        return WH_ENOMEM;
+    s->cap = n;
+    return WH_OK;
+}
+
+wh::GemmArgs gemm(int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda, int ta, const __nv_bfloat16* B,
+                  int64_t ldb, int tb) {
+    wh::GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A;
+    g.lda = lda;
+    g.transA = ta;
+    g.B = B;
+    g.ldb = ldb;
+    g.transB = tb;
+    return g;
+}
+
+// forward of rows [0, n) into H1/H2 (bf16) and y; Z1/Z2 saved when given
+int forward(wh_surrogate* s, const __nv_bfloat16* X, int64_t n, __nv_bfloat16* H1, __nv_bfloat16* H2, float* Z1,
+            float* Z2, float* y, cudaStream_t st) {
+    wh::GemmArgs g1 = gemm(n, 256, 192, X, 192, 0, s->w1b, 256, 0);
+    g1.bias = s->P + wh::MLP_B1_OFF;
+    g1.Z = Z1;
+    g1.ldz = 256;
+    g1.Cb = H1;
+    g1.ldc = 256;
+    if (wh::launch_gemm(g1, 0, st) != cudaSuccess) return WH_ECUDA;
+    wh::GemmArgs g2 = gemm(n, 256, 256, H1, 256, 0, s->w2b, 256, 0);
+    g2.bias = s->P + wh::MLP_B2_OFF;
+    g2.Z = Z2;
+    g2.ldz = 256;
+    g2.Cb = H2;
+    g2.ldc = 256;
+    if (wh::launch_gemm(g2, 0, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_mlp_out(H2, s->P + wh::MLP_W3_OFF, s->P + wh::MLP_B3_OFF, n, y, st) != cudaSuccess)
+        return WH_ECUDA;
+    return WH_OK;
+}
+
+}  // namespace
+
+extern "C" int wh_surrogate_create(uint64_t seed, wh_surrogate** out) {
+    if (!out) return WH_EINVAL;
+    wh_surrogate* s = new (std::nothrow) wh_surrogate;
+    if (!s) return WH_ENOMEM;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return WH_ECUDA;
+    }
+    if (dalloc(&s->P, wh::MLP_NPARAM) || dalloc(&s->Mo, wh::MLP_NPARAM) || dalloc(&s->Ve, wh::MLP_NPARAM) ||
+        dalloc(&s->G, wh::MLP_NPARAM) || dalloc(&s->w1b, wh::MLP_W1) || dalloc(&s->w2b, wh::MLP_W2) ||
+        dalloc(&s->loss, 1)) {
+        free_all(s);
+        delete s;
+        return WH_ENOMEM;
+    }
+    // Xavier-uniform weights, zero biases
+    std::vector<float> h(wh::MLP_NPARAM, 0.0f);
+    uint64_t st = seed ^ 0x6A09E667F3BCC909ull;
+    auto fill = [&](int64_t off, int64_t n, int fan_in, int fan_out) {
+        const double bound = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int64_t i = 0; i < n; ++i) {
+            const double u = (double)(sm64(st) >> 11) * (1.0 / 9007199254740992.0);
+            h[off + i] = (float)((2.0 * u - 1.0) * bound);
+        }
+    };
+    fill(0, wh::MLP_W1, 192, 256);
+    fill(wh::MLP_W2_OFF, wh::MLP_W2, 256, 256);
+    fill(wh::MLP_W3_OFF, 256, 256, 1);
+    int rc = upload_params(s, h.data());
+    if (rc == WH_OK && (cudaMemset(s->Mo, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
+                        cudaMemset(s->Ve, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
+                        cudaMemset(s->G, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess))
+        rc = WH_ECUDA;
+    if (rc != WH_OK) {
+        free_all(s);
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return WH_OK;
+}
+
+extern "C" int wh_surrogate_set_params(wh_surrogate* s, const float* host_params) {
+    if (!s || !host_params) return WH_EINVAL;
+    int rc = upload_params(s, host_params);
+    if (rc != WH_OK) return rc;
+    s->step = 0;
+    if (cudaMemset(s->Mo, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
+        cudaMemset(s->Ve, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess)
+        return WH_ECUDA;
+    return WH_OK;
+}
+
+extern "C" int wh_surrogate_get_params(wh_surrogate* s, float* host_params, float* host_grads) {
+    if (!s || (!host_params && !host_grads)) return WH_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return WH_ECUDA;
+    if (host_params &&
+        cudaMemcpy(host_params, s->P, sizeof(float) * wh::MLP_NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return WH_ECUDA;
+    if (host_grads && cudaMemcpy(host_grads, s->G, sizeof(float) * wh::MLP_NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return WH_ECUDA;
+    return WH_OK;
+}
+
+extern "C" int wh_surrogate_predict(wh_surrogate* s, const uint16_t* X, int64_t n, float* y, void* stream) {
+    if (!s || n < 0 || (n > 0 && (!X || !y))) return WH_EINVAL;
+    if (n == 0) return WH_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t chunk = n < kInferChunk ? n : kInferChunk;
+    if (chunk > s->icap) {
+        if (s->iH1) cudaFree(s->iH1);
+        if (s->iH2) cudaFree(s->iH2);
+        s->iH1 = s->iH2 = nullptr;
+        s->icap = 0;
+        if (dalloc(&s->iH1, (size_t)chunk * 256) || dalloc(&s->iH2, (size_t)chunk * 256)) return WH_ENOMEM;
+        s->icap = chunk;
+    }
+    const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
+    for (int64_t r = 0; r < n; r += chunk) {
+        const int64_t m = n - r < chunk ? n - r : chunk;
+        const int rc = forward(s, Xb + r * 192, m, s->iH1, s->iH2, nullptr, nullptr, y + r, st);
+        if (rc != WH_OK) return rc;
+    }
+    return WH_OK;
+}
+
+extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const float* target, int32_t n, float lr,
+                                       float* loss_out, void* stream) {
+    if (!s || n < 1 || !X || !target || !(lr > 0.0f)) return WH_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = reserve_train(s, n);
+    if (rc != WH_OK) return rc;
+    const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
+    rc = forward(s, Xb, n, s->H1, s->H2, s->Z1, s->Z2, s->y, st);
+    if (rc != WH_OK) return rc;
+    if (cudaMemsetAsync(s->loss, 0, sizeof(float), st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_train_tail(s->y, target, n, s->dy, s->loss, s->P + wh::MLP_W3_OFF, s->Z2, s->dZ2, st) !=
+        cudaSuccess)
+        return WH_ECUDA;
+    // output layer
+    if (wh::launch_colsum(s->H2, n, 256, s->dy, s->G + wh::MLP_W3_OFF, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_sum(s->dy, n, s->G + wh::MLP_B3_OFF, st) != cudaSuccess) return WH_ECUDA;
+    // layer 2: dW2 = H1^T dZ2, db2 = colsum dZ2, dZ1 = (dZ2 W2^T) * gelu'(Z1)
+    if (wh::launch_colsum(s->dZ2, n, 256, nullptr, s->G + wh::MLP_B2_OFF, st) != cudaSuccess) return WH_ECUDA;
+    wh::GemmArgs gw2 = gemm(256, 256, n, s->H1, 256, 1, s->dZ2, 256, 0);
+    gw2.Cf = s->G + wh::MLP_W2_OFF;
+    gw2.ldc = 256;
+    if (wh::launch_gemm(gw2, 1, st) != cudaSuccess) return WH_ECUDA;
+    wh::GemmArgs gd1 = gemm(n, 256, 256, s->dZ2, 256, 0, s->w2b, 256, 1);
+    gd1.Z = s->Z1;
+    gd1.ldz = 256;
+    gd1.Cb = s->dZ1;
+    gd1.ldc = 256;
+    if (wh::launch_gemm(gd1, 2, st) != cudaSuccess) return WH_ECUDA;
+    // layer 1: dW1 = X^T dZ1, db1 = colsum dZ1
+    if (wh::launch_colsum(s->dZ1, n, 256, nullptr, s->G + wh::MLP_B1_OFF, st) != cudaSuccess) return WH_ECUDA;
+    wh::GemmArgs gw1 = gemm(192, 256, n, Xb, 192, 1, s->dZ1, 256, 0);
+    gw1.Cf = s->G;
+    gw1.ldc = 256;
+    if (wh::launch_gemm(gw1, 1, st) != cudaSuccess) return WH_ECUDA;
+    s->step += 1;
+    if (wh::launch_adam(s->P, s->Mo, s->Ve, s->G, wh::MLP_NPARAM, lr, s->step, s->w1b, s->w2b, st) != cudaSuccess)
+        return WH_ECUDA;
+    if (loss_out && cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return WH_ECUDA;
+    return WH_OK;
+}
+
+extern "C" void wh_surrogate_destroy(wh_surrogate* s) {
+    if (!s) return;
+    free_all(s);
+    delete s;
+}

@@ -1,0 +1,130 @@
+"""Surrogate on the GPU against the oracle: features bit-exact, forward and
+one training step (loss, every gradient, the Adam update) within bf16
+tolerance, and training that actually reduces the error."""
+import numpy as np
+import pytest
+
+import oracle
+import wh_gen
+
+pytestmark = pytest.mark.gpu
+
+
+def tour_locs(inst, t, smap):
+    locs = []
+    for o in inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]:
+        locs.extend(smap[inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]]].tolist())
+    return locs
+
+
+def gpu_features(wh, inst, maps=None):
+    import torch
+    lay = wh.Layout.of(inst.layout)
+    prob = wh.to_device(inst, slot_map=None if maps is None else maps.ravel(),
+                        slot_map_stride=0 if maps is None else inst.n_sku)
+    X = wh.features(lay, prob)
+    torch.cuda.synchronize()
+    assert lay.status() == 0
+    lay.close()
+    return X
+
+
+@pytest.mark.parametrize("which", ["tiny", "midsize", "paperscale", "paperscale_maps"])
+def test_features_bit_exact(gpu_lib, which):
+    import torch
+    if which == "tiny":
+        inst, maps = wh_gen.tiny(seed=1, n_plans=6), None
+    elif which == "midsize":
+        inst, maps = wh_gen.midsize(seed=2, n_plans=6), None
+    else:
+        inst = wh_gen.paperscale(seed=3, n_plans=2)
+        rng = np.random.default_rng(0)
+        maps = None if which == "paperscale" else np.stack(
+            [rng.permutation(inst.layout.n_loc)[: inst.n_sku] for _ in range(2)]).astype(np.int32)
+    X = gpu_features(gpu_lib, inst, maps).view(torch.int16).cpu().numpy()
+    for t in range(inst.n_tours):
+        plan = int(np.searchsorted(inst.plan_tour_off, t, side="right") - 1)
+        smap = inst.slot_map if maps is None else maps[plan]
+        want = oracle.bf16(oracle.features(inst.layout, tour_locs(inst, t, smap)))
+        want_bits = torch.from_numpy(want).to(torch.bfloat16).view(torch.int16).numpy()
+        assert np.array_equal(X[t], want_bits), f"tour {t}"
+
+
+def bf16_params(seed, scale=0.06):
+    rng = np.random.default_rng(seed)
+    d = {"w1": rng.normal(size=(192, 256)) * scale, "b1": rng.normal(size=256) * 0.05,
+         "w2": rng.normal(size=(256, 256)) * scale, "b2": rng.normal(size=256) * 0.05,
+         "w3": rng.normal(size=256) * scale, "b3": rng.normal(size=1) * 0.05}
+    return {k: oracle.bf16(v.astype(np.float32)) for k, v in d.items()}
+
+
+def batch(wh, n_plans=12):
+    """Features (bf16, device) and normalised optimal costs of mid-size tours."""
+    import torch
+    inst = wh_gen.midsize(seed=4, n_plans=n_plans)
+    X = gpu_features(wh, inst)
+    _, tr, _, _ = oracle.eval_plans(inst)
+    lay = inst.layout
+    norm = 2 * (lay.n_aisles - 1) * lay.aisle_pitch + lay.n_aisles * (
+        lay.cross_aisle_width + (lay.slots_per_side - 1) * lay.slot_pitch)
+    return X, torch.as_tensor(tr / norm, dtype=torch.float32).cuda()
+
+
+def test_predict_matches_oracle(gpu_lib):
+    wh = gpu_lib
+    X, _ = batch(wh)
+    p = bf16_params(1)
+    s = wh.Surrogate(0)
+    s.set_params(wh.pack_params(p))
+    y = s.predict(X).cpu().numpy()
+    want = oracle.mlp_forward(p, X.float().cpu().numpy())
+    scale = np.abs(want).mean()
+    assert np.abs(y - want).max() <= 1e-2 * scale + 1e-4
+    s.close()
+
+
+def test_train_step_matches_oracle(gpu_lib):
+    import torch
+    wh = gpu_lib
+    X, t = batch(wh)
+    X, t = X[:1024].contiguous(), t[:1024].contiguous()
+    p = bf16_params(2)
+    s = wh.Surrogate(0)
+    p0 = wh.pack_params(p)
+    s.set_params(p0)
+    loss = s.train_step(X, t, 1e-3)
+    torch.cuda.synchronize()
+    p1, g = s.params()
+    Xh = X.float().cpu().numpy()
+    want_loss, want_g = oracle.mlp_backward(p, Xh, t.cpu().numpy().astype(np.float64))
+    assert abs(loss.item() - want_loss) <= 1e-3 * want_loss + 1e-7
+    got = wh.unpack_params(g)
+    for k in want_g:
+        err = np.linalg.norm(got[k].astype(np.float64) - want_g[k]) / (np.linalg.norm(want_g[k]) + 1e-30)
+        assert err < 3e-2, f"gradient {k}: relative error {err:.3g}"
+    # Adam: the device step equals the oracle's step on the device's own gradients
+    q = p0.astype(np.float64)
+    m, v = np.zeros_like(q), np.zeros_like(q)
+    oracle.adam(q, m, v, g.astype(np.float64), 1e-3, 1)
+    np.testing.assert_allclose(p1, q, rtol=1e-5, atol=2e-7)
+    s.close()
+
+
+def test_training_reduces_error(gpu_lib):
+    import torch
+    wh = gpu_lib
+    X, t = batch(wh, n_plans=96)
+    n = X.shape[0]
+    idx = torch.randperm(n, generator=torch.Generator().manual_seed(0)).cuda()
+    train, held = idx[: n - 2000], idx[n - 2000:]
+    s = wh.Surrogate(7)
+    err0 = ((s.predict(X[held]) - t[held]).abs() / t[held].clamp_min(1e-6)).mean().item()
+    g = torch.Generator(device="cuda").manual_seed(1)
+    for step in range(400):
+        b = train[torch.randint(0, train.numel(), (2048,), device="cuda", generator=g)]
+        s.train_step(X[b].contiguous(), t[b].contiguous(), 2e-3)
+    torch.cuda.synchronize()
+    rel = ((s.predict(X[held]) - t[held]).abs() / t[held].clamp_min(1e-6))
+    err1 = rel.mean().item()
+    assert err1 < 0.5 * err0 and err1 < 0.15, (err0, err1)
+    s.close()
