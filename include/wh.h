@@ -181,14 +181,18 @@ int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * pointers of `plans` are written): an order swap exchanges two entries of
  * order_seq; a relocation removes the order from its tour and appends it to
  * the end of the target tour, shifting order_seq and tour_off between them; a
- * SKU swap exchanges two entries of the plan's slotting.  Tour costs are not
- * refreshed: call wh_eval_plans afterwards.  Each plan's segment of order_seq
+ * SKU swap exchanges two entries of the plan's slotting.  costs (may be NULL):
+ * the plans' current per-tour and per-plan costs, updated in place for the
+ * applied moves from the new tour costs that the wh_eval_moves call which
+ * scored exactly these moves (same `moves` pointer, the last move evaluation
+ * on this handle) computed -- no full re-evaluation is needed; when NULL the
+ * costs are left stale (refresh them with wh_eval_plans).  Each plan's segment of order_seq
  * may hold at most max(n_orders, 1) entries (WH_STATUS_BAD_OFFSET otherwise,
  * and that plan is left unchanged).  Returns WH_OK, WH_EINVAL, WH_ERANGE
  * (n_orders beyond 50,000: the staging buffer) or WH_ECUDA. */
 int wh_ls_apply(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *moves,
                 int32_t moves_per_plan, const int64_t *delta, const int32_t *status, int32_t *applied,
-                void *stream);
+                const wh_costs *costs, void *stream);
 
 /* ------------------------------------------------------------------------
  * Learned prescreen (machine learning in the decision loop, Sec. 1 and
@@ -236,6 +240,19 @@ int wh_surrogate_predict(wh_surrogate *s, const uint16_t *X, int64_t n, float *y
  * NULL) receives the loss before the step.  Allocates scratch when n grows. */
 int wh_surrogate_train_step(wh_surrogate *s, const uint16_t *X, const float *target, int32_t n, float lr,
                             float *loss_out, void *stream);
+
+/* Prescreen of local-search moves: for plan p's moves [p*moves_per_plan,
+ * (p+1)*moves_per_plan) the surrogate predicts each move's change of the
+ * plan's optimal cost (sum over the tours the move changes of predicted new
+ * minus predicted current length) and keeps the `keep` moves with the lowest
+ * prediction (ties: lowest index) in kept[(p*keep + j)*4 .. +3]; places
+ * without an eligible move get {9, 0, 0, p}, which wh_eval_moves reports as
+ * invalid.  Score the kept moves exactly with wh_eval_moves.  Synchronises
+ * `stream` once; may allocate scratch.  Returns WH_OK, WH_EINVAL, WH_ERANGE,
+ * WH_ENOMEM or WH_ECUDA. */
+int wh_surrogate_screen(wh_layout *layout, wh_surrogate *s, const wh_orders *orders, const wh_plans *plans,
+                        const int32_t *moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders_per_tour,
+                        int32_t max_lines_per_tour, int32_t *kept, void *stream);
 
 void wh_surrogate_destroy(wh_surrogate *s);
 

@@ -365,9 +365,10 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
             }
         }
         bool run = active && ok && primary;
+        bool deferred = false;
         if (run && n > SHORT_MAX) {
             const int slot = atomicAdd(M.long_count, 1);
-            if (slot < M.long_cap) M.long_list[slot] = (int32_t)i;
+            if (slot < M.long_cap) { M.long_list[slot] = (int32_t)i; deferred = true; }
             else { flag(a.status, WH_STATUS_LONG_OVERFLOW); M.mstatus[tk.x] = 3; }
             run = false;
         }
@@ -388,6 +389,8 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
             ds = (long long)cs - M.tour_s_old[tk.y];
             dr = (long long)cr - M.tour_rr_old[tk.y];
         }
+        if (active && !deferred)   // deferred tasks: k_mv_long writes
+            M.task_cost[i] = run ? make_int2(cs, cr) : make_int2(-1, -1);
         const int key = active ? tk.x : -1;
         const long long ss = segmented_sum(ds, key, lane);
         const long long sr = segmented_sum(dr, key, lane);
@@ -425,6 +428,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
             if (lane == 0) {
                 flag(a.status, n > LONG_MAXL ? WH_STATUS_TOUR_TOO_LONG : WH_STATUS_BAD_ORDER);
                 M.mstatus[tk.x] = 3;
+                M.task_cost[i] = make_int2(-1, -1);
             }
             __syncwarp();
             continue;
@@ -466,8 +470,10 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
                     last_hi = k;
                 }
             }
-            const long long ds = (long long)sshape_cost(a.g, m, last_a, last_hi) - M.tour_s_old[tk.y];
-            const long long dr = (long long)dp_final(v) - M.tour_rr_old[tk.y];
+            const int cs = sshape_cost(a.g, m, last_a, last_hi), cr = dp_final(v);
+            M.task_cost[i] = make_int2(cs, cr);
+            const long long ds = (long long)cs - M.tour_s_old[tk.y];
+            const long long dr = (long long)cr - M.tour_rr_old[tk.y];
             atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x]), (unsigned long long)ds);
             atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x + 1]), (unsigned long long)dr);
         }
@@ -516,6 +522,11 @@ cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s) {
 size_t moves_eval_smem_bytes(bool k16, int max_rec) {
     const size_t slots = max_rec > SHORT_MAX / 2 ? (size_t)max_rec : (size_t)(SHORT_MAX / 2);
     return (k16 ? sizeof(uint32_t) : sizeof(uint2)) * slots * MV_THREADS;
+}
+
+cudaError_t launch_moves_fill(const MoveArgs& M, cudaStream_t s) {
+    if (M.n_moves > 0) k_mv_fill<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s) {
@@ -624,12 +635,130 @@ __global__ void k_ls_apply(LsArgs L) {
                 smap[mv.y] = smap[mv.z];
                 smap[mv.z] = x;
             }
+            // costs: the changed tours take their tasks' new costs, the plan its delta
+            if (L.task_cost && L.applied[p] == k) {
+                const int64_t m = (int64_t)p * L.moves_per_plan + k;
+                for (int64_t i = L.task_off[m] + tid; i < L.task_off[m + 1]; i += T) {
+                    const int2 c = L.task_cost[i];
+                    if (c.x < 0) continue;
+                    const int t = L.tasks[i].y;
+                    if (L.tour_s) L.tour_s[t] = c.x;
+                    if (L.tour_rr) L.tour_rr[t] = c.y;
+                }
+                if (tid == 0) {
+                    if (L.plan_s) L.plan_s[p] += L.delta[2 * m];
+                    if (L.plan_rr) L.plan_rr[p] += L.delta[2 * m + 1];
+                }
+            }
         }
         __syncthreads();
     }
 }
 
+// Features of every task's changed tour (rows of non-counted tasks are
+// written too and ignored by the selection).
+__global__ void __launch_bounds__(128) k_task_features(MoveArgs M, FeatConst c, uint4* X) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    FeatThread f;
+    f.tab = reinterpret_cast<uint32_t*>(smem) + tid;
+    f.list = smem + sizeof(uint32_t) * FEAT_SLOTS * T + tid;
+    f.cnt = smem + (sizeof(uint32_t) + 1) * FEAT_SLOTS * T + (size_t)tid * FEAT_CNT_STRIDE;
+    f.T = T;
+    f.n_aisles = 0;
+    f.n_lines = 0;
+    f.overflow = false;
+    for (int i = 0; i < FEAT_SLOTS; ++i) f.tab[i * T] = 0;
+    for (int i = 0; i < FEAT_CNT_STRIDE / 4; ++i) reinterpret_cast<uint32_t*>(f.cnt)[i] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * T + tid; i < M.n_tasks; i += (int64_t)gridDim.x * T) {
+        const int4 tk = M.tasks[i];
+        bool primary = false, ok = false;
+        if (tk.y >= 0 && tk.y < M.a.n_tours) {
+            const int4 mv = M.moves[tk.x];
+            ok = walk_task(M, tk, mv, primary, [&](uint32_t key) { feat_insert(f, key); });
+        }
+        // mark the tasks that count (one per changed tour) for the selection
+        M.task_cost[i] = (ok && primary && !f.overflow) ? make_int2(0, 0) : make_int2(-1, -1);
+        f.overflow = false;
+        feat_finish(f, c, X + i * 24);
+    }
+}
+
+// Predicted delta of every move (sum over its counted tasks, in order), then
+// per plan the `keep` moves with the lowest predicted delta (ties: lowest
+// index); unfilled places get an invalid move that scores status 3.
+__global__ void k_screen_score(ScreenArgs S) {
+    const MoveArgs& M = S.M;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M.n_moves; m += gridDim.x * blockDim.x) {
+        float sc = 3.0e38f;
+        if (M.mstatus[m] == 0) {
+            sc = 0.0f;
+            for (int64_t i = M.task_off[m]; i < M.task_off[m + 1]; ++i) {
+                const int4 tk = M.tasks[i];
+                if (tk.y < 0) continue;
+                // counted task: an order move, or the first task of its tour for a SKU swap
+                const int2 c = M.task_cost[i];
+                if (c.x < 0) continue;
+                sc += S.y_task[i] - S.y_tour[tk.y];
+            }
+        }
+        S.score[m] = sc;
+    }
+}
+
+__global__ void k_screen_select(ScreenArgs S) {
+    const int lane = threadIdx.x & 31;
+    const int n_plans = S.M.a.n_plans;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_plans; p += warps) {
+        uint32_t taken[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // up to 256 moves per plan
+        for (int j = 0; j < S.keep; ++j) {
+            float best = 3.0e38f;
+            int bk = 0x7fffffff;
+            for (int k = lane; k < S.moves_per_plan; k += 32) {
+                if (taken[k >> 5] >> (k & 31) & 1u) continue;
+                const float v = S.score[p * S.moves_per_plan + k];
+                if (v < best || (v == best && k < bk)) { best = v; bk = k; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                if (ov < best || (ov == best && ok < bk)) { best = ov; bk = ok; }
+            }
+            int4 out = make_int4(9, 0, 0, (int)p);
+            if (best < 1.0e38f && bk < S.moves_per_plan) {
+                out = S.M.moves[p * S.moves_per_plan + bk];
+                taken[bk >> 5] |= 1u << (bk & 31);
+            }
+            if (lane == 0) S.kept[p * S.keep + j] = out;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_task_features(const MoveArgs& M, const FeatConst& c, void* X, int num_sms, cudaStream_t s) {
+    if (M.n_tasks == 0) return cudaSuccess;
+    const size_t smem = (sizeof(uint32_t) + 1) * FEAT_SLOTS * 128 + (size_t)FEAT_CNT_STRIDE * 128;
+    cudaError_t e = cudaFuncSetAttribute(k_task_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_task_features, 128, smem);
+    if (e != cudaSuccess) return e;
+    int64_t want = (M.n_tasks + 127) / 128;
+    int grid = per_sm * num_sms;
+    if (grid > want) grid = (int)want;
+    if (grid < 1) grid = 1;
+    k_task_features<<<grid, 128, smem, s>>>(M, c, static_cast<uint4*>(X));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_screen_select(const ScreenArgs& S, cudaStream_t s) {
+    k_screen_score<<<grid_of(S.M.n_moves, 256), 256, 0, s>>>(S);
+    k_screen_select<<<grid_of((int64_t)S.M.a.n_plans * 32, 256), 256, 0, s>>>(S);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s) {
     const size_t smem = sizeof(int32_t) * (size_t)L.seg_cap;

@@ -23,8 +23,16 @@ struct wh_layout {
     size_t scratch_bytes = 0;
     void* mv_scratch = nullptr;   // device: move-evaluation index structures
     size_t mv_scratch_bytes = 0;
-    void* mv_tasks = nullptr;     // device: move tasks + long-task list
+    void* mv_tasks = nullptr;     // device: move tasks + their costs + long-task list
     size_t mv_tasks_bytes = 0;
+    void* sr_scratch = nullptr;   // device: screening features and predictions
+    size_t sr_scratch_bytes = 0;
+    // the task list of the last wh_eval_moves call (for wh_ls_apply's cost update)
+    const int32_t* last_moves = nullptr;
+    int32_t last_n_moves = 0;
+    const int64_t* last_task_off = nullptr;
+    const int4* last_tasks = nullptr;
+    const int2* last_task_cost = nullptr;
     // kernel timing (wh_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> events;       // pool, reused across sessions
@@ -286,28 +294,18 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     return WH_OK;
 }
 
-extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* tour_s,
-                             const int32_t* tour_rr, const int32_t* moves, int32_t n_moves, int32_t max_orders,
-                             int32_t max_lines, int64_t* delta, int32_t* status, void* stream) {
-    if (!h || !orders || !plans || n_moves < 0 || max_orders < 0 || max_lines < 0) return WH_EINVAL;
-    const wh_orders o = *orders;
-    const wh_plans p = *plans;
-    int rc = check_problem(o, p);
-    if (rc != WH_OK) return rc;
-    if (n_moves == 0) return WH_OK;
-    if (!moves || !delta || !status || !tour_s || !tour_rr || p.n_plans < 1) return WH_EINVAL;
-    rc = bind_device(h);
-    if (rc != WH_OK) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace {
 
-    wh::MoveArgs M;
+// Scratch, index structures and the task list of a move evaluation (up to
+// and including the task fill).  Synchronises `s` once to size the list.
+int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int32_t* moves, int32_t n_moves,
+                  int32_t max_orders, int32_t max_lines, int64_t* delta, int32_t* status, wh::MoveArgs& M,
+                  cudaStream_t s) {
     std::memset(&M, 0, sizeof(M));
     wh_costs none;
     std::memset(&none, 0, sizeof(none));
     fill_args(M.a, h->g, o, p, none, WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL);
     M.a.status = h->meta;
-    M.tour_s_old = tour_s;
-    M.tour_rr_old = tour_rr;
     M.moves = reinterpret_cast<const int4*>(moves);
     M.n_moves = n_moves;
     M.max_orders = max_orders;
@@ -318,16 +316,16 @@ extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_pla
 
     const size_t n_ot = (size_t)p.n_plans * (size_t)o.n_orders;
     const size_t nb = ((size_t)n_moves + 1 + 1023) / 1024;
-    size_t off[8], total = 0;
-    const size_t sizes[8] = {sizeof(int32_t) * n_ot, sizeof(int32_t) * ((size_t)p.n_tours + 1),
+    size_t off[7], total = 0;
+    const size_t sizes[7] = {sizeof(int32_t) * n_ot, sizeof(int32_t) * ((size_t)p.n_tours + 1),
                              sizeof(int32_t) * ((size_t)o.n_sku + 1), sizeof(int32_t) * ((size_t)o.n_sku + 1),
                              sizeof(int32_t) * ((size_t)o.n_lines + 1), sizeof(int64_t) * ((size_t)n_moves + 1),
-                             sizeof(int64_t) * (nb + 1), 0};
-    for (int i = 0; i < 8; ++i) {
+                             sizeof(int64_t) * (nb + 1)};
+    for (int i = 0; i < 7; ++i) {
         off[i] = total;
         total += align_up(sizes[i]);
     }
-    rc = grow(&h->mv_scratch, &h->mv_scratch_bytes, total);
+    int rc = grow(&h->mv_scratch, &h->mv_scratch_bytes, total);
     if (rc != WH_OK) return rc;
     char* base = static_cast<char*>(h->mv_scratch);
     M.order_tour = reinterpret_cast<int32_t*>(base + off[0]);
@@ -347,18 +345,136 @@ extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_pla
     M.n_tasks = n_tasks;
     M.long_cap = (int32_t)std::min<int64_t>(n_tasks + 1, 0x7fffffff);
     const size_t task_bytes = align_up(sizeof(int4) * (size_t)(n_tasks + 1));
-    rc = grow(&h->mv_tasks, &h->mv_tasks_bytes, task_bytes + align_up(sizeof(int32_t) * (size_t)M.long_cap));
+    const size_t cost_bytes = align_up(sizeof(int2) * (size_t)(n_tasks + 1));
+    rc = grow(&h->mv_tasks, &h->mv_tasks_bytes, task_bytes + cost_bytes + align_up(sizeof(int32_t) * (size_t)M.long_cap));
     if (rc != WH_OK) return rc;
-    M.tasks = static_cast<int4*>(h->mv_tasks);
-    M.long_list = reinterpret_cast<int32_t*>(static_cast<char*>(h->mv_tasks) + task_bytes);
+    char* tb = static_cast<char*>(h->mv_tasks);
+    M.tasks = reinterpret_cast<int4*>(tb);
+    M.task_cost = reinterpret_cast<int2*>(tb + task_bytes);
+    M.long_list = reinterpret_cast<int32_t*>(tb + task_bytes + cost_bytes);
+    return WH_OK;
+}
+
+}  // namespace
+
+extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* tour_s,
+                             const int32_t* tour_rr, const int32_t* moves, int32_t n_moves, int32_t max_orders,
+                             int32_t max_lines, int64_t* delta, int32_t* status, void* stream) {
+    if (!h || !orders || !plans || n_moves < 0 || max_orders < 0 || max_lines < 0) return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
+    if (n_moves == 0) return WH_OK;
+    if (!moves || !delta || !status || !tour_s || !tour_rr || p.n_plans < 1) return WH_EINVAL;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last_moves = nullptr;
+    wh::MoveArgs M;
+    rc = prepare_moves(h, o, p, moves, n_moves, max_orders, max_lines, delta, status, M, s);
+    if (rc != WH_OK) return rc;
+    M.tour_s_old = tour_s;
+    M.tour_rr_old = tour_rr;
     const bool k16 = wh::key16_ok(h->g);
     if (wh::launch_moves_eval(M, k16, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    h->last_moves = moves;
+    h->last_n_moves = n_moves;
+    h->last_task_off = M.task_off;
+    h->last_tasks = M.tasks;
+    h->last_task_cost = M.task_cost;
     return WH_OK;
+}
+
+extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orders* orders, const wh_plans* plans,
+                                   const int32_t* moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders,
+                                   int32_t max_lines, int32_t* kept, void* stream) {
+    if (!h || !sg || !orders || !plans || !moves || !kept || moves_per_plan < 1 || moves_per_plan > 256 ||
+        keep < 1 || keep > moves_per_plan || max_orders < 0 || max_lines < 0)
+        return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
+    if (h->g.L > 256) return WH_ERANGE;
+    if (p.n_plans == 0) return WH_OK;
+    const int64_t n_moves64 = (int64_t)p.n_plans * moves_per_plan;
+    if (n_moves64 > 0x7fffffff) return WH_ERANGE;
+    const int32_t n_moves = (int32_t)n_moves64;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last_moves = nullptr;
+    // per-move status and the task list (into the screening scratch's delta/status)
+    const size_t feat_row = sizeof(uint16_t) * WH_FEATURES;
+    wh::MoveArgs M;
+    // status, delta and scores live in the screening scratch
+    const size_t head = align_up(sizeof(int32_t) * (size_t)n_moves) + align_up(sizeof(int64_t) * 2 * (size_t)n_moves) +
+                        align_up(sizeof(float) * (size_t)n_moves);
+    rc = grow(&h->sr_scratch, &h->sr_scratch_bytes, head);
+    if (rc != WH_OK) return rc;
+    {
+        char* b = static_cast<char*>(h->sr_scratch);
+        int32_t* st = reinterpret_cast<int32_t*>(b);
+        int64_t* dl = reinterpret_cast<int64_t*>(b + align_up(sizeof(int32_t) * (size_t)n_moves));
+        rc = prepare_moves(h, o, p, moves, n_moves, max_orders, max_lines, dl, st, M, s);
+        if (rc != WH_OK) return rc;
+    }
+    if (wh::launch_moves_fill(M, s) != cudaSuccess) return WH_ECUDA;
+    // features and predictions of the current tours and of the tasks' changed tours
+    const size_t need = head + align_up(feat_row * (size_t)(p.n_tours + 1)) + align_up(sizeof(float) * (size_t)(p.n_tours + 1)) +
+                        align_up(feat_row * (size_t)(M.n_tasks + 1)) + align_up(sizeof(float) * (size_t)(M.n_tasks + 1));
+    if (need > h->sr_scratch_bytes) {
+        // grow keeping nothing: the head (status, delta) must be rebuilt, so
+        // size for the worst case and redo the preparation
+        rc = grow(&h->sr_scratch, &h->sr_scratch_bytes, need + need / 4);
+        if (rc != WH_OK) return rc;
+        char* b = static_cast<char*>(h->sr_scratch);
+        int32_t* st = reinterpret_cast<int32_t*>(b);
+        int64_t* dl = reinterpret_cast<int64_t*>(b + align_up(sizeof(int32_t) * (size_t)n_moves));
+        rc = prepare_moves(h, o, p, moves, n_moves, max_orders, max_lines, dl, st, M, s);
+        if (rc != WH_OK) return rc;
+        if (wh::launch_moves_fill(M, s) != cudaSuccess) return WH_ECUDA;
+    }
+    char* b = static_cast<char*>(h->sr_scratch);
+    size_t at = align_up(sizeof(int32_t) * (size_t)n_moves) + align_up(sizeof(int64_t) * 2 * (size_t)n_moves);
+    float* score = reinterpret_cast<float*>(b + at);
+    at = head;
+    uint16_t* X_tour = reinterpret_cast<uint16_t*>(b + at);
+    at += align_up(feat_row * (size_t)(p.n_tours + 1));
+    float* y_tour = reinterpret_cast<float*>(b + at);
+    at += align_up(sizeof(float) * (size_t)(p.n_tours + 1));
+    uint16_t* X_task = reinterpret_cast<uint16_t*>(b + at);
+    at += align_up(feat_row * (size_t)(M.n_tasks + 1));
+    float* y_task = reinterpret_cast<float*>(b + at);
+
+    rc = wh_surrogate_features(h, orders, plans, X_tour, stream);
+    if (rc != WH_OK) return rc;
+    rc = wh_surrogate_predict(sg, X_tour, p.n_tours, y_tour, stream);
+    if (rc != WH_OK) return rc;
+    wh::FeatConst c;
+    c.A = h->g.A;
+    c.L = h->g.L;
+    c.magic_a = (((uint64_t)1 << 40) + (uint64_t)h->g.A - 1) / (uint64_t)h->g.A;
+    c.magic_l = (((uint64_t)1 << 40) + (uint64_t)h->g.L - 1) / (uint64_t)h->g.L;
+    c.inv_a = (float)(1.0 / (double)h->g.A);
+    if (wh::launch_task_features(M, c, X_task, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    rc = wh_surrogate_predict(sg, X_task, M.n_tasks, y_task, stream);
+    if (rc != WH_OK) return rc;
+    wh::ScreenArgs S;
+    S.M = M;
+    S.y_tour = y_tour;
+    S.y_task = y_task;
+    S.score = score;
+    S.moves_per_plan = moves_per_plan;
+    S.keep = keep;
+    S.kept = reinterpret_cast<int4*>(kept);
+    return wh::launch_screen_select(S, s) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
 extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* moves,
                            int32_t moves_per_plan, const int64_t* delta, const int32_t* status, int32_t* applied,
-                           void* stream) {
+                           const wh_costs* costs, void* stream) {
     if (!h || !orders || !plans || moves_per_plan < 1 || moves_per_plan > 256) return WH_EINVAL;
     const wh_orders o = *orders;
     const wh_plans p = *plans;
@@ -381,6 +497,16 @@ extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans
     L.status = status;
     L.applied = applied;
     L.seg_cap = std::max(o.n_orders, 1);
+    if (costs) {
+        if (h->last_moves != moves || (int64_t)h->last_n_moves != (int64_t)p.n_plans * moves_per_plan) return WH_EINVAL;
+        L.task_off = h->last_task_off;
+        L.tasks = h->last_tasks;
+        L.task_cost = h->last_task_cost;
+        L.tour_s = costs->tour_s;
+        L.tour_rr = costs->tour_rr;
+        L.plan_s = costs->plan_s;
+        L.plan_rr = costs->plan_rr;
+    }
     return wh::launch_ls_apply(L, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
@@ -473,6 +599,7 @@ extern "C" void wh_destroy(wh_layout* h) {
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
         if (h->mv_scratch) cudaFree(h->mv_scratch);
         if (h->mv_tasks) cudaFree(h->mv_tasks);
+        if (h->sr_scratch) cudaFree(h->sr_scratch);
         if (h->scratch) cudaFree(h->scratch);
         if (h->meta) cudaFree(h->meta);
     }

@@ -93,6 +93,7 @@ struct MoveArgs {
     int64_t* task_off;          // [n_moves+1]: exclusive scan of task counts
     int64_t* scan_aux;          // block totals of that scan
     int4* tasks;                // [n_tasks]
+    int2* task_cost;            // [n_tasks]: new (S-shape, optimal) cost of the task's tour, -1 if not counted
     int64_t n_tasks;
     int32_t* long_list;         // tasks over SHORT_MAX lines
     int32_t* long_count;
@@ -107,11 +108,35 @@ struct LsArgs {
     const int32_t* status;
     int32_t* applied;           // [n_plans]
     int32_t seg_cap;            // shared-memory staging capacity (orders)
+    // incremental cost update (all NULL: none): the tasks of the wh_eval_moves
+    // call that scored these moves
+    const int64_t* task_off;
+    const int4* tasks;
+    const int2* task_cost;
+    int32_t* tour_s;
+    int32_t* tour_rr;
+    int64_t* plan_s;
+    int64_t* plan_rr;
 };
+
+struct ScreenArgs {
+    MoveArgs M;                 // the scored moves and their task list
+    const float* y_tour;        // predicted cost of every current tour
+    const float* y_task;        // predicted cost of every task's changed tour
+    float* score;               // [n_moves] predicted delta
+    int32_t moves_per_plan;
+    int32_t keep;
+    int4* kept;                 // [n_plans][keep]
+};
+
+struct FeatConst;
+cudaError_t launch_task_features(const MoveArgs& M, const FeatConst& c, void* X, int num_sms, cudaStream_t s);
+cudaError_t launch_screen_select(const ScreenArgs& S, cudaStream_t s);
 
 cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s);
 cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s);
 cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s);
+cudaError_t launch_moves_fill(const MoveArgs& M, cudaStream_t s);
 
 // Surrogate (k_surrogate.cu).  Packed parameter vector: w1 [192][256],
 // b1 [256], w2 [256][256], b2 [256], w3 [256], b3 [1].

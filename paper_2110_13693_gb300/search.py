@@ -1,0 +1,75 @@
+"""Plan-level local search on the device: exact best-improvement steps and
+surrogate-prescreened steps (the learned prescreen keeps a few moves per plan
+for exact scoring), plus the surrogate's training data and error statistics.
+
+Every step runs in the library's kernels; Python only sequences the calls.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+
+def norm_of(layout) -> int:
+    """Normaliser of tour lengths: the longest S-shape span 2*x_{A-1} + A*Y."""
+    Y = layout.cross_aisle_width + (layout.slots_per_side - 1) * layout.slot_pitch
+    return 2 * (layout.n_aisles - 1) * layout.aisle_pitch + layout.n_aisles * Y
+
+
+def plain_step(lay, prob, costs, moves, M, max_orders=0, max_lines=0):
+    return lay.ls_step(prob, costs, moves, M, max_orders, max_lines)
+
+
+def screened_step(lay, sg, prob, costs, moves, M, keep, max_orders=0, max_lines=0):
+    kept = lay.screen(sg, prob, moves, M, keep, max_orders, max_lines)
+    return lay.ls_step(prob, costs, kept, keep, max_orders, max_lines)
+
+
+def keep_count(M: int, frac: float = 0.05) -> int:
+    """Moves kept per plan by the prescreen: ceil(frac * M)."""
+    return max(1, int(math.ceil(frac * M - 1e-9)))
+
+
+def training_set(wh, lay, prob, costs, layout):
+    """Features of every tour of `prob` and their normalised optimal cost."""
+    X = wh.features(lay, prob)
+    t = costs.tour_rr[:prob.n_tours].float() / float(norm_of(layout))
+    return X, t
+
+
+def train(sg, X, t, steps: int, batch: int, lr: float, seed: int = 0):
+    import torch
+    g = torch.Generator(device=X.device).manual_seed(seed)
+    n = X.shape[0]
+    losses = []
+    for step in range(steps):
+        b = torch.randint(0, n, (batch,), device=X.device, generator=g)
+        losses.append(sg.train_step(X[b].contiguous(), t[b].contiguous(), lr))
+    return [float(x.item()) for x in losses[-5:]]
+
+
+def errors(sg, X, t):
+    """(mean, p99) relative error of the surrogate's predictions."""
+    rel = ((sg.predict(X) - t).abs() / t.clamp_min(1e-6)).cpu().numpy()
+    return float(rel.mean()), float(np.percentile(rel, 99))
+
+
+def run_search(wh, lay, prob, costs, moves_fn, steps, M, max_orders, max_lines, sg=None, keep=None):
+    """Run `steps` steps (screened when sg is given); returns [(seconds, best
+    plan cost, mean plan cost)] after each step, wall clock, device synchronised."""
+    import torch
+    trace = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(steps):
+        mv = moves_fn(step)
+        if sg is None:
+            plain_step(lay, prob, costs, mv, M, max_orders, max_lines)
+        else:
+            screened_step(lay, sg, prob, costs, mv, M, keep, max_orders, max_lines)
+        pr = costs.plan_rr[:prob.n_plans]
+        best, mean = int(pr.min().item()), float(pr.double().mean().item())
+        trace.append((time.perf_counter() - t0, best, mean))
+    return trace

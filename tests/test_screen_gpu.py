@@ -1,0 +1,135 @@
+"""Learned prescreen and incremental local search on the GPU: the kept moves
+are the lowest predicted deltas (checked against the oracle's features and
+MLP), the incremental cost update equals a full re-evaluation, and a
+screened search improves plans exactly (costs re-checked by the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+import wh_gen
+from paper_2110_13693_gb300 import search
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(wh, inst, per_plan=True):
+    n = inst.n_plans
+    smap = np.tile(inst.slot_map, (n, 1)).ravel().astype(np.int32) if per_plan else inst.slot_map
+    lay = wh.Layout.of(inst.layout)
+    prob = wh.to_device(inst, slot_map=smap, slot_map_stride=inst.n_sku if per_plan else 0)
+    costs = wh.evaluate(lay, prob)
+    return lay, prob, costs
+
+
+def moves_for(inst, seed, step, M):
+    import torch
+    mv = wh_gen.gen_moves(seed, step, inst, M)
+    mv[..., 3] = np.arange(inst.n_plans)[:, None]
+    return torch.as_tensor(mv.reshape(-1, 4)).cuda()
+
+
+def test_incremental_costs_equal_full_refresh(gpu_lib):
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.paperscale(seed=21, n_plans=24)
+    a = setup(wh, inst)
+    b = setup(wh, inst)
+    for step in range(4):
+        mv = moves_for(inst, 3, step, 32)
+        ra = a[0].ls_step(a[1], a[2], mv, 32, 24)
+        rb = b[0].ls_step(b[1], b[2], mv, 32, 24, refresh=True)
+        torch.cuda.synchronize()
+        assert torch.equal(ra, rb)
+        for x, y in ((a[2].tour_rr, b[2].tour_rr), (a[2].tour_s, b[2].tour_s)):
+            assert torch.equal(x[:a[1].n_tours], y[:b[1].n_tours])
+        assert torch.equal(a[2].plan_rr[:24], b[2].plan_rr[:24]) and torch.equal(a[2].plan_s[:24], b[2].plan_s[:24])
+    assert a[0].status() == 0
+
+
+def moved_tours(inst, smap, mv):
+    """Changed tours of a move as (new pick list, old tour index) pairs (Python, from the definition)."""
+    typ, x, y, p = (int(v) for v in mv)
+    t0, t1 = inst.plan_tour_off[p], inst.plan_tour_off[p + 1]
+    tours = {t: inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]].tolist() for t in range(t0, t1)}
+    where = {o: t for t, os in tours.items() for o in os}
+    lines = lambda os, m: [m[s] for o in os for s in inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]]]
+    if typ == 0:
+        ta, tb = where[x], where[y]
+        return [(lines([y if o == x else o for o in tours[ta]], smap), ta),
+                (lines([x if o == y else o for o in tours[tb]], smap), tb)]
+    if typ == 1:
+        ta, tb = where[x], t0 + y
+        return [(lines([o for o in tours[ta] if o != x], smap), ta), (lines(tours[tb] + [x], smap), tb)]
+    m2 = smap.copy()
+    m2[x], m2[y] = m2[y], m2[x]
+    hit = {where[o] for o in range(inst.n_orders) if o in where and
+           (set(inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]].tolist()) & {x, y})}
+    return [(lines(tours[t], m2), t) for t in sorted(hit)]
+
+
+def test_screen_keeps_lowest_predicted_deltas(gpu_lib):
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.tiny(seed=22, n_plans=5)
+    lay, prob, costs = setup(wh, inst)
+    sg = wh.Surrogate(3)
+    X, t = search.training_set(wh, lay, prob, costs, inst.layout)
+    search.train(sg, X, t, 60, 256, 3e-3)
+    M, keep = 32, 4
+    mv = moves_for(inst, 5, 0, M)
+    kept = lay.screen(sg, prob, mv, M, keep, 8).cpu().numpy().reshape(inst.n_plans, keep, 4)
+    params = wh.unpack_params(sg.params()[0])
+    w = {k: (oracle.bf16(v) if k in ("w1", "w2") else v) for k, v in params.items()}
+    pred = lambda locs: oracle.mlp_forward(w, oracle.bf16(oracle.features(inst.layout, locs))[None])[0]
+    d, st = oracle.eval_moves(inst, mv.cpu().numpy(), 8, 0, slot_map=np.tile(inst.slot_map, (5, 1)).ravel(),
+                              slot_map_stride=inst.n_sku)
+    smap = inst.slot_map
+    old = {}
+    for p in range(inst.n_plans):
+        scores = {}
+        for k in range(M):
+            m = p * M + k
+            if st[m] != 0:
+                continue
+            sc = 0.0
+            for locs, t_old in moved_tours(inst, smap, mv[m].cpu().numpy()):
+                if t_old not in old:
+                    orig = [smap[s] for o in inst.order_seq[inst.tour_off[t_old]:inst.tour_off[t_old + 1]]
+                            for s in inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]]]
+                    old[t_old] = pred(orig)
+                sc += pred(locs) - old[t_old]
+            scores[k] = sc
+        order = sorted(scores.values())
+        kth = order[min(keep, len(order)) - 1] if order else None
+        moves_p = mv[p * M:(p + 1) * M].cpu().numpy().tolist()
+        for j in range(keep):
+            if j >= len(scores):
+                assert kept[p, j, 0] == 9
+                continue
+            k = moves_p.index(kept[p, j].tolist())
+            assert scores[k] <= kth + 1e-3 * max(1.0, abs(kth)), (p, j, scores[k], kth)
+    sg.close()
+    lay.close()
+
+
+def test_screened_search_improves_exactly(gpu_lib):
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.paperscale(seed=23, n_plans=16)
+    lay, prob, costs = setup(wh, inst)
+    sg = wh.Surrogate(4)
+    X, t = search.training_set(wh, lay, prob, costs, inst.layout)
+    search.train(sg, X, t, 150, 1024, 2e-3)
+    start = costs.plan_rr[:16].clone()
+    trace = search.run_search(wh, lay, prob, costs, lambda s: moves_for(inst, 8, s, 64), 4, 64, 24, 0,
+                              sg=sg, keep=search.keep_count(64))
+    assert (costs.plan_rr[:16] <= start).all() and trace[-1][1] <= int(start.min().item())
+    # the incrementally kept costs are the exact costs of the edited plans
+    cur = wh_gen.Instance(inst.layout, inst.n_sku, inst.order_off, inst.line_sku, prob.slot_map.cpu().numpy(),
+                          inst.plan_tour_off, prob.tour_off.cpu().numpy(), prob.order_seq.cpu().numpy())
+    want = oracle.eval_plans(cur, slot_map=cur.slot_map, slot_map_stride=inst.n_sku)
+    assert np.array_equal(costs.plan_rr[:16].cpu().numpy(), want[3])
+    assert np.array_equal(costs.tour_rr[:prob.n_tours].cpu().numpy(), want[1])
+    assert lay.status() == 0
+    sg.close()
+    lay.close()
