@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and move-delta measurements")
     ap.add_argument("--extra-steps", type=int, default=20)
+    ap.add_argument("--ab-steps", type=int, default=30, help="plain local-search steps of the prescreen A/B")
+    ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--case", choices=["batched-small", "moves-small"], default=None,
                     help="run a small case of one kernel three times (for profiler captures) and exit")
     return ap.parse_args()
@@ -262,6 +264,82 @@ def run_moves(wh, dev, steps):
             "timing": "wall clock around the calls (each call synchronises once)"}
 
 
+def run_surrogate_ab(wh, dev, steps, train_steps):
+    """Config 5: the MLP prescreen on the paper-scale population.  Trained on
+    ~10M exactly scored tours of the paper-scale generator (four random
+    populations), judged on a held-out one, then plain exact search and
+    screened search (64 moves per plan, 5 % kept) run from the same start."""
+    import numpy as np
+    import torch
+    import wh_gen
+    from paper_2110_13693_gb300 import search
+    n_plans, M = 16384, 64
+    inst0 = wh_gen.paperscale(seed=4, n_plans=n_plans)
+    lay = wh.Layout.of(inst0.layout)
+    t0 = time.perf_counter()
+    Xs, ts = [], []
+    for k in range(5):
+        inst = inst0 if k == 0 else wh_gen.paperscale(seed=4, n_plans=n_plans, plan_base=k * n_plans)
+        prob = wh.to_device(inst, dev)
+        costs = wh.evaluate(lay, prob)
+        X, t = search.training_set(wh, lay, prob, costs, inst.layout)
+        Xs.append(X)
+        ts.append(t)
+    X_train, t_train = torch.cat(Xs[1:]), torch.cat(ts[1:])
+    X_held, t_held = Xs[0][:500000], ts[0][:500000]
+    data_s = time.perf_counter() - t0
+    sg = wh.Surrogate(11)
+    t1 = time.perf_counter()
+    search.train(sg, X_train, t_train, train_steps, 4096, 2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    mean_err, p99_err = search.errors(sg, X_held, t_held)
+    del Xs, ts, X_train, t_train
+
+    def population():
+        base = wh.to_device(inst0, dev)
+        smap = base.slot_map.repeat(n_plans)
+        prob = wh.DeviceProblem(base.order_off, base.line_sku, smap, base.plan_tour_off, base.tour_off.clone(),
+                                base.order_seq.clone(), inst0.n_sku, inst0.n_sku)
+        return prob, wh.evaluate(lay, prob)
+
+    moves = {}
+
+    def moves_fn(step):
+        if step not in moves:
+            mv = wh_gen.gen_moves(23, step, inst0, M)
+            mv[..., 3] = np.arange(n_plans)[:, None]
+            moves[step] = torch.as_tensor(mv.reshape(-1, 4)).to(dev)
+        return moves[step]
+
+    for s in range(steps * 2):
+        moves_fn(s)                       # generated outside the timed searches
+    keep = search.keep_count(M)
+    prob, costs = population()
+    start_best = int(costs.plan_rr[:n_plans].min().item())
+    plain = search.run_search(wh, lay, prob, costs, moves_fn, steps, M, 24, 0)
+    target = plain[-1][1]
+    prob, costs = population()
+    screened = search.run_search(wh, lay, prob, costs, moves_fn, steps * 2, M, 24, 0, sg=sg, keep=keep)
+    hit = next((tr[0] for tr in screened if tr[1] <= target), None)
+    t_eq = plain[-1][0]
+    best_at_eq = min((tr[1] for tr in screened if tr[0] <= t_eq), default=start_best)
+    assert lay.status() == 0
+    sg.close()
+    lay.close()
+    return {"workload": "paper scale, 16,384 plans with their own slottings, 64 moves per plan per step; "
+                        f"surrogate trained on {4 * inst0.n_tours} exactly scored tours of the same generator",
+            "surrogate_mean_rel_error": mean_err, "surrogate_p99_rel_error": p99_err,
+            "held_out_tours": 500000, "train_steps": train_steps, "batch": 4096, "train_seconds": train_s,
+            "data_seconds": data_s, "keep_per_plan": keep, "start_best": start_best,
+            "plain": {"steps": len(plain), "seconds": plain[-1][0], "best": plain[-1][1], "mean": plain[-1][2],
+                      "ms_per_step": plain[-1][0] * 1e3 / len(plain)},
+            "screened": {"steps": len(screened), "seconds": screened[-1][0], "best": screened[-1][1],
+                         "mean": screened[-1][2], "ms_per_step": screened[-1][0] * 1e3 / len(screened),
+                         "seconds_to_plain_best": hit, "best_at_plain_wall_time": best_at_eq},
+            "screened_reaches_plain_best_faster": hit is not None and hit < plain[-1][0]}
+
+
 # -------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -375,6 +453,7 @@ def run_ours(args):
     if not args.no_extra and world == 1:
         extra["batched"] = run_batched(wh, dev, args.extra_steps)
         extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4))
+        extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

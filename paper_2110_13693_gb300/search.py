@@ -32,10 +32,17 @@ def keep_count(M: int, frac: float = 0.05) -> int:
     return max(1, int(math.ceil(frac * M - 1e-9)))
 
 
+# The regression target is the normalised optimal length times this constant,
+# which brings typical targets to O(1): with targets near 0.03 (paper scale)
+# and Xavier-initialised bf16 layers, training stalls at ~30 % error; scaled,
+# it reaches ~2 %.  Rankings and relative errors do not depend on it.
+TARGET_SCALE = 32.0
+
+
 def training_set(wh, lay, prob, costs, layout):
-    """Features of every tour of `prob` and their normalised optimal cost."""
+    """Features of every tour of `prob` and TARGET_SCALE x their normalised optimal cost."""
     X = wh.features(lay, prob)
-    t = costs.tour_rr[:prob.n_tours].float() / float(norm_of(layout))
+    t = costs.tour_rr[:prob.n_tours].float() * (TARGET_SCALE / float(norm_of(layout)))
     return X, t
 
 
