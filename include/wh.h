@@ -65,6 +65,7 @@ extern "C" {
 #define WH_STATUS_BAD_OFFSET 8u   /* offsets decreasing or past the end of their array */
 #define WH_STATUS_TOUR_TOO_LONG 16u
 #define WH_STATUS_LONG_OVERFLOW 32u /* more long tours in one call than the deferral list holds */
+#define WH_STATUS_TIMEOUT 64u       /* a bounded wait inside a kernel gave up (the kernel returned early) */
 
 /* Limits of this implementation. */
 #define WH_MAX_AISLES 65534
@@ -232,8 +233,16 @@ int wh_surrogate_set_params(wh_surrogate *s, const float *host_params);
  * arrays of WH_MLP_NPARAM floats (either may be NULL).  Synchronises. */
 int wh_surrogate_get_params(wh_surrogate *s, float *host_params, float *host_grads);
 
-/* y[i] = MLP(X[i]) for n rows of bf16 features (device); fp32 outputs. */
+/* y[i] = MLP(X[i]) for n rows of bf16 features (device, row-major [n][192],
+ * 16-byte aligned); fp32 outputs.  Runs on the tcgen05 tensor cores; its
+ * bounded waits report WH_STATUS_TIMEOUT through wh_surrogate_get_status.
+ * Allocates nothing.  Returns WH_OK, WH_EINVAL (NULL or misaligned X) or
+ * WH_ECUDA. */
 int wh_surrogate_predict(wh_surrogate *s, const uint16_t *X, int64_t n, float *y, void *stream);
+
+/* Read and clear the surrogate's device status word (WH_STATUS_* bits of the
+ * prediction kernels).  Synchronises the device. */
+int wh_surrogate_get_status(wh_surrogate *s, uint32_t *out);
 
 /* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared
  * error 0.5*mean((y - target)^2) of n rows; *loss_out (device float, may be

@@ -20,6 +20,7 @@ WH_OK, WH_EINVAL, WH_ERANGE, WH_ENOMEM, WH_ECUDA, WH_ETIMEOUT = 0, -1, -2, -3, -
 WH_ROUTE_SSHAPE, WH_ROUTE_OPTIMAL = 1, 2
 WH_STATUS_BAD_ORDER, WH_STATUS_BAD_SKU, WH_STATUS_BAD_LOC = 1, 2, 4
 WH_STATUS_BAD_OFFSET, WH_STATUS_TOUR_TOO_LONG, WH_STATUS_LONG_OVERFLOW = 8, 16, 32
+WH_STATUS_TIMEOUT = 64
 WH_NOALLOC_MAX_LINES, WH_NOALLOC_MAX_TOURS = 1 << 20, 1 << 20
 ERRORS = {WH_EINVAL: "WH_EINVAL", WH_ERANGE: "WH_ERANGE", WH_ENOMEM: "WH_ENOMEM",
           WH_ECUDA: "WH_ECUDA", WH_ETIMEOUT: "WH_ETIMEOUT"}
@@ -101,6 +102,7 @@ SIGNATURES = {
     "wh_surrogate_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(wh_orders),
                                            ctypes.POINTER(wh_plans), ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_surrogate_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "wh_surrogate_destroy": (None, [ctypes.c_void_p]),
 }
 WH_MLP_NPARAM, WH_FEATURES = 115457, 192
@@ -488,6 +490,12 @@ def wh_surrogate_get_params(s):
     return p, g
 
 
+def wh_surrogate_get_status(s) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load().wh_surrogate_get_status(s, ctypes.byref(v)), "wh_surrogate_get_status")
+    return int(v.value)
+
+
 def wh_surrogate_predict(s, X, n: int, y, stream=None) -> None:
     _check(load().wh_surrogate_predict(s, ctypes.c_void_p(X), n, ctypes.c_void_p(y), _stream_ptr(stream)),
            "wh_surrogate_predict")
@@ -546,6 +554,10 @@ class Surrogate:
         y = torch.empty(max(n, 1), dtype=torch.float32, device=X.device)
         wh_surrogate_predict(self.handle, X.data_ptr(), n, y.data_ptr(), stream)
         return y[:n]
+
+    def status(self) -> int:
+        """Read and clear the WH_STATUS_* bits of the prediction kernels (synchronises)."""
+        return wh_surrogate_get_status(self.handle)
 
     def train_step(self, X, target, lr: float, stream=None):
         """Returns the loss (device tensor) before the step."""

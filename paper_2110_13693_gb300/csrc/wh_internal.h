@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/wh.h"
@@ -140,6 +141,7 @@ cudaError_t launch_moves_fill(const MoveArgs& M, cudaStream_t s);
 
 // Surrogate (k_surrogate.cu).  Packed parameter vector: w1 [192][256],
 // b1 [256], w2 [256][256], b2 [256], w3 [256], b3 [1].
+constexpr int64_t MLP_IN = 192;
 constexpr int64_t MLP_W1 = 192 * 256;
 constexpr int64_t MLP_B1_OFF = MLP_W1;
 constexpr int64_t MLP_W2_OFF = MLP_B1_OFF + 256;
@@ -183,6 +185,12 @@ cudaError_t launch_sum(const float* v, int n, float* out, cudaStream_t s);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr, int step, void* w1b,
                         void* w2b, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* p, int64_t n, void* out, cudaStream_t s);
+// fused tcgen05 inference (k_mlp_tc.cu): W1t [256][192] and W2t [256][256]
+// are the transposed bf16 weights the tensor maps mw1 / mw2 describe
+cudaError_t launch_transpose_bf16(const float* p, int K, int N, void* out, cudaStream_t s);
+cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const CUtensorMap& mw2, const float* P,
+                          int64_t n, float* y, int* status, int num_sms, cudaStream_t s);
+size_t mlp_tc_smem_bytes();
 
 struct Tuning {
     int threads;          // CTA size: 32 tours in flight per warp

@@ -1,8 +1,13 @@
 // C-ABI of the surrogate MLP (declared in include/wh.h): parameters, Adam
 // state and activation scratch on the device; prediction and training steps
-// enqueued on the caller's stream.
+// enqueued on the caller's stream.  Prediction runs the fused tcgen05 kernel
+// (k_mlp_tc.cu) on transposed bf16 weights that are refreshed on the stream
+// whenever the parameters have changed; training runs the mma.sync GEMMs.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -20,13 +25,48 @@ struct wh_surrogate {
     int64_t cap = 0;       // rows of training scratch
     float *Z1 = nullptr, *Z2 = nullptr, *y = nullptr, *dy = nullptr, *loss = nullptr;
     __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
-    int64_t icap = 0;      // rows of inference scratch
-    __nv_bfloat16 *iH1 = nullptr, *iH2 = nullptr;
+    __nv_bfloat16 *w1t = nullptr, *w2t = nullptr;   // [256][192], [256][256]: K contiguous
+    CUtensorMap mw1, mw2;
+    bool t_stale = true;   // w1t / w2t lag the parameters
+    int* status = nullptr; // WH_STATUS_* bits of the inference kernel
+    int num_sms = 0;
 };
 
 namespace {
 
-constexpr int64_t kInferChunk = 1 << 18;
+// rows per inference launch: TMA row coordinates are 32-bit
+constexpr int64_t kInferChunk = (int64_t)1 << 30;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D bf16 tensor map of a row-major [rows][cols] matrix, box [box_rows][64]
+// (128 bytes wide, the 128-byte swizzle), rows past the end read as zero
+int encode_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return WH_ECUDA;
+    const cuuint64_t dim[2] = {cols, rows};
+    const cuuint64_t stride[1] = {cols * 2};
+    const cuuint32_t box[2] = {64, box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dim, stride, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? WH_OK : WH_EINVAL;
+}
 
 // SplitMix64 (Steele, Lea & Flood 2014)
 uint64_t sm64(uint64_t& s) {
@@ -38,7 +78,7 @@ uint64_t sm64(uint64_t& s) {
 
 void free_all(wh_surrogate* s) {
     void* ptrs[] = {s->P, s->Mo, s->Ve, s->G, s->w1b, s->w2b, s->Z1, s->Z2, s->y, s->dy, s->loss,
-                    s->H1, s->H2, s->dZ2, s->dZ1, s->iH1, s->iH2};
+                    s->H1, s->H2, s->dZ2, s->dZ1, s->w1t, s->w2t, s->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -47,6 +87,7 @@ int upload_params(wh_surrogate* s, const float* host) {
     if (cudaMemcpy(s->P, host, sizeof(float) * wh::MLP_NPARAM, cudaMemcpyHostToDevice) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_to_bf16(s->P, wh::MLP_W1, s->w1b, nullptr) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_to_bf16(s->P + wh::MLP_W2_OFF, wh::MLP_W2, s->w2b, nullptr) != cudaSuccess) return WH_ECUDA;
+    s->t_stale = true;
     return cudaDeviceSynchronize() == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
@@ -123,7 +164,7 @@ extern "C" int wh_surrogate_create(uint64_t seed, wh_surrogate** out) {
     }
     if (dalloc(&s->P, wh::MLP_NPARAM) || dalloc(&s->Mo, wh::MLP_NPARAM) || dalloc(&s->Ve, wh::MLP_NPARAM) ||
         dalloc(&s->G, wh::MLP_NPARAM) || dalloc(&s->w1b, wh::MLP_W1) || dalloc(&s->w2b, wh::MLP_W2) ||
-        dalloc(&s->loss, 1)) {
+        dalloc(&s->loss, 1) || dalloc(&s->w1t, wh::MLP_W1) || dalloc(&s->w2t, wh::MLP_W2) || dalloc(&s->status, 1)) {
         free_all(s);
         delete s;
         return WH_ENOMEM;
@@ -141,8 +182,13 @@ extern "C" int wh_surrogate_create(uint64_t seed, wh_surrogate** out) {
     fill(0, wh::MLP_W1, 192, 256);
     fill(wh::MLP_W2_OFF, wh::MLP_W2, 256, 256);
     fill(wh::MLP_W3_OFF, 256, 256, 1);
-    int rc = upload_params(s, h.data());
-    if (rc == WH_OK && (cudaMemset(s->Mo, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
+    int rc = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess ? WH_OK
+                                                                                                         : WH_ECUDA;
+    if (rc == WH_OK) rc = encode_map(&s->mw1, s->w1t, 256, 192, 256);
+    if (rc == WH_OK) rc = encode_map(&s->mw2, s->w2t, 256, 256, 256);
+    if (rc == WH_OK) rc = upload_params(s, h.data());
+    if (rc == WH_OK && (cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess ||
+                        cudaMemset(s->Mo, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
                         cudaMemset(s->Ve, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
                         cudaMemset(s->G, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess))
         rc = WH_ECUDA;
@@ -180,22 +226,31 @@ extern "C" int wh_surrogate_get_params(wh_surrogate* s, float* host_params, floa
 extern "C" int wh_surrogate_predict(wh_surrogate* s, const uint16_t* X, int64_t n, float* y, void* stream) {
     if (!s || n < 0 || (n > 0 && (!X || !y))) return WH_EINVAL;
     if (n == 0) return WH_OK;
+    if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return WH_EINVAL;   // TMA base alignment
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t chunk = n < kInferChunk ? n : kInferChunk;
-    if (chunk > s->icap) {
-        if (s->iH1) cudaFree(s->iH1);
-        if (s->iH2) cudaFree(s->iH2);
-        s->iH1 = s->iH2 = nullptr;
-        s->icap = 0;
-        if (dalloc(&s->iH1, (size_t)chunk * 256) || dalloc(&s->iH2, (size_t)chunk * 256)) return WH_ENOMEM;
-        s->icap = chunk;
+    if (s->t_stale) {
+        if (wh::launch_transpose_bf16(s->P, 192, 256, s->w1t, st) != cudaSuccess ||
+            wh::launch_transpose_bf16(s->P + wh::MLP_W2_OFF, 256, 256, s->w2t, st) != cudaSuccess)
+            return WH_ECUDA;
+        s->t_stale = false;
     }
-    const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
-    for (int64_t r = 0; r < n; r += chunk) {
-        const int64_t m = n - r < chunk ? n - r : chunk;
-        const int rc = forward(s, Xb + r * 192, m, s->iH1, s->iH2, nullptr, nullptr, y + r, st);
+    for (int64_t r = 0; r < n; r += kInferChunk) {
+        const int64_t m = n - r < kInferChunk ? n - r : kInferChunk;
+        CUtensorMap mx;
+        int rc = encode_map(&mx, X + r * wh::MLP_IN, (uint64_t)m, wh::MLP_IN, 128);
         if (rc != WH_OK) return rc;
+        if (wh::launch_mlp_tc(mx, s->mw1, s->mw2, s->P, m, y + r, s->status, s->num_sms, st) != cudaSuccess)
+            return WH_ECUDA;
     }
+    return WH_OK;
+}
+
+extern "C" int wh_surrogate_get_status(wh_surrogate* s, uint32_t* out) {
+    if (!s || !out) return WH_EINVAL;
+    int v = 0;
+    if (cudaMemcpy(&v, s->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return WH_ECUDA;
+    if (cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) return WH_ECUDA;
+    *out = (uint32_t)v;
     return WH_OK;
 }
 
@@ -236,6 +291,7 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     s->step += 1;
     if (wh::launch_adam(s->P, s->Mo, s->Ve, s->G, wh::MLP_NPARAM, lr, s->step, s->w1b, s->w2b, st) != cudaSuccess)
         return WH_ECUDA;
+    s->t_stale = true;
     if (loss_out && cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return WH_ECUDA;
     return WH_OK;

@@ -70,6 +70,13 @@ def batch(wh, n_plans=12):
     return X, torch.as_tensor(tr / norm, dtype=torch.float32).cuda()
 
 
+def close_to(y, want):
+    """bf16 activations may round the other way where fp32 and float64
+    pre-activations straddle a rounding boundary: 1 % of the output scale."""
+    scale = np.abs(want).mean()
+    return np.abs(y - want).max() <= 1e-2 * scale + 1e-4
+
+
 def test_predict_matches_oracle(gpu_lib):
     wh = gpu_lib
     X, _ = batch(wh)
@@ -78,8 +85,70 @@ def test_predict_matches_oracle(gpu_lib):
     s.set_params(wh.pack_params(p))
     y = s.predict(X).cpu().numpy()
     want = oracle.mlp_forward(p, X.float().cpu().numpy())
-    scale = np.abs(want).mean()
-    assert np.abs(y - want).max() <= 1e-2 * scale + 1e-4
+    assert close_to(y, want)
+    assert s.status() == 0
+    s.close()
+
+
+def rand_features(seed, n):
+    """bf16 rows with the value ranges of tour features: small histogram
+    counts and four scalars in [0, 1]."""
+    rng = np.random.default_rng(seed)
+    x = rng.poisson(0.4, size=(n, 192)).astype(np.float32)
+    x[:, 128:132] = rng.random((n, 4))
+    return oracle.bf16(x)
+
+
+# one tile, a ragged tail, several tiles per CTA (phases wrap on every
+# barrier), more tiles than SMs with a tail
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 152 * 128 * 3 + 77])
+def test_tensor_core_predict_ragged(gpu_lib, n):
+    import torch
+    wh = gpu_lib
+    Xh = rand_features(n, n)
+    X = torch.from_numpy(Xh).to(torch.bfloat16).cuda()
+    p = bf16_params(3)
+    s = wh.Surrogate(0)
+    s.set_params(wh.pack_params(p))
+    y = s.predict(X).cpu().numpy()
+    idx = np.arange(n) if n <= 1000 else np.unique(np.concatenate(
+        [np.arange(200), np.arange(n - 200, n), np.random.default_rng(n).integers(0, n, 600)]))
+    assert close_to(y[idx], oracle.mlp_forward(p, Xh[idx]))
+    # a row-offset view (16-byte aligned) predicts the same rows
+    if n > 8:
+        y5 = s.predict(X[5:]).cpu().numpy()
+        np.testing.assert_array_equal(y5, y[5:])
+    assert s.status() == 0
+    s.close()
+
+
+def test_tensor_core_predict_large(gpu_lib):
+    import torch
+    wh = gpu_lib
+    n = (1 << 21) + 19
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randint(0, 3, (n, 192), device="cuda", generator=g).to(torch.bfloat16)
+    X[:, 128:132] = torch.rand((n, 4), device="cuda", generator=g).to(torch.bfloat16)
+    p = bf16_params(4)
+    s = wh.Surrogate(0)
+    s.set_params(wh.pack_params(p))
+    y = s.predict(X)
+    idx = torch.cat([torch.arange(64), torch.arange(n - 64, n),
+                     torch.randint(0, n, (256,), generator=torch.Generator().manual_seed(6))]).cuda()
+    want = oracle.mlp_forward(p, X[idx].float().cpu().numpy())
+    assert close_to(y[idx].cpu().numpy(), want)
+    assert s.status() == 0
+    s.close()
+
+
+def test_predict_rejects_misaligned_rows(gpu_lib):
+    import torch
+    wh = gpu_lib
+    flat = torch.zeros(192 * 9 + 1, dtype=torch.bfloat16, device="cuda")
+    X = flat[1:].view(9, 192)                 # 2-byte offset
+    s = wh.Surrogate(0)
+    with pytest.raises(RuntimeError):
+        s.predict(X)
     s.close()
 
 
@@ -107,6 +176,10 @@ def test_train_step_matches_oracle(gpu_lib):
     m, v = np.zeros_like(q), np.zeros_like(q)
     oracle.adam(q, m, v, g.astype(np.float64), 1e-3, 1)
     np.testing.assert_allclose(p1, q, rtol=1e-5, atol=2e-7)
+    # prediction after the step uses the updated weights
+    p1d = wh.unpack_params(p1)
+    w = {k: (oracle.bf16(v) if k in ("w1", "w2") else v) for k, v in p1d.items()}
+    assert close_to(s.predict(X).cpu().numpy(), oracle.mlp_forward(w, Xh))
     s.close()
 
 
