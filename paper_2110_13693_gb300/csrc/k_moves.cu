@@ -655,32 +655,64 @@ __global__ void k_ls_apply(LsArgs L) {
     }
 }
 
-// Features of every task's changed tour (rows of non-counted tasks are
-// written too and ignored by the selection).
-__global__ void __launch_bounds__(128) k_task_features(MoveArgs M, FeatConst c, uint4* X) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int T = blockDim.x, tid = threadIdx.x;
-    FeatThread f;
-    f.tab = reinterpret_cast<uint32_t*>(smem) + tid;
-    f.list = smem + sizeof(uint32_t) * FEAT_SLOTS * T + tid;
-    f.cnt = smem + (sizeof(uint32_t) + 1) * FEAT_SLOTS * T + (size_t)tid * FEAT_CNT_STRIDE;
-    f.T = T;
-    f.n_aisles = 0;
-    f.n_lines = 0;
-    f.overflow = false;
-    for (int i = 0; i < FEAT_SLOTS; ++i) f.tab[i * T] = 0;
-    for (int i = 0; i < FEAT_CNT_STRIDE / 4; ++i) reinterpret_cast<uint32_t*>(f.cnt)[i] = 0;
-    for (int64_t i = (int64_t)blockIdx.x * T + tid; i < M.n_tasks; i += (int64_t)gridDim.x * T) {
+// Features of every task's changed tour, one task per warp (WarpFeat): the
+// same walk as walk_task with lane j taking the tour's orders j, j + 32, ...
+// (the added order last); the SKU-swap rule that picks the counted task of
+// a tour reduces over the lanes.  Marks in task_cost which tasks count
+// (rows of non-counted tasks are written too and ignored by the selection).
+constexpr int TF_THREADS = 256;
+
+__global__ void __launch_bounds__(TF_THREADS) k_task_features(MoveArgs M, FeatConst c, uint4* X) {
+    __shared__ WarpFeat ws[TF_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpFeat& w = ws[wid];
+    wf_init(w, lane);
+    const EvalArgs& a = M.a;
+    const int64_t n_warps = (int64_t)gridDim.x * (TF_THREADS / 32);
+    for (int64_t i = (int64_t)blockIdx.x * (TF_THREADS / 32) + wid; i < M.n_tasks; i += n_warps) {
         const int4 tk = M.tasks[i];
-        bool primary = false, ok = false;
-        if (tk.y >= 0 && tk.y < M.a.n_tours) {
+        bool ok = false, primary = false, over = false;
+        uint32_t n_lines = 0;
+        if (tk.y >= 0 && tk.y < a.n_tours) {
             const int4 mv = M.moves[tk.x];
-            ok = walk_task(M, tk, mv, primary, [&](uint32_t key) { feat_insert(f, key); });
+            const bool swap = mv.x == 2;
+            const int32_t* map = a.slot_map + (int64_t)mv.w * a.slot_stride;
+            const int q0 = a.tour_off[tk.y], q1 = a.tour_off[tk.y + 1];
+            const int add = (!swap && tk.z >= 0) ? tk.z : -1;
+            const int rem = (!swap && tk.w >= 0) ? tk.w : -1;
+            bool bad = !(q0 >= 0 && q1 >= q0 && (int64_t)q1 <= a.n_seq);
+            int hit_min = 0x7fffffff;
+            bool own_has_s1 = false;
+            const int q_end = bad ? q0 : (add >= 0 ? q1 + 1 : q1);
+            for (int qb = q0; qb < q_end; qb += 32) {
+                const int q = qb + lane;
+                if (bad || q >= q_end) continue;
+                const int o = q < q1 ? a.order_seq[q] : add;
+                if (q < q1 && o == rem) continue;
+                int lb, le;
+                if (order_lines_checked(a, o, lb, le) < 0) { bad = true; continue; }
+                for (int l = lb; l < le; ++l) {
+                    const int s = a.line_sku[l];
+                    if ((unsigned)s >= (unsigned)a.n_sku) { bad = true; break; }
+                    if (swap && (s == mv.y || s == mv.z)) {
+                        hit_min = min(hit_min, o);
+                        if (o == tk.z && s == mv.y) own_has_s1 = true;
+                    }
+                    const int loc = task_loc(map, s, swap, mv.y, mv.z);
+                    if ((unsigned)loc >= (unsigned)a.g.n_loc) { bad = true; break; }
+                    over |= !wf_insert(w, loc_key(a.g, loc));
+                    ++n_lines;
+                }
+            }
+            ok = !__any_sync(0xffffffffu, bad);
+            hit_min = __reduce_min_sync(0xffffffffu, hit_min);
+            own_has_s1 = __any_sync(0xffffffffu, own_has_s1);
+            primary = !swap || (hit_min == tk.z && (tk.w == -2 || !own_has_s1));
         }
-        // mark the tasks that count (one per changed tour) for the selection
-        M.task_cost[i] = (ok && primary && !f.overflow) ? make_int2(0, 0) : make_int2(-1, -1);
-        f.overflow = false;
-        feat_finish(f, c, X + i * 24);
+        over = __any_sync(0xffffffffu, over);
+        n_lines = __reduce_add_sync(0xffffffffu, n_lines);
+        if (lane == 0) M.task_cost[i] = (ok && primary && !over) ? make_int2(0, 0) : make_int2(-1, -1);
+        wf_finish(w, c, lane, n_lines, X + i * 24);
     }
 }
 
@@ -740,17 +772,14 @@ __global__ void k_screen_select(ScreenArgs S) {
 
 cudaError_t launch_task_features(const MoveArgs& M, const FeatConst& c, void* X, int num_sms, cudaStream_t s) {
     if (M.n_tasks == 0) return cudaSuccess;
-    const size_t smem = (sizeof(uint32_t) + 1) * FEAT_SLOTS * 128 + (size_t)FEAT_CNT_STRIDE * 128;
-    cudaError_t e = cudaFuncSetAttribute(k_task_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_task_features, 128, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_task_features, TF_THREADS, 0);
     if (e != cudaSuccess) return e;
-    int64_t want = (M.n_tasks + 127) / 128;
-    int grid = per_sm * num_sms;
-    if (grid > want) grid = (int)want;
+    int64_t grid = (int64_t)per_sm * num_sms;
+    const int64_t want = (M.n_tasks + TF_THREADS / 32 - 1) / (TF_THREADS / 32);
+    if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    k_task_features<<<grid, 128, smem, s>>>(M, c, static_cast<uint4*>(X));
+    k_task_features<<<(int)grid, TF_THREADS, 0, s>>>(M, c, static_cast<uint4*>(X));
     return cudaGetLastError();
 }
 

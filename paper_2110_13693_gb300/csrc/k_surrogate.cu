@@ -15,7 +15,7 @@ namespace wh {
 
 namespace {
 
-constexpr int FEAT_THREADS = 128;
+constexpr int FEAT_THREADS = 256;
 constexpr int G_BM = 128, G_BN = 128, G_BK = 32, G_PAD = 8, G_THREADS = 256;
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -24,24 +24,16 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 // --------------------------------------------------------------- features
-// One tour per thread: gather the tour's line keys, hash the visited aisles,
-// write the tour's 192 bf16 features.
+// One tour per warp (WarpFeat): lane j gathers the lines of the tour's
+// orders j, j + 32, ...; the warp writes the tour's 192 bf16 features.
 __global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst c, uint4* X) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int T = blockDim.x, tid = threadIdx.x;
-    FeatThread f;
-    f.tab = reinterpret_cast<uint32_t*>(smem) + tid;
-    f.list = smem + sizeof(uint32_t) * FEAT_SLOTS * T + tid;
-    unsigned char* cnt_base = smem + (sizeof(uint32_t) + 1) * FEAT_SLOTS * T;
-    f.cnt = cnt_base + (size_t)tid * FEAT_CNT_STRIDE;
-    f.T = T;
-    f.n_aisles = 0;
-    f.n_lines = 0;
-    f.overflow = false;
-    for (int i = 0; i < FEAT_SLOTS; ++i) f.tab[i * T] = 0;
-    for (int i = 0; i < FEAT_CNT_STRIDE / 4; ++i) reinterpret_cast<uint32_t*>(f.cnt)[i] = 0;
+    __shared__ WarpFeat ws[FEAT_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpFeat& w = ws[wid];
+    wf_init(w, lane);
     const bool shared_map = a.slot_stride == 0;
-    for (int t = blockIdx.x * T + tid; t < a.n_tours; t += gridDim.x * T) {
+    const int64_t n_warps = (int64_t)gridDim.x * (FEAT_THREADS / 32);
+    for (int64_t t = (int64_t)blockIdx.x * (FEAT_THREADS / 32) + wid; t < a.n_tours; t += n_warps) {
         int plan = 0;
         if (!shared_map) {
             int lo = 0, hi = a.n_plans - 1;
@@ -54,11 +46,15 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst
         const int32_t* map = a.slot_map + (int64_t)plan * a.slot_stride;
         const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];
         bool bad = q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq;
-        for (int q = q0; !bad && q < q1; ++q) {
+        bool over = false;
+        uint32_t n_lines = 0;
+        for (int qb = q0; !bad && qb < q1; qb += 32) {
+            const int q = qb + lane;
+            if (q >= q1) continue;
             const int o = a.order_seq[q];
-            if ((unsigned)o >= (unsigned)a.n_orders) { bad = true; break; }
+            if ((unsigned)o >= (unsigned)a.n_orders) { bad = true; continue; }
             const int lb = a.order_off[o], le = a.order_off[o + 1];
-            if (lb < 0 || le < lb || le > a.n_lines) { bad = true; break; }
+            if (lb < 0 || le < lb || le > a.n_lines) { bad = true; continue; }
             for (int l = lb; l < le; ++l) {
                 uint32_t key;
                 if (shared_map) {
@@ -69,14 +65,15 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst
                     key = (unsigned)loc < (unsigned)a.g.n_loc ? loc_key(a.g, loc) : KEY_BAD;
                 }
                 if (key == KEY_BAD) { bad = true; break; }
-                feat_insert(f, key);
+                over |= !wf_insert(w, key);
+                ++n_lines;
             }
         }
-        if (bad || f.overflow) {
-            flag(a.status, bad ? WH_STATUS_BAD_ORDER : WH_STATUS_TOUR_TOO_LONG);
-            f.overflow = false;
-        }
-        feat_finish(f, c, X + (int64_t)t * 24);
+        bad = __any_sync(0xffffffffu, bad);
+        over = __any_sync(0xffffffffu, over);
+        n_lines = __reduce_add_sync(0xffffffffu, n_lines);
+        if ((bad || over) && lane == 0) flag(a.status, bad ? WH_STATUS_BAD_ORDER : WH_STATUS_TOUR_TOO_LONG);
+        wf_finish(w, c, lane, n_lines, X + t * 24);
     }
 }
 
@@ -287,23 +284,16 @@ int blocks_for(int64_t n, int t, int cap = 4096) {
 
 }  // namespace
 
-size_t features_smem_bytes() {
-    return (sizeof(uint32_t) + 1) * FEAT_SLOTS * FEAT_THREADS + (size_t)FEAT_CNT_STRIDE * FEAT_THREADS;
-}
-
 cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, int num_sms, cudaStream_t s) {
     if (a.n_tours == 0) return cudaSuccess;
-    const size_t smem = features_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_features, FEAT_THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_features, FEAT_THREADS, 0);
     if (e != cudaSuccess) return e;
-    int grid = per_sm * num_sms;
-    const int want = (a.n_tours + FEAT_THREADS - 1) / FEAT_THREADS;
+    int64_t grid = (int64_t)per_sm * num_sms;
+    const int64_t want = ((int64_t)a.n_tours + FEAT_THREADS / 32 - 1) / (FEAT_THREADS / 32);
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    k_features<<<grid, FEAT_THREADS, smem, s>>>(a, c, static_cast<uint4*>(X));
+    k_features<<<(int)grid, FEAT_THREADS, 0, s>>>(a, c, static_cast<uint4*>(X));
     return cudaGetLastError();
 }
 

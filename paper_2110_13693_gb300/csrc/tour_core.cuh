@@ -347,83 +347,91 @@ __device__ __forceinline__ long long segmented_sum(long long v, int key, int lan
 // visited aisles of the deepest and shallowest pick's slot bin
 // floor(k*64/L), leftmost / rightmost aisle and aisle count times 1/A, line
 // count / 64, and a 60-bin histogram of the visited aisles floor(a*60/A).
-// Per-aisle extremes come from a per-thread open-addressing hash of the
-// visited aisles (no sort).  Bins use exact multiply-shift division:
-// floor(n/d) = (n * ceil(2^40/d)) >> 40 for n < 2^22 and d < 2^16.
-constexpr int FEAT_SLOTS = 128;        // hash slots per thread (distinct aisles per tour)
-constexpr int FEAT_CNT_STRIDE = 196;   // bytes per thread row of counters (49 words: no bank conflicts)
+// Bins use exact multiply-shift division: floor(n/d) = (n * ceil(2^40/d)) >> 40
+// for n < 2^22 and d < 2^16.
+//
+// Warp-cooperative: the lanes of a warp gather a tour's lines
+// in parallel (one order per lane) and merge the picks into a per-warp
+// open-addressing table of visited aisles (shared-memory atomics keep each
+// aisle's smallest and largest slot index); the table then feeds the
+// histograms and the four scalars, written as one coalesced 384-byte row.
+constexpr int WF_SLOTS = 128;    // distinct aisles per tour
 
-struct FeatThread {
-    uint32_t* tab;      // [FEAT_SLOTS][T] entries ((a+1) << 16 | kmin << 8 | kmax), 0 = empty
-    uint8_t* list;      // [FEAT_SLOTS][T] occupied slot indices
-    uint8_t* cnt;       // this thread's FEAT_CNT_STRIDE counter bytes
-    int T;
-    int n_aisles;       // occupied slots
-    int n_lines;
-    bool overflow;
+struct WarpFeat {
+    uint32_t key[WF_SLOTS];     // aisle + 1, 0 = empty
+    uint32_t lo[WF_SLOTS];      // smallest slot index seen, 0xFFFFFFFF = none
+    uint32_t hi[WF_SLOTS];      // largest slot index seen
+    uint32_t cnt[WH_FEATURES];  // histogram counters
 };
 
-__device__ __forceinline__ void feat_insert(FeatThread& f, uint32_t key32) {
-    const uint32_t a = key32 >> 16, k = key32 & 0xFFu;
-    ++f.n_lines;
-    uint32_t h = (a * 2654435761u) >> 25;   // 7 bits
-    for (int probe = 0; probe < FEAT_SLOTS; ++probe) {
-        uint32_t* e = f.tab + h * f.T;
-        const uint32_t v = *e;
-        if (v == 0) {
-            *e = ((a + 1) << 16) | (k << 8) | k;
-            f.list[f.n_aisles * f.T] = (uint8_t)h;
-            ++f.n_aisles;
-            return;
-        }
-        if ((v >> 16) == a + 1) {
-            const uint32_t lo = min((v >> 8) & 0xFFu, k), hi = max(v & 0xFFu, k);
-            *e = ((a + 1) << 16) | (lo << 8) | hi;
-            return;
-        }
-        h = (h + 1) & (FEAT_SLOTS - 1);
+__device__ __forceinline__ void wf_init(WarpFeat& w, int lane) {
+    for (int i = lane; i < WF_SLOTS; i += 32) {
+        w.key[i] = 0u;
+        w.lo[i] = 0xFFFFFFFFu;
+        w.hi[i] = 0u;
     }
-    f.overflow = true;
+    for (int i = lane; i < WH_FEATURES; i += 32) w.cnt[i] = 0u;
+    __syncwarp();
+}
+
+// Merge one pick (key32 = aisle << 16 | slot index); false when the tour
+// visits more than WF_SLOTS aisles.
+__device__ __forceinline__ bool wf_insert(WarpFeat& w, uint32_t key32) {
+    const uint32_t a = key32 >> 16, k = key32 & 0xFFu;
+    uint32_t h = (a * 2654435761u) >> 25;   // 7 bits
+    for (int probe = 0; probe < WF_SLOTS; ++probe) {
+        const uint32_t old = atomicCAS(&w.key[h], 0u, a + 1u);
+        if (old == 0u || old == a + 1u) {
+            atomicMin(&w.lo[h], k);
+            atomicMax(&w.hi[h], k);
+            return true;
+        }
+        h = (h + 1u) & (WF_SLOTS - 1);
+    }
+    return false;
 }
 
 __device__ __forceinline__ uint32_t feat_div(uint32_t n, uint64_t magic) {
     return (uint32_t)(((uint64_t)n * magic) >> 40);
 }
 
-// Write the tour's 192 bf16 features to row (16-byte aligned) and leave the
-// thread's hash table and counters zeroed for the next tour.
-__device__ __forceinline__ void feat_finish(FeatThread& f, const FeatConst& c, uint4* row) {
-    int amin = 0x7fffffff, amax = -1;
-    for (int j = 0; j < f.n_aisles; ++j) {
-        const uint32_t h = f.list[j * f.T];
-        uint32_t* e = f.tab + h * f.T;
-        const uint32_t v = *e;
-        *e = 0;
-        const int a = (int)(v >> 16) - 1;
-        const uint32_t lo = (v >> 8) & 0xFFu, hi = v & 0xFFu;
-        f.cnt[feat_div(hi * 64u, c.magic_l)] += 1;
-        f.cnt[64 + feat_div(lo * 64u, c.magic_l)] += 1;
-        f.cnt[132 + feat_div((uint32_t)a * 60u, c.magic_a)] += 1;
+// Write the tour's 192 bf16 features to row (16-byte aligned, lanes 0..23
+// write 16 bytes each) and leave the table and counters empty.  n_lines is
+// the warp's total line count.
+__device__ __forceinline__ void wf_finish(WarpFeat& w, const FeatConst& c, int lane, uint32_t n_lines, uint4* row) {
+    __syncwarp();
+    int amin = 0x7fffffff, amax = -1, na = 0;
+    for (int i = lane; i < WF_SLOTS; i += 32) {
+        const uint32_t kv = w.key[i];
+        if (kv == 0u) continue;
+        const int a = (int)kv - 1;
+        const uint32_t lo = w.lo[i], hi = w.hi[i];
+        atomicAdd(&w.cnt[feat_div(hi * 64u, c.magic_l)], 1u);
+        atomicAdd(&w.cnt[64 + feat_div(lo * 64u, c.magic_l)], 1u);
+        atomicAdd(&w.cnt[132 + feat_div((uint32_t)a * 60u, c.magic_a)], 1u);
         amin = min(amin, a);
         amax = max(amax, a);
+        ++na;
+        w.key[i] = 0u;
+        w.lo[i] = 0xFFFFFFFFu;
+        w.hi[i] = 0u;
     }
-    const float sc[4] = {f.n_aisles ? (float)amin * c.inv_a : 0.0f, f.n_aisles ? (float)amax * c.inv_a : 0.0f,
-                         (float)f.n_aisles * c.inv_a, (float)f.n_lines * (1.0f / 64.0f)};
-    uint32_t* words = reinterpret_cast<uint32_t*>(f.cnt);
-#pragma unroll 4
-    for (int q = 0; q < 24; ++q) {          // 8 features per 16-byte store
-        const uint32_t w0 = words[2 * q], w1 = words[2 * q + 1];
-        words[2 * q] = 0;
-        words[2 * q + 1] = 0;
+    amin = __reduce_min_sync(0xffffffffu, amin);
+    amax = __reduce_max_sync(0xffffffffu, amax);
+    na = (int)__reduce_add_sync(0xffffffffu, (unsigned)na);
+    __syncwarp();
+    if (lane < 24) {
         float v[8];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            v[b] = (float)((w0 >> (8 * b)) & 0xFFu);
-            v[4 + b] = (float)((w1 >> (8 * b)) & 0xFFu);
+        for (int b = 0; b < 8; ++b) {
+            v[b] = (float)w.cnt[8 * lane + b];
+            w.cnt[8 * lane + b] = 0u;
         }
-        if (q == 16) {                       // features 128..135: the four scalars, then counters
-#pragma unroll
-            for (int b = 0; b < 4; ++b) v[b] = sc[b];
+        if (lane == 16) {   // features 128..131: the four scalars
+            v[0] = na ? (float)amin * c.inv_a : 0.0f;
+            v[1] = na ? (float)amax * c.inv_a : 0.0f;
+            v[2] = (float)na * c.inv_a;
+            v[3] = (float)n_lines * (1.0f / 64.0f);
         }
         uint4 o;
         __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
@@ -432,10 +440,9 @@ __device__ __forceinline__ void feat_finish(FeatThread& f, const FeatConst& c, u
         o.y = *reinterpret_cast<uint32_t*>(&p1);
         o.z = *reinterpret_cast<uint32_t*>(&p2);
         o.w = *reinterpret_cast<uint32_t*>(&p3);
-        row[q] = o;
+        row[lane] = o;
     }
-    f.n_aisles = 0;
-    f.n_lines = 0;
+    __syncwarp();
 }
 
 }  // namespace

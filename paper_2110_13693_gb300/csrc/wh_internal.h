@@ -174,7 +174,6 @@ struct FeatConst {
     uint64_t magic_l;   // ceil(2^40 / L)
     float inv_a;        // (float)(1.0 / A)
 };
-size_t features_smem_bytes();
 cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, int num_sms, cudaStream_t s);
 cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 0 bias+GELU, 1 fp32, 2 GELU grad
 cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s);
