@@ -314,16 +314,6 @@ __global__ void __launch_bounds__(256, 2) k_eval_batch(BatchArgs b) {
     }
 }
 
-__device__ __forceinline__ int warp_inclusive_scan(int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
-
 // One warp per deferred tour (more than SHORT_MAX lines): keys gathered into
 // a per-warp shared-memory buffer, bitonic-sorted there, then one lane runs
 // the record scan and the DP.
@@ -536,9 +526,11 @@ cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int
 }
 
 cudaError_t launch_eval_long(const LongArgs& L, bool shared_map, int num_sms, cudaStream_t s) {
-    const int grid = num_sms * 2;
-    if (shared_map) k_eval_long<true><<<grid, LONG_WARPS * 32, 0, s>>>(L);
-    else k_eval_long<false><<<grid, LONG_WARPS * 32, 0, s>>>(L);
+    auto kern = shared_map ? k_eval_long<true> : k_eval_long<false>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LONG_WARPS * 32, 0);
+    if (e != cudaSuccess) return e;
+    kern<<<num_sms * (per_sm > 0 ? per_sm : 1), LONG_WARPS * 32, 0, s>>>(L);
     return cudaGetLastError();
 }
 

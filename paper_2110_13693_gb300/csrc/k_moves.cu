@@ -402,6 +402,54 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
     }
 }
 
+// Warp-parallel form of walk_task: lane j walks the changed tour's orders
+// j, j + 32, ... (the added order last) and stores its keys at positions
+// given by a warp prefix sum of the order line counts; only the first `cap`
+// keys are stored.  Returns ok and sets n and primary (all warp-uniform).
+__device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk, const int4 mv, uint32_t* kb,
+                                               int cap, int lane, int& n_out, bool& primary) {
+    const EvalArgs& a = M.a;
+    const bool swap = mv.x == 2;
+    const int32_t* map = a.slot_map + (int64_t)mv.w * a.slot_stride;
+    const int q0 = a.tour_off[tk.y], q1 = a.tour_off[tk.y + 1];
+    const int add = (!swap && tk.z >= 0) ? tk.z : -1;
+    const int rem = (!swap && tk.w >= 0) ? tk.w : -1;
+    bool bad = !(q0 >= 0 && q1 >= q0 && (int64_t)q1 <= a.n_seq);
+    const int q_end = bad ? q0 : (add >= 0 ? q1 + 1 : q1);
+    int hit_min = 0x7fffffff, n = 0;
+    bool own_has_s1 = false;
+    for (int qb = q0; qb < q_end; qb += 32) {
+        const int q = qb + lane;
+        int o = -1, lb = 0, le = 0;
+        if (!bad && q < q_end) {
+            o = q < q1 ? a.order_seq[q] : add;
+            if (q < q1 && o == rem) o = -1;
+            else if (order_lines_checked(a, o, lb, le) < 0) { bad = true; lb = le = 0; }
+        }
+        const int cnt = le - lb;
+        const int incl = warp_inclusive_scan(cnt);
+        int pos = n + incl - cnt;
+        for (int l = lb; l < le; ++l, ++pos) {
+            const int s = a.line_sku[l];
+            if ((unsigned)s >= (unsigned)a.n_sku) { bad = true; break; }
+            if (swap && (s == mv.y || s == mv.z)) {
+                hit_min = min(hit_min, o);
+                if (o == tk.z && s == mv.y) own_has_s1 = true;
+            }
+            const int loc = task_loc(map, s, swap, mv.y, mv.z);
+            if ((unsigned)loc >= (unsigned)a.g.n_loc) { bad = true; break; }
+            if (pos < cap) kb[pos] = loc_key(a.g, loc);
+        }
+        n += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    const bool ok = !__any_sync(0xffffffffu, bad);
+    hit_min = __reduce_min_sync(0xffffffffu, hit_min);
+    own_has_s1 = __any_sync(0xffffffffu, own_has_s1);
+    primary = !swap || (hit_min == tk.z && (tk.w == -2 || !own_has_s1));
+    n_out = n;
+    return ok;
+}
+
 // one warp per task of more than SHORT_MAX lines
 __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
     __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
@@ -414,15 +462,8 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
         const int4 tk = M.tasks[i];
         const int4 mv = M.moves[tk.x];
         int n = 0;
-        bool primary = false, ok = true;
-        if (lane == 0) {
-            ok = walk_task(M, tk, mv, primary, [&](uint32_t k) {
-                if (n < LONG_MAXL) kb[n] = k;
-                ++n;
-            });
-        }
-        n = __shfl_sync(0xffffffffu, n, 0);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
+        bool primary = false;
+        const bool ok = walk_task_warp(M, tk, mv, kb, LONG_MAXL, lane, n, primary);
         __syncwarp();
         if (!ok || n > LONG_MAXL) {
             if (lane == 0) {
@@ -544,7 +585,9 @@ cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStre
         if (grid > want) grid = (int)want;
         if (grid < 1) grid = 1;
         kern<<<grid, MV_THREADS, smem, s>>>(M);
-        k_mv_long<<<num_sms * 2, LONG_WARPS * 32, 0, s>>>(M);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mv_long, LONG_WARPS * 32, 0);
+        if (e != cudaSuccess) return e;
+        k_mv_long<<<num_sms * (per_sm > 0 ? per_sm : 1), LONG_WARPS * 32, 0, s>>>(M);
     }
     if (M.n_moves > 0) k_mv_finish<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
     return cudaGetLastError();

@@ -340,7 +340,16 @@ __device__ __forceinline__ long long segmented_sum(long long v, int key, int lan
     return v;
 }
 
-// ------------------------------------------------------------------ kernels
+// inclusive prefix sum over the 32 lanes of a warp
+__device__ __forceinline__ int warp_inclusive_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
 
 // ------------------------------------------------------ surrogate features
 // 192 features of a tour (the surrogate's input): histograms over its
