@@ -187,13 +187,16 @@ int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * applied moves from the new tour costs that the wh_eval_moves call which
  * scored exactly these moves (same `moves` pointer, the last move evaluation
  * on this handle) computed -- no full re-evaluation is needed; when NULL the
- * costs are left stale (refresh them with wh_eval_plans).  Each plan's segment of order_seq
+ * costs are left stale (refresh them with wh_eval_plans).  tour_changed (device,
+ * one byte per tour, may be NULL; needs costs): set to 1 for every tour an
+ * applied move rewrote, for wh_surrogate_screen's prediction cache; other
+ * bytes are left as they are.  Each plan's segment of order_seq
  * may hold at most max(n_orders, 1) entries (WH_STATUS_BAD_OFFSET otherwise,
  * and that plan is left unchanged).  Returns WH_OK, WH_EINVAL, WH_ERANGE
  * (n_orders beyond 50,000: the staging buffer) or WH_ECUDA. */
 int wh_ls_apply(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *moves,
                 int32_t moves_per_plan, const int64_t *delta, const int32_t *status, int32_t *applied,
-                const wh_costs *costs, void *stream);
+                const wh_costs *costs, uint8_t *tour_changed, void *stream);
 
 /* ------------------------------------------------------------------------
  * Learned prescreen (machine learning in the decision loop, Sec. 1 and
@@ -256,12 +259,20 @@ int wh_surrogate_train_step(wh_surrogate *s, const uint16_t *X, const float *tar
  * minus predicted current length) and keeps the `keep` moves with the lowest
  * prediction (ties: lowest index) in kept[(p*keep + j)*4 .. +3]; places
  * without an eligible move get {9, 0, 0, p}, which wh_eval_moves reports as
- * invalid.  Score the kept moves exactly with wh_eval_moves.  Synchronises
- * `stream` once; may allocate scratch.  Returns WH_OK, WH_EINVAL, WH_ERANGE,
- * WH_ENOMEM or WH_ECUDA. */
+ * invalid.  Score the kept moves exactly with wh_eval_moves.
+ * Prediction cache of the current tours (both may be NULL):
+ *   y_tour_cache NULL: every tour is predicted, nothing kept;
+ *   y_tour_cache set, tour_changed NULL: every tour is predicted into the
+ *     cache (float per tour, device);
+ *   both set: only the tours whose tour_changed byte is non-zero (as
+ *     wh_ls_apply sets them) are predicted into the cache, and their bytes
+ *     are cleared; the other entries must hold the current predictions.
+ * Synchronises `stream` (once, twice with tour_changed); may allocate
+ * scratch.  Returns WH_OK, WH_EINVAL, WH_ERANGE, WH_ENOMEM or WH_ECUDA. */
 int wh_surrogate_screen(wh_layout *layout, wh_surrogate *s, const wh_orders *orders, const wh_plans *plans,
                         const int32_t *moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders_per_tour,
-                        int32_t max_lines_per_tour, int32_t *kept, void *stream);
+                        int32_t max_lines_per_tour, float *y_tour_cache, uint8_t *tour_changed, int32_t *kept,
+                        void *stream);
 
 void wh_surrogate_destroy(wh_surrogate *s);
 

@@ -67,7 +67,7 @@ SIGNATURES = {
     "wh_get_last_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "wh_ls_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                    ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "wh_eval_moves": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -101,7 +101,8 @@ SIGNATURES = {
                                                ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(wh_orders),
                                            ctypes.POINTER(wh_plans), ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "wh_surrogate_destroy": (None, [ctypes.c_void_p]),
 }
@@ -175,12 +176,13 @@ def wh_eval_moves(layout, orders: wh_orders, plans: wh_plans, tour_s, tour_rr, m
 
 
 def wh_ls_apply(layout, orders: wh_orders, plans: wh_plans, moves, moves_per_plan: int, delta, status, applied,
-                costs=None, stream=None) -> None:
-    """costs: a wh_costs to update in place (or None)."""
+                costs=None, tour_changed=None, stream=None) -> None:
+    """costs: a wh_costs to update in place (or None); tour_changed: device
+    pointer of a uint8 per tour, set for every rewritten tour (or None)."""
     _check(load().wh_ls_apply(layout, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(moves),
                               moves_per_plan, ctypes.c_void_p(delta), ctypes.c_void_p(status),
                               ctypes.c_void_p(applied), ctypes.byref(costs) if costs is not None else None,
-                              _stream_ptr(stream)), "wh_ls_apply")
+                              ctypes.c_void_p(tour_changed), _stream_ptr(stream)), "wh_ls_apply")
 
 
 def wh_get_last_status(layout, stream=None) -> int:
@@ -351,29 +353,36 @@ class Layout:
         return delta[:n], status[:n]
 
     def ls_step(self, prob: DeviceProblem, costs: Costs, moves, moves_per_plan: int, max_orders: int = 0,
-                max_lines: int = 0, stream=None, refresh: bool = False):
+                max_lines: int = 0, stream=None, refresh: bool = False, changed=None):
         """One exact local-search step: score the moves, apply each plan's best
         improving move in place and update the costs of the changed tours
-        (refresh=True re-scores every tour instead).  Returns applied [n_plans]."""
+        (refresh=True re-scores every tour instead).  `changed` (uint8 device
+        tensor, one byte per tour) gets a 1 for every rewritten tour.  Returns
+        applied [n_plans]."""
         import torch
         mv = moves.reshape(-1, 4).contiguous()
         delta, status = self.eval_moves(prob, costs, mv, max_orders, max_lines, stream)
         applied = torch.empty(max(prob.n_plans, 1), dtype=torch.int32, device=mv.device)
         wh_ls_apply(self.handle, prob.orders(), prob.plans(), _ptr(mv), moves_per_plan, _ptr(delta), _ptr(status),
-                    _ptr(applied), None if refresh else costs.c(), stream)
+                    _ptr(applied), None if refresh else costs.c(), None if changed is None else _ptr(changed), stream)
         if refresh:
             self.eval_plans(prob, costs, 3, stream)
         return applied[:prob.n_plans]
 
     def screen(self, surrogate: "Surrogate", prob: DeviceProblem, moves, moves_per_plan: int, keep: int,
-               max_orders: int = 0, max_lines: int = 0, stream=None):
+               max_orders: int = 0, max_lines: int = 0, stream=None, y_tour=None, changed=None):
         """The `keep` most promising moves per plan by the surrogate's
-        prediction: int32 [n_plans * keep, 4] (device)."""
+        prediction: int32 [n_plans * keep, 4] (device).  With y_tour (float32
+        per tour) the current tours' predictions are kept there between
+        calls: with `changed` (uint8 per tour, as ls_step sets it) only the
+        flagged tours are re-predicted and their flags cleared, without it
+        every tour is."""
         import torch
         mv = moves.reshape(-1, 4).contiguous()
         kept = torch.empty((max(prob.n_plans * keep, 1), 4), dtype=torch.int32, device=mv.device)
         wh_surrogate_screen(self.handle, surrogate.handle, prob.orders(), prob.plans(), _ptr(mv), moves_per_plan,
-                            keep, max_orders, max_lines, _ptr(kept), stream)
+                            keep, max_orders, max_lines, _ptr(kept), None if y_tour is None else _ptr(y_tour),
+                            None if changed is None else _ptr(changed), stream)
         return kept[:prob.n_plans * keep]
 
     def set_timing(self, enable: bool) -> None:
@@ -508,10 +517,11 @@ def wh_surrogate_train_step(s, X, target, n: int, lr: float, loss=0, stream=None
 
 
 def wh_surrogate_screen(layout, s, orders: wh_orders, plans: wh_plans, moves, moves_per_plan: int, keep: int,
-                        max_orders: int, max_lines: int, kept, stream=None) -> None:
+                        max_orders: int, max_lines: int, kept, y_tour=None, tour_changed=None, stream=None) -> None:
     _check(load().wh_surrogate_screen(layout, s, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(moves),
-                                      moves_per_plan, keep, max_orders, max_lines, ctypes.c_void_p(kept),
-                                      _stream_ptr(stream)), "wh_surrogate_screen")
+                                      moves_per_plan, keep, max_orders, max_lines, ctypes.c_void_p(y_tour),
+                                      ctypes.c_void_p(tour_changed), ctypes.c_void_p(kept), _stream_ptr(stream)),
+           "wh_surrogate_screen")
 
 
 def wh_surrogate_destroy(s) -> None:

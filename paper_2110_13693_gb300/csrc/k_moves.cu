@@ -687,6 +687,7 @@ __global__ void k_ls_apply(LsArgs L) {
                     const int t = L.tasks[i].y;
                     if (L.tour_s) L.tour_s[t] = c.x;
                     if (L.tour_rr) L.tour_rr[t] = c.y;
+                    if (L.tour_changed) L.tour_changed[t] = 1;
                 }
                 if (tid == 0) {
                     if (L.plan_s) L.plan_s[p] += L.delta[2 * m];

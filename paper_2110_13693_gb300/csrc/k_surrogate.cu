@@ -25,15 +25,19 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 
 // --------------------------------------------------------------- features
 // One tour per warp (WarpFeat): lane j gathers the lines of the tour's
-// orders j, j + 32, ...; the warp writes the tour's 192 bf16 features.
-__global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst c, uint4* X) {
+// orders j, j + 32, ...; the warp writes the tour's 192 bf16 features.  Row
+// r holds tour list[r] when a list is given, else tour r.
+__global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst c, const int32_t* list,
+                                                           int64_t n_rows, uint4* X) {
     __shared__ WarpFeat ws[FEAT_THREADS / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpFeat& w = ws[wid];
     wf_init(w, lane);
     const bool shared_map = a.slot_stride == 0;
+    const bool keyed = a.line_key != nullptr;   // per-line keys precomputed (shared slotting)
     const int64_t n_warps = (int64_t)gridDim.x * (FEAT_THREADS / 32);
-    for (int64_t t = (int64_t)blockIdx.x * (FEAT_THREADS / 32) + wid; t < a.n_tours; t += n_warps) {
+    for (int64_t r = (int64_t)blockIdx.x * (FEAT_THREADS / 32) + wid; r < n_rows; r += n_warps) {
+        const int t = list ? list[r] : (int)r;
         int plan = 0;
         if (!shared_map) {
             int lo = 0, hi = a.n_plans - 1;
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst
             if (lb < 0 || le < lb || le > a.n_lines) { bad = true; continue; }
             for (int l = lb; l < le; ++l) {
                 uint32_t key;
-                if (shared_map) {
+                if (keyed) {
                     key = a.line_key[l];
                 } else {
                     const int s = a.line_sku[l];
@@ -73,7 +77,30 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(EvalArgs a, FeatConst
         over = __any_sync(0xffffffffu, over);
         n_lines = __reduce_add_sync(0xffffffffu, n_lines);
         if ((bad || over) && lane == 0) flag(a.status, bad ? WH_STATUS_BAD_ORDER : WH_STATUS_TOUR_TOO_LONG);
-        wf_finish(w, c, lane, n_lines, X + t * 24);
+        wf_finish(w, c, lane, n_lines, X + r * 24);
+    }
+}
+
+// list <- indices of the set bytes of flag (any order), *count <- their number
+__global__ void k_compact_flags(const uint8_t* flag, int64_t n, int32_t* list, int32_t* count) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool f = i < n && flag[i] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        int off = 0;
+        if (lane == 0 && m) off = atomicAdd(count, __popc(m));
+        off = __shfl_sync(0xffffffffu, off, 0);
+        if (f) list[off + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+}
+
+// y_tour[list[j]] = y[j] and clear the tour's flag
+__global__ void k_scatter_pred(const int32_t* list, const float* y, int64_t n, float* y_tour, uint8_t* flag) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int t = list[j];
+        y_tour[t] = y[j];
+        flag[t] = 0;
     }
 }
 
@@ -284,16 +311,31 @@ int blocks_for(int64_t n, int t, int cap = 4096) {
 
 }  // namespace
 
-cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, int num_sms, cudaStream_t s) {
-    if (a.n_tours == 0) return cudaSuccess;
+cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, const int32_t* list, int64_t n_rows,
+                            int num_sms, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_features, FEAT_THREADS, 0);
     if (e != cudaSuccess) return e;
     int64_t grid = (int64_t)per_sm * num_sms;
-    const int64_t want = ((int64_t)a.n_tours + FEAT_THREADS / 32 - 1) / (FEAT_THREADS / 32);
+    const int64_t want = (n_rows + FEAT_THREADS / 32 - 1) / (FEAT_THREADS / 32);
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    k_features<<<(int)grid, FEAT_THREADS, 0, s>>>(a, c, static_cast<uint4*>(X));
+    k_features<<<(int)grid, FEAT_THREADS, 0, s>>>(a, c, list, n_rows, static_cast<uint4*>(X));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_flags(const uint8_t* flag, int64_t n, int32_t* list, int32_t* count, cudaStream_t s) {
+    if (cudaMemsetAsync(count, 0, sizeof(int32_t), s) != cudaSuccess) return cudaGetLastError();
+    if (n <= 0) return cudaSuccess;
+    k_compact_flags<<<blocks_for(n, 256), 256, 0, s>>>(flag, n, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_pred(const int32_t* list, const float* y, int64_t n, float* y_tour, uint8_t* flag,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_scatter_pred<<<blocks_for(n, 256), 256, 0, s>>>(list, y, n, y_tour, flag);
     return cudaGetLastError();
 }
 

@@ -388,9 +388,10 @@ extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_pla
 
 extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orders* orders, const wh_plans* plans,
                                    const int32_t* moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders,
-                                   int32_t max_lines, int32_t* kept, void* stream) {
+                                   int32_t max_lines, float* y_tour_cache, uint8_t* tour_changed, int32_t* kept,
+                                   void* stream) {
     if (!h || !sg || !orders || !plans || !moves || !kept || moves_per_plan < 1 || moves_per_plan > 256 ||
-        keep < 1 || keep > moves_per_plan || max_orders < 0 || max_lines < 0)
+        keep < 1 || keep > moves_per_plan || max_orders < 0 || max_lines < 0 || (tour_changed && !y_tour_cache))
         return WH_EINVAL;
     const wh_orders o = *orders;
     const wh_plans p = *plans;
@@ -423,7 +424,8 @@ extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orde
     if (wh::launch_moves_fill(M, s) != cudaSuccess) return WH_ECUDA;
     // features and predictions of the current tours and of the tasks' changed tours
     const size_t need = head + align_up(feat_row * (size_t)(p.n_tours + 1)) + align_up(sizeof(float) * (size_t)(p.n_tours + 1)) +
-                        align_up(feat_row * (size_t)(M.n_tasks + 1)) + align_up(sizeof(float) * (size_t)(M.n_tasks + 1));
+                        align_up(feat_row * (size_t)(M.n_tasks + 1)) + align_up(sizeof(float) * (size_t)(M.n_tasks + 1)) +
+                        align_up(sizeof(int32_t) * (size_t)(p.n_tours + 2));
     if (need > h->sr_scratch_bytes) {
         // grow keeping nothing: the head (status, delta) must be rebuilt, so
         // size for the worst case and redo the preparation
@@ -447,23 +449,43 @@ extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orde
     uint16_t* X_task = reinterpret_cast<uint16_t*>(b + at);
     at += align_up(feat_row * (size_t)(M.n_tasks + 1));
     float* y_task = reinterpret_cast<float*>(b + at);
+    at += align_up(sizeof(float) * (size_t)(M.n_tasks + 1));
+    int32_t* list = reinterpret_cast<int32_t*>(b + at);   // [n_tours] + count
 
-    rc = wh_surrogate_features(h, orders, plans, X_tour, stream);
-    if (rc != WH_OK) return rc;
-    rc = wh_surrogate_predict(sg, X_tour, p.n_tours, y_tour, stream);
-    if (rc != WH_OK) return rc;
     wh::FeatConst c;
     c.A = h->g.A;
     c.L = h->g.L;
     c.magic_a = (((uint64_t)1 << 40) + (uint64_t)h->g.A - 1) / (uint64_t)h->g.A;
     c.magic_l = (((uint64_t)1 << 40) + (uint64_t)h->g.L - 1) / (uint64_t)h->g.L;
     c.inv_a = (float)(1.0 / (double)h->g.A);
+    // predictions of the current tours: all of them, or (with a cache) the
+    // flagged ones, scattered into the cache
+    if (!tour_changed) {
+        float* yt = y_tour_cache ? y_tour_cache : y_tour;
+        if (wh::launch_features(M.a, c, X_tour, nullptr, p.n_tours, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+        rc = wh_surrogate_predict(sg, X_tour, p.n_tours, yt, stream);
+        if (rc != WH_OK) return rc;
+    } else {
+        int32_t* count = list + p.n_tours + 1;
+        if (wh::launch_compact_flags(tour_changed, p.n_tours, list, count, s) != cudaSuccess) return WH_ECUDA;
+        int32_t n_changed = 0;
+        if (cudaMemcpyAsync(&n_changed, count, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return WH_ECUDA;
+        if (n_changed > 0) {
+            if (wh::launch_features(M.a, c, X_tour, list, n_changed, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+            rc = wh_surrogate_predict(sg, X_tour, n_changed, y_tour, stream);
+            if (rc != WH_OK) return rc;
+            if (wh::launch_scatter_pred(list, y_tour, n_changed, y_tour_cache, tour_changed, s) != cudaSuccess)
+                return WH_ECUDA;
+        }
+    }
     if (wh::launch_task_features(M, c, X_task, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
     rc = wh_surrogate_predict(sg, X_task, M.n_tasks, y_task, stream);
     if (rc != WH_OK) return rc;
     wh::ScreenArgs S;
     S.M = M;
-    S.y_tour = y_tour;
+    S.y_tour = y_tour_cache ? y_tour_cache : y_tour;
     S.y_task = y_task;
     S.score = score;
     S.moves_per_plan = moves_per_plan;
@@ -474,14 +496,14 @@ extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orde
 
 extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* moves,
                            int32_t moves_per_plan, const int64_t* delta, const int32_t* status, int32_t* applied,
-                           const wh_costs* costs, void* stream) {
+                           const wh_costs* costs, uint8_t* tour_changed, void* stream) {
     if (!h || !orders || !plans || moves_per_plan < 1 || moves_per_plan > 256) return WH_EINVAL;
     const wh_orders o = *orders;
     const wh_plans p = *plans;
     int rc = check_problem(o, p);
     if (rc != WH_OK) return rc;
     if (p.n_plans == 0) return WH_OK;
-    if (!moves || !delta || !status || !applied) return WH_EINVAL;
+    if (!moves || !delta || !status || !applied || (tour_changed && !costs)) return WH_EINVAL;
     if (o.n_orders > 50000) return WH_ERANGE;
     rc = bind_device(h);
     if (rc != WH_OK) return rc;
@@ -506,6 +528,7 @@ extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans
         L.tour_rr = costs->tour_rr;
         L.plan_s = costs->plan_s;
         L.plan_rr = costs->plan_rr;
+        L.tour_changed = tour_changed;
     }
     return wh::launch_ls_apply(L, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
@@ -542,7 +565,7 @@ extern "C" int wh_surrogate_features(wh_layout* h, const wh_orders* orders, cons
     c.magic_a = (((uint64_t)1 << 40) + (uint64_t)h->g.A - 1) / (uint64_t)h->g.A;
     c.magic_l = (((uint64_t)1 << 40) + (uint64_t)h->g.L - 1) / (uint64_t)h->g.L;
     c.inv_a = (float)(1.0 / (double)h->g.A);
-    return wh::launch_features(a, c, X, h->num_sms, s) == cudaSuccess ? WH_OK : WH_ECUDA;
+    return wh::launch_features(a, c, X, nullptr, p.n_tours, h->num_sms, s) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {

@@ -118,6 +118,7 @@ struct LsArgs {
     int32_t* tour_rr;
     int64_t* plan_s;
     int64_t* plan_rr;
+    uint8_t* tour_changed;      // NULL or set to 1 for every rewritten tour
 };
 
 struct ScreenArgs {
@@ -174,7 +175,12 @@ struct FeatConst {
     uint64_t magic_l;   // ceil(2^40 / L)
     float inv_a;        // (float)(1.0 / A)
 };
-cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, int num_sms, cudaStream_t s);
+// features of tours list[0..n_rows) (list NULL: tours 0..n_rows) into rows 0..n_rows of X
+cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, const int32_t* list, int64_t n_rows,
+                            int num_sms, cudaStream_t s);
+cudaError_t launch_compact_flags(const uint8_t* flag, int64_t n, int32_t* list, int32_t* count, cudaStream_t s);
+cudaError_t launch_scatter_pred(const int32_t* list, const float* y, int64_t n, float* y_tour, uint8_t* flag,
+                                cudaStream_t s);
 cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 0 bias+GELU, 1 fp32, 2 GELU grad
 cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s);
 cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, float* loss, const float* w3,

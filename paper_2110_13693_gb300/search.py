@@ -22,9 +22,21 @@ def plain_step(lay, prob, costs, moves, M, max_orders=0, max_lines=0):
     return lay.ls_step(prob, costs, moves, M, max_orders, max_lines)
 
 
-def screened_step(lay, sg, prob, costs, moves, M, keep, max_orders=0, max_lines=0):
-    kept = lay.screen(sg, prob, moves, M, keep, max_orders, max_lines)
-    return lay.ls_step(prob, costs, kept, keep, max_orders, max_lines)
+def screened_step(lay, sg, prob, costs, moves, M, keep, max_orders=0, max_lines=0, cache=None):
+    """Prescreen the moves, then score the kept ones exactly and apply the best.
+    cache: (y_tour, changed) device tensors that carry the current tours'
+    predictions from step to step (only the rewritten tours are re-predicted)."""
+    y_tour, changed = cache if cache is not None else (None, None)
+    kept = lay.screen(sg, prob, moves, M, keep, max_orders, max_lines, y_tour=y_tour, changed=changed)
+    return lay.ls_step(prob, costs, kept, keep, max_orders, max_lines, changed=changed)
+
+
+def new_cache(prob):
+    """An empty prediction cache: every tour flagged as changed."""
+    import torch
+    dev = prob.order_off.device
+    return (torch.empty(max(prob.n_tours, 1), dtype=torch.float32, device=dev),
+            torch.ones(max(prob.n_tours, 1), dtype=torch.uint8, device=dev))
 
 
 def keep_count(M: int, frac: float = 0.05) -> int:
@@ -68,6 +80,7 @@ def run_search(wh, lay, prob, costs, moves_fn, steps, M, max_orders, max_lines, 
     plan cost, mean plan cost)] after each step, wall clock, device synchronised."""
     import torch
     trace = []
+    cache = new_cache(prob) if sg is not None else None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for step in range(steps):
@@ -75,7 +88,7 @@ def run_search(wh, lay, prob, costs, moves_fn, steps, M, max_orders, max_lines, 
         if sg is None:
             plain_step(lay, prob, costs, mv, M, max_orders, max_lines)
         else:
-            screened_step(lay, sg, prob, costs, mv, M, keep, max_orders, max_lines)
+            screened_step(lay, sg, prob, costs, mv, M, keep, max_orders, max_lines, cache)
         pr = costs.plan_rr[:prob.n_plans]
         best, mean = int(pr.min().item()), float(pr.double().mean().item())
         trace.append((time.perf_counter() - t0, best, mean))

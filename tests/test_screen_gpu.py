@@ -133,3 +133,36 @@ def test_screened_search_improves_exactly(gpu_lib):
     assert lay.status() == 0
     sg.close()
     lay.close()
+
+
+def test_prediction_cache_matches_full_recompute(gpu_lib):
+    """Screening with the tour-prediction cache (only the tours the previous
+    step rewrote are re-predicted) keeps exactly the moves that screening
+    with every tour re-predicted keeps, step after step."""
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.paperscale(seed=24, n_plans=12)
+    lay, prob, costs = setup(wh, inst)
+    lay2, prob2, costs2 = setup(wh, inst)
+    sg = wh.Surrogate(5)
+    X, t = search.training_set(wh, lay, prob, costs, inst.layout)
+    search.train(sg, X, t, 60, 1024, 2e-3)
+    y_tour, changed = search.new_cache(prob)
+    for step in range(4):
+        mv = moves_for(inst, 9, step, 32)
+        ka = lay.screen(sg, prob, mv, 32, 4, 24, y_tour=y_tour, changed=changed)
+        kb = lay2.screen(sg, prob2, mv, 32, 4, 24)
+        assert torch.equal(ka, kb), step
+        assert int(changed.sum().item()) == 0
+        lay.ls_step(prob, costs, ka, 4, 24, changed=changed)
+        lay2.ls_step(prob2, costs2, kb, 4, 24)
+        assert torch.equal(costs.plan_rr[:12], costs2.plan_rr[:12])
+        # unflagged entries hold the current tours' predictions
+        fresh = sg.predict(wh.features(lay2, prob2))
+        keep = changed[:prob.n_tours] == 0
+        assert torch.equal(y_tour[:prob.n_tours][keep], fresh[keep])
+        assert int(changed.sum().item()) > 0
+    assert lay.status() == 0 and lay2.status() == 0 and sg.status() == 0
+    sg.close()
+    lay.close()
+    lay2.close()
