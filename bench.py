@@ -122,6 +122,45 @@ def algorithmic_bytes(inst):
     return 4 * lines + 4 * (inst.n_tours + 1) + 8 * inst.n_tours + 16 * inst.n_plans + 4 * inst.n_sku
 
 
+def algorithmic_bytes_one_rule(inst):
+    """As algorithmic_bytes with one routing rule written (S-shape only)."""
+    lines = int(inst.tour_lines().sum())
+    return 4 * lines + 4 * (inst.n_tours + 1) + 4 * inst.n_tours + 8 * inst.n_plans + 4 * inst.n_sku
+
+
+def run_sshape(wh, lay, probs, batches, costs, stream, steps):
+    """The streaming path: the same plan batches scored under the S-shape
+    rule alone (its own sort-free kernel), with the HBM roofline of that
+    kernel from CUDA events around each launch."""
+    import torch
+    for i in range(3):
+        lay.eval_plans(probs[i % len(probs)], costs, 1, stream)
+    torch.cuda.synchronize()
+    lay.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_tours = 0
+    for i in range(steps):
+        lay.eval_plans(probs[i % len(probs)], costs, 1, stream)
+        n_tours += batches[i % len(batches)].n_tours
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kt = lay.timing()
+    lay.set_timing(False)
+    assert lay.status() == 0
+    ms = e0.elapsed_time(e1)
+    name, (launches, kms) = max(kt.items(), key=lambda kv: kv[1][1])
+    per_launch_s = kms / 1e3 / max(launches, 1)
+    alg = sum(algorithmic_bytes_one_rule(batches[i % len(batches)]) for i in range(steps)) / steps
+    peak, kind = measured_peaks()
+    achieved = alg / per_launch_s / 1e9
+    return {"workload": "the headline plan batches, S-shape rule only", "tours_per_s": n_tours / (ms / 1e3),
+            "ms_per_step": ms / steps, "steps": steps,
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_launch": alg,
+                         "launch_ms": per_launch_s * 1e3}}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -459,6 +498,8 @@ def run_ours(args):
     launches = sum(v[0] for v in ktime.values())
 
     extra = {}
+    if world == 1:
+        extra["sshape_only"] = run_sshape(wh, lay, probs, batches, costs, stream, min(args.steps, 200))
     if not args.no_extra and world == 1:
         extra["batched"] = run_batched(wh, dev, args.extra_steps)
         extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4))

@@ -211,6 +211,37 @@ __device__ __forceinline__ void prep_instance(const EvalArgs& a, uint32_t mask, 
             line_key[l] = key;
         }
     }
+    if (a.order_agg) {
+        for (int o = i0; o < a.n_orders; o += stride) {
+            const int lb = a.order_off[o], le = a.order_off[o + 1];
+            uint64_t bits = 0;
+            uint32_t kmax = 0, fl = 0;
+            if (lb < 0 || le < lb || le > a.n_lines) {
+                flag(a.status, WH_STATUS_BAD_OFFSET);
+                fl = 4u;
+            } else {
+                for (int l = lb; l < le; ++l) {
+                    const int sku = a.line_sku[l];
+                    if ((unsigned)sku >= (unsigned)a.n_sku) {
+                        flag(a.status, WH_STATUS_BAD_SKU);
+                        fl |= 1u;
+                        continue;
+                    }
+                    const int loc = a.slot_map[sku];
+                    if ((unsigned)loc >= (unsigned)a.g.n_loc) {
+                        flag(a.status, WH_STATUS_BAD_LOC);
+                        fl |= 1u;
+                        continue;
+                    }
+                    const uint32_t key = loc_key(a.g, loc);
+                    bits |= 1ull << (key >> 16);
+                    kmax = max(kmax, key);
+                    fl |= 2u;
+                }
+            }
+            a.order_agg[o] = make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), kmax, fl);
+        }
+    }
     const bool zs = a.plan_s && (mask & WH_ROUTE_SSHAPE);
     const bool zr = a.plan_rr && (mask & WH_ROUTE_OPTIMAL);
     for (int p = i0; p < a.n_plans; p += stride) {
@@ -225,7 +256,7 @@ __device__ __forceinline__ void prep_instance(const EvalArgs& a, uint32_t mask, 
 // ------------------------------------------------------------------ kernels
 
 __global__ void k_prep(EvalArgs a) {
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;   // (lines, orders and plans by grid stride)
     if (i0 == 0) *a.long_count = 0;
     prep_instance(a, a.mask, i0, gridDim.x * blockDim.x);
 }
@@ -268,6 +299,212 @@ __global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
     eval_chunks<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, a.mask, 0, c_begin, c_end,
                                                 reinterpret_cast<uint32_t*>(buf_base) + tid,
                                                 reinterpret_cast<uint2*>(buf_base) + tid, T, lane);
+}
+
+// S-shape only (routing mask = S-shape): no sort.  The S-shape length of a
+// tour depends only on its number of pick aisles, its rightmost pick aisle
+// and that aisle's deepest pick (the closed form of Eq. (2) under the S-shape
+// rule), so one pass over the lines marks the visited aisles in a per-thread
+// shared-memory bitmap and keeps the rightmost aisle's deepest slot.  Tours of
+// any length stay in their thread (nothing is deferred); few registers, so
+// many warps hide the gather latency.
+constexpr int SSHAPE_MAX_WORDS = 64;   // bitmap words per thread: A <= 2048
+
+template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
+__global__ void __launch_bounds__(256) k_eval_sshape(EvalArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);
+    void* s_tab = smem + sizeof(uint32_t) * (size_t)a.n_orders;
+    size_t off_b = 0;
+    if (SMEM_TABLES)
+        off_b = (sizeof(uint32_t) * (size_t)a.n_orders + (SHARED_MAP ? (KEY16 ? 2 : 4) : 4) * (size_t)a.n_lines + 15) &
+                ~(size_t)15;
+    uint32_t* bm = reinterpret_cast<uint32_t*>(smem + off_b) + tid;   // word w at bm[w * T]
+    const int nw = (a.g.A + 31) >> 5;
+    KeySrc src = global_src(a);
+    if constexpr (SMEM_TABLES) {
+        stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T);
+        __syncthreads();
+    }
+    for (int w = 0; w < nw; ++w) bm[w * T] = 0u;
+    const int warps = gridDim.x * (T >> 5);
+    const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
+    const int n_chunks = (a.n_tours + 31) >> 5;
+    const int per = (n_chunks + warps - 1) / warps;
+    const int c_begin = gw * per;
+    const int c_end = min(c_begin + per, n_chunks);
+    if (c_begin >= c_end) return;
+    int plan = 0;
+    {
+        const int t0 = c_begin * 32;
+        int lo = 0, hi = a.n_plans - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.plan_tour_off[mid] <= t0) lo = mid; else hi = mid - 1;
+        }
+        plan = lo;
+    }
+    for (int c = c_begin; c < c_end; ++c) {
+        const int t = c * 32 + lane;
+        const bool active = t < a.n_tours;
+        while (plan + 1 < a.n_plans && a.plan_tour_off[plan + 1] <= t) ++plan;
+        if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
+        int m = 0, r = -1, dr = 0;
+        bool bad = false, kbad = false;
+        if (active) {
+            const int q0 = __ldg(a.tour_off + t), q1 = __ldg(a.tour_off + t + 1);
+            if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
+                flag(a.status, WH_STATUS_BAD_OFFSET);
+                bad = true;
+            } else {
+                // one flat loop over the tour's lines (one line per lane per
+                // iteration; a lane opens its next order when the current one
+                // is used up), so lanes stay in step whatever the order sizes
+                int q = q0, l = 0, le = 0;
+                int o_next = q0 < q1 ? __ldg(a.order_seq + q0) : 0;
+                for (;;) {
+                    bool more = true;
+                    while (l == le) {
+                        if (q == q1) { more = false; break; }
+                        const int o = o_next;
+                        ++q;
+                        o_next = q < q1 ? __ldg(a.order_seq + q) : 0;
+                        if ((unsigned)o >= (unsigned)a.n_orders) {
+                            flag(a.status, WH_STATUS_BAD_ORDER);
+                            bad = true;
+                            more = false;
+                            break;
+                        }
+                        bool global = true;
+                        if constexpr (SMEM_TABLES) {
+                            const uint32_t d = src.desc[o];
+                            if ((d & 0xFFu) != 0xFFu) {
+                                l = (int)(d >> 8);
+                                le = l + (int)(d & 0xFFu);
+                                global = false;
+                            }
+                        }
+                        if (global) {
+                            l = src.off[o];
+                            le = src.off[o + 1];
+                            if (l < 0 || le < l || le > a.n_lines) {
+                                flag(a.status, WH_STATUS_BAD_OFFSET);
+                                bad = true;
+                                more = false;
+                                break;
+                            }
+                        }
+                    }
+                    if (!more) break;
+                    const uint32_t key = key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
+                    ++l;
+                    if (key == (KEY16 ? KEY16_BAD : KEY_BAD)) {
+                        kbad = true;
+                        continue;
+                    }
+                    const int ai = (int)(KEY16 ? key >> 8 : key >> 16);
+                    const int dk = (int)(KEY16 ? key & 0xFFu : key & 0xFFFFu);
+                    uint32_t* wp = bm + (ai >> 5) * T;
+                    const uint32_t bit = 1u << (ai & 31), wv = *wp;
+                    if (!(wv & bit)) {
+                        *wp = wv | bit;
+                        ++m;
+                    }
+                    dr = ai > r ? dk : (ai == r ? max(dr, dk) : dr);
+                    r = max(r, ai);
+                }
+            }
+            if (m > 0)
+                for (int w = 0; w < nw; ++w) bm[w * T] = 0u;
+        }
+        const bool ok = active && !bad && !kbad;
+        const int cs = ok ? sshape_cost(a.g, m, r, dr) : 0;
+        if (active && !ok) {
+            if (a.tour_s) a.tour_s[t] = -1;
+        } else if (ok && a.tour_s) {
+            a.tour_s[t] = cs;
+        }
+        const int key = active ? plan : -1;
+        const long long ss = segmented_sum(cs, key, lane);
+        const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+        if (active && (lane == 0 || prev_key != key) && a.plan_s && ss)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)ss);
+    }
+}
+
+// S-shape only with per-order aggregates (shared slotting, <= 64 aisles):
+// a tour's pick-aisle set is the union of its orders' aisle sets and its
+// rightmost aisle's deepest pick is the largest key over its orders, so each
+// tour merges one 16-byte record per order (no per-line work).  No shared
+// memory: full occupancy hides the order-id and record loads.
+__global__ void __launch_bounds__(256) k_eval_sshape_agg(EvalArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int n_chunks = (a.n_tours + 31) >> 5;
+    const int per = (n_chunks + warps - 1) / warps;
+    const int c_begin = gw * per;
+    const int c_end = min(c_begin + per, n_chunks);
+    if (c_begin >= c_end) return;
+    int plan = 0;
+    {
+        const int t0 = c_begin * 32;
+        int lo = 0, hi = a.n_plans - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.plan_tour_off[mid] <= t0) lo = mid; else hi = mid - 1;
+        }
+        plan = lo;
+    }
+    for (int c = c_begin; c < c_end; ++c) {
+        const int t = c * 32 + lane;
+        const bool active = t < a.n_tours;
+        while (plan + 1 < a.n_plans && a.plan_tour_off[plan + 1] <= t) ++plan;
+        uint64_t bits = 0;
+        uint32_t kmax = 0, fl = 0;
+        bool bad = false;
+        if (active) {
+            const int q0 = __ldg(a.tour_off + t), q1 = __ldg(a.tour_off + t + 1);
+            if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
+                flag(a.status, WH_STATUS_BAD_OFFSET);
+                bad = true;
+            } else {
+                int q = q0;
+                for (; q + 4 <= q1; q += 4) {   // four independent order ids in flight
+                    int o[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) o[j] = __ldg(a.order_seq + q + j);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if ((unsigned)o[j] >= (unsigned)a.n_orders) { bad = true; continue; }
+                        const uint4 r = __ldg(a.order_agg + o[j]);
+                        bits |= (uint64_t)r.x | ((uint64_t)r.y << 32);
+                        kmax = (r.w & 2u) ? max(kmax, r.z) : kmax;
+                        fl |= r.w;
+                    }
+                }
+                for (; q < q1; ++q) {
+                    const int o = __ldg(a.order_seq + q);
+                    if ((unsigned)o >= (unsigned)a.n_orders) { bad = true; continue; }
+                    const uint4 r = __ldg(a.order_agg + o);
+                    bits |= (uint64_t)r.x | ((uint64_t)r.y << 32);
+                    kmax = (r.w & 2u) ? max(kmax, r.z) : kmax;
+                    fl |= r.w;
+                }
+                if (bad) flag(a.status, WH_STATUS_BAD_ORDER);
+            }
+        }
+        const bool ok = active && !bad && !(fl & 5u);
+        const int m = __popcll(bits);
+        const int cs = ok ? sshape_cost(a.g, m, (int)(kmax >> 16), (int)(kmax & 0xFFFFu)) : 0;
+        if (active && a.tour_s) a.tour_s[t] = ok ? cs : -1;
+        const int key = active ? plan : -1;
+        const long long ss = segmented_sum(cs, key, lane);
+        const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+        if (active && (lane == 0 || prev_key != key) && a.plan_s && ss)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)ss);
+    }
 }
 
 // Persistent batch kernel: CTAs pop work items (instance, chunk range) from
@@ -444,6 +681,19 @@ cudaError_t launch_short_t(const EvalArgs& a, const Tuning& t, size_t smem, int 
     return cudaGetLastError();
 }
 
+template <bool K16, bool SH, bool SM>
+cudaError_t launch_sshape_t(const EvalArgs& a, const Tuning& t, size_t smem, int num_sms, cudaStream_t s,
+                            int* grid_out) {
+    auto kern = k_eval_sshape<K16, SH, SM>;
+    const int warps_needed = (a.n_tours + 31) / 32;
+    int grid = 0;
+    cudaError_t e = grid_for(kern, t.threads, smem, num_sms, (warps_needed + t.threads / 32 - 1) / (t.threads / 32), &grid);
+    if (e != cudaSuccess) return e;
+    if (grid_out) *grid_out = grid;
+    kern<<<grid, t.threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <bool K16, bool SM>
 cudaError_t launch_batch_t(const BatchArgs& b, const Tuning& t, size_t smem, int num_sms, cudaStream_t s) {
     auto kern = k_eval_batch<K16, SM>;
@@ -457,6 +707,10 @@ cudaError_t launch_batch_t(const BatchArgs& b, const Tuning& t, size_t smem, int
 }  // namespace
 
 bool key16_ok(const Geo& g) { return g.A <= 255 && g.L <= 256; }
+
+bool sshape_kernel_applies(const EvalArgs& a) {
+    return a.mask == WH_ROUTE_SSHAPE && (a.g.A + 31) / 32 <= SSHAPE_MAX_WORDS;
+}
 
 
 static size_t buffer_bytes(bool k16, int max_rec, int threads) {
@@ -480,9 +734,35 @@ size_t eval_batch_smem_bytes(const BatchArgs& b, const Tuning& t, bool k16) {
     return s + buffer_bytes(k16, b.max_rec, t.threads);
 }
 
+static cudaError_t launch_sshape(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s, int* grid_out) {
+    if (a.order_agg) {
+        int grid = 0;
+        const int warps_needed = (a.n_tours + 31) / 32;
+        cudaError_t e = grid_for(k_eval_sshape_agg, 256, 0, num_sms, (warps_needed + 7) / 8, &grid);
+        if (e != cudaSuccess) return e;
+        if (grid_out) *grid_out = grid;
+        k_eval_sshape_agg<<<grid, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    const bool shared_map = a.slot_stride == 0;
+    const bool k16 = t.key16 && key16_ok(a.g);
+    const bool sm = t.smem_tables != 0;
+    const size_t smem = (sm ? table_bytes(k16, shared_map, a.n_orders, a.n_lines) : 0) +
+                        sizeof(uint32_t) * (size_t)((a.g.A + 31) / 32) * (size_t)t.threads;
+#define WH_LAUNCH(K, H, M) launch_sshape_t<K, H, M>(a, t, smem, num_sms, s, grid_out)
+    if (k16) {
+        if (shared_map) return sm ? WH_LAUNCH(true, true, true) : WH_LAUNCH(true, true, false);
+        return sm ? WH_LAUNCH(true, false, true) : WH_LAUNCH(true, false, false);
+    }
+    if (shared_map) return sm ? WH_LAUNCH(false, true, true) : WH_LAUNCH(false, true, false);
+    return sm ? WH_LAUNCH(false, false, true) : WH_LAUNCH(false, false, false);
+#undef WH_LAUNCH
+}
+
 cudaError_t launch_prep(const EvalArgs& a, cudaStream_t s) {
     int work = a.n_plans;
     if (a.line_key && a.n_lines > work) work = a.n_lines;
+    if (a.order_agg && a.n_orders > work) work = a.n_orders;
     int grid = (work + 255) / 256;
     if (grid > 4096) grid = 4096;
     if (grid < 1) grid = 1;
@@ -502,6 +782,7 @@ cudaError_t launch_prep_batch(const BatchArgs& b, int max_work, cudaStream_t s) 
 cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s, int* grid_out) {
     if (t.threads % 32 != 0 || t.threads > 256 || t.threads < 32) return cudaErrorInvalidValue;
     if (a.n_tours == 0) return cudaSuccess;
+    if (sshape_kernel_applies(a)) return launch_sshape(a, t, num_sms, s, grid_out);
     const size_t smem = eval_short_smem_bytes(a, t);
     const bool shared_map = a.slot_stride == 0;
     const bool k16 = t.key16 && key16_ok(a.g);

@@ -62,8 +62,8 @@ struct wh_batch {
 };
 
 namespace {
-enum KernelId { K_PREP = 0, K_EVAL_SHORT = 1, K_EVAL_LONG = 2, K_COUNT = 3 };
-const char* const kKernelNames[K_COUNT] = {"k_prep", "k_eval_short", "k_eval_long"};
+enum KernelId { K_PREP = 0, K_EVAL_SHORT = 1, K_EVAL_LONG = 2, K_EVAL_SSHAPE = 3, K_COUNT = 4 };
+const char* const kKernelNames[K_COUNT] = {"k_prep", "k_eval_short", "k_eval_long", "k_eval_sshape"};
 
 // Brackets one launch with events when timing is on.
 class LaunchTimer {
@@ -264,20 +264,25 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     const wh::Tuning t = default_tuning(a);
 
     const bool shared_map = p.slot_map_stride == 0;
-    const size_t key_bytes = shared_map ? align_up(sizeof(uint32_t) * (size_t)o.n_lines) : 0;
+    // S-shape alone under a shared slotting on <= 64 aisles: per-order
+    // aggregates instead of per-line keys
+    const bool agg = shared_map && routing_mask == WH_ROUTE_SSHAPE && h->g.A <= 64 && o.n_orders > 0;
+    const size_t key_bytes = shared_map && !agg ? align_up(sizeof(uint32_t) * (size_t)o.n_lines) : 0;
+    const size_t agg_bytes = agg ? align_up(sizeof(uint4) * (size_t)o.n_orders) : 0;
     const size_t list_bytes = align_up(sizeof(int32_t) * 3 * ((size_t)p.n_tours + 1));
-    rc = reserve_scratch(h, key_bytes + list_bytes);
+    rc = reserve_scratch(h, key_bytes + agg_bytes + list_bytes);
     if (rc != WH_OK) return rc;
     char* base = static_cast<char*>(h->scratch);
-    a.line_key = shared_map && o.n_lines > 0 ? reinterpret_cast<uint32_t*>(base) : nullptr;
-    a.long_list = reinterpret_cast<int32_t*>(base + key_bytes);
+    a.line_key = shared_map && !agg && o.n_lines > 0 ? reinterpret_cast<uint32_t*>(base) : nullptr;
+    a.order_agg = agg ? reinterpret_cast<uint4*>(base + key_bytes) : nullptr;
+    a.long_list = reinterpret_cast<int32_t*>(base + key_bytes + agg_bytes);
 
     {
         LaunchTimer lt(h, K_PREP, s);
         if (!lt.ok() || wh::launch_prep(a, s) != cudaSuccess) return WH_ECUDA;
     }
     {
-        LaunchTimer lt(h, K_EVAL_SHORT, s);
+        LaunchTimer lt(h, wh::sshape_kernel_applies(a) ? K_EVAL_SSHAPE : K_EVAL_SHORT, s);
         if (!lt.ok() || wh::launch_eval_short(a, t, h->num_sms, s, nullptr) != cudaSuccess) return WH_ECUDA;
     }
     if (p.n_tours > 0) {
@@ -594,8 +599,8 @@ extern "C" int wh_set_timing(wh_layout* h, int enable) {
 extern "C" int wh_get_timing(wh_layout* h, int32_t* n_kernels, const char** names, int32_t* launches,
                              double* total_ms, int32_t cap) {
     if (!h || !n_kernels || cap < 0 || (cap > 0 && (!names || !launches || !total_ms))) return WH_EINVAL;
-    double ms[K_COUNT] = {0, 0, 0};
-    int32_t cnt[K_COUNT] = {0, 0, 0};
+    double ms[K_COUNT] = {};
+    int32_t cnt[K_COUNT] = {};
     if (h->n_recorded > 0) {
         DeviceGuard guard(h->device);
         for (size_t i = 0; i < h->n_recorded; ++i) {

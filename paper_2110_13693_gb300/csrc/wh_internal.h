@@ -44,6 +44,11 @@ struct EvalArgs {
     int32_t* long_list;         // tours deferred to the long-tour kernel: (inst, tour, plan)
     int32_t* long_count;
     int32_t long_cap;           // capacity of long_list in entries
+    // S-shape only under a shared slotting on at most 64 aisles: per order
+    // {visited-aisle bits 0-31, bits 32-63, largest key, flags} built by
+    // k_prep (flags: 1 invalid line, 2 has lines, 4 invalid offsets); NULL
+    // otherwise
+    uint4* order_agg;
 };
 
 // A work item of the batched launch: 32-tour chunks [chunk_begin, chunk_end)
@@ -209,6 +214,9 @@ bool key16_ok(const Geo& g);   // A <= 255 and L <= 256
 // long-tour counter, plan offset checks
 cudaError_t launch_prep(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_prep_batch(const BatchArgs& b, int max_work, cudaStream_t s);
+// routing mask S-shape only on a layout of at most 2,048 aisles: the
+// sort-free S-shape kernel scores the short-tour pass (and every tour)
+bool sshape_kernel_applies(const EvalArgs& a);
 cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s,
                               int* grid_out);
 cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int num_sms, cudaStream_t s);

@@ -207,31 +207,39 @@ def test_tour_too_long_is_flagged(gpu_lib):
     assert ts[0] == want[0][0] and tr[1] == want[1][1] and pr[0] == want[3][0]
 
 
-def test_bad_ids_are_flagged_not_faulted(gpu_lib):
+@pytest.mark.parametrize("mask", [3, 1])
+def test_bad_ids_are_flagged_not_faulted(gpu_lib, mask):
+    """Invalid ids are flagged and their tours report -1, under both rules
+    and under the S-shape rule alone (its own kernels)."""
     import paper_2110_13693_gb300 as wh
     lay = wh_gen.Layout(10, 30)
     slot = np.arange(lay.n_loc, dtype=np.int32)
     good = make_instance(lay, [[1, 2], [3], [4]], slot, [[[0], [1, 2]]])
     want = oracle.eval_plans(good)
+    col = 1 if mask == 3 else 0           # the optimal cost, or the S-shape one
+
+    def run(inst):
+        got = gpu_eval(gpu_lib, inst, mask=mask)
+        return got[col], got[4]
 
     bad_order = make_instance(lay, [[1, 2], [3], [4]], slot, [[[0], [1, 7]]])
-    ts, tr, ps, pr, st = gpu_eval(gpu_lib, bad_order)
-    assert st & wh.WH_STATUS_BAD_ORDER and tr[1] == -1 and tr[0] == want[1][0]
+    c, st = run(bad_order)
+    assert st & wh.WH_STATUS_BAD_ORDER and c[1] == -1 and c[0] == want[col][0]
 
     bad_sku = make_instance(lay, [[1, 2], [3], [4]], slot, [[[0], [1, 2]]])
     bad_sku.line_sku = np.asarray([1, 2, 3, 9999], np.int32)
-    ts, tr, ps, pr, st = gpu_eval(gpu_lib, bad_sku)
-    assert st & wh.WH_STATUS_BAD_SKU and tr[1] == -1 and tr[0] == want[1][0]
+    c, st = run(bad_sku)
+    assert st & wh.WH_STATUS_BAD_SKU and c[1] == -1 and c[0] == want[col][0]
 
     bad_loc = make_instance(lay, [[1, 2], [3], [4]], slot.copy(), [[[0], [1, 2]]])
     bad_loc.slot_map[4] = lay.n_loc + 5
-    ts, tr, ps, pr, st = gpu_eval(gpu_lib, bad_loc)
-    assert st & wh.WH_STATUS_BAD_LOC and tr[1] == -1
+    c, st = run(bad_loc)
+    assert st & wh.WH_STATUS_BAD_LOC and c[1] == -1
 
     bad_off = make_instance(lay, [[1, 2], [3], [4]], slot, [[[0], [1, 2]]])
     bad_off.tour_off = np.asarray([0, 2, 1], np.int32)
-    ts, tr, ps, pr, st = gpu_eval(gpu_lib, bad_off)
-    assert st & wh.WH_STATUS_BAD_OFFSET and tr[1] == -1
+    c, st = run(bad_off)
+    assert st & wh.WH_STATUS_BAD_OFFSET and c[1] == -1
 
 
 def test_repeatable(gpu_lib):
@@ -254,3 +262,59 @@ def test_large_order_book_global_tables(gpu_lib):
     got = gpu_eval(gpu_lib, inst)
     assert got[4] == 0
     assert_exact(got, oracle.eval_plans(inst))
+
+
+def random_instance(lay, seed, n_orders=300, n_plans=8, max_tour=40):
+    rng = np.random.default_rng(seed)
+    n_sku = min(lay.n_loc, 2000)
+    slot = rng.permutation(lay.n_loc)[:n_sku]
+    orders = [rng.integers(0, n_sku, size=int(rng.integers(1, 8))).tolist() for _ in range(n_orders)]
+    plans = []
+    for _ in range(n_plans):
+        perm = rng.permutation(n_orders).tolist()
+        cuts, at = [], 0
+        while at < n_orders:
+            at += int(rng.integers(1, max_tour + 1))
+            cuts.append(min(at, n_orders))
+        plans.append([perm[a:b] for a, b in zip([0] + cuts[:-1], cuts)])
+    return make_instance(lay, orders, slot, plans, n_sku)
+
+
+def sshape_cases():
+    yield "tiny", wh_gen.tiny(seed=31, n_plans=16), None
+    yield "midsize", wh_gen.midsize(seed=32, n_plans=64), None
+    inst = wh_gen.paperscale(seed=33, n_plans=6)
+    yield "paperscale", inst, None
+    rng = np.random.default_rng(3)
+    maps = np.stack([rng.permutation(inst.layout.n_loc)[: inst.n_sku] for _ in range(inst.n_plans)])
+    yield "paperscale_maps", inst, np.ascontiguousarray(maps.astype(np.int32).ravel())
+    # the widest bitmap (2,048 aisles = 64 words) and one aisle past it (the
+    # general kernel takes over), long tours of up to 40 orders
+    yield "a2048", random_instance(wh_gen.Layout(2048, 3), 34), None
+    yield "a2049", random_instance(wh_gen.Layout(2049, 3), 35), None
+    yield "a1", random_instance(wh_gen.Layout(1, 40), 36), None
+
+
+@pytest.mark.parametrize("case", [c[0] for c in sshape_cases()])
+def test_sshape_only_kernel(gpu_lib, case):
+    """Routing mask S-shape only runs the sort-free kernel: tour and plan
+    S-shape costs bit-equal to the oracle's, the optimal outputs untouched."""
+    name, inst, maps = next(c for c in sshape_cases() if c[0] == case)
+    stride = inst.n_sku if maps is not None else 0
+    got = gpu_eval(gpu_lib, inst, mask=1, slot_map=maps, stride=stride, prefill=-7)
+    want = oracle.eval_plans(inst, slot_map=maps, slot_map_stride=stride) if maps is not None else oracle.eval_plans(inst)
+    assert got[4] == 0
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[2], want[2])
+    assert (got[1] == -7).all() and (got[3] == -7).all()
+
+
+def test_sshape_only_large_order_book(gpu_lib):
+    lay = wh_gen.Layout(60, 150)
+    off, lines = wh_gen.gen_orders(22, 24000, 18000, 12, 0.4, 1.1)
+    slot = wh_gen.gen_slot_abc(22, lay, 18000, 0.1)
+    pto, to, seq = wh_gen.gen_plans(22, 1, off, 3, 20, 60)
+    inst = wh_gen.Instance(lay, 18000, off, lines, slot, pto, to, seq)
+    got = gpu_eval(gpu_lib, inst, mask=1, prefill=-7)
+    want = oracle.eval_plans(inst)
+    assert got[4] == 0
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[2], want[2])
