@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--extra-steps", type=int, default=20)
     ap.add_argument("--ab-steps", type=int, default=30, help="plain local-search steps of the prescreen A/B")
     ap.add_argument("--train-steps", type=int, default=2500)
-    ap.add_argument("--case", choices=["batched-small", "moves-small"], default=None,
+    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small"], default=None,
                     help="run a small case of one kernel three times (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -581,7 +581,8 @@ def run_reference(args):
 
 def run_case(name):
     """Small cases for profiler captures: 128 batched instances x 64 plans,
-    or paper-scale move deltas on 1,024 plans x 64 moves."""
+    paper-scale move deltas on 1,024 plans x 64 moves, or the surrogate's
+    kernels (features, prescreen, tensor-core inference)."""
     import numpy as np
     import torch
     import paper_2110_13693_gb300 as wh
@@ -603,6 +604,28 @@ def run_case(name):
         torch.cuda.synchronize()
         assert b.status() == 0
         b.close()
+    elif name == "surrogate-small":
+        # features of every tour of 1,024 paper-scale plans, one prescreen of
+        # 64 moves per plan, and inference on 1M feature rows (384 MB, above L2)
+        n = 1024
+        inst = wh_gen.paperscale(seed=4, n_plans=n)
+        lay = wh.Layout.of(inst.layout)
+        base = wh.to_device(inst)
+        prob = wh.DeviceProblem(base.order_off, base.line_sku, base.slot_map.repeat(n), base.plan_tour_off,
+                                base.tour_off, base.order_seq, inst.n_sku, inst.n_sku)
+        sg = wh.Surrogate(1)
+        X = wh.features(lay, prob)
+        mv = wh_gen.gen_moves(17, 0, inst, 64)
+        mv[..., 3] = np.arange(n)[:, None]
+        lay.screen(sg, prob, torch.as_tensor(mv.reshape(-1, 4)).cuda(), 64, 4, 24)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        Xr = torch.randint(0, 3, (1 << 20, 192), device="cuda", generator=g).to(torch.bfloat16)
+        for _ in range(3):
+            sg.predict(Xr)
+        torch.cuda.synchronize()
+        assert lay.status() == 0 and sg.status() == 0 and X.shape[0] == prob.n_tours
+        sg.close()
+        lay.close()
     else:
         n = 1024
         inst = wh_gen.paperscale(seed=4, n_plans=n)
