@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and move-delta measurements")
     ap.add_argument("--extra-steps", type=int, default=20)
-    ap.add_argument("--ab-steps", type=int, default=30, help="plain local-search steps of the prescreen A/B")
+    ap.add_argument("--ab-steps", type=int, default=100, help="plain local-search steps of the prescreen A/B")
     ap.add_argument("--train-steps", type=int, default=2500)
     ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small"], default=None,
                     help="run a small case of one kernel three times (for profiler captures) and exit")
