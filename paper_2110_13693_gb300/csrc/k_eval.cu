@@ -433,13 +433,16 @@ __global__ void __launch_bounds__(256) k_eval_sshape(EvalArgs a) {
     }
 }
 
+constexpr int SSHAPE_AGG_THREADS = 256;
+
 // S-shape only with per-order aggregates (shared slotting, <= 64 aisles):
 // a tour's pick-aisle set is the union of its orders' aisle sets and its
 // rightmost aisle's deepest pick is the largest key over its orders, so each
 // tour merges one 16-byte record per order (no per-line work).  No shared
 // memory: full occupancy hides the order-id and record loads.
-__global__ void __launch_bounds__(256) k_eval_sshape_agg(EvalArgs a) {
+__global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs a) {
     const int lane = threadIdx.x & 31;
+    const bool vec = (reinterpret_cast<uintptr_t>(a.order_seq) & 15u) == 0;
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int n_chunks = (a.n_tours + 31) >> 5;
@@ -470,28 +473,31 @@ __global__ void __launch_bounds__(256) k_eval_sshape_agg(EvalArgs a) {
                 flag(a.status, WH_STATUS_BAD_OFFSET);
                 bad = true;
             } else {
-                int q = q0;
-                for (; q + 4 <= q1; q += 4) {   // four independent order ids in flight
-                    int o[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) o[j] = __ldg(a.order_seq + q + j);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if ((unsigned)o[j] >= (unsigned)a.n_orders) { bad = true; continue; }
-                        const uint4 r = __ldg(a.order_agg + o[j]);
-                        bits |= (uint64_t)r.x | ((uint64_t)r.y << 32);
-                        kmax = (r.w & 2u) ? max(kmax, r.z) : kmax;
-                        fl |= r.w;
+                auto take = [&](int o) {
+                    if ((unsigned)o >= (unsigned)a.n_orders) {
+                        bad = true;
+                        return;
                     }
-                }
-                for (; q < q1; ++q) {
-                    const int o = __ldg(a.order_seq + q);
-                    if ((unsigned)o >= (unsigned)a.n_orders) { bad = true; continue; }
                     const uint4 r = __ldg(a.order_agg + o);
                     bits |= (uint64_t)r.x | ((uint64_t)r.y << 32);
                     kmax = (r.w & 2u) ? max(kmax, r.z) : kmax;
                     fl |= r.w;
+                };
+                // the thread's run of order ids: scalar loads up to a 16-byte
+                // boundary, then four ids per vector load (a quarter of the
+                // load requests), then the tail
+                int q = q0;
+                if (vec) {
+                    for (; q < q1 && (q & 3); ++q) take(__ldg(a.order_seq + q));
+                    for (; q + 4 <= q1; q += 4) {
+                        const int4 v = __ldg(reinterpret_cast<const int4*>(a.order_seq + q));
+                        take(v.x);
+                        take(v.y);
+                        take(v.z);
+                        take(v.w);
+                    }
                 }
+                for (; q < q1; ++q) take(__ldg(a.order_seq + q));
                 if (bad) flag(a.status, WH_STATUS_BAD_ORDER);
             }
         }
@@ -738,10 +744,11 @@ static cudaError_t launch_sshape(const EvalArgs& a, const Tuning& t, int num_sms
     if (a.order_agg) {
         int grid = 0;
         const int warps_needed = (a.n_tours + 31) / 32;
-        cudaError_t e = grid_for(k_eval_sshape_agg, 256, 0, num_sms, (warps_needed + 7) / 8, &grid);
+        const int want = (warps_needed + SSHAPE_AGG_THREADS / 32 - 1) / (SSHAPE_AGG_THREADS / 32);
+        cudaError_t e = grid_for(k_eval_sshape_agg, SSHAPE_AGG_THREADS, 0, num_sms, want, &grid);
         if (e != cudaSuccess) return e;
         if (grid_out) *grid_out = grid;
-        k_eval_sshape_agg<<<grid, 256, 0, s>>>(a);
+        k_eval_sshape_agg<<<grid, SSHAPE_AGG_THREADS, 0, s>>>(a);
         return cudaGetLastError();
     }
     const bool shared_map = a.slot_stride == 0;

@@ -117,3 +117,16 @@ def test_adam_matches_torch():
         tp.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_inference_erf_approximation_bound():
+    """The tensor-core inference evaluates erf by Abramowitz & Stegun 7.1.26
+    (Hastings' rational approximation); its published bound |error| <= 1.5e-7
+    holds for the formula with these coefficients (float64, dense grid)."""
+    from scipy.special import erf
+    p, a = 0.3275911, (0.254829592, -0.284496736, 1.421413741, -1.453152027, 1.061405429)
+    x = np.linspace(-8.0, 8.0, 400001)
+    t = 1.0 / (1.0 + p * np.abs(x))
+    poly = t * (a[0] + t * (a[1] + t * (a[2] + t * (a[3] + t * a[4]))))
+    approx = np.sign(x) * (1.0 - poly * np.exp(-x * x))
+    assert np.abs(approx - erf(x)).max() <= 1.5e-7
