@@ -11,8 +11,8 @@
 //                   a 3-stage ring;
 //   MMA warp        tcgen05.mma kind::f16 (M 128, N 256, K 16) into two fp32
 //                   TMEM accumulators (layer 1 at column 0, layer 2 at 256);
-//   8 epilogue warps  tcgen05.ld of the accumulators, bias + GELU (erf form,
-//                   erf by Abramowitz & Stegun 7.1.26),
+//   16 epilogue warps tcgen05.ld of the accumulators, bias + GELU (erf form,
+//                   erf by Abramowitz & Stegun 7.1.28, packed fp32x2 math),
 //                   bf16 rounding, the layer-1 activations written back to
 //                   shared memory as the next A operand (same swizzle), and
 //                   the final dot product with w3.
@@ -35,7 +35,9 @@ namespace wh {
 namespace {
 
 constexpr int TC_ROWS = 128;                      // rows per tile (MMA M)
-constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_EPI_WARPS = 16;                 // four per TMEM lane quarter
+constexpr int TC_PARTS = TC_EPI_WARPS / 4;        // column parts per row
+constexpr int TC_PART_COLS = 256 / TC_PARTS;
 constexpr int TC_PRODUCER = TC_EPI_WARPS;         // warp index
 constexpr int TC_MMA = TC_EPI_WARPS + 1;          // warp index
 constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
@@ -48,8 +50,8 @@ constexpr uint32_t OFF_X = 0;
 constexpr uint32_t OFF_W = OFF_X + X_BYTES;
 constexpr uint32_t OFF_H = OFF_W + TC_STAGES * W_CHUNK;
 constexpr uint32_t OFF_PAR = OFF_H + H_BYTES;     // b1, b2, w3 (fp32)
-constexpr uint32_t OFF_RED = OFF_PAR + 3 * 256 * 4;  // [2 tiles][128] fp32 partial sums
-constexpr uint32_t OFF_BAR = OFF_RED + 2 * 128 * 4;
+constexpr uint32_t OFF_RED = OFF_PAR + 3 * 256 * 4;  // [2 tiles][parts 1..][128] fp32 partial sums
+constexpr uint32_t OFF_BAR = OFF_RED + 2 * (TC_PARTS - 1) * 128 * 4;
 // x_full, x_empty, w_full[], w_empty[], acc1, h1, acc2, done, red[2]
 constexpr int N_BARS = 2 + 2 * TC_STAGES + 6;
 constexpr uint32_t OFF_MISC = OFF_BAR + 8 * N_BARS;  // TMEM base address, abort flag
@@ -171,23 +173,62 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// erf by the rational approximation of Abramowitz & Stegun, Handbook of
-// Mathematical Functions, formula 7.1.26 (after Hastings): for x >= 0,
-// erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2) with
-// t = 1 / (1 + p x), |error| <= 1.5e-7; odd in x.  Far below the bf16
-// resolution (2^-8) of the activations it feeds, and cheaper than erff: one
-// reciprocal, four FMAs, one exponential.
-__device__ __forceinline__ float erf_as(float x) {
-    const float ax = fabsf(x);
-    const float t = 1.0f / fmaf(0.3275911f, ax, 1.0f);
-    float q = fmaf(1.061405429f, t, -1.453152027f);
-    q = fmaf(q, t, 1.421413741f);
-    q = fmaf(q, t, -0.284496736f);
-    q = fmaf(q, t, 0.254829592f);
-    return copysignf(fmaf(-q * t, __expf(-ax * ax), 1.0f), x);
+// Pairs of fp32 values in one 64-bit register for the packed fp32x2
+// arithmetic of sm_100 and later (add / mul / fma .f32x2, element-wise,
+// round to nearest): the epilogue's FMA-pipe work in half the instructions.
+__device__ __forceinline__ uint64_t pk(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
+__device__ __forceinline__ void upk(uint64_t r, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t dup2(float x) { return pk(x, x); }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+// gelu(z) = z/2 (1 + erf(z / sqrt 2)) of both halves of z.  erf by the
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.28 (after Hastings): for x >= 0,
+// erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16, |error| <= 3e-7; odd
+// in x (large x: the power overflows to inf and erf to 1).  Far below the
+// bf16 resolution (2^-8) of the activations it feeds; one reciprocal per
+// value and FMAs, all but the reciprocal on packed pairs.
+__device__ __forceinline__ uint64_t gelu2(uint64_t z) {
+    float x0, x1;
+    upk(mul2(z, dup2(0.70710678118654752f)), x0, x1);
+    const uint64_t ax = pk(fabsf(x0), fabsf(x1));
+    uint64_t p = fma2(dup2(0.0000430638f), ax, dup2(0.0002765672f));
+    p = fma2(p, ax, dup2(0.0001520143f));
+    p = fma2(p, ax, dup2(0.0092705272f));
+    p = fma2(p, ax, dup2(0.0422820123f));
+    p = fma2(p, ax, dup2(0.0705230784f));
+    p = fma2(p, ax, dup2(1.0f));
+    p = mul2(p, p);   // ^2
+    p = mul2(p, p);   // ^4
+    p = mul2(p, p);   // ^8
+    p = mul2(p, p);   // ^16
+    float p0, p1;
+    upk(p, p0, p1);
+    const float m0 = 1.0f - 1.0f / p0, m1 = 1.0f - 1.0f / p1;   // |erf|
+    const uint64_t er = pk(copysignf(m0, x0), copysignf(m1, x1));
+    const uint64_t hz = mul2(z, dup2(0.5f));
+    return fma2(hz, er, hz);
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
@@ -230,8 +271,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_init(h1_full, TC_EPI_WARPS * 32);
         mbar_init(acc2_full, 1);
         mbar_init(done, 1);
-        mbar_init(red_full, TC_EPI_WARPS * 16);
-        mbar_init(red_full + 8, TC_EPI_WARPS * 16);
+        mbar_init(red_full, (TC_PARTS - 1) * 128);
+        mbar_init(red_full + 8, (TC_PARTS - 1) * 128);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == TC_MMA) {
@@ -319,8 +360,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and
-        // the column half w / 4
-        const int quarter = warp & 3, half = warp >> 2;
+        // the column part w / 4 (TC_PART_COLS columns of each layer)
+        const int quarter = warp & 3, part_id = warp >> 2;
         const int r = 32 * quarter + lane;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
         const float b3 = P[MLP_B3_OFF];
@@ -331,18 +372,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!__all_sync(0xffffffffu, mbar_wait(acc1_full, ph, abort, status))) break;
             tc_fence_after();
 #pragma unroll 1
-            for (int cc = 0; cc < 4; ++cc) {
-                const int c0 = 128 * half + 32 * cc;
+            for (int cc = 0; cc < TC_PART_COLS / 32; ++cc) {
+                const int c0 = TC_PART_COLS * part_id + 32 * cc;
                 float v[32];
                 tc_ld32(tmem + lane_addr + (uint32_t)c0, v);
 #pragma unroll
                 for (int g8 = 0; g8 < 4; ++g8) {
-                    uint4 o;
+                    uint32_t w[4];
                     const int c = c0 + 8 * g8;
-                    o.x = pack_bf16(gelu(v[8 * g8 + 0] + par[c + 0]), gelu(v[8 * g8 + 1] + par[c + 1]));
-                    o.y = pack_bf16(gelu(v[8 * g8 + 2] + par[c + 2]), gelu(v[8 * g8 + 3] + par[c + 3]));
-                    o.z = pack_bf16(gelu(v[8 * g8 + 4] + par[c + 4]), gelu(v[8 * g8 + 5] + par[c + 5]));
-                    o.w = pack_bf16(gelu(v[8 * g8 + 6] + par[c + 6]), gelu(v[8 * g8 + 7] + par[c + 7]));
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint64_t b = *reinterpret_cast<const uint64_t*>(par + c + 2 * j);
+                        float g0, g1;
+                        upk(gelu2(add2(pk(v[8 * g8 + 2 * j], v[8 * g8 + 2 * j + 1]), b)), g0, g1);
+                        w[j] = pack_bf16(g0, g1);
+                    }
+                    const uint4 o = make_uint4(w[0], w[1], w[2], w[3]);
                     // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r % 8)
                     const int chunk = (c & 63) >> 3;
                     unsigned char* dst = smem + OFF_H + (c >> 6) * ATOM + r * 128 + ((chunk ^ (r & 7)) << 4);
@@ -354,28 +399,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive(h1_full);
             if (!__all_sync(0xffffffffu, mbar_wait(acc2_full, ph, abort, status))) break;
             tc_fence_after();
-            float part = 0.0f;
+            uint64_t part2 = dup2(0.0f);
 #pragma unroll 1
-            for (int cc = 0; cc < 4; ++cc) {
-                const int c0 = 128 * half + 32 * cc;
+            for (int cc = 0; cc < TC_PART_COLS / 32; ++cc) {
+                const int c0 = TC_PART_COLS * part_id + 32 * cc;
                 float v[32];
                 tc_ld32(tmem + lane_addr + 256u + (uint32_t)c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float h = __bfloat162float(__float2bfloat16_rn(gelu(v[j] + par[256 + c0 + j])));
-                    part = fmaf(h, par[512 + c0 + j], part);
+                for (int j = 0; j < 32; j += 2) {
+                    const uint64_t b = *reinterpret_cast<const uint64_t*>(par + 256 + c0 + j);
+                    float g0, g1;
+                    upk(gelu2(add2(pk(v[j], v[j + 1]), b)), g0, g1);
+                    // the layer-2 activations are bf16 values
+                    const uint32_t hb = pack_bf16(g0, g1);
+                    const uint64_t h = pk(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u));
+                    part2 = fma2(h, *reinterpret_cast<const uint64_t*>(par + 512 + c0 + j), part2);
                 }
             }
-            // the second column half hands its partial sums to the first
-            float* rb = red + (it & 1) * 128;
+            float pa, pb;
+            upk(part2, pa, pb);
+            const float part = pa + pb;
+            // the other column parts hand their partial sums to part 0, which
+            // adds them in a fixed order
+            float* rb = red + (it & 1) * (TC_PARTS - 1) * 128;
             const uint32_t rbar = red_full + 8u * (uint32_t)(it & 1);
-            if (half == 1) {
-                rb[r] = part;
+            if (part_id > 0) {
+                rb[(part_id - 1) * 128 + r] = part;
                 mbar_arrive(rbar);
             } else {
                 if (!__all_sync(0xffffffffu, mbar_wait(rbar, (uint32_t)(it >> 1) & 1u, abort, status))) break;
                 const int64_t row = tile * TC_ROWS + r;
-                if (row < n) y[row] = part + rb[r] + b3;
+                float sum = part;
+#pragma unroll
+                for (int k = 0; k < TC_PARTS - 1; ++k) sum += rb[k * 128 + r];
+                if (row < n) y[row] = sum + b3;
             }
         }
     }
