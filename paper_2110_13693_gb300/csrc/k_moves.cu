@@ -450,13 +450,29 @@ __device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk,
     return ok;
 }
 
-// one warp per task of more than SHORT_MAX lines
-__global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
+// Tasks of more than SHORT_MAX lines, in two kernels.  k_mv_long_rec: one
+// warp per task walks the changed tour (walk_task_warp), sorts its keys in
+// shared memory and extracts the per-aisle records in parallel (a ballot
+// numbers the aisle runs) into a column matrix in global memory; a task with
+// more than MVL_RMAX records runs its scan and DP on one lane right away.
+// k_mv_long_dp: one task per thread runs the DP over its records (coalesced
+// column reads), so the DP, one step per visited aisle, keeps every lane busy.
+__device__ __forceinline__ void mv_long_commit(const MoveArgs& M, int64_t i, int cs, int cr) {
+    const int4 tk = M.tasks[i];
+    M.task_cost[i] = make_int2(cs, cr);
+    const long long ds = (long long)cs - M.tour_s_old[tk.y];
+    const long long dr = (long long)cr - M.tour_rr_old[tk.y];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x]), (unsigned long long)ds);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x + 1]), (unsigned long long)dr);
+}
+
+__global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long_rec(MoveArgs M) {
     __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int count = min(*M.long_count, M.long_cap);
+    const int count = min(min(*M.long_count, M.long_cap), M.long_rec_cap);
     uint32_t* kb = buf[warp];
     const EvalArgs& a = M.a;
+    const int64_t cap = M.long_rec_cap;
     for (int w = blockIdx.x * LONG_WARPS + warp; w < count; w += gridDim.x * LONG_WARPS) {
         const int64_t i = M.long_list[w];
         const int4 tk = M.tasks[i];
@@ -465,18 +481,19 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
         bool primary = false;
         const bool ok = walk_task_warp(M, tk, mv, kb, LONG_MAXL, lane, n, primary);
         __syncwarp();
-        if (!ok || n > LONG_MAXL) {
+        if (!ok || n > LONG_MAXL || n < 1) {
             if (lane == 0) {
                 flag(a.status, n > LONG_MAXL ? WH_STATUS_TOUR_TOO_LONG : WH_STATUS_BAD_ORDER);
                 M.mstatus[tk.x] = 3;
                 M.task_cost[i] = make_int2(-1, -1);
+                M.long_m[w] = -1;
             }
             __syncwarp();
             continue;
         }
         int p2 = 64;
         while (p2 < n) p2 <<= 1;
-        for (int j = n + lane; j < p2; j += 32) kb[j] = KEY_NONE;
+        for (int x = n + lane; x < p2; x += 32) kb[x] = KEY_NONE;
         __syncwarp();
         for (int k = 2; k <= p2; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -491,34 +508,69 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long(MoveArgs M) {
                 __syncwarp();
             }
         }
-        if (lane == 0) {
-            DP5 v;
-            dp_init(v);
-            int m = 0, pa = 0, lo = 0, prev = 0, gi = 0, last_a = 0, last_hi = 0;
-            for (int x = 0; x < n; ++x) {
-                const uint32_t key = kb[x];
-                const int ai = (int)(key >> 16), k = (int)(key & 0xFFFFu);
-                const bool first = (x == 0) || ((int)(kb[x - 1] >> 16) != ai);
-                const bool last = (x == n - 1) || ((int)(kb[x + 1] >> 16) != ai);
-                gi = first ? 0 : max(gi, k - prev);
-                lo = first ? k : lo;
-                prev = k;
-                if (last) {
-                    dp_aisle(v, a.g, ai - pa, lo, k, gi);
-                    pa = ai;
-                    ++m;
-                    last_a = ai;
-                    last_hi = k;
+        // per-aisle records: run r of the sorted keys -> long_rec[r * cap + w]
+        int m = 0;
+        for (int x0 = 0; x0 < n; x0 += 32) {
+            const int x = x0 + lane;
+            const bool in = x < n;
+            const uint32_t key = in ? kb[x] : 0u;
+            const int ai = (int)(key >> 16);
+            const bool first = in && (x == 0 || (int)(kb[x - 1] >> 16) != ai);
+            const bool last = in && (x == n - 1 || (int)(kb[x + 1] >> 16) != ai);
+            const unsigned fm = __ballot_sync(0xffffffffu, first);
+            const int r = m + __popc(fm & ((2u << lane) - 1u)) - 1;
+            if (last && r < MVL_RMAX) {
+                const int hi = (int)(key & 0xFFFFu);
+                int lo = hi, gi = 0;
+                for (int y = x; y > 0 && (int)(kb[y - 1] >> 16) == ai; --y) {
+                    const int kp = (int)(kb[y - 1] & 0xFFFFu);
+                    gi = max(gi, lo - kp);
+                    lo = kp;
                 }
+                M.long_rec[r * cap + w] =
+                    make_uint2(((uint32_t)ai << 16) | (uint32_t)lo, ((uint32_t)hi << 16) | (uint32_t)gi);
             }
-            const int cs = sshape_cost(a.g, m, last_a, last_hi), cr = dp_final(v);
-            M.task_cost[i] = make_int2(cs, cr);
-            const long long ds = (long long)cs - M.tour_s_old[tk.y];
-            const long long dr = (long long)cr - M.tour_rr_old[tk.y];
-            atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x]), (unsigned long long)ds);
-            atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x + 1]), (unsigned long long)dr);
+            m += __popc(fm);
+        }
+        if (lane == 0) {
+            const uint32_t kl = kb[n - 1];   // rightmost aisle, its deepest slot
+            M.long_key[w] = kl;
+            if (m <= MVL_RMAX) {
+                M.long_m[w] = m;
+            } else {
+                // more aisles than the record matrix keeps: scan and DP here
+                M.long_m[w] = -1;
+                DP5 v;
+                dp_init(v);
+                int pa = 0, lo = 0, prev = 0, gi = 0;
+                for (int x = 0; x < n; ++x) {
+                    const uint32_t key = kb[x];
+                    const int ai = (int)(key >> 16), k = (int)(key & 0xFFFFu);
+                    const bool first = (x == 0) || ((int)(kb[x - 1] >> 16) != ai);
+                    const bool last = (x == n - 1) || ((int)(kb[x + 1] >> 16) != ai);
+                    gi = first ? 0 : max(gi, k - prev);
+                    lo = first ? k : lo;
+                    prev = k;
+                    if (last) {
+                        dp_aisle(v, a.g, ai - pa, lo, k, gi);
+                        pa = ai;
+                    }
+                }
+                mv_long_commit(M, i, sshape_cost(a.g, m, (int)(kl >> 16), (int)(kl & 0xFFFFu)), dp_final(v));
+            }
         }
         __syncwarp();
+    }
+}
+
+__global__ void k_mv_long_dp(MoveArgs M) {
+    const int count = min(min(*M.long_count, M.long_cap), M.long_rec_cap);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
+        const int m = M.long_m[w];
+        if (m < 0) continue;
+        const uint32_t kl = M.long_key[w];
+        mv_long_commit(M, M.long_list[w], sshape_cost(M.a.g, m, (int)(kl >> 16), (int)(kl & 0xFFFFu)),
+                       rr_records32(M.a.g, M.long_rec + w, M.long_rec_cap, m));
     }
 }
 
@@ -585,9 +637,17 @@ cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStre
         if (grid > want) grid = (int)want;
         if (grid < 1) grid = 1;
         kern<<<grid, MV_THREADS, smem, s>>>(M);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mv_long, LONG_WARPS * 32, 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moves_long(const MoveArgs& M, int num_sms, cudaStream_t s) {
+    if (M.n_tasks > 0 && M.long_rec_cap > 0) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mv_long_rec, LONG_WARPS * 32, 0);
         if (e != cudaSuccess) return e;
-        k_mv_long<<<num_sms * (per_sm > 0 ? per_sm : 1), LONG_WARPS * 32, 0, s>>>(M);
+        k_mv_long_rec<<<num_sms * (per_sm > 0 ? per_sm : 1), LONG_WARPS * 32, 0, s>>>(M);
+        k_mv_long_dp<<<grid_of(M.long_rec_cap, 128), 128, 0, s>>>(M);
     }
     if (M.n_moves > 0) k_mv_finish<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
     return cudaGetLastError();

@@ -216,7 +216,7 @@ __device__ __forceinline__ void scan16(const uint32_t (&x)[R], uint32_t* rec, in
     }
 }
 
-__device__ __forceinline__ int rr_records32(const Geo& g, const uint2* rec, int stride, int m) {
+__device__ __forceinline__ int rr_records32(const Geo& g, const uint2* rec, int64_t stride, int m) {
     DP5 v;
     dp_init(v);
     int pa = 0;

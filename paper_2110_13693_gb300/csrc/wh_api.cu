@@ -25,6 +25,8 @@ struct wh_layout {
     size_t mv_scratch_bytes = 0;
     void* mv_tasks = nullptr;     // device: move tasks + their costs + long-task list
     size_t mv_tasks_bytes = 0;
+    void* mv_long = nullptr;      // device: long tasks' record matrix, record counts, largest keys
+    size_t mv_long_bytes = 0;
     void* sr_scratch = nullptr;   // device: screening features and predictions
     size_t sr_scratch_bytes = 0;
     // the task list of the last wh_eval_moves call (for wh_ls_apply's cost update)
@@ -362,6 +364,35 @@ int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int
 
 }  // namespace
 
+namespace {
+
+// The long tasks listed by the short-task pass: read their number (one
+// stream synchronisation), size the record matrix, run the record and DP
+// kernels, then the final status pass.
+int eval_long_tasks(wh_layout* h, wh::MoveArgs& M, cudaStream_t s) {
+    int32_t n_long = 0;
+    if (M.n_tasks > 0) {
+        if (cudaMemcpyAsync(&n_long, M.long_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return WH_ECUDA;
+        n_long = std::min(n_long, M.long_cap);
+    }
+    M.long_rec_cap = n_long;
+    if (n_long > 0) {
+        const size_t rec = align_up(sizeof(uint2) * (size_t)wh::MVL_RMAX * (size_t)n_long);
+        const size_t col = align_up(sizeof(int32_t) * (size_t)n_long);
+        const int rc = grow(&h->mv_long, &h->mv_long_bytes, rec + 2 * col);
+        if (rc != WH_OK) return rc;
+        char* b = static_cast<char*>(h->mv_long);
+        M.long_rec = reinterpret_cast<uint2*>(b);
+        M.long_m = reinterpret_cast<int32_t*>(b + rec);
+        M.long_key = reinterpret_cast<uint32_t*>(b + rec + col);
+    }
+    return wh::launch_moves_long(M, h->num_sms, s) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
+}  // namespace
+
 extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* tour_s,
                              const int32_t* tour_rr, const int32_t* moves, int32_t n_moves, int32_t max_orders,
                              int32_t max_lines, int64_t* delta, int32_t* status, void* stream) {
@@ -383,6 +414,8 @@ extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_pla
     M.tour_rr_old = tour_rr;
     const bool k16 = wh::key16_ok(h->g);
     if (wh::launch_moves_eval(M, k16, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    rc = eval_long_tasks(h, M, s);
+    if (rc != WH_OK) return rc;
     h->last_moves = moves;
     h->last_n_moves = n_moves;
     h->last_task_off = M.task_off;
@@ -627,6 +660,7 @@ extern "C" void wh_destroy(wh_layout* h) {
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
         if (h->mv_scratch) cudaFree(h->mv_scratch);
         if (h->mv_tasks) cudaFree(h->mv_tasks);
+        if (h->mv_long) cudaFree(h->mv_long);
         if (h->sr_scratch) cudaFree(h->sr_scratch);
         if (h->scratch) cudaFree(h->scratch);
         if (h->meta) cudaFree(h->meta);

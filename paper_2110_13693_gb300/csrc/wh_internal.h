@@ -104,6 +104,13 @@ struct MoveArgs {
     int32_t* long_list;         // tasks over SHORT_MAX lines
     int32_t* long_count;
     int32_t long_cap;
+    // long tasks' per-aisle records for the one-task-per-thread DP: record r
+    // of list entry w at long_rec[r * long_rec_cap + w]; long_m[w] records
+    // (-1: scored already), long_key[w] the largest key
+    uint2* long_rec;
+    int32_t* long_m;
+    uint32_t* long_key;
+    int32_t long_rec_cap;
 };
 
 struct LsArgs {
@@ -142,7 +149,11 @@ cudaError_t launch_screen_select(const ScreenArgs& S, cudaStream_t s);
 
 cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s);
 cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s);
+// task fill + tasks of <= SHORT_MAX lines; the long ones are listed
 cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s);
+// the listed long tasks (records, then their DPs) and the final status pass
+cudaError_t launch_moves_long(const MoveArgs& M, int num_sms, cudaStream_t s);
+constexpr int MVL_RMAX = 48;    // records per long task kept for the per-thread DP
 cudaError_t launch_moves_fill(const MoveArgs& M, cudaStream_t s);
 
 // Surrogate (k_surrogate.cu).  Packed parameter vector: w1 [192][256],

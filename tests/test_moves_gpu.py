@@ -72,6 +72,38 @@ def test_paperscale_long_tours_and_popular_skus(gpu_lib):
     assert st == 0 and (s == 0).sum() > 40
 
 
+def long_instance(lay, seed, n_orders=400, lines=(8, 12), per_tour=8, n_plans=3):
+    """Orders of many lines on a random slotting, tours of `per_tour` orders
+    (about 80 lines each, all above the one-tour-per-thread limit of 64)."""
+    rng = np.random.default_rng(seed)
+    n_sku = lay.n_loc
+    slot = rng.permutation(lay.n_loc).astype(np.int32)
+    sizes = rng.integers(lines[0], lines[1] + 1, n_orders)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    line_sku = np.concatenate([rng.choice(n_sku, size=int(k), replace=False) for k in sizes]).astype(np.int32)
+    pto, to, seq = [0], [0], []
+    for _ in range(n_plans):
+        perm = rng.permutation(n_orders)
+        for t0 in range(0, n_orders, per_tour):
+            seq.extend(perm[t0:t0 + per_tour].tolist())
+            to.append(len(seq))
+        pto.append(len(to) - 1)
+    return wh_gen.Instance(lay, n_sku, off, line_sku, slot, np.asarray(pto, np.int32), np.asarray(to, np.int32),
+                           np.asarray(seq, np.int32))
+
+
+@pytest.mark.parametrize("lay", [wh_gen.Layout(40, 100), wh_gen.Layout(300, 10)])
+def test_long_tasks_batched_and_wide(gpu_lib, lay):
+    """Tasks of about 80 lines: on 40 aisles every task's records fit the
+    batched per-lane DP; on 300 aisles most tasks visit more aisles than it
+    keeps and take the single-lane path.  Several batches of 32 per warp."""
+    inst = long_instance(lay, lay.n_aisles)
+    assert (inst.tour_lines() > 64).all()
+    maps = np.tile(inst.slot_map, (inst.n_plans, 1)).astype(np.int32)
+    s, st = check(gpu_lib, inst, moves_for(inst, 7, 64), maps=maps)
+    assert st == 0 and (s == 0).sum() > 150
+
+
 def test_status_cases(gpu_lib):
     inst = wh_gen.tiny(seed=7, n_plans=2)
     t0, t1 = inst.plan_tour_off[0], inst.plan_tour_off[1]
