@@ -302,27 +302,49 @@ __device__ __forceinline__ bool walk_task(const MoveArgs& M, const int4 tk, cons
     int hit_min = 0x7fffffff;
     bool own_has_s1 = false;
     bool ok = q0 >= 0 && q1 >= q0 && (int64_t)q1 <= a.n_seq;
-    for (int q = q0; ok && q <= q1; ++q) {
-        int o;
-        if (q < q1) {
-            o = a.order_seq[q];
-            if (o == rem) continue;
-        } else {
-            if (add < 0) break;
-            o = add;
-        }
-        int lb, le;
-        if (order_lines_checked(a, o, lb, le) < 0) { ok = false; break; }
-        for (int l = lb; l < le; ++l) {
-            const int s = a.line_sku[l];
-            if ((unsigned)s >= (unsigned)a.n_sku) { ok = false; break; }
-            if (swap && (s == mv.y || s == mv.z)) {
-                hit_min = min(hit_min, o);
-                if (o == tk.z && s == mv.y) own_has_s1 = true;
+    // the orders walked: positions q0..q1-1 of order_seq (without `rem`),
+    // then the added order; ids two ahead and line bounds one ahead are in
+    // flight while the current order's lines are gathered
+    const int q_end = !ok ? q0 : (add >= 0 ? q1 + 1 : q1);
+    auto order_at = [&](int q) { return q < q1 ? a.order_seq[q] : add; };
+    int o0 = q0 < q_end ? order_at(q0) : 0;
+    int o1 = q0 + 1 < q_end ? order_at(q0 + 1) : 0;
+    int lb0 = 0, le0 = 0;
+    bool v0 = q0 < q_end && order_lines_checked(a, o0, lb0, le0) >= 0;
+    for (int q = q0; ok && q < q_end; ++q) {
+        const int o = o0;
+        const int lb = lb0, le = le0;
+        const bool valid = v0;
+        const int o2 = q + 2 < q_end ? order_at(q + 2) : 0;
+        v0 = q + 1 < q_end && order_lines_checked(a, o1, lb0, le0) >= 0;
+        o0 = o1;
+        o1 = o2;
+        if (q < q1 && o == rem) continue;
+        if (!valid) { ok = false; break; }
+        // four lines at a time: their SKU loads, then their slot loads (the
+        // plan's own slotting, mostly DRAM), are in flight together
+        for (int l = lb; ok && l < le; l += 4) {
+            int sk[4], loc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sk[j] = l + j < le ? a.line_sku[l + j] : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                loc[j] = -1;
+                if (l + j >= le) continue;
+                const int sj = sk[j];
+                if ((unsigned)sj >= (unsigned)a.n_sku) { ok = false; continue; }
+                if (swap && (sj == mv.y || sj == mv.z)) {
+                    hit_min = min(hit_min, o);
+                    if (o == tk.z && sj == mv.y) own_has_s1 = true;
+                }
+                loc[j] = task_loc(map, sj, swap, mv.y, mv.z);
             }
-            const int loc = task_loc(map, s, swap, mv.y, mv.z);
-            if ((unsigned)loc >= (unsigned)a.g.n_loc) { ok = false; break; }
-            emit(loc_key(a.g, loc));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!ok || l + j >= le) continue;
+                if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) { ok = false; continue; }
+                emit(loc_key(a.g, loc[j]));
+            }
         }
     }
     primary = !swap || (hit_min == tk.z && (tk.w == -2 || !own_has_s1));
