@@ -133,3 +133,37 @@ def test_repeat_and_empty(gpu_lib):
     d, s = lay.eval_moves(prob, costs, torch.zeros((0, 4), dtype=torch.int32, device="cuda"))
     assert d.shape[0] == 0 and s.shape[0] == 0
     lay.close()
+
+
+def test_paperscale_full_size_sampled(gpu_lib):
+    """The benchmark's launch: 16,384 paper-scale plans with their own
+    slottings x 64 moves (1,048,576 moves, long tasks included).  Sampled
+    moves are re-scored one by one by the oracle on their plan alone; every
+    status is in range and every non-zero status has zero deltas."""
+    import torch
+    wh = gpu_lib
+    n_plans, M = 16384, 64
+    inst = wh_gen.paperscale(seed=4, n_plans=n_plans)
+    lay = wh.Layout.of(inst.layout)
+    base = wh.to_device(inst)
+    prob = wh.DeviceProblem(base.order_off, base.line_sku, base.slot_map.repeat(n_plans), base.plan_tour_off,
+                            base.tour_off, base.order_seq, inst.n_sku, inst.n_sku)
+    costs = wh.evaluate(lay, prob)
+    mv = wh_gen.gen_moves(17, 0, inst, M)
+    mv[..., 3] = np.arange(n_plans)[:, None]
+    mv = mv.reshape(-1, 4)
+    delta, status = lay.eval_moves(prob, costs, torch.as_tensor(mv).cuda(), 24)
+    d, s = delta.cpu().numpy(), status.cpu().numpy()
+    assert lay.status() == 0
+    assert set(np.unique(s).tolist()) <= {0, 1, 2, 3} and (s == 0).mean() > 0.5
+    assert (d[s != 0] == 0).all()
+    rng = np.random.default_rng(0)
+    picks = np.concatenate([[0, len(mv) - 1], rng.integers(0, len(mv), 250)])
+    for k in picks:
+        p = int(mv[k, 3])
+        one = inst.subset_plans([p])
+        m1 = mv[k].copy()
+        m1[3] = 0
+        wd, ws = oracle.eval_moves(one, m1[None], 24, 0, slot_map=inst.slot_map, slot_map_stride=inst.n_sku)
+        assert s[k] == ws[0] and (d[k] == wd[0]).all(), (k, mv[k], d[k], wd[0], s[k], ws[0])
+    lay.close()

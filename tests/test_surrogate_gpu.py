@@ -201,3 +201,26 @@ def test_training_reduces_error(gpu_lib):
     err1 = rel.mean().item()
     assert err1 < 0.5 * err0 and err1 < 0.15, (err0, err1)
     s.close()
+
+
+def test_features_full_paperscale_sampled(gpu_lib):
+    """Features of every tour of the 16,384-plan paper-scale population with
+    per-plan slottings (2.7 M tours, the prescreen's workload); sampled rows
+    bit-equal to the oracle's."""
+    import torch
+    wh = gpu_lib
+    n_plans = 16384
+    inst = wh_gen.paperscale(seed=4, n_plans=n_plans)
+    lay = wh.Layout.of(inst.layout)
+    base = wh.to_device(inst)
+    prob = wh.DeviceProblem(base.order_off, base.line_sku, base.slot_map.repeat(n_plans), base.plan_tour_off,
+                            base.tour_off, base.order_seq, inst.n_sku, inst.n_sku)
+    X = wh.features(lay, prob).view(torch.int16)
+    assert lay.status() == 0
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([[0, inst.n_tours - 1], rng.integers(0, inst.n_tours, 300)])
+    got = X[torch.as_tensor(rows).cuda()].cpu().numpy()
+    for r, t in enumerate(rows):
+        want = oracle.bf16(oracle.features(inst.layout, tour_locs(inst, int(t), inst.slot_map)))
+        assert np.array_equal(got[r], torch.from_numpy(want).to(torch.bfloat16).view(torch.int16).numpy()), t
+    lay.close()
