@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = 0; k0 < g.K; k0 += G_BK) {
+    // K range of this split (one split unless gridDim.z > 1)
+    const int per = (((g.K + (int)gridDim.z - 1) / (int)gridDim.z) + G_BK - 1) / G_BK * G_BK;
+    const int k_begin = (int)blockIdx.z * per, k_end = min(g.K, k_begin + per);
+    for (int k0 = k_begin; k0 < k_end; k0 += G_BK) {
 #pragma unroll 4
         for (int i = 0; i < (G_BM * G_BK) / G_THREADS; ++i) {
             const int e = tid + i * G_THREADS;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
             const int64_t gm = m0 + m;
             const int gk = k0 + k;
             __nv_bfloat16 v = zero;
-            if (gm < g.M && gk < g.K) v = g.transA ? g.A[(int64_t)gk * g.lda + gm] : g.A[gm * g.lda + gk];
+            if (gm < g.M && gk < k_end) v = g.transA ? g.A[(int64_t)gk * g.lda + gm] : g.A[gm * g.lda + gk];
             As[m][k] = v;
         }
 #pragma unroll 4
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
             if (g.transB) { n = e / G_BK; k = e % G_BK; } else { n = e % G_BN; k = e / G_BN; }
             const int gn = n0 + n, gk = k0 + k;
             __nv_bfloat16 v = zero;
-            if (gn < g.N && gk < g.K) v = g.transB ? g.B[(int64_t)gn * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gn];
+            if (gn < g.N && gk < k_end) v = g.transB ? g.B[(int64_t)gn * g.ldb + gk] : g.B[(int64_t)gk * g.ldb + gn];
             Bs[n][k] = v;
         }
         __syncthreads();
@@ -199,6 +202,8 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
                     g.Cb[m * g.ldc + n] = __float2bfloat16_rn(gelu_f(z));
                 } else if constexpr (EPI == EPI_GELU_GRAD) {
                     g.Cb[m * g.ldc + n] = __float2bfloat16_rn(v * gelu_grad_f(g.Z[m * g.ldz + n]));
+                } else if (gridDim.z > 1) {
+                    g.Cpart[((int64_t)blockIdx.z * g.M + m) * g.ldc + n] = v;
                 } else {
                     g.Cf[m * g.ldc + n] = v;
                 }
@@ -250,20 +255,35 @@ __global__ void k_dz2(const float* dy, const float* w3, const float* Z2, int64_t
 
 // out[j] = sum_m X[m, j] * (scale ? scale[m] : 1), X bf16 [n][cols]; one block per
 // 32 columns, threads stride over rows
-__global__ void k_colsum(const __nv_bfloat16* X, int64_t n, int cols, const float* scale, float* out) {
-    __shared__ float part[8][33];
+// column sums of X [n][cols] (rows scaled by scale[m] when given): block
+// (x, y) sums columns 32x..32x+31 over the rows of split y; split partials go
+// to part[y][cols] (added in order by k_split_reduce), or straight to out
+// with one split
+__global__ void k_colsum(const __nv_bfloat16* X, int64_t n, int cols, const float* scale, float* out, float* part) {
+    __shared__ float ps[8][33];
     const int c = blockIdx.x * 32 + (threadIdx.x & 31);
     const int r0 = threadIdx.x >> 5;
+    const int64_t per = (n + gridDim.y - 1) / gridDim.y;
+    const int64_t m0 = (int64_t)blockIdx.y * per, m1 = min(n, m0 + per);
     float s = 0.0f;
     if (c < cols)
-        for (int64_t m = r0; m < n; m += 8) s += __bfloat162float(X[m * cols + c]) * (scale ? scale[m] : 1.0f);
-    part[r0][threadIdx.x & 31] = s;
+        for (int64_t m = m0 + r0; m < m1; m += 8) s += __bfloat162float(X[m * cols + c]) * (scale ? scale[m] : 1.0f);
+    ps[r0][threadIdx.x & 31] = s;
     __syncthreads();
     if (r0 == 0 && c < cols) {
         float t = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) t += part[i][threadIdx.x & 31];
-        out[c] = t;
+        for (int i = 0; i < 8; ++i) t += ps[i][threadIdx.x & 31];
+        if (gridDim.y > 1) part[(int64_t)blockIdx.y * cols + c] = t;
+        else out[c] = t;
+    }
+}
+
+__global__ void k_split_reduce(const float* part, int splits, int64_t n, float* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float t = 0.0f;
+        for (int z = 0; z < splits; ++z) t += part[(int64_t)z * n + i];
+        out[i] = t;
     }
 }
 
@@ -362,9 +382,34 @@ cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s) {
-    k_colsum<<<(cols + 31) / 32, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(X), n, cols, scale, out);
+cudaError_t launch_split_reduce(const float* part, int splits, int64_t n, float* out, cudaStream_t s) {
+    k_split_reduce<<<blocks_for(n, 256), 256, 0, s>>>(part, splits, n, out);
     return cudaGetLastError();
+}
+
+// split K so that the few output tiles of a weight gradient (K = the batch)
+// still fill the GPU; deterministic (fixed-order reduction of the splits)
+cudaError_t launch_gemm_splitk(const GemmArgs& g, int splits, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    if (splits <= 1 || !g.Cpart) return launch_gemm(g, EPI_F32, s);
+    const dim3 grid((g.N + G_BN - 1) / G_BN, (unsigned)((g.M + G_BM - 1) / G_BM), (unsigned)splits);
+    k_gemm<EPI_F32><<<grid, G_THREADS, 0, s>>>(g);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_split_reduce(g.Cpart, splits, g.M * g.ldc, g.Cf, s);
+}
+
+// column sums; the scratch `part` (>= 64 * cols floats) lets the rows split
+cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s,
+                          float* part) {
+    int splits = part ? (int)((n + 255) / 256) : 1;
+    if (splits > 64) splits = 64;
+    if (splits < 1) splits = 1;
+    k_colsum<<<dim3((cols + 31) / 32, splits), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(X), n, cols, scale,
+                                                            out, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    return launch_split_reduce(part, splits, cols, out, s);
 }
 
 cudaError_t launch_sum(const float* v, int n, float* out, cudaStream_t s) {

@@ -183,6 +183,9 @@ struct GemmArgs {
     __nv_bfloat16* Cb;
     float* Cf;
     int64_t ldc;
+    // fp32 output in splits of K (gridDim.z > 1): split z writes
+    // Cpart[z][M][ldc], then launch_split_reduce adds them in a fixed order
+    float* Cpart;
 };
 
 struct FeatConst {
@@ -201,7 +204,11 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 0
 cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s);
 cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, float* loss, const float* w3,
                               const float* Z2, void* dZ2, cudaStream_t s);
-cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s);
+// out[i] = sum over z < splits of part[z * n + i], in order of z
+cudaError_t launch_split_reduce(const float* part, int splits, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_gemm_splitk(const GemmArgs& g, int splits, cudaStream_t s);
+cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s,
+                          float* part = nullptr);
 cudaError_t launch_sum(const float* v, int n, float* out, cudaStream_t s);
 cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr, int step, void* w1b,
                         void* w2b, cudaStream_t s);

@@ -24,6 +24,7 @@ struct wh_surrogate {
     int step = 0;
     int64_t cap = 0;       // rows of training scratch
     float *Z1 = nullptr, *Z2 = nullptr, *y = nullptr, *dy = nullptr, *loss = nullptr;
+    float* part = nullptr; // split partials of the weight gradients and column sums
     __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     __nv_bfloat16 *w1t = nullptr, *w2t = nullptr;   // [256][192], [256][256]: K contiguous
     CUtensorMap mw1, mw2;
@@ -78,7 +79,7 @@ uint64_t sm64(uint64_t& s) {
 
 void free_all(wh_surrogate* s) {
     void* ptrs[] = {s->P, s->Mo, s->Ve, s->G, s->w1b, s->w2b, s->Z1, s->Z2, s->y, s->dy, s->loss,
-                    s->H1, s->H2, s->dZ2, s->dZ1, s->w1t, s->w2t, s->status};
+                    s->H1, s->H2, s->dZ2, s->dZ1, s->w1t, s->w2t, s->status, s->part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -100,7 +101,15 @@ int dalloc(T** p, size_t n) {
     return WH_OK;
 }
 
+constexpr int kMaxSplits = 32;   // K splits of a weight gradient (K = the batch)
+
+int splits_for(int64_t n) {
+    const int64_t k = (n + 127) / 128;
+    return (int)(k < 1 ? 1 : (k > kMaxSplits ? kMaxSplits : k));
+}
+
 int reserve_train(wh_surrogate* s, int64_t n) {
+    if (!s->part && dalloc(&s->part, (size_t)kMaxSplits * 256 * 256)) return WH_ENOMEM;
     if (n <= s->cap) return WH_OK;
     void* old[] = {s->Z1, s->Z2, s->y, s->dy, s->H1, s->H2, s->dZ2, s->dZ1};
     for (void* p : old)
@@ -268,14 +277,16 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
         cudaSuccess)
         return WH_ECUDA;
     // output layer
-    if (wh::launch_colsum(s->H2, n, 256, s->dy, s->G + wh::MLP_W3_OFF, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_colsum(s->H2, n, 256, s->dy, s->G + wh::MLP_W3_OFF, st, s->part) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_sum(s->dy, n, s->G + wh::MLP_B3_OFF, st) != cudaSuccess) return WH_ECUDA;
     // layer 2: dW2 = H1^T dZ2, db2 = colsum dZ2, dZ1 = (dZ2 W2^T) * gelu'(Z1)
-    if (wh::launch_colsum(s->dZ2, n, 256, nullptr, s->G + wh::MLP_B2_OFF, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_colsum(s->dZ2, n, 256, nullptr, s->G + wh::MLP_B2_OFF, st, s->part) != cudaSuccess)
+        return WH_ECUDA;
     wh::GemmArgs gw2 = gemm(256, 256, n, s->H1, 256, 1, s->dZ2, 256, 0);
+    gw2.Cpart = s->part;
     gw2.Cf = s->G + wh::MLP_W2_OFF;
     gw2.ldc = 256;
-    if (wh::launch_gemm(gw2, 1, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_gemm_splitk(gw2, splits_for(n), st) != cudaSuccess) return WH_ECUDA;
     wh::GemmArgs gd1 = gemm(n, 256, 256, s->dZ2, 256, 0, s->w2b, 256, 1);
     gd1.Z = s->Z1;
     gd1.ldz = 256;
@@ -283,11 +294,13 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     gd1.ldc = 256;
     if (wh::launch_gemm(gd1, 2, st) != cudaSuccess) return WH_ECUDA;
     // layer 1: dW1 = X^T dZ1, db1 = colsum dZ1
-    if (wh::launch_colsum(s->dZ1, n, 256, nullptr, s->G + wh::MLP_B1_OFF, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_colsum(s->dZ1, n, 256, nullptr, s->G + wh::MLP_B1_OFF, st, s->part) != cudaSuccess)
+        return WH_ECUDA;
     wh::GemmArgs gw1 = gemm(192, 256, n, Xb, 192, 1, s->dZ1, 256, 0);
+    gw1.Cpart = s->part;
     gw1.Cf = s->G;
     gw1.ldc = 256;
-    if (wh::launch_gemm(gw1, 1, st) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_gemm_splitk(gw1, splits_for(n), st) != cudaSuccess) return WH_ECUDA;
     s->step += 1;
     if (wh::launch_adam(s->P, s->Mo, s->Ve, s->G, wh::MLP_NPARAM, lr, s->step, s->w1b, s->w2b, st) != cudaSuccess)
         return WH_ECUDA;
