@@ -235,10 +235,21 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&p);
 }
 
+// Training forward: the pre-activations (fp32) and activations (bf16) of
+// both hidden layers, row-major [n][256], for the backward pass; all NULL for
+// inference.
+struct MlpSave {
+    float* Z1;
+    __nv_bfloat16* H1;
+    float* Z2;
+    __nv_bfloat16* H2;
+};
+
+template <bool SAVE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw1,
              const __grid_constant__ CUtensorMap mw2, const float* __restrict__ P, int64_t n, float* __restrict__ y,
-             int* status) {
+             int* status, MlpSave save) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(smem);
@@ -368,6 +379,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int64_t it = 0;
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
             const uint32_t ph = (uint32_t)it & 1u;
+            const int64_t row = tile * TC_ROWS + r;
+            const bool save_rows = SAVE && row < n;
             // the TMEM loads below are warp-collective: leave together
             if (!__all_sync(0xffffffffu, mbar_wait(acc1_full, ph, abort, status))) break;
             tc_fence_after();
@@ -383,11 +396,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint64_t b = *reinterpret_cast<const uint64_t*>(par + c + 2 * j);
+                        const uint64_t z = add2(pk(v[8 * g8 + 2 * j], v[8 * g8 + 2 * j + 1]), b);
+                        if (save_rows) *reinterpret_cast<uint64_t*>(save.Z1 + row * 256 + c + 2 * j) = z;
                         float g0, g1;
-                        upk(gelu2(add2(pk(v[8 * g8 + 2 * j], v[8 * g8 + 2 * j + 1]), b)), g0, g1);
+                        upk(gelu2(z), g0, g1);
                         w[j] = pack_bf16(g0, g1);
                     }
                     const uint4 o = make_uint4(w[0], w[1], w[2], w[3]);
+                    if (save_rows) *reinterpret_cast<uint4*>(save.H1 + row * 256 + c) = o;
                     // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r % 8)
                     const int chunk = (c & 63) >> 3;
                     unsigned char* dst = smem + OFF_H + (c >> 6) * ATOM + r * 128 + ((chunk ^ (r & 7)) << 4);
@@ -408,10 +424,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 32; j += 2) {
                     const uint64_t b = *reinterpret_cast<const uint64_t*>(par + 256 + c0 + j);
+                    const uint64_t z = add2(pk(v[j], v[j + 1]), b);
                     float g0, g1;
-                    upk(gelu2(add2(pk(v[j], v[j + 1]), b)), g0, g1);
+                    upk(gelu2(z), g0, g1);
                     // the layer-2 activations are bf16 values
                     const uint32_t hb = pack_bf16(g0, g1);
+                    if (save_rows) {
+                        *reinterpret_cast<uint64_t*>(save.Z2 + row * 256 + c0 + j) = z;
+                        *reinterpret_cast<uint32_t*>(save.H2 + row * 256 + c0 + j) = hb;
+                    }
                     const uint64_t h = pk(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u));
                     part2 = fma2(h, *reinterpret_cast<const uint64_t*>(par + 512 + c0 + j), part2);
                 }
@@ -428,7 +449,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_arrive(rbar);
             } else {
                 if (!__all_sync(0xffffffffu, mbar_wait(rbar, (uint32_t)(it >> 1) & 1u, abort, status))) break;
-                const int64_t row = tile * TC_ROWS + r;
                 float sum = part;
 #pragma unroll
                 for (int k = 0; k < TC_PARTS - 1; ++k) sum += rb[k * 128 + r];
@@ -463,13 +483,21 @@ cudaError_t launch_transpose_bf16(const float* p, int K, int N, void* out, cudaS
 }
 
 cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const CUtensorMap& mw2, const float* P,
-                          int64_t n, float* y, int* status, int num_sms, cudaStream_t s) {
+                          int64_t n, float* y, int* status, int num_sms, cudaStream_t s, float* Z1, void* H1,
+                          float* Z2, void* H2) {
     if (n <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    const bool save_acts = Z1 && H1 && Z2 && H2;
+    auto kern = save_acts ? k_mlp_tc<true> : k_mlp_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     const int grid = (int)(tiles < num_sms ? tiles : num_sms);
-    k_mlp_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(mx, mw1, mw2, P, n, y, status);
+    MlpSave save;
+    save.Z1 = Z1;
+    save.H1 = static_cast<__nv_bfloat16*>(H1);
+    save.Z2 = Z2;
+    save.H2 = static_cast<__nv_bfloat16*>(H2);
+    kern<<<grid, TC_THREADS, TC_SMEM, s>>>(mx, mw1, mw2, P, n, y, status, save);
     return cudaGetLastError();
 }
 

@@ -2,13 +2,14 @@
 // a tour's normalised optimal length (the learned prescreen of local-search
 // moves; the paper puts machine learning in the decision loop, Sec. 1 and
 // Fig. 1).  MLP 192 -> 256 -> GELU -> 256 -> GELU -> 1, bf16 weights and
-// activations, fp32 accumulation; training by forward, backward and Adam on
-// fp32 master weights, all on the device.
+// activations, fp32 accumulation; training by forward (k_mlp_tc.cu, on the
+// tcgen05 tensor cores), backward and Adam on fp32 master weights, all on the
+// device.
 //
-// The GEMMs use the warp-level tensor-core instruction mma.sync m16n8k16
-// (bf16 in, fp32 accumulate) on 128x128x32 shared-memory tiles; operands may
-// be transposed, epilogues fuse bias + GELU (keeping the fp32
-// pre-activation), the GELU derivative, or write fp32.
+// The backward GEMMs use the warp-level tensor-core instruction mma.sync
+// m16n8k16 (bf16 in, fp32 accumulate) on 128x128x32 shared-memory tiles;
+// operands may be transposed, epilogues fuse the GELU derivative or write
+// fp32 (the weight gradients in splits of K, reduced in a fixed order).
 #include "tour_core.cuh"
 
 namespace wh {
@@ -18,7 +19,6 @@ namespace {
 constexpr int FEAT_THREADS = 256;
 constexpr int G_BM = 128, G_BN = 128, G_BK = 32, G_PAD = 8, G_THREADS = 256;
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
@@ -105,7 +105,7 @@ __global__ void k_scatter_pred(const int32_t* list, const float* y, int64_t n, f
 }
 
 // ------------------------------------------------------------------ GEMM
-enum { EPI_BIAS_GELU = 0, EPI_F32 = 1, EPI_GELU_GRAD = 2 };
+enum { EPI_F32 = 1, EPI_GELU_GRAD = 2 };
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(
@@ -196,11 +196,7 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
                 const int n = n0 + wn * 32 + nt * 8 + tig * 2 + (r & 1);
                 if (m >= g.M || n >= g.N) continue;
                 const float v = acc[mt][nt][r];
-                if constexpr (EPI == EPI_BIAS_GELU) {
-                    const float z = v + g.bias[n];
-                    if (g.Z) g.Z[m * g.ldz + n] = z;
-                    g.Cb[m * g.ldc + n] = __float2bfloat16_rn(gelu_f(z));
-                } else if constexpr (EPI == EPI_GELU_GRAD) {
+                if constexpr (EPI == EPI_GELU_GRAD) {
                     g.Cb[m * g.ldc + n] = __float2bfloat16_rn(v * gelu_grad_f(g.Z[m * g.ldz + n]));
                 } else if (gridDim.z > 1) {
                     g.Cpart[((int64_t)blockIdx.z * g.M + m) * g.ldc + n] = v;
@@ -212,26 +208,6 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmArgs g) {
     }
 }
 
-// y[m] = H[m,:] . w + b, one warp per row (256 bf16 = one 16-byte load per lane)
-__global__ void k_mlp_out(const __nv_bfloat16* H, const float* w, const float* b, int64_t M, float* y) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += warps) {
-        const uint4 v = reinterpret_cast<const uint4*>(H + m * 256)[lane];
-        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-        float s = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float2 f = __bfloat1622float2(h[i]);
-            s += f.x * w[lane * 8 + 2 * i] + f.y * w[lane * 8 + 2 * i + 1];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) y[m] = s + b[0];
-    }
-}
-
-// dy = (y - t) / n; loss += 0.5 (y - t)^2 / n
 __global__ void k_loss(const float* y, const float* t, int n, float* dy, float* loss) {
     float part = 0.0f;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
@@ -363,15 +339,9 @@ cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     const dim3 grid((g.N + G_BN - 1) / G_BN, (unsigned)((g.M + G_BM - 1) / G_BM));
     if (grid.y > 65535u * 1024u) return cudaErrorInvalidValue;
-    if (epi == EPI_BIAS_GELU) k_gemm<EPI_BIAS_GELU><<<grid, G_THREADS, 0, s>>>(g);
-    else if (epi == EPI_GELU_GRAD) k_gemm<EPI_GELU_GRAD><<<grid, G_THREADS, 0, s>>>(g);
-    else k_gemm<EPI_F32><<<grid, G_THREADS, 0, s>>>(g);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s) {
-    if (M <= 0) return cudaSuccess;
-    k_mlp_out<<<blocks_for(M * 32, 256, 8192), 256, 0, s>>>(static_cast<const __nv_bfloat16*>(H), w, b, M, y);
+    if (epi == EPI_GELU_GRAD) k_gemm<EPI_GELU_GRAD><<<grid, G_THREADS, 0, s>>>(g);
+    else if (epi == EPI_F32) k_gemm<EPI_F32><<<grid, G_THREADS, 0, s>>>(g);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

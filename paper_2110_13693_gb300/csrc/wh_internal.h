@@ -177,7 +177,6 @@ struct GemmArgs {
     const __nv_bfloat16* B;
     int64_t ldb;
     int transB;
-    const float* bias;
     float* Z;
     int64_t ldz;
     __nv_bfloat16* Cb;
@@ -200,8 +199,7 @@ cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, cons
 cudaError_t launch_compact_flags(const uint8_t* flag, int64_t n, int32_t* list, int32_t* count, cudaStream_t s);
 cudaError_t launch_scatter_pred(const int32_t* list, const float* y, int64_t n, float* y_tour, uint8_t* flag,
                                 cudaStream_t s);
-cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 0 bias+GELU, 1 fp32, 2 GELU grad
-cudaError_t launch_mlp_out(const void* H, const float* w, const float* b, int64_t M, float* y, cudaStream_t s);
+cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 1 fp32, 2 GELU grad
 cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, float* loss, const float* w3,
                               const float* Z2, void* dZ2, cudaStream_t s);
 // out[i] = sum over z < splits of part[z * n + i], in order of z
@@ -216,8 +214,11 @@ cudaError_t launch_to_bf16(const float* p, int64_t n, void* out, cudaStream_t s)
 // fused tcgen05 inference (k_mlp_tc.cu): W1t [256][192] and W2t [256][256]
 // are the transposed bf16 weights the tensor maps mw1 / mw2 describe
 cudaError_t launch_transpose_bf16(const float* p, int K, int N, void* out, cudaStream_t s);
+// Z1 / H1 / Z2 / H2 (all or none): the training forward's saved pre-
+// activations (fp32) and activations (bf16), [n][256]
 cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const CUtensorMap& mw2, const float* P,
-                          int64_t n, float* y, int* status, int num_sms, cudaStream_t s);
+                          int64_t n, float* y, int* status, int num_sms, cudaStream_t s, float* Z1 = nullptr,
+                          void* H1 = nullptr, float* Z2 = nullptr, void* H2 = nullptr);
 size_t mlp_tc_smem_bytes();
 
 struct Tuning {

@@ -1,8 +1,10 @@
 // C-ABI of the surrogate MLP (declared in include/wh.h): parameters, Adam
 // state and activation scratch on the device; prediction and training steps
-// enqueued on the caller's stream.  Prediction runs the fused tcgen05 kernel
+// enqueued on the caller's stream.  Forward passes (prediction, and the
+// training forward with its saved activations) run the fused tcgen05 kernel
 // (k_mlp_tc.cu) on transposed bf16 weights that are refreshed on the stream
-// whenever the parameters have changed; training runs the mma.sync GEMMs.
+// whenever the parameters have changed; the backward GEMMs run on mma.sync
+// (k_surrogate.cu), the weight gradients split along the batch.
 #include <cudaTypedefs.h>
 
 #include <cmath>
@@ -139,25 +141,13 @@ wh::GemmArgs gemm(int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda, 
     return g;
 }
 
-// forward of rows [0, n) into H1/H2 (bf16) and y; Z1/Z2 saved when given
-int forward(wh_surrogate* s, const __nv_bfloat16* X, int64_t n, __nv_bfloat16* H1, __nv_bfloat16* H2, float* Z1,
-            float* Z2, float* y, cudaStream_t st) {
-    wh::GemmArgs g1 = gemm(n, 256, 192, X, 192, 0, s->w1b, 256, 0);
-    g1.bias = s->P + wh::MLP_B1_OFF;
-    g1.Z = Z1;
-    g1.ldz = 256;
-    g1.Cb = H1;
-    g1.ldc = 256;
-    if (wh::launch_gemm(g1, 0, st) != cudaSuccess) return WH_ECUDA;
-    wh::GemmArgs g2 = gemm(n, 256, 256, H1, 256, 0, s->w2b, 256, 0);
-    g2.bias = s->P + wh::MLP_B2_OFF;
-    g2.Z = Z2;
-    g2.ldz = 256;
-    g2.Cb = H2;
-    g2.ldc = 256;
-    if (wh::launch_gemm(g2, 0, st) != cudaSuccess) return WH_ECUDA;
-    if (wh::launch_mlp_out(H2, s->P + wh::MLP_W3_OFF, s->P + wh::MLP_B3_OFF, n, y, st) != cudaSuccess)
+// the transposed bf16 weights the tensor maps describe, when stale
+int refresh_transposed(wh_surrogate* s, cudaStream_t st) {
+    if (!s->t_stale) return WH_OK;
+    if (wh::launch_transpose_bf16(s->P, 192, 256, s->w1t, st) != cudaSuccess ||
+        wh::launch_transpose_bf16(s->P + wh::MLP_W2_OFF, 256, 256, s->w2t, st) != cudaSuccess)
         return WH_ECUDA;
+    s->t_stale = false;
     return WH_OK;
 }
 
@@ -237,12 +227,8 @@ extern "C" int wh_surrogate_predict(wh_surrogate* s, const uint16_t* X, int64_t 
     if (n == 0) return WH_OK;
     if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return WH_EINVAL;   // TMA base alignment
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (s->t_stale) {
-        if (wh::launch_transpose_bf16(s->P, 192, 256, s->w1t, st) != cudaSuccess ||
-            wh::launch_transpose_bf16(s->P + wh::MLP_W2_OFF, 256, 256, s->w2t, st) != cudaSuccess)
-            return WH_ECUDA;
-        s->t_stale = false;
-    }
+    int rc0 = refresh_transposed(s, st);
+    if (rc0 != WH_OK) return rc0;
     for (int64_t r = 0; r < n; r += kInferChunk) {
         const int64_t m = n - r < kInferChunk ? n - r : kInferChunk;
         CUtensorMap mx;
@@ -270,8 +256,19 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     int rc = reserve_train(s, n);
     if (rc != WH_OK) return rc;
     const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
-    rc = forward(s, Xb, n, s->H1, s->H2, s->Z1, s->Z2, s->y, st);
+    // forward on the tensor cores, keeping both layers' pre-activations and
+    // activations for the backward pass
+    if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return WH_EINVAL;
+    rc = refresh_transposed(s, st);
     if (rc != WH_OK) return rc;
+    {
+        CUtensorMap mx;
+        rc = encode_map(&mx, X, (uint64_t)n, wh::MLP_IN, 128);
+        if (rc != WH_OK) return rc;
+        if (wh::launch_mlp_tc(mx, s->mw1, s->mw2, s->P, n, s->y, s->status, s->num_sms, st, s->Z1, s->H1, s->Z2,
+                              s->H2) != cudaSuccess)
+            return WH_ECUDA;
+    }
     if (cudaMemsetAsync(s->loss, 0, sizeof(float), st) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_train_tail(s->y, target, n, s->dy, s->loss, s->P + wh::MLP_W3_OFF, s->Z2, s->dZ2, st) !=
         cudaSuccess)
