@@ -458,24 +458,30 @@ def run_ours(args):
                                 ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off", "order_seq")),
                               b.n_sku)
         host.append(hp)
-    plan_out = torch.empty((2, PLANS_PER_STEP), dtype=torch.int64).pin_memory()
+    # every step copies its own inputs in and its plan costs back; the copy of
+    # a step overlaps the evaluation of the previous one (HostPipeline: a copy
+    # stream and a compute stream, one device buffer set per rotated batch)
+    plan_outs = [torch.empty((2, PLANS_PER_STEP), dtype=torch.int64).pin_memory() for _ in probs]
+    pipe = wh.HostPipeline(lay, [(p, costs) for p in probs], mask)
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
-    for i in range(3):
-        wh.evaluate_host(lay, host[i % len(host)], probs[i % len(probs)], costs, plan_out, mask, stream)
-        stream.synchronize()
+    for i in range(len(probs)):
+        pipe.wait(pipe.submit(host[i], plan_outs[i])[0])
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    e_tours, h2d, d2h = 0, 0, 0
+    e0.record(pipe.copy)
+    e_tours, h2d, d2h, prev = 0, 0, 0, None
     for i in range(e2e_steps):
         b = i % len(probs)
-        hb, db = wh.evaluate_host(lay, host[b], probs[b], costs, plan_out, mask, stream)
-        stream.synchronize()           # the step's plan costs are on the host now
+        ticket, hb, db = pipe.submit(host[b], plan_outs[b])
+        if prev is not None:
+            pipe.wait(prev)            # the previous step's plan costs are on the host now
+        prev = ticket
         e_tours += tours[b]
         h2d, d2h = hb, db
-    e1.record(stream)
+    e1.record(pipe.compute)          # after the last step's copy back
+    pipe.wait(prev)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     e2e_ms, e_tours = combine(e2e_ms, e_tours, dev)

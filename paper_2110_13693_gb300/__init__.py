@@ -430,6 +430,48 @@ def evaluate_host(layout: Layout, host: DeviceProblem, dev: DeviceProblem, costs
     return h2d, d2h
 
 
+class HostPipeline:
+    """End-to-end scoring of host-resident plan batches (pinned memory) with
+    the host->device copy of one batch overlapping the evaluation of the
+    previous one: two device buffer sets (DeviceProblem + Costs, shaped like
+    the batches), a copy stream and a compute stream ordered by CUDA events.
+    Every submitted batch has all its inputs copied in and its per-plan costs
+    copied back; wait(ticket) returns once that batch's costs are on the host."""
+
+    def __init__(self, layout: "Layout", bufs, mask: int = 3):
+        import torch
+        self.layout, self.bufs, self.mask = layout, list(bufs), mask
+        self.copy, self.compute = torch.cuda.Stream(), torch.cuda.Stream()
+        self.copied = [torch.cuda.Event() for _ in self.bufs]
+        self.done = [torch.cuda.Event() for _ in self.bufs]
+        self.k = 0
+
+    def submit(self, host: DeviceProblem, host_plan_out):
+        """Enqueue one batch; returns (ticket, bytes host->device, bytes device->host)."""
+        import torch
+        slot = self.k % len(self.bufs)
+        self.k += 1
+        dev, costs = self.bufs[slot]
+        h2d = 0
+        self.copy.wait_event(self.done[slot])          # the buffer's previous batch is finished
+        with torch.cuda.stream(self.copy):
+            for name in ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off", "order_seq"):
+                src, dst = getattr(host, name), getattr(dev, name)
+                dst.copy_(src, non_blocking=True)
+                h2d += src.numel() * src.element_size()
+            self.copied[slot].record(self.copy)
+        self.compute.wait_event(self.copied[slot])
+        with torch.cuda.stream(self.compute):
+            self.layout.eval_plans(dev, costs, self.mask, self.compute)
+            host_plan_out[0].copy_(costs.plan_s[:dev.n_plans], non_blocking=True)
+            host_plan_out[1].copy_(costs.plan_rr[:dev.n_plans], non_blocking=True)
+            self.done[slot].record(self.compute)
+        return slot, h2d, 2 * dev.n_plans * 8
+
+    def wait(self, ticket) -> None:
+        self.done[ticket].synchronize()
+
+
 class Batch:
     """Owning wrapper of a ``wh_batch``: many instances (each a Layout
     geometry tuple, a DeviceProblem and its Costs) scored in one launch."""

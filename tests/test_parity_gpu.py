@@ -318,3 +318,29 @@ def test_sshape_only_large_order_book(gpu_lib):
     want = oracle.eval_plans(inst)
     assert got[4] == 0
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[2], want[2])
+
+
+def test_host_pipeline_matches_oracle(gpu_lib):
+    """HostPipeline (copies of one batch overlapping the evaluation of the
+    previous one) returns every batch's plan costs, equal to the oracle's."""
+    import torch
+    wh = gpu_lib
+    insts = [wh_gen.midsize(seed=40 + i, n_plans=48) for i in range(3)]
+    lay = wh.Layout.of(insts[0].layout)
+    host, bufs, outs = [], [], []
+    for inst in insts:
+        host.append(wh.DeviceProblem(*(torch.as_tensor(getattr(inst, f)).pin_memory() for f in
+                                       ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off",
+                                        "order_seq")), inst.n_sku))
+        prob = wh.to_device(inst)
+        bufs.append((prob, wh.alloc_costs(prob.n_tours, prob.n_plans)))
+        outs.append(torch.zeros((2, inst.n_plans), dtype=torch.int64).pin_memory())
+    pipe = wh.HostPipeline(lay, bufs, 3)
+    tickets = [pipe.submit(host[i % 3], outs[i % 3])[0] for i in range(6)]
+    for t in tickets:
+        pipe.wait(t)
+    for inst, out in zip(insts, outs):
+        want = oracle.eval_plans(inst)
+        assert np.array_equal(out[0].numpy(), want[2]) and np.array_equal(out[1].numpy(), want[3])
+    assert lay.status() == 0
+    lay.close()
