@@ -609,23 +609,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
             __syncwarp();
             continue;
         }
-        int p2 = 64;
-        while (p2 < n) p2 <<= 1;
-        for (int i = n + lane; i < p2; i += 32) kb[i] = KEY_NONE;
-        __syncwarp();
-        for (int k = 2; k <= p2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = lane; i < p2; i += 32) {
-                    const int l = i ^ j;
-                    if (l > i) {
-                        const uint32_t x = kb[i], y = kb[l];
-                        const bool up = (i & k) == 0;
-                        if ((x > y) == up) { kb[i] = y; kb[l] = x; }
-                    }
-                }
-                __syncwarp();
-            }
-        }
+        warp_sort_buffer(kb, n, lane);
         if (lane == 0) {
             DP5 v;
             dp_init(v);

@@ -513,23 +513,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long_rec(MoveArgs M) {
             __syncwarp();
             continue;
         }
-        int p2 = 64;
-        while (p2 < n) p2 <<= 1;
-        for (int x = n + lane; x < p2; x += 32) kb[x] = KEY_NONE;
-        __syncwarp();
-        for (int k = 2; k <= p2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int x = lane; x < p2; x += 32) {
-                    const int l = x ^ j;
-                    if (l > x) {
-                        const uint32_t u = kb[x], v = kb[l];
-                        const bool up = (x & k) == 0;
-                        if ((u > v) == up) { kb[x] = v; kb[l] = u; }
-                    }
-                }
-                __syncwarp();
-            }
-        }
+        warp_sort_buffer(kb, n, lane);
         // per-aisle records: run r of the sorted keys -> long_rec[r * cap + w]
         int m = 0;
         for (int x0 = 0; x0 < n; x0 += 32) {

@@ -340,6 +340,81 @@ __device__ __forceinline__ long long segmented_sum(long long v, int key, int lan
     return v;
 }
 
+// Bitonic sort of the 32 * KPL keys kb[0..32*KPL) held KPL per lane (lane
+// holds elements KPL*lane .. KPL*lane + KPL-1): partners at distance < KPL
+// are in the lane's own registers, farther ones in lane ^ (d / KPL) (one
+// shuffle).  Sorted keys are written back to kb.
+template <int KPL>
+__device__ __forceinline__ void warp_sort_keys(uint32_t* kb, int lane) {
+    uint32_t x[KPL];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) x[j] = kb[KPL * lane + j];
+#pragma unroll
+    for (int k = 2; k <= 32 * KPL; k <<= 1) {
+#pragma unroll
+        for (int d = k >> 1; d > 0; d >>= 1) {
+            if (d < KPL) {
+#pragma unroll
+                for (int j = 0; j < KPL; ++j) {
+                    const int jp = j ^ d;
+                    if (jp > j) {
+                        const int e = KPL * lane + j;
+                        const bool asc = (e & k) == 0;
+                        const uint32_t lo = min(x[j], x[jp]), hi = max(x[j], x[jp]);
+                        x[j] = asc ? lo : hi;
+                        x[jp] = asc ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < KPL; ++j) {
+                    const int e = KPL * lane + j;
+                    const uint32_t other = __shfl_xor_sync(0xffffffffu, x[j], d / KPL);
+                    const bool lower = (e & d) == 0, asc = (e & k) == 0;
+                    x[j] = (lower == asc) ? min(x[j], other) : max(x[j], other);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) kb[KPL * lane + j] = x[j];
+}
+
+// Sort kb[0..n) ascending (n <= LONG_MAXL) by one warp: padded with KEY_NONE
+// to a power of two >= 64; up to 256 keys in registers (warp_sort_keys),
+// longer runs by a bitonic network in shared memory.
+__device__ __forceinline__ void warp_sort_buffer(uint32_t* kb, int n, int lane) {
+    int p2 = 64;
+    while (p2 < n) p2 <<= 1;
+    for (int x = n + lane; x < p2; x += 32) kb[x] = KEY_NONE;
+    __syncwarp();
+    if (p2 == 64) {
+        warp_sort_keys<2>(kb, lane);
+    } else if (p2 == 128) {
+        warp_sort_keys<4>(kb, lane);
+    } else if (p2 == 256) {
+        warp_sort_keys<8>(kb, lane);
+    } else {
+        for (int k = 2; k <= p2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int x = lane; x < p2; x += 32) {
+                    const int l = x ^ j;
+                    if (l > x) {
+                        const uint32_t u = kb[x], v = kb[l];
+                        const bool up = (x & k) == 0;
+                        if ((u > v) == up) {
+                            kb[x] = v;
+                            kb[l] = u;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // inclusive prefix sum over the 32 lanes of a warp
 __device__ __forceinline__ int warp_inclusive_scan(int v) {
     const int lane = threadIdx.x & 31;
