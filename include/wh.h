@@ -165,8 +165,9 @@ int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * (same tour, same SKU), 3 invalid (id out of range, order not in the plan,
  * SKU swap under a shared slotting, or a malformed tour); deltas are 0 unless
  * the status is 0.  Each plan must hold every order at most once.
- * All arrays are device memory.  The call synchronises `stream` once (to size
- * its task list) and may allocate scratch.  Returns WH_OK, WH_EINVAL, WH_ENOMEM
+ * All arrays are device memory.  The call synchronises `stream` twice (to
+ * size its task list, then the record matrix of the tasks of more than 64
+ * lines) and may allocate scratch.  Returns WH_OK, WH_EINVAL, WH_ENOMEM
  * or WH_ECUDA. */
 int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *tour_s,
                   const int32_t *tour_rr, const int32_t *moves, int32_t n_moves, int32_t max_orders_per_tour,
