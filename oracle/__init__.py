@@ -93,6 +93,9 @@ def _load():
             lib.or_eval_moves.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
                                           ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, i64p, i32p]
+            lib.or_batch_grow.restype = ctypes.c_int
+            lib.or_batch_grow.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int32,
+                                          ctypes.c_int32, i32p, i32p, i32p]
             lib.or_ls_step.restype = ctypes.c_int
             lib.or_ls_step.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
                                        ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
@@ -188,6 +191,22 @@ def eval_moves(inst, moves, max_orders: int = 0, max_lines: int = 0, slot_map=No
     if rc != 0:
         raise ValueError(f"or_eval_moves error {rc}")
     return delta[:n], status[:n]
+
+
+def batch_grow(layout, order_off, line_sku, n_sku: int, slot_map, max_orders: int, max_lines: int):
+    """Seed-and-grow batching of the orders into tours (see or_batch_grow):
+    (tour_off [n_tours + 1], order_seq [n_orders]) of one plan."""
+    lib = _load()
+    off, lines, smap = _i32(order_off), _i32(line_sku), _i32(slot_map)
+    n_orders = off.shape[0] - 1
+    to = np.zeros(n_orders + 1, np.int32)
+    seq = np.zeros(max(n_orders, 1), np.int32)
+    nt = ctypes.c_int32(0)
+    rc = lib.or_batch_grow(ctypes.byref(_layout(layout)), n_orders, _ptr(off), _ptr(lines), n_sku, _ptr(smap),
+                           max_orders, max_lines, _ptr(to), _ptr(seq), ctypes.byref(nt))
+    if rc != 0:
+        raise ValueError(f"or_batch_grow error {rc}")
+    return to[:nt.value + 1].copy(), seq[:n_orders].copy()
 
 
 def ls_step(inst, moves, moves_per_plan: int, max_orders: int = 0, max_lines: int = 0, slot_map=None,

@@ -670,6 +670,77 @@ int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, c
     return OR_OK;
 }
 
+/* ------------------------------------------------------- batch formation */
+
+int or_batch_grow(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+                  int32_t n_sku, const int32_t *slot_map, int32_t max_orders, int32_t max_lines,
+                  int32_t *tour_off, int32_t *order_seq, int32_t *n_tours) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    if (n_orders < 0 || max_orders < 0 || max_lines < 0) return OR_EINVAL;
+    const int32_t n_loc = g->n_aisles * 2 * g->slots_per_side;
+    const int32_t n_lines = n_orders > 0 ? order_off[n_orders] : 0;
+    for (int32_t l = 0; l < n_lines; ++l) {
+        const int32_t s = line_sku[l];
+        if (s < 0 || s >= n_sku || slot_map[s] < 0 || slot_map[s] >= n_loc) return OR_ERANGE;
+    }
+    int32_t *locs = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_lines + 1));
+    int64_t *alone = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_orders + 1));
+    char *used = (char *)calloc((size_t)(n_orders + 1), 1);
+    if (!locs || !alone || !used) { free(locs); free(alone); free(used); return OR_ENOMEM; }
+
+    /* the length of each order's tour alone */
+    for (int32_t o = 0; o < n_orders; ++o) {
+        int32_t n = 0;
+        for (int32_t l = order_off[o]; l < order_off[o + 1]; ++l) locs[n++] = slot_map[line_sku[l]];
+        alone[o] = or_rr_tour(g, locs, n);
+    }
+
+    int32_t done = 0, tours = 0;
+    tour_off[0] = 0;
+    while (done < n_orders) {
+        /* seed: the longest order alone */
+        int32_t seed = -1;
+        for (int32_t o = 0; o < n_orders; ++o)
+            if (!used[o] && (seed < 0 || alone[o] > alone[seed])) seed = o;
+        used[seed] = 1;
+        order_seq[done++] = seed;
+        int32_t n_tour = 0, lines = order_off[seed + 1] - order_off[seed], count = 1;
+        for (int32_t l = order_off[seed]; l < order_off[seed + 1]; ++l) locs[n_tour++] = slot_map[line_sku[l]];
+        int64_t cost = alone[seed];
+        /* grow: the order that lengthens the tour least */
+        while (max_orders == 0 || count < max_orders) {
+            int32_t best = -1;
+            int64_t best_cost = 0;
+            for (int32_t o = 0; o < n_orders; ++o) {
+                if (used[o]) continue;
+                const int32_t ol = order_off[o + 1] - order_off[o];
+                if (max_lines > 0 && lines + ol > max_lines) continue;
+                int32_t n = n_tour;
+                for (int32_t l = order_off[o]; l < order_off[o + 1]; ++l) locs[n++] = slot_map[line_sku[l]];
+                const int64_t c = or_rr_tour(g, locs, n);
+                if (best < 0 || c - cost < best_cost - cost) {
+                    best = o;
+                    best_cost = c;
+                }
+            }
+            if (best < 0) break;
+            used[best] = 1;
+            order_seq[done++] = best;
+            for (int32_t l = order_off[best]; l < order_off[best + 1]; ++l) locs[n_tour++] = slot_map[line_sku[l]];
+            lines += order_off[best + 1] - order_off[best];
+            ++count;
+            cost = best_cost;
+        }
+        tour_off[++tours] = done;
+    }
+    *n_tours = tours;
+    free(locs);
+    free(alone);
+    free(used);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------- surrogate */
 
 int or_features(const or_layout *g, const int32_t *locs, int32_t n, float *out) {

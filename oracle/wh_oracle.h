@@ -105,6 +105,23 @@ int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, c
                const int32_t *plan_tour_off, int32_t *tour_off, int32_t *order_seq, const int32_t *moves,
                int32_t moves_per_plan, int32_t max_orders, int32_t max_lines, int32_t *applied);
 
+/* ------------------------------------------------------- batch formation
+ * Seed-and-grow batching of orders into picker tours (the paper's
+ * clustering of orders and suggestion of which orders are picked together,
+ * Sec. 5 and Sec. 6), scored by the exact optimal route length:
+ *   seed  - the unassigned order whose tour alone is longest (ties: lowest id);
+ *   grow  - while the tour holds fewer than max_orders orders (0: no cap), add
+ *           the unassigned order whose lines fit (lines of the tour + its
+ *           lines <= max_lines; 0: no cap) and that lengthens the tour least
+ *           (ties: lowest id); stop when none fits;
+ * until every order is in a tour.  Tours are emitted in order of formation,
+ * the orders of a tour in order of insertion: tour_off [n_orders + 1] and
+ * order_seq [n_orders] (a plan's CSR); *n_tours receives the tour count.
+ * SKUs to locations by slot_map.  Returns OR_OK or an error. */
+int or_batch_grow(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+                  int32_t n_sku, const int32_t *slot_map, int32_t max_orders, int32_t max_lines,
+                  int32_t *tour_off, int32_t *order_seq, int32_t *n_tours);
+
 /* ------------------------------------------------------------- surrogate
  * Learned prescreen (the paper's machine-learning-in-the-loop idea, Sec. 1 and
  * Fig. 1): a small MLP predicts a tour's normalised optimal length from a
