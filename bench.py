@@ -352,6 +352,48 @@ def run_moves(wh, dev, steps):
             "timing": "wall clock around the calls (each call synchronises once)"}
 
 
+def run_batch_grow(wh, dev):
+    """Batch formation (seed and grow by exact optimal length) of the mid-size
+    order book under 304 ABC slottings (each with its own 10 % of swaps), one
+    CTA per slotting; quality: the formed plan's optimal cost against random
+    plans of the same capacity under the same slotting."""
+    import numpy as np
+    import torch
+    import wh_gen
+    inst = wh_gen.midsize(seed=2, n_plans=64)
+    lay = wh.Layout.of(inst.layout)
+    prob = wh.to_device(inst, dev)
+    n_maps = 304
+    maps = torch.as_tensor(np.stack([wh_gen.gen_slot_abc(100 + i, inst.layout, inst.n_sku, 0.1)
+                                     for i in range(n_maps)]).astype(np.int32)).to(dev)
+    lay.batch_grow(prob, maps[:1], 20, 60)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tour_off, order_seq, n_tours = lay.batch_grow(prob, maps, 20, 60)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    assert lay.status() == 0 and int(n_tours.min().item()) > 0
+    # the first slotting's formed plan against the generator's random plans
+    nt = int(n_tours[0].item())
+    m0 = maps[0].contiguous()
+    formed = wh.DeviceProblem(prob.order_off, prob.line_sku, m0,
+                              torch.tensor([0, nt], dtype=torch.int32, device=dev),
+                              tour_off[0, :nt + 1].contiguous(), order_seq[0].contiguous(), inst.n_sku)
+    rand = wh.DeviceProblem(prob.order_off, prob.line_sku, m0, prob.plan_tour_off, prob.tour_off, prob.order_seq,
+                            inst.n_sku)
+    f_cost = int(wh.evaluate(lay, formed).plan_rr[0].item())
+    r_cost = wh.evaluate(lay, rand).plan_rr[:inst.n_plans].double().mean().item()
+    lay.close()
+    return {"workload": f"mid-size order book (4,000 orders) under {n_maps} ABC slottings, tours of <= 20 orders / "
+                        "60 lines, one launch",
+            "ms": ms, "orders_per_s": n_maps * inst.n_orders / (ms / 1e3),
+            "tours_per_s": float(n_tours.double().sum().item()) / (ms / 1e3),
+            "formed_plan_optimal_cost": f_cost, "random_plans_mean_optimal_cost": r_cost,
+            "formed_over_random": f_cost / r_cost}
+
+
 def run_surrogate_ab(wh, dev, steps, train_steps):
     """Config 5: the MLP prescreen on the paper-scale population.  Trained on
     ~10M exactly scored tours of the paper-scale generator (four random
@@ -555,6 +597,7 @@ def run_ours(args):
         extra["batched"] = run_batched(wh, dev, args.extra_steps)
         extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4))
         extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps)
+        extra["batch_formation"] = run_batch_grow(wh, dev)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -199,6 +199,29 @@ int wh_ls_apply(wh_layout *layout, const wh_orders *orders, const wh_plans *plan
                 int32_t moves_per_plan, const int64_t *delta, const int32_t *status, int32_t *applied,
                 const wh_costs *costs, uint8_t *tour_changed, void *stream);
 
+/* Batch formation (Sec. 5 and Sec. 6: clustering the orders and suggesting
+ * which orders are picked together): for each of n_maps slottings
+ * (slot_map + p * slot_map_stride; stride 0: one shared slotting), partition
+ * the orders into tours by seed and grow, scored by the exact optimal route
+ * length:
+ *   seed - the unassigned order whose tour alone is longest (ties: lowest id);
+ *   grow - while the tour holds fewer than max_orders orders (0: no cap), add
+ *          the unassigned order whose lines fit (tour lines + its lines <=
+ *          max_lines; 0: no cap) and that lengthens the tour least (ties:
+ *          lowest id); stop when none fits;
+ * until every order is in a tour.  Outputs (device, caller-owned), per
+ * slotting p: tour_off[p * (n_orders + 1) ...] (tour offsets into order_seq),
+ * order_seq[p * n_orders ...] (tours in order of formation, orders in order
+ * of insertion), n_tours[p] (-1 when the slotting maps a line outside the
+ * layout: status bit WH_STATUS_BAD_LOC).  Needs A <= 255 and L <= 256
+ * (WH_ERANGE otherwise) and the
+ * order book in shared memory (about 9 B per order + 2 B per line + 38 B per
+ * aisle <= 200 KB, WH_ERANGE otherwise).  Asynchronous on `stream`; allocates
+ * nothing.  Returns WH_OK, WH_EINVAL, WH_ERANGE or WH_ECUDA. */
+int wh_batch_grow(wh_layout *layout, const wh_orders *orders, const int32_t *slot_map, int64_t slot_map_stride,
+                  int32_t n_maps, int32_t max_orders, int32_t max_lines, int32_t *tour_off, int32_t *order_seq,
+                  int32_t *n_tours, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned prescreen (machine learning in the decision loop, Sec. 1 and
  * Fig. 1): an MLP 192 -> 256 -> GELU -> 256 -> GELU -> 1 predicts a tour's

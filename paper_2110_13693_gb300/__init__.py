@@ -104,6 +104,9 @@ SIGNATURES = {
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_destroy": (None, [ctypes.c_void_p]),
 }
 WH_MLP_NPARAM, WH_FEATURES = 115457, 192
@@ -385,6 +388,23 @@ class Layout:
                             None if changed is None else _ptr(changed), stream)
         return kept[:prob.n_plans * keep]
 
+    def batch_grow(self, prob: DeviceProblem, slot_maps, max_orders: int, max_lines: int = 0, stream=None):
+        """Seed-and-grow batching of prob's orders under each slotting of
+        slot_maps (int32 device, [n_maps, n_sku] or [n_sku]): returns
+        (tour_off [n_maps, n_orders + 1], order_seq [n_maps, n_orders],
+        n_tours [n_maps]) device tensors (valid tour_off entries: n_tours + 1)."""
+        import torch
+        maps = slot_maps.reshape(-1, prob.n_sku).contiguous()
+        n_maps = int(maps.shape[0])
+        n_orders = int(prob.order_off.numel()) - 1
+        dev = maps.device
+        tour_off = torch.zeros((n_maps, n_orders + 1), dtype=torch.int32, device=dev)
+        order_seq = torch.zeros((n_maps, max(n_orders, 1)), dtype=torch.int32, device=dev)
+        n_tours = torch.zeros(n_maps, dtype=torch.int32, device=dev)
+        wh_batch_grow(self.handle, prob.orders(), _ptr(maps), prob.n_sku, n_maps, max_orders, max_lines,
+                      _ptr(tour_off), _ptr(order_seq), _ptr(n_tours), stream)
+        return tour_off, order_seq[:, :n_orders], n_tours
+
     def set_timing(self, enable: bool) -> None:
         wh_set_timing(self.handle, enable)
 
@@ -539,6 +559,13 @@ def wh_surrogate_get_params(s):
     fp = ctypes.POINTER(ctypes.c_float)
     _check(load().wh_surrogate_get_params(s, p.ctypes.data_as(fp), g.ctypes.data_as(fp)), "wh_surrogate_get_params")
     return p, g
+
+
+def wh_batch_grow(layout, orders: wh_orders, slot_map, slot_map_stride: int, n_maps: int, max_orders: int,
+                  max_lines: int, tour_off, order_seq, n_tours, stream=None) -> None:
+    _check(load().wh_batch_grow(layout, ctypes.byref(orders), ctypes.c_void_p(slot_map), slot_map_stride, n_maps,
+                                max_orders, max_lines, ctypes.c_void_p(tour_off), ctypes.c_void_p(order_seq),
+                                ctypes.c_void_p(n_tours), _stream_ptr(stream)), "wh_batch_grow")
 
 
 def wh_surrogate_get_status(s) -> int:

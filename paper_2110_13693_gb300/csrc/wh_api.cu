@@ -606,6 +606,38 @@ extern "C" int wh_surrogate_features(wh_layout* h, const wh_orders* orders, cons
     return wh::launch_features(a, c, X, nullptr, p.n_tours, h->num_sms, s) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
+extern "C" int wh_batch_grow(wh_layout* h, const wh_orders* orders, const int32_t* slot_map,
+                             int64_t slot_map_stride, int32_t n_maps, int32_t max_orders, int32_t max_lines,
+                             int32_t* tour_off, int32_t* order_seq, int32_t* n_tours, void* stream) {
+    if (!h || !orders || n_maps < 0 || max_orders < 0 || max_lines < 0 || slot_map_stride < 0) return WH_EINVAL;
+    if (n_maps == 0) return WH_OK;
+    const wh_orders o = *orders;
+    if (!slot_map || !tour_off || !order_seq || !n_tours || !o.order_off || (o.n_lines > 0 && !o.line_sku) ||
+        o.n_orders < 0 || o.n_lines < 0 || o.n_sku < 1)
+        return WH_EINVAL;
+    if (slot_map_stride != 0 && slot_map_stride < o.n_sku) return WH_EINVAL;
+    if (h->g.A > 255 || h->g.L > 256) return WH_ERANGE;   // 16-bit keys, 256-bit depth masks
+    if (wh::batch_grow_smem_bytes(o.n_orders, o.n_lines, h->g.A) > 200 * 1024) return WH_ERANGE;
+    int rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    wh::BatchGrowArgs B;
+    std::memset(&B, 0, sizeof(B));
+    wh_plans p;
+    std::memset(&p, 0, sizeof(p));
+    p.slot_map = slot_map;
+    p.slot_map_stride = slot_map_stride;
+    wh_costs none;
+    std::memset(&none, 0, sizeof(none));
+    fill_args(B.a, h->g, o, p, none, WH_ROUTE_OPTIMAL);
+    B.a.status = h->meta;
+    B.max_orders = max_orders;
+    B.max_lines = max_lines;
+    B.tour_off = tour_off;
+    B.order_seq = order_seq;
+    B.n_tours = n_tours;
+    return wh::launch_batch_grow(B, n_maps, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {
     if (!h || !status) return WH_EINVAL;
     if (h->device < 0) {

@@ -143,6 +143,19 @@ struct ScreenArgs {
     int4* kept;                 // [n_plans][keep]
 };
 
+// seed-and-grow batch formation (k_batch.cu): one CTA per slotting
+// a.slot_map + p * a.slot_stride; per slotting p, tour_off[p][n_orders + 1],
+// order_seq[p][n_orders], n_tours[p]
+struct BatchGrowArgs {
+    EvalArgs a;
+    int32_t max_orders, max_lines;
+    int32_t* tour_off;
+    int32_t* order_seq;
+    int32_t* n_tours;
+};
+size_t batch_grow_smem_bytes(int n_orders, int n_lines, int A);
+cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s);
+
 struct FeatConst;
 cudaError_t launch_task_features(const MoveArgs& M, const FeatConst& c, void* X, int num_sms, cudaStream_t s);
 cudaError_t launch_screen_select(const ScreenArgs& S, cudaStream_t s);
