@@ -394,6 +394,25 @@ def run_batch_grow(wh, dev):
             "formed_over_random": f_cost / r_cost}
 
 
+def run_layout_sweep(wh, dev):
+    """Layout sweep (Eq. (1) reading): the mid-size orders and 256 random
+    plans on 4 aisle counts x 3 pitches of about 8,000 locations, each layout
+    ABC-slotted and scored on the device; utilisation, feasibility (aisle width
+    >= 1 picker width) and the Pareto front of utilisation against length."""
+    import wh_gen
+    from paper_2110_13693_gb300 import sweep
+    inst = wh_gen.midsize(seed=2, n_plans=256)
+    t0 = time.perf_counter()
+    rows = sweep.layout_sweep(wh, inst, aisle_counts=[20, 40, 80, 100], pitches=[3, 4, 5], n_loc=8000,
+                              rack_depth=1.0, k=1.0, delta=1.0, device=dev)
+    el = time.perf_counter() - t0
+    front = sweep.pareto(rows)
+    return {"workload": "mid-size orders, 256 random plans, 12 layouts of ~8,000 locations "
+                        "(aisles 20/40/80/100, pitch 3/4/5)",
+            "layouts": len(rows), "seconds": el,
+            "pareto": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in front]}
+
+
 def run_surrogate_ab(wh, dev, steps, train_steps):
     """Config 5: the MLP prescreen on the paper-scale population.  Trained on
     ~10M exactly scored tours of the paper-scale generator (four random
@@ -598,6 +617,7 @@ def run_ours(args):
         extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4))
         extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps)
         extra["batch_formation"] = run_batch_grow(wh, dev)
+        extra["layout_sweep"] = run_layout_sweep(wh, dev)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
