@@ -413,6 +413,34 @@ def run_layout_sweep(wh, dev):
             "pareto": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in front]}
 
 
+def run_routes(wh, dev):
+    """Explicit optimal pick sequences for every tour of 1,024 paper-scale
+    plans (one thread per tour: tracking DP, backtrack, Euler circuit), one
+    launch after a warm-up; the route lengths are checked against the
+    evaluator's optimal tour lengths."""
+    import torch
+    import wh_gen
+    inst = wh_gen.paperscale(seed=4, n_plans=1024)
+    lay = wh.Layout.of(inst.layout)
+    prob = wh.to_device(inst, dev)
+    tours = torch.arange(inst.n_tours, dtype=torch.int32, device=dev)
+    lay.routes(prob, tours[:1024])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pts, npt, length = lay.routes(prob, tours)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    assert lay.status() == 0
+    rr = wh.evaluate(lay, prob).tour_rr[:inst.n_tours]
+    assert torch.equal(length, rr)
+    lay.close()
+    return {"workload": f"all {inst.n_tours:,} tours of 1,024 paper-scale plans, one launch",
+            "ms": ms, "tours_per_s": inst.n_tours / (ms / 1e3),
+            "points_per_s": float(npt.double().sum().item()) / (ms / 1e3), "lengths_equal_optimal": True}
+
+
 def run_surrogate_ab(wh, dev, steps, train_steps):
     """Config 5: the MLP prescreen on the paper-scale population.  Trained on
     ~10M exactly scored tours of the paper-scale generator (four random
@@ -618,6 +646,7 @@ def run_ours(args):
         extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps)
         extra["batch_formation"] = run_batch_grow(wh, dev)
         extra["layout_sweep"] = run_layout_sweep(wh, dev)
+        extra["routes"] = run_routes(wh, dev)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

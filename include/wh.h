@@ -222,6 +222,29 @@ int wh_batch_grow(wh_layout *layout, const wh_orders *orders, const int32_t *slo
                   int32_t n_maps, int32_t max_orders, int32_t max_lines, int32_t *tour_off, int32_t *order_seq,
                   int32_t *n_tours, void *stream);
 
+/* Explicit optimal routes (Sec. 5, Eq. (2): the picking route of a tour is
+ * the best order of its picking positions, shortest paths between them; Sec.
+ * 6 hands the picker that sequence).  For each of the n listed tours
+ * (tours[i]: a global tour index into plans->tour_off; the tour's plan, for
+ * per-plan slottings, is found from plan_tour_off), write its distinct pick
+ * points in visiting order along an optimal closed walk from the depot,
+ * obtained from the Ratliff-Rosenthal DP's decisions (Ratliff & Rosenthal,
+ * Oper. Res. 31(3), 1983) and an Euler circuit of the route subgraph they
+ * fix.  A pick point is aisle << 16 | slot index: the two sides of an aisle
+ * at one depth are one point.  Outputs (device, caller-owned):
+ * points[i * max_points ...] (int32, n_points[i] entries used),
+ * n_points[i] (-1 on error), length[i] (the route's length, which equals the
+ * optimal tour length; -1 on error).  Walking the points in order with
+ * shortest paths between consecutive ones, from and back to the depot,
+ * covers exactly length[i].  A tour with more than min(max_points, 256)
+ * distinct points sets WH_STATUS_TOUR_TOO_LONG; a bad tour index or offsets
+ * WH_STATUS_BAD_OFFSET; bad ids WH_STATUS_BAD_ORDER / WH_STATUS_BAD_LOC.  One
+ * thread per tour, about 10 KB of local memory each; meant for the tours of
+ * a chosen plan, not for scoring.  Asynchronous on `stream`; allocates
+ * nothing.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_routes(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *tours, int32_t n,
+              int32_t max_points, int32_t *points, int32_t *n_points, int32_t *length, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned prescreen (machine learning in the decision loop, Sec. 1 and
  * Fig. 1): an MLP 192 -> 256 -> GELU -> 256 -> GELU -> 1 predicts a tour's

@@ -107,6 +107,9 @@ SIGNATURES = {
     "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_routes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
+                                 ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_destroy": (None, [ctypes.c_void_p]),
 }
 WH_MLP_NPARAM, WH_FEATURES = 115457, 192
@@ -405,6 +408,21 @@ class Layout:
                       _ptr(tour_off), _ptr(order_seq), _ptr(n_tours), stream)
         return tour_off, order_seq[:, :n_orders], n_tours
 
+    def routes(self, prob: DeviceProblem, tours, max_points: int = 256, stream=None):
+        """Optimal pick sequences of the listed tours (int32 device tensor of
+        global tour indices): (points [n, max_points] int32, aisle << 16 |
+        slot in visiting order, n_points [n], length [n]) device tensors."""
+        import torch
+        tl = tours.reshape(-1).to(torch.int32).contiguous()
+        n = int(tl.numel())
+        dev = tl.device
+        points = torch.full((max(n, 1), max(max_points, 1)), -1, dtype=torch.int32, device=dev)
+        n_points = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        length = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        wh_routes(self.handle, prob.orders(), prob.plans(), _ptr(tl), n, max_points, _ptr(points), _ptr(n_points),
+                  _ptr(length), stream)
+        return points[:n, :max_points], n_points[:n], length[:n]
+
     def set_timing(self, enable: bool) -> None:
         wh_set_timing(self.handle, enable)
 
@@ -566,6 +584,13 @@ def wh_batch_grow(layout, orders: wh_orders, slot_map, slot_map_stride: int, n_m
     _check(load().wh_batch_grow(layout, ctypes.byref(orders), ctypes.c_void_p(slot_map), slot_map_stride, n_maps,
                                 max_orders, max_lines, ctypes.c_void_p(tour_off), ctypes.c_void_p(order_seq),
                                 ctypes.c_void_p(n_tours), _stream_ptr(stream)), "wh_batch_grow")
+
+
+def wh_routes(layout, orders: wh_orders, plans: wh_plans, tours, n: int, max_points: int, points, n_points, length,
+              stream=None) -> None:
+    _check(load().wh_routes(layout, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(tours), n, max_points,
+                            ctypes.c_void_p(points), ctypes.c_void_p(n_points), ctypes.c_void_p(length),
+                            _stream_ptr(stream)), "wh_routes")
 
 
 def wh_surrogate_get_status(s) -> int:

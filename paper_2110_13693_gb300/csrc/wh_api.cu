@@ -638,6 +638,30 @@ extern "C" int wh_batch_grow(wh_layout* h, const wh_orders* orders, const int32_
     return wh::launch_batch_grow(B, n_maps, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
+extern "C" int wh_routes(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* tours,
+                         int32_t n, int32_t max_points, int32_t* points, int32_t* n_points, int32_t* length,
+                         void* stream) {
+    if (!h || !orders || !plans || n < 0 || max_points < 0) return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    int rc = check_problem(o, p);
+    if (rc != WH_OK) return rc;
+    if (n == 0) return WH_OK;
+    if (!tours || !n_points || !length || (max_points > 0 && !points)) return WH_EINVAL;
+    if (p.slot_map_stride != 0 && (p.n_plans < 1 || !p.plan_tour_off)) return WH_EINVAL;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    wh::EvalArgs a;
+    wh_costs none;
+    std::memset(&none, 0, sizeof(none));
+    fill_args(a, h->g, o, p, none, WH_ROUTE_OPTIMAL);
+    a.status = h->meta;
+    return wh::launch_routes(a, tours, n, max_points, points, n_points, length, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? WH_OK
+               : WH_ECUDA;
+}
+
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {
     if (!h || !status) return WH_EINVAL;
     if (h->device < 0) {

@@ -156,6 +156,11 @@ struct BatchGrowArgs {
 size_t batch_grow_smem_bytes(int n_orders, int n_lines, int A);
 cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s);
 
+// explicit optimal routes of listed tours (k_route.cu)
+constexpr int ROUTE_MAX_POINTS = 256;
+cudaError_t launch_routes(const EvalArgs& a, const int32_t* tours, int32_t n, int32_t max_points, int32_t* points,
+                          int32_t* n_points, int32_t* length, cudaStream_t s);
+
 struct FeatConst;
 cudaError_t launch_task_features(const MoveArgs& M, const FeatConst& c, void* X, int num_sms, cudaStream_t s);
 cudaError_t launch_screen_select(const ScreenArgs& S, cudaStream_t s);
