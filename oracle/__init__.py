@@ -33,6 +33,16 @@ Functions and the independent checks that pin them (all in ``tests/``):
                         with the same bf16 rounding points, backward by
                         finite differences and by torch autograd, Adam by
                         torch.optim.Adam.
+* ``kmeans_features`` / ``kmeans_slotting`` -- K-means slotting; features
+                        pinned by the dense co-occurrence matrix times the
+                        sign matrix (numpy) and exact integer square roots;
+                        the clustering by scikit-learn's Lloyd K-means on
+                        separated blobs (same assignment), the fixed point
+                        (every SKU at its nearest centroid, every centroid
+                        the rounded mean of its members) and hand-sized
+                        cases; the placement by its definition (a bijection
+                        onto the first n_sku aisle-major locations, clusters
+                        in weight order, SKUs in frequency order).
 * ``eval_moves``     -- move deltas by applying each move to a copy and
                         re-scoring the plan; pinned by building the moved
                         plans explicitly in Python and differencing two
@@ -96,6 +106,17 @@ def _load():
             lib.or_batch_grow.restype = ctypes.c_int
             lib.or_batch_grow.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int32,
                                           ctypes.c_int32, i32p, i32p, i32p]
+            lib.or_kmeans_features.restype = ctypes.c_int
+            lib.or_kmeans_features.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_int32, i32p, i32p]
+            lib.or_kmeans_slotting.restype = ctypes.c_int
+            lib.or_kmeans_slotting.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, i32p, i32p, i32p, i32p, i32p]
+            lib.or_kmeans_lloyd.restype = ctypes.c_int
+            lib.or_kmeans_lloyd.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, i32p, i32p]
+            lib.or_kmeans_pp_init.restype = ctypes.c_int
+            lib.or_kmeans_pp_init.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, i32p]
             lib.or_ls_step.restype = ctypes.c_int
             lib.or_ls_step.argtypes = [lp, ctypes.c_int32, i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int64,
                                        ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
@@ -207,6 +228,71 @@ def batch_grow(layout, order_off, line_sku, n_sku: int, slot_map, max_orders: in
     if rc != 0:
         raise ValueError(f"or_batch_grow error {rc}")
     return to[:nt.value + 1].copy(), seq[:n_orders].copy()
+
+
+KM_DIM, KM_SKETCH, KM_SCALE = 32, 31, 1024
+
+
+def kmeans_features(order_off, line_sku, n_sku: int, signs, freq_weight: int):
+    """(x [n_sku, 32] int32, freq [n_sku] int32): steps 1-2 of or_kmeans_slotting."""
+    lib = _load()
+    off, lines = _i32(order_off), _i32(line_sku)
+    sg = np.ascontiguousarray(signs, dtype=np.int8).reshape(n_sku, KM_DIM)
+    x = np.zeros((n_sku, KM_DIM), np.int32)
+    freq = np.zeros(n_sku, np.int32)
+    rc = lib.or_kmeans_features(off.shape[0] - 1, _ptr(off), _ptr(lines), n_sku, sg.ctypes.data, freq_weight,
+                                _ptr(x), _ptr(freq))
+    if rc != 0:
+        raise ValueError(f"or_kmeans_features error {rc}")
+    return x, freq
+
+
+def kmeans_lloyd(x, centroids, iters: int):
+    """Lloyd rounds from the given centroids: (centroids [k, 32], assign [n])."""
+    lib = _load()
+    xx = np.ascontiguousarray(x, dtype=np.int32).reshape(-1, KM_DIM)
+    cent = np.array(centroids, dtype=np.int32).reshape(-1, KM_DIM).copy()
+    assign = np.zeros(xx.shape[0], np.int32)
+    rc = lib.or_kmeans_lloyd(_ptr(xx), xx.shape[0], cent.shape[0], iters, _ptr(cent), _ptr(assign))
+    if rc != 0:
+        raise ValueError(f"or_kmeans_lloyd error {rc}")
+    return cent, assign
+
+
+def kmeans_pp_init(x, k: int, u):
+    """K-means++ seeds (SKU ids) of the feature rows x from draws u (uint64 [k])."""
+    lib = _load()
+    xx = np.ascontiguousarray(x, dtype=np.int32).reshape(-1, KM_DIM)
+    uu = np.ascontiguousarray(u, dtype=np.uint64)
+    init = np.zeros(k, np.int32)
+    rc = lib.or_kmeans_pp_init(_ptr(xx), xx.shape[0], k, uu.ctypes.data, _ptr(init))
+    if rc != 0:
+        raise ValueError(f"or_kmeans_pp_init error {rc}")
+    return init
+
+
+def kmeans_slotting(layout, order_off, line_sku, n_sku: int, signs, freq_weight: int, k: int, iters: int,
+                    init=None, u=None):
+    """K-means slotting (see or_kmeans_slotting), seeded by the SKU ids `init`
+    or, when it is None, by K-means++ from the uint64 draws `u`: (x [n_sku,
+    32], seeds [k], centroids [k, 32], assign [n_sku], slot_map [n_sku])."""
+    lib = _load()
+    off, lines = _i32(order_off), _i32(line_sku)
+    ini = None if init is None else _i32(init)
+    uu = None if u is None else np.ascontiguousarray(u, dtype=np.uint64)
+    sg = np.ascontiguousarray(signs, dtype=np.int8).reshape(n_sku, KM_DIM)
+    x = np.zeros((n_sku, KM_DIM), np.int32)
+    seeds = np.zeros(k, np.int32)
+    cent = np.zeros((k, KM_DIM), np.int32)
+    assign = np.zeros(n_sku, np.int32)
+    smap = np.zeros(n_sku, np.int32)
+    rc = lib.or_kmeans_slotting(ctypes.byref(_layout(layout)), off.shape[0] - 1, _ptr(off), _ptr(lines), n_sku,
+                                sg.ctypes.data, freq_weight, k, None if ini is None else ini.ctypes.data,
+                                None if uu is None else uu.ctypes.data, iters, _ptr(x), _ptr(seeds), _ptr(cent),
+                                _ptr(assign), _ptr(smap))
+    if rc != 0:
+        raise ValueError(f"or_kmeans_slotting error {rc}")
+    return x, seeds, cent, assign, smap
 
 
 def ls_step(inst, moves, moves_per_plan: int, max_orders: int = 0, max_lines: int = 0, slot_map=None,

@@ -873,3 +873,229 @@ void or_adam(double *p, double *m, double *v, const double *g, int64_t n, double
         p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
     }
 }
+
+/* ------------------------------------------------------------ K-means slotting
+ * Subproblem 3 (Sec. 5): product placement by picking frequency, with an
+ * unsupervised K-means classification (MacQueen 1967) deciding which products
+ * are stored together; the reading's steps, in order, are in the header. */
+
+static int64_t floor_div64(int64_t a, int64_t b) { /* b > 0 */
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) --q;
+    return q;
+}
+
+/* floor(sqrt(v)) exactly: a floating-point estimate corrected by integer
+ * comparisons */
+static int64_t isqrt64(int64_t v) {
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r > 0 && r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+static int32_t bitlen32(int32_t v) {
+    int32_t b = 0;
+    while (v > 0) { ++b; v >>= 1; }
+    return b;
+}
+
+static int64_t sqdist(const int32_t *x, const int32_t *c) {
+    int64_t d = 0;
+    for (int j = 0; j < OR_KM_DIM; ++j) {
+        const int64_t e = (int64_t)x[j] - (int64_t)c[j];
+        d += e * e;
+    }
+    return d;
+}
+
+static int32_t nearest(const int32_t *x, const int32_t *cent, int32_t k) {
+    int32_t best = 0;
+    int64_t bd = sqdist(x, cent);
+    for (int32_t c = 1; c < k; ++c) {
+        const int64_t d = sqdist(x, cent + (int64_t)c * OR_KM_DIM);
+        if (d < bd) { bd = d; best = c; }   /* ties: the lowest cluster */
+    }
+    return best;
+}
+
+typedef struct {
+    int64_t cluster_rank, freq;
+    int32_t sku;
+} km_key_t;
+
+static int cmp_km_key(const void *p, const void *q) {
+    const km_key_t *a = (const km_key_t *)p, *b = (const km_key_t *)q;
+    if (a->cluster_rank != b->cluster_rank) return a->cluster_rank < b->cluster_rank ? -1 : 1;
+    if (a->freq != b->freq) return a->freq > b->freq ? -1 : 1;   /* more picks first */
+    return a->sku < b->sku ? -1 : (a->sku > b->sku);
+}
+
+typedef struct {
+    int64_t weight;
+    int32_t cluster;
+} km_cluster_t;
+
+static int cmp_km_cluster(const void *p, const void *q) {
+    const km_cluster_t *a = (const km_cluster_t *)p, *b = (const km_cluster_t *)q;
+    if (a->weight != b->weight) return a->weight > b->weight ? -1 : 1;   /* heavier first */
+    return a->cluster < b->cluster ? -1 : (a->cluster > b->cluster);
+}
+
+int or_kmeans_features(int32_t n_orders, const int32_t *order_off, const int32_t *line_sku, int32_t n_sku,
+                       const int8_t *signs, int32_t freq_weight, int32_t *x, int32_t *freq) {
+    if (n_orders < 0 || n_sku < 1 || !order_off || !signs || !x || !freq) return OR_EINVAL;
+    int64_t *co = (int64_t *)calloc((size_t)n_sku * OR_KM_DIM, sizeof(int64_t));
+    if (!co) return OR_ENOMEM;
+    memset(freq, 0, sizeof(int32_t) * (size_t)n_sku);
+    int rc = OR_OK;
+    for (int32_t o = 0; o < n_orders && rc == OR_OK; ++o) {
+        const int32_t lb = order_off[o], le = order_off[o + 1];
+        if (lb < 0 || le < lb) { rc = OR_EINVAL; break; }
+        for (int32_t l = lb; l < le; ++l) {
+            const int32_t s = line_sku[l];
+            if (s < 0 || s >= n_sku) { rc = OR_ERANGE; break; }
+            ++freq[s];
+            /* co-occurrence row of s, projected: every other line of the order */
+            for (int32_t m = lb; m < le; ++m) {
+                if (m == l) continue;
+                const int32_t t = line_sku[m];
+                if (t < 0 || t >= n_sku) { rc = OR_ERANGE; break; }
+                for (int j = 0; j < OR_KM_SKETCH; ++j) co[(int64_t)s * OR_KM_DIM + j] += signs[(int64_t)t * OR_KM_DIM + j];
+            }
+        }
+    }
+    for (int32_t s = 0; s < n_sku && rc == OR_OK; ++s) {
+        const int64_t *c = co + (int64_t)s * OR_KM_DIM;
+        int64_t nn = 0;
+        for (int j = 0; j < OR_KM_SKETCH; ++j) nn += c[j] * c[j];
+        const int64_t n = isqrt64(nn);
+        int32_t *xs = x + (int64_t)s * OR_KM_DIM;
+        for (int j = 0; j < OR_KM_SKETCH; ++j) xs[j] = n > 0 ? (int32_t)(c[j] * OR_KM_SCALE / n) : 0;
+        xs[OR_KM_SKETCH] = freq_weight * bitlen32(freq[s]);
+    }
+    free(co);
+    return rc;
+}
+
+int or_kmeans_lloyd(const int32_t *x, int32_t n, int32_t k, int32_t iters, int32_t *centroids, int32_t *assign) {
+    if (n < 1 || k < 1 || iters < 0 || !x || !centroids || !assign) return OR_EINVAL;
+    int64_t *sum = (int64_t *)malloc(sizeof(int64_t) * (size_t)k * OR_KM_DIM);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    if (!sum || !cnt) { free(sum); free(cnt); return OR_ENOMEM; }
+    for (int32_t it = 0; it < iters; ++it) {
+        /* assignment: the nearest centroid */
+        memset(sum, 0, sizeof(int64_t) * (size_t)k * OR_KM_DIM);
+        memset(cnt, 0, sizeof(int64_t) * (size_t)k);
+        for (int32_t s = 0; s < n; ++s) {
+            const int32_t c = nearest(x + (int64_t)s * OR_KM_DIM, centroids, k);
+            ++cnt[c];
+            for (int j = 0; j < OR_KM_DIM; ++j) sum[(int64_t)c * OR_KM_DIM + j] += x[(int64_t)s * OR_KM_DIM + j];
+        }
+        /* update: the members' mean, rounded to the nearest integer (halves up) */
+        for (int32_t c = 0; c < k; ++c) {
+            if (cnt[c] == 0) continue;
+            for (int j = 0; j < OR_KM_DIM; ++j)
+                centroids[(int64_t)c * OR_KM_DIM + j] =
+                    (int32_t)floor_div64(2 * sum[(int64_t)c * OR_KM_DIM + j] + cnt[c], 2 * cnt[c]);
+        }
+    }
+    for (int32_t s = 0; s < n; ++s) assign[s] = nearest(x + (int64_t)s * OR_KM_DIM, centroids, k);
+    free(sum);
+    free(cnt);
+    return OR_OK;
+}
+
+int or_kmeans_pp_init(const int32_t *x, int32_t n, int32_t k, const uint64_t *u, int32_t *init) {
+    if (n < 1 || k < 1 || k > n || !x || !u || !init) return OR_EINVAL;
+    int64_t *d = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!d) return OR_ENOMEM;
+    init[0] = (int32_t)(u[0] % (uint64_t)n);
+    for (int32_t s = 0; s < n; ++s) d[s] = sqdist(x + (int64_t)s * OR_KM_DIM, x + (int64_t)init[0] * OR_KM_DIM);
+    for (int32_t c = 1; c < k; ++c) {
+        int64_t total = 0;
+        for (int32_t s = 0; s < n; ++s) total += d[s];
+        int32_t pick;
+        if (total == 0) {
+            pick = (int32_t)(u[c] % (uint64_t)n);
+        } else {
+            /* the SKU whose share of the running sum of D^2 covers the draw */
+            const int64_t target = (int64_t)(u[c] % (uint64_t)total);
+            int64_t run = 0;
+            pick = n - 1;
+            for (int32_t s = 0; s < n; ++s) {
+                run += d[s];
+                if (run > target) { pick = s; break; }
+            }
+        }
+        init[c] = pick;
+        for (int32_t s = 0; s < n; ++s) {
+            const int64_t e = sqdist(x + (int64_t)s * OR_KM_DIM, x + (int64_t)pick * OR_KM_DIM);
+            if (e < d[s]) d[s] = e;
+        }
+    }
+    free(d);
+    return OR_OK;
+}
+
+int or_kmeans_slotting(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+                       int32_t n_sku, const int8_t *signs, int32_t freq_weight, int32_t k, const int32_t *init,
+                       const uint64_t *u, int32_t iters, int32_t *x_out, int32_t *init_out, int32_t *centroids,
+                       int32_t *assign, int32_t *slot_map) {
+    int rc = layout_check(g);
+    if (rc != OR_OK) return rc;
+    if (k < 1 || k > n_sku || iters < 0 || freq_weight < 0 || freq_weight > OR_KM_MAX_FREQ_WEIGHT ||
+        (!init && !u) || !centroids || !assign || !slot_map)
+        return OR_EINVAL;
+    const int64_t n_loc = (int64_t)g->n_aisles * 2 * g->slots_per_side;
+    if (n_sku > n_loc) return OR_ERANGE;
+    int32_t *x = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_sku * OR_KM_DIM);
+    int32_t *freq = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_sku);
+    km_cluster_t *cl = (km_cluster_t *)malloc(sizeof(km_cluster_t) * (size_t)k);
+    int64_t *cl_rank = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    km_key_t *keys = (km_key_t *)malloc(sizeof(km_key_t) * (size_t)n_sku);
+    int32_t *seed = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    if (!x || !freq || !cl || !cl_rank || !keys || !seed) { rc = OR_ENOMEM; goto done; }
+    /* 1-2: features */
+    rc = or_kmeans_features(n_orders, order_off, line_sku, n_sku, signs, freq_weight, x, freq);
+    if (rc != OR_OK) goto done;
+    /* 3: initial centroids: the given SKUs, else K-means++ seeding */
+    if (init) {
+        memcpy(seed, init, sizeof(int32_t) * (size_t)k);
+    } else {
+        rc = or_kmeans_pp_init(x, n_sku, k, u, seed);
+        if (rc != OR_OK) goto done;
+    }
+    for (int32_t c = 0; c < k; ++c) {
+        if (seed[c] < 0 || seed[c] >= n_sku) { rc = OR_ERANGE; goto done; }
+        memcpy(centroids + (int64_t)c * OR_KM_DIM, x + (int64_t)seed[c] * OR_KM_DIM, sizeof(int32_t) * OR_KM_DIM);
+    }
+    if (init_out) memcpy(init_out, seed, sizeof(int32_t) * (size_t)k);
+    /* 4: Lloyd rounds */
+    rc = or_kmeans_lloyd(x, n_sku, k, iters, centroids, assign);
+    if (rc != OR_OK) goto done;
+    /* 5: cluster weight = picks of its members (the final assignment) */
+    for (int32_t c = 0; c < k; ++c) { cl[c].weight = 0; cl[c].cluster = c; }
+    for (int32_t s = 0; s < n_sku; ++s) cl[assign[s]].weight += freq[s];
+    /* 6: zones: clusters by weight (heavier first, ties lowest id); SKUs by
+     * (their cluster's rank, more picks first, lower id) */
+    qsort(cl, (size_t)k, sizeof(km_cluster_t), cmp_km_cluster);
+    for (int32_t r = 0; r < k; ++r) cl_rank[cl[r].cluster] = r;
+    for (int32_t s = 0; s < n_sku; ++s) {
+        keys[s].cluster_rank = cl_rank[assign[s]];
+        keys[s].freq = freq[s];
+        keys[s].sku = s;
+    }
+    qsort(keys, (size_t)n_sku, sizeof(km_key_t), cmp_km_key);
+    /* 7: the r-th SKU takes the r-th location in aisle-major order: aisle,
+     * then depth from the front, then side */
+    for (int32_t r = 0; r < n_sku; ++r) {
+        const int32_t L = g->slots_per_side;
+        const int32_t a = r / (2 * L), q = r % (2 * L), depth = q / 2, side = q % 2;
+        slot_map[keys[r].sku] = (a * 2 + side) * L + depth;
+    }
+    if (x_out) memcpy(x_out, x, sizeof(int32_t) * (size_t)n_sku * OR_KM_DIM);
+done:
+    free(x); free(freq); free(cl); free(cl_rank); free(keys); free(seed);
+    return rc;
+}

@@ -122,6 +122,54 @@ int or_batch_grow(const or_layout *g, int32_t n_orders, const int32_t *order_off
                   int32_t n_sku, const int32_t *slot_map, int32_t max_orders, int32_t max_lines,
                   int32_t *tour_off, int32_t *order_seq, int32_t *n_tours);
 
+/* ------------------------------------------------------------ K-means slotting
+ * Subproblem 3 (Sec. 5): products are placed by picking frequency, and an
+ * unsupervised K-means classification (MacQueen 1967) decides which are
+ * stored together; subroutine 4 scores the placement.  The paper gives no
+ * features, initialisation or zone rule; the reading, all in integers:
+ *   1. freq_s = lines of SKU s; co_s[j] = sum over every line of s and every
+ *      OTHER line of the same order of signs[sku of that line][j] (the SKU's
+ *      co-occurrence row projected on OR_KM_SKETCH random +-1 directions,
+ *      signs [n_sku][OR_KM_DIM], column OR_KM_SKETCH unused).
+ *   2. x_s[j] = trunc(co_s[j] * OR_KM_SCALE / n_s), n_s = floor(sqrt(sum co_s^2))
+ *      (0 when n_s = 0) for j < OR_KM_SKETCH; x_s[OR_KM_SKETCH] =
+ *      freq_weight * bitlen(freq_s) (bitlen(0) = 0, else floor(log2) + 1).
+ *   3. centroid c = x of SKU init[c]; with init NULL, K-means++ seeding
+ *      (Arthur & Vassilvitskii 2007) in integers from the caller's draws
+ *      u[0..k): the first SKU is u[0] mod n_sku; with D(s) the squared
+ *      distance from x_s to the nearest SKU chosen so far and T = sum D, the
+ *      next is the first s (in id order) whose running sum D(0) + .. + D(s)
+ *      exceeds u[c] mod T (u[c] mod n_sku when T = 0).
+ *   4. iters Lloyd rounds: each SKU to its nearest centroid (squared
+ *      Euclidean, ties to the lowest cluster); each non-empty cluster's
+ *      centroid to floor((2 * sum + n) / (2 * n)) per coordinate (the mean
+ *      rounded to the nearest integer, halves up); empty clusters keep theirs.
+ *   5. a final assignment against the final centroids; weight of a cluster =
+ *      the picks (freq) of its members.
+ *   6. clusters ranked by weight (heavier first, ties lowest id); SKUs ordered
+ *      by (cluster rank, freq descending, id).
+ *   7. the r-th SKU of that order takes the r-th location in aisle-major order
+ *      (aisle, then depth from the front, then side): r -> aisle r / 2L,
+ *      depth (r mod 2L) / 2, side r mod 2.  Needs n_sku <= n_locations.
+ * centroids [k][OR_KM_DIM], assign [n_sku], slot_map [n_sku]; x_out
+ * [n_sku][OR_KM_DIM] and init_out [k] (the seeds used) may be NULL.
+ * Returns OR_OK or an error. */
+#define OR_KM_DIM 32
+#define OR_KM_SKETCH 31
+#define OR_KM_SCALE 1024
+#define OR_KM_MAX_FREQ_WEIGHT 256
+int or_kmeans_features(int32_t n_orders, const int32_t *order_off, const int32_t *line_sku, int32_t n_sku,
+                       const int8_t *signs, int32_t freq_weight, int32_t *x, int32_t *freq);
+int or_kmeans_pp_init(const int32_t *x, int32_t n, int32_t k, const uint64_t *u, int32_t *init);
+/* step 4 and the final assignment of step 5 on rows x [n][OR_KM_DIM]:
+ * centroids [k][OR_KM_DIM] holds the initial centroids on entry and the final
+ * ones on return; assign [n] the final assignment. */
+int or_kmeans_lloyd(const int32_t *x, int32_t n, int32_t k, int32_t iters, int32_t *centroids, int32_t *assign);
+int or_kmeans_slotting(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
+                       int32_t n_sku, const int8_t *signs, int32_t freq_weight, int32_t k, const int32_t *init,
+                       const uint64_t *u, int32_t iters, int32_t *x_out, int32_t *init_out, int32_t *centroids,
+                       int32_t *assign, int32_t *slot_map);
+
 /* ------------------------------------------------------------- surrogate
  * Learned prescreen (the paper's machine-learning-in-the-loop idea, Sec. 1 and
  * Fig. 1): a small MLP predicts a tour's normalised optimal length from a

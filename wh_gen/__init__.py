@@ -44,6 +44,12 @@ def _load():
             lib.gen_orders.restype = ctypes.c_int64
             lib.gen_orders.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, i32p, i32p, ctypes.c_int64]
+            lib.gen_orders_cat.restype = ctypes.c_int64
+            lib.gen_orders_cat.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                           i32p, i32p, ctypes.c_int64]
+            lib.gen_signs.restype = ctypes.c_int
+            lib.gen_signs.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
             lib.gen_slot_random.restype = ctypes.c_int
             lib.gen_slot_random.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, i32p]
             lib.gen_slot_abc.restype = ctypes.c_int
@@ -165,6 +171,26 @@ def gen_orders(seed: int, n_orders: int, n_sku: int, max_lines: int, p_geom: flo
     return off, np.ascontiguousarray(lines[:n])
 
 
+def gen_orders_cat(seed: int, n_orders: int, n_sku: int, max_lines: int, p_geom: float, zipf_s: float,
+                   n_cat: int, p_in: float):
+    """Orders with categories (see gen.c): SKU s in category s mod n_cat; an
+    order's lines come from its category with probability p_in."""
+    lib = _load()
+    off = np.zeros(n_orders + 1, np.int32)
+    cap = max(1, n_orders * max_lines)
+    lines = np.zeros(cap, np.int32)
+    n = _check(lib.gen_orders_cat(seed, n_orders, n_sku, max_lines, p_geom, zipf_s, n_cat, p_in, _p(off),
+                                  _p(lines), cap), "gen_orders_cat")
+    return off, np.ascontiguousarray(lines[:n])
+
+
+def gen_signs(seed: int, shape) -> np.ndarray:
+    """int8 array of the given shape with entries in {-1, +1}."""
+    out = np.zeros(int(np.prod(shape)), np.int8)
+    _check(_load().gen_signs(seed, out.shape[0], out.ctypes.data), "gen_signs")
+    return out.reshape(shape)
+
+
 def gen_slot_random(seed: int, n_sku: int, n_loc: int):
     out = np.zeros(n_sku, np.int32)
     _check(_load().gen_slot_random(seed, n_sku, n_loc, _p(out)), "gen_slot_random")
@@ -263,4 +289,29 @@ def paperscale(seed: int = 4, n_plans: int = 16384, plan_base: int = 0) -> Insta
     return Instance(lay, 50000, off, lines, slot, pto, to, seq, {"name": "paperscale", "seed": seed})
 
 
-PRESETS = {"tiny": tiny, "midsize": midsize, "paperscale": paperscale}
+def midsize_cat(seed: int = 6, n_plans: int = 256, plan_base: int = 0) -> Instance:
+    """The mid-size layout and catalogue with a category structure: 8,000 SKUs
+    in 64 categories (s mod 64), Zipf(1.1) popularity, 4,000 orders of 1..12
+    lines of which 80 % come from the order's category; ABC slotting with 10 %
+    swapped; plans as ``midsize``."""
+    lay = Layout(40, 100)
+    off, lines = gen_orders_cat(seed, 4000, 8000, 12, 0.4, 1.1, 64, 0.8)
+    slot = gen_slot_abc(seed, lay, 8000, 0.10)
+    pto, to, seq = gen_plans(seed, 1, off, n_plans, 20, 60, plan_base)
+    return Instance(lay, 8000, off, lines, slot, pto, to, seq, {"name": "midsize_cat", "seed": seed})
+
+
+def paperscale_cat(seed: int = 7, n_plans: int = 256, plan_base: int = 0) -> Instance:
+    """The paper-scale layout (500 x 200, 200,000 locations) with 50,000 SKUs
+    in 256 categories, Zipf(1.0), 4,000 orders of which 80 % of the lines come
+    from the order's category; ABC slotting with 10 % swapped; tours of at
+    most 24 orders."""
+    lay = Layout(500, 200)
+    off, lines = gen_orders_cat(seed, 4000, 50000, 12, 0.4, 1.0, 256, 0.8)
+    slot = gen_slot_abc(seed, lay, 50000, 0.10)
+    pto, to, seq = gen_plans(seed, 1, off, n_plans, 24, 0, plan_base)
+    return Instance(lay, 50000, off, lines, slot, pto, to, seq, {"name": "paperscale_cat", "seed": seed})
+
+
+PRESETS = {"tiny": tiny, "midsize": midsize, "paperscale": paperscale, "midsize_cat": midsize_cat,
+           "paperscale_cat": paperscale_cat}

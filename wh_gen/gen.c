@@ -35,6 +35,8 @@
 #define TAG_PLAN 5u
 #define TAG_MOVE 6u
 #define TAG_INST 7u
+#define TAG_CATEGORY 8u
+#define TAG_SIGN 9u
 
 typedef struct { uint64_t s; } rng_t;
 
@@ -126,6 +128,81 @@ int64_t gen_orders(uint64_t seed, int32_t n_orders, int32_t n_sku, int32_t max_l
     free(size_cdf);
     free(sku_cdf);
     return pos;
+}
+
+/* Orders with a category structure (the paper's retail case study clusters
+ * "different categories"): SKU s belongs to category s mod n_cat, so every
+ * category holds SKUs of every popularity.  Each order draws its category
+ * uniformly, a size as gen_orders, and each line: with probability p_in the
+ * i-th SKU of the order's category with Zipf popularity P(i) ~ (i+1)^-s over
+ * the first floor(n_sku / n_cat) members (SKU id = category + i * n_cat),
+ * otherwise a SKU of the whole catalogue by Zipf popularity (SKU id = rank).
+ * SKUs are distinct within an order (redraw on repeat).  Same outputs and
+ * return value as gen_orders. */
+int64_t gen_orders_cat(uint64_t seed, int32_t n_orders, int32_t n_sku, int32_t max_lines, double p_geom,
+                       double zipf_s, int32_t n_cat, double p_in, int32_t *order_off, int32_t *line_sku,
+                       int64_t line_cap) {
+    if (n_orders < 0 || n_sku <= 0 || max_lines <= 0 || n_cat <= 0 || n_cat > n_sku || !(zipf_s > 0.0) ||
+        !(p_geom > 0.0 && p_geom <= 1.0) || !(p_in >= 0.0 && p_in <= 1.0))
+        return GEN_EINVAL;
+    const int32_t per_cat = n_sku / n_cat;
+    if (max_lines > per_cat || (int64_t)n_orders * max_lines > line_cap) return GEN_EINVAL;
+    double *size_cdf = (double *)malloc(sizeof(double) * (size_t)max_lines);
+    double *sku_cdf = (double *)malloc(sizeof(double) * (size_t)n_sku);
+    double *cat_cdf = (double *)malloc(sizeof(double) * (size_t)per_cat);
+    if (!size_cdf || !sku_cdf || !cat_cdf) {
+        free(size_cdf); free(sku_cdf); free(cat_cdf);
+        return GEN_ENOMEM;
+    }
+    double acc = 0.0, w = 1.0;
+    for (int32_t k = 0; k < max_lines; ++k) { acc += w; size_cdf[k] = acc; w *= (1.0 - p_geom); }
+    for (int32_t k = 0; k < max_lines; ++k) size_cdf[k] /= acc;
+    size_cdf[max_lines - 1] = 2.0;
+    double z = 0.0;
+    for (int32_t i = 0; i < n_sku; ++i) { z += pow((double)(i + 1), -zipf_s); sku_cdf[i] = z; }
+    for (int32_t i = 0; i < n_sku; ++i) sku_cdf[i] /= z;
+    sku_cdf[n_sku - 1] = 2.0;
+    z = 0.0;
+    for (int32_t i = 0; i < per_cat; ++i) { z += pow((double)(i + 1), -zipf_s); cat_cdf[i] = z; }
+    for (int32_t i = 0; i < per_cat; ++i) cat_cdf[i] /= z;
+    cat_cdf[per_cat - 1] = 2.0;
+    int64_t pos = 0;
+    order_off[0] = 0;
+    for (int32_t o = 0; o < n_orders; ++o) {
+        rng_t rs = stream(seed, TAG_ORDER_SIZE, (uint64_t)o);
+        int32_t k = cdf_search(size_cdf, max_lines, unit(&rs)) + 1;
+        rng_t rc = stream(seed, TAG_CATEGORY, (uint64_t)o);
+        const int32_t cat = below(&rc, n_cat);
+        rng_t rk = stream(seed, TAG_ORDER_SKU, (uint64_t)o);
+        for (int32_t j = 0; j < k; ++j) {
+            int32_t sku;
+            for (;;) {
+                if (unit(&rk) < p_in) sku = cat + cdf_search(cat_cdf, per_cat, unit(&rk)) * n_cat;
+                else sku = cdf_search(sku_cdf, n_sku, unit(&rk));
+                int dup = 0;
+                for (int64_t q = pos - j; q < pos; ++q) if (line_sku[q] == sku) { dup = 1; break; }
+                if (!dup) break;
+            }
+            line_sku[pos++] = sku;
+        }
+        order_off[o + 1] = (int32_t)pos;
+    }
+    free(size_cdf);
+    free(sku_cdf);
+    free(cat_cdf);
+    return pos;
+}
+
+/* n values in {-1, +1}, each from one bit of stream (seed, TAG_SIGN, i / 64) --
+ * the random sign matrix of a sketch, drawn by the caller and passed in. */
+int gen_signs(uint64_t seed, int64_t n, int8_t *out) {
+    if (n < 0) return GEN_EINVAL;
+    for (int64_t i = 0; i < n; i += 64) {
+        rng_t r = stream(seed, TAG_SIGN, (uint64_t)(i / 64));
+        const uint64_t bits = sm64_next(&r);
+        for (int64_t b = 0; b < 64 && i + b < n; ++b) out[i + b] = (int8_t)(((bits >> b) & 1u) ? 1 : -1);
+    }
+    return GEN_OK;
 }
 
 /* ---------------------------------------------------------------- slotting */
