@@ -413,6 +413,58 @@ def run_layout_sweep(wh, dev):
             "pareto": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in front]}
 
 
+def run_kmeans(wh, dev):
+    """K-means slotting on the category workloads: one call (features,
+    K-means++ seeding, Lloyd rounds, zones) timed with CUDA events after a
+    warm-up, and the slotting scored by the evaluator against the ABC one on
+    the same random plans and on seed-and-grow plans formed under each."""
+    import numpy as np
+    import torch
+    import wh_gen
+
+    def one(inst, k, iters, fw):
+        lay = wh.Layout.of(inst.layout)
+        prob = wh.to_device(inst, dev)
+        sg = torch.as_tensor(wh_gen.gen_signs(3, (inst.n_sku, 32))).to(dev)
+        u = torch.as_tensor(np.array([wh_gen.stream_word(5, 11, i) for i in range(k)], np.uint64).view(np.int64)).to(dev)
+        lay.kmeans_slotting(prob, sg, k, iters, fw, u=u)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, seeds, cent, assign, smap = lay.kmeans_slotting(prob, sg, k, iters, fw, u=u)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        assert lay.status() == 0
+        km = wh.DeviceProblem(prob.order_off, prob.line_sku, smap, prob.plan_tour_off, prob.tour_off,
+                              prob.order_seq, inst.n_sku)
+        abc_rand = wh.evaluate(lay, prob).plan_rr[:inst.n_plans].double().mean().item()
+        km_rand = wh.evaluate(lay, km).plan_rr[:inst.n_plans].double().mean().item()
+        row = {"ms": ms, "k": k, "iters": iters, "freq_weight": fw,
+               "random_plans_optimal_abc": abc_rand, "random_plans_optimal_kmeans": km_rand,
+               "kmeans_over_abc_random_plans": km_rand / abc_rand}
+        if inst.layout.n_aisles <= 255:
+            maps = torch.stack([prob.slot_map, smap])
+            to, seq, nt = lay.batch_grow(prob, maps, 20, 60)
+            costs = []
+            for i in range(2):
+                n_t = int(nt[i].item())
+                formed = wh.DeviceProblem(prob.order_off, prob.line_sku, maps[i].contiguous(),
+                                          torch.tensor([0, n_t], dtype=torch.int32, device=dev),
+                                          to[i, :n_t + 1].contiguous(), seq[i].contiguous(), inst.n_sku)
+                costs.append(int(wh.evaluate(lay, formed).plan_rr[0].item()))
+            row.update({"grown_plan_optimal_abc": costs[0], "grown_plan_optimal_kmeans": costs[1],
+                        "kmeans_over_abc_grown_plans": costs[1] / costs[0]})
+        lay.close()
+        return row
+
+    mid = one(wh_gen.midsize_cat(seed=6, n_plans=256), 64, 20, 64)
+    paper = one(wh_gen.paperscale_cat(seed=7, n_plans=256), 256, 20, 64)
+    return {"workload": "category order books: mid-size (8,000 SKUs, 64 categories, 40 x 100 layout, k = 64) and "
+                        "paper-scale (50,000 SKUs, 256 categories, 500 x 200 layout, k = 256), 20 Lloyd rounds",
+            "midsize": mid, "paperscale": paper}
+
+
 def run_routes(wh, dev):
     """Explicit optimal pick sequences for every tour of 1,024 paper-scale
     plans (one thread per tour: tracking DP, backtrack, Euler circuit), one
@@ -647,6 +699,7 @@ def run_ours(args):
         extra["batch_formation"] = run_batch_grow(wh, dev)
         extra["layout_sweep"] = run_layout_sweep(wh, dev)
         extra["routes"] = run_routes(wh, dev)
+        extra["kmeans_slotting"] = run_kmeans(wh, dev)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -222,6 +222,45 @@ int wh_batch_grow(wh_layout *layout, const wh_orders *orders, const int32_t *slo
                   int32_t n_maps, int32_t max_orders, int32_t max_lines, int32_t *tour_off, int32_t *order_seq,
                   int32_t *n_tours, void *stream);
 
+/* K-means slotting (Sec. 5, subproblem 3: products placed by picking
+ * frequency, an unsupervised K-means classification (MacQueen 1967) deciding
+ * which are stored together; subroutine 4 scores the placement with
+ * wh_eval_plans).  The paper fixes no features, seeding or zone rule; this is
+ * the library's reading, all in integers (so the result is exact):
+ *   1. freq_s = lines of SKU s; co_s[j] = sum over every line of s and every
+ *      OTHER line of the same order of signs[that line's SKU][j], j < 31 (the
+ *      SKU's co-occurrence row projected on 31 random +-1 directions);
+ *   2. x_s[j] = trunc(co_s[j] * 1024 / floor(sqrt(sum co_s^2))) (0 when the
+ *      root is 0), j < 31; x_s[31] = freq_weight * bitlen(freq_s);
+ *   3. seeds: init[0..k) when init is non-NULL, else K-means++ (Arthur &
+ *      Vassilvitskii 2007) from the draws u[0..k): seed 0 = u[0] mod n_sku,
+ *      seed c = the first SKU whose running sum of D^2 (squared distance to
+ *      the nearest seed so far, in SKU order) exceeds u[c] mod sum D^2
+ *      (u[c] mod n_sku when that sum is 0); centroid c = x of seed c;
+ *   4. iters Lloyd rounds: nearest centroid (squared Euclidean, ties to the
+ *      lowest cluster), then every non-empty centroid = floor((2 * sum + n) /
+ *      (2 * n)) per coordinate (the mean, rounded to nearest, halves up);
+ *   5. a final assignment; a cluster's weight = the picks of its members;
+ *   6. clusters ranked by weight (heavier first, ties lowest id), SKUs by
+ *      (cluster rank, picks descending, id); the r-th SKU takes the r-th
+ *      location in aisle-major order: aisle r / 2L, depth index (r mod 2L) / 2,
+ *      side r mod 2 (locations past n_sku stay empty).
+ * Inputs (device): signs int8 [n_sku][32] of +-1 (column 31 unused; 16-byte
+ * aligned); init int32 [k] or NULL; u uint64 [k] (needed when init is NULL).
+ * Outputs (device, caller-owned): centroids int32 [k][32], assign int32
+ * [n_sku], slot_map int32 [n_sku] (a slotting for wh_plans.slot_map);
+ * optional x_out int32 [n_sku][32] (16-byte aligned) and init_out int32 [k]
+ * (the seeds used).  Needs 1 <= k <= min(256, n_sku), 0 <= freq_weight <= 256,
+ * iters >= 0, n_sku <= the layout's locations and n_lines < 2^26 (WH_EINVAL
+ * or WH_ERANGE otherwise).  A SKU id or seed outside [0, n_sku) sets
+ * WH_STATUS_BAD_SKU, bad order offsets WH_STATUS_BAD_OFFSET (the outputs are
+ * then unspecified).  Asynchronous on `stream`; uses the handle's scratch
+ * (about 400 B per SKU), growing it when needed.  Returns WH_OK, WH_EINVAL,
+ * WH_ERANGE, WH_ENOMEM or WH_ECUDA. */
+int wh_kmeans_slotting(wh_layout *layout, const wh_orders *orders, const int8_t *signs, int32_t freq_weight,
+                       int32_t k, const int32_t *init, const uint64_t *u, int32_t iters, int32_t *x_out,
+                       int32_t *init_out, int32_t *centroids, int32_t *assign, int32_t *slot_map, void *stream);
+
 /* Explicit optimal routes (Sec. 5, Eq. (2): the picking route of a tour is
  * the best order of its picking positions, shortest paths between them; Sec.
  * 6 hands the picker that sequence).  For each of the n listed tours

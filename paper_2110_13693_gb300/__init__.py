@@ -107,6 +107,10 @@ SIGNATURES = {
     "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_kmeans_slotting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "wh_routes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p]),
@@ -408,6 +412,29 @@ class Layout:
                       _ptr(tour_off), _ptr(order_seq), _ptr(n_tours), stream)
         return tour_off, order_seq[:, :n_orders], n_tours
 
+    def kmeans_slotting(self, prob: DeviceProblem, signs, k: int, iters: int, freq_weight: int = 64, init=None,
+                        u=None, stream=None):
+        """K-means slotting of prob's SKUs (see wh_kmeans_slotting): signs int8
+        [n_sku, 32] of +-1 and either init (int32 [k] SKU ids) or u (uint64
+        draws [k], K-means++), device tensors.  Returns (x [n_sku, 32], seeds
+        [k], centroids [k, 32], assign [n_sku], slot_map [n_sku]) device
+        tensors."""
+        import torch
+        dev = prob.order_off.device
+        n_sku = prob.n_sku
+        sg = signs.reshape(n_sku, 32).to(torch.int8).contiguous()
+        x = torch.empty((n_sku, 32), dtype=torch.int32, device=dev)
+        seeds = torch.empty(k, dtype=torch.int32, device=dev)
+        cent = torch.empty((k, 32), dtype=torch.int32, device=dev)
+        assign = torch.empty(n_sku, dtype=torch.int32, device=dev)
+        smap = torch.empty(n_sku, dtype=torch.int32, device=dev)
+        ini = None if init is None else init.to(torch.int32).contiguous()
+        uu = None if u is None else u.contiguous()
+        wh_kmeans_slotting(self.handle, prob.orders(), _ptr(sg), freq_weight, k,
+                           None if ini is None else _ptr(ini), None if uu is None else _ptr(uu), iters, _ptr(x),
+                           _ptr(seeds), _ptr(cent), _ptr(assign), _ptr(smap), stream)
+        return x, seeds, cent, assign, smap
+
     def routes(self, prob: DeviceProblem, tours, max_points: int = 256, stream=None):
         """Optimal pick sequences of the listed tours (int32 device tensor of
         global tour indices): (points [n, max_points] int32, aisle << 16 |
@@ -584,6 +611,14 @@ def wh_batch_grow(layout, orders: wh_orders, slot_map, slot_map_stride: int, n_m
     _check(load().wh_batch_grow(layout, ctypes.byref(orders), ctypes.c_void_p(slot_map), slot_map_stride, n_maps,
                                 max_orders, max_lines, ctypes.c_void_p(tour_off), ctypes.c_void_p(order_seq),
                                 ctypes.c_void_p(n_tours), _stream_ptr(stream)), "wh_batch_grow")
+
+
+def wh_kmeans_slotting(layout, orders: wh_orders, signs, freq_weight: int, k: int, init, u, iters: int, x_out,
+                       init_out, centroids, assign, slot_map, stream=None) -> None:
+    _check(load().wh_kmeans_slotting(layout, ctypes.byref(orders), ctypes.c_void_p(signs), freq_weight, k,
+                                     ctypes.c_void_p(init), ctypes.c_void_p(u), iters, ctypes.c_void_p(x_out),
+                                     ctypes.c_void_p(init_out), ctypes.c_void_p(centroids), ctypes.c_void_p(assign),
+                                     ctypes.c_void_p(slot_map), _stream_ptr(stream)), "wh_kmeans_slotting")
 
 
 def wh_routes(layout, orders: wh_orders, plans: wh_plans, tours, n: int, max_points: int, points, n_points, length,

@@ -638,6 +638,84 @@ extern "C" int wh_batch_grow(wh_layout* h, const wh_orders* orders, const int32_
     return wh::launch_batch_grow(B, n_maps, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
 }
 
+extern "C" int wh_kmeans_slotting(wh_layout* h, const wh_orders* orders, const int8_t* signs, int32_t freq_weight,
+                                  int32_t k, const int32_t* init, const uint64_t* u, int32_t iters, int32_t* x_out,
+                                  int32_t* init_out, int32_t* centroids, int32_t* assign, int32_t* slot_map,
+                                  void* stream) {
+    if (!h || !orders || !signs || !centroids || !assign || !slot_map || (!init && !u)) return WH_EINVAL;
+    const wh_orders o = *orders;
+    if (o.n_orders < 0 || o.n_lines < 0 || o.n_sku < 1 || !o.order_off || (o.n_lines > 0 && !o.line_sku))
+        return WH_EINVAL;
+    if (k < 1 || k > o.n_sku || iters < 0 || freq_weight < 0) return WH_EINVAL;
+    if (k > wh::KM_MAX_K || freq_weight > wh::KM_MAX_FREQ_WEIGHT || o.n_lines >= (1 << 26)) return WH_ERANGE;
+    if ((int64_t)o.n_sku > (int64_t)h->g.n_loc) return WH_ERANGE;
+    if ((reinterpret_cast<uintptr_t>(signs) & 15) != 0 || (reinterpret_cast<uintptr_t>(x_out) & 15) != 0)
+        return WH_EINVAL;
+    int rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    const size_t n = (size_t)o.n_sku, K = (size_t)k;
+    const size_t nb = (n + 255) / 256;
+    const size_t sz[] = {
+        align_up(8 * n * wh::KM_DIM),             // co
+        align_up(4 * n),                          // freq
+        x_out ? 0 : align_up(4 * n * wh::KM_DIM), // x
+        init ? 0 : align_up(8 * n),               // dmin
+        init ? 0 : align_up(8 * nb),              // bsum
+        align_up(4),                              // done
+        init_out ? 0 : align_up(4 * K),           // seeds
+        align_up(8 * K * wh::KM_DIM),             // sum
+        align_up(4 * K),                          // cnt
+        align_up(8 * K),                          // weight
+        align_up(4 * K),                          // off
+        align_up(4 * K),                          // cur
+        align_up(4 * (K + 1)),                    // off_by_rank
+        align_up(8 * n),                          // mkey
+    };
+    size_t total = 0;
+    for (size_t v : sz) total += v;
+    rc = reserve_scratch(h, total);
+    if (rc != WH_OK) return rc;
+    char* q = static_cast<char*>(h->scratch);
+    auto take = [&](size_t bytes) -> void* {
+        void* r = bytes ? q : nullptr;
+        q += bytes;
+        return r;
+    };
+    wh::KmArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.g = h->g;
+    A.n_orders = o.n_orders;
+    A.n_lines = o.n_lines;
+    A.n_sku = o.n_sku;
+    A.order_off = o.order_off;
+    A.line_sku = o.line_sku;
+    A.signs = signs;
+    A.fw = freq_weight;
+    A.k = k;
+    A.iters = iters;
+    A.init = init;
+    A.u = u;
+    A.co = static_cast<long long*>(take(sz[0]));
+    A.freq = static_cast<int32_t*>(take(sz[1]));
+    A.x = x_out ? x_out : static_cast<int32_t*>(take(sz[2]));
+    A.dmin = static_cast<long long*>(take(sz[3]));
+    A.bsum = static_cast<long long*>(take(sz[4]));
+    A.done = static_cast<unsigned int*>(take(sz[5]));
+    A.seeds = init_out ? init_out : static_cast<int32_t*>(take(sz[6]));
+    A.cent = centroids;
+    A.sum = static_cast<long long*>(take(sz[7]));
+    A.cnt = static_cast<int32_t*>(take(sz[8]));
+    A.weight = static_cast<long long*>(take(sz[9]));
+    A.off = static_cast<int32_t*>(take(sz[10]));
+    A.cur = static_cast<int32_t*>(take(sz[11]));
+    A.off_by_rank = static_cast<int32_t*>(take(sz[12]));
+    A.mkey = static_cast<unsigned long long*>(take(sz[13]));
+    A.assign = assign;
+    A.slot_map = slot_map;
+    A.status = h->meta;
+    return wh::launch_kmeans(A, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
 extern "C" int wh_routes(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* tours,
                          int32_t n, int32_t max_points, int32_t* points, int32_t* n_points, int32_t* length,
                          void* stream) {

@@ -156,6 +156,43 @@ struct BatchGrowArgs {
 size_t batch_grow_smem_bytes(int n_orders, int n_lines, int A);
 cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s);
 
+// K-means slotting (k_kmeans.cu)
+constexpr int KM_DIM = 32;       // feature row: 31 sketch coordinates + the pick-count coordinate
+constexpr int KM_SKETCH = 31;
+constexpr int KM_SCALE = 1024;
+constexpr int KM_MAX_K = 256;
+constexpr int KM_MAX_FREQ_WEIGHT = 256;
+struct KmArgs {
+    Geo g;
+    int32_t n_orders, n_lines, n_sku;
+    const int32_t* order_off;
+    const int32_t* line_sku;
+    const int8_t* signs;         // [n_sku][32], column 31 unused
+    int32_t fw, k, iters;
+    const int32_t* init;         // [k] or null: K-means++ from u
+    const uint64_t* u;           // [k]
+    long long* co;               // [n_sku][32] scratch
+    int32_t* freq;               // [n_sku]
+    int32_t* x;                  // [n_sku][32]
+    long long* dmin;             // [n_sku]
+    long long* bsum;             // [blocks]
+    unsigned int* done;
+    int32_t* seeds;              // [k]
+    int32_t* cent;               // [k][32]
+    long long* sum;              // [k][32]
+    int32_t* cnt;                // [k]
+    long long* weight;           // [k]
+    int32_t* off;                // [k]
+    int32_t* cur;                // [k]
+    int32_t* off_by_rank;        // [k + 1]
+    unsigned long long* mkey;    // [n_sku]
+    int32_t* assign;             // [n_sku]
+    int32_t* slot_map;           // [n_sku]
+    uint32_t* status;
+};
+size_t kmeans_assign_smem(int k);
+cudaError_t launch_kmeans(const KmArgs& A, cudaStream_t s);
+
 // explicit optimal routes of listed tours (k_route.cu)
 constexpr int ROUTE_MAX_POINTS = 256;
 cudaError_t launch_routes(const EvalArgs& a, const int32_t* tours, int32_t n, int32_t max_points, int32_t* points,
