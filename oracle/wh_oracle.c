@@ -587,6 +587,20 @@ int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off
                 smap_copy[b] = tmp;
                 after_map = smap_copy;
             }
+        } else if (type == 3) {
+            /* relocate SKU a to location b, which no SKU of the plan holds */
+            const int64_t n_loc = (int64_t)g->n_aisles * 2 * g->slots_per_side;
+            if (slot_map_stride == 0 || a < 0 || a >= n_sku || b < 0 || b >= n_loc) st = 3;
+            else if (smap[a] == b) st = 2;
+            else {
+                for (int32_t s = 0; s < n_sku; ++s)
+                    if (smap[s] == b) { st = 3; break; }
+                if (st == 0) {
+                    memcpy(smap_copy, smap, sizeof(int32_t) * (size_t)n_sku);
+                    smap_copy[a] = b;
+                    after_map = smap_copy;
+                }
+            }
         } else {
             st = 3;
         }
@@ -658,11 +672,13 @@ int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, c
                 order_seq[end] = a;
                 for (int32_t t = tb + 1; t <= ta; ++t) tour_off[t] += 1;
             }
-        } else {
+        } else if (type == 2) {
             int32_t *smap = slot_map + (int64_t)p * slot_map_stride;
             const int32_t tmp = smap[a];
             smap[a] = smap[b];
             smap[b] = tmp;
+        } else {
+            slot_map[(int64_t)p * slot_map_stride + a] = b;
         }
     }
     free(delta);

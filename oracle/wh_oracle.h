@@ -77,13 +77,17 @@ int or_eval_plans(const or_layout *g, int32_t n_orders, const int32_t *order_off
  *   type 0: swap orders a and b between their tours of `plan`,
  *   type 1: relocate order a into tour b of `plan` (b local to the plan),
  *   type 2: swap the locations of SKUs a and b in `plan`'s slotting
- *           (per-plan slottings only, slot_map_stride > 0).
+ *           (per-plan slottings only, slot_map_stride > 0);
+ *   type 3: relocate SKU a to location b, which must be empty in `plan`'s
+ *           slotting (no SKU maps to it; subroutine 4 of Sec. 5 weighs moves
+ *           into available empty places; per-plan slottings only).
  * Each move is applied to a copy of its plan, the whole plan is evaluated
  * before and after, and delta[2m], delta[2m+1] = (after - before) for the
  * S-shape and optimal rule.  status[m]: 0 applied, 1 infeasible (a changed
  * tour would exceed max_orders orders or max_lines lines; 0 = no cap),
- * 2 no-op (same tour or same SKU), 3 invalid (id out of range, order not in
- * the plan, SKU swap under a shared slotting).  Deltas are 0 unless the
+ * 2 no-op (same tour, same SKU, or the SKU already at b), 3 invalid (id out
+ * of range, order not in the plan, SKU move under a shared slotting, target
+ * location occupied).  Deltas are 0 unless the
  * status is 0. */
 int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off,
                   const int32_t *line_sku, int32_t n_sku, const int32_t *slot_map,
@@ -99,7 +103,8 @@ int or_eval_moves(const or_layout *g, int32_t n_orders, const int32_t *order_off
  * within the plan or -1.  The plans are edited in place: an order swap
  * exchanges the two entries of order_seq, a relocation removes the order from
  * its tour and appends it to the end of the target tour (tour_off shifts
- * between them), a SKU swap exchanges two entries of the plan's slotting. */
+ * between them), a SKU swap exchanges two entries of the plan's slotting, a
+ * relocation sets the SKU's entry to the new location. */
 int or_ls_step(const or_layout *g, int32_t n_orders, const int32_t *order_off, const int32_t *line_sku,
                int32_t n_sku, int32_t *slot_map, int64_t slot_map_stride, int32_t n_plans,
                const int32_t *plan_tour_off, int32_t *tour_off, int32_t *order_seq, const int32_t *moves,

@@ -54,3 +54,35 @@ def test_ls_trajectory_is_monotone():
         assert (new <= cost).all()
         assert ((new < cost) == (applied >= 0)).all()
         cost = new.copy()
+
+
+def test_ls_step_with_relocations():
+    """Relocations into empty locations mixed with the other moves: the
+    applied one follows the argmin rule, a relocation sets exactly the SKU's
+    slot and keeps the slotting injective."""
+    base = wh_gen.tiny(seed=13, n_plans=4)
+    lay = wh_gen.Layout(20, 30)
+    inst = wh_gen.Instance(lay, base.n_sku, base.order_off, base.line_sku, base.slot_map, base.plan_tour_off,
+                           base.tour_off, base.order_seq)
+    rng = np.random.default_rng(4)
+    maps = np.stack([rng.permutation(lay.n_loc)[:inst.n_sku] for _ in range(4)]).astype(np.int32)
+    M = 48
+    mv = np.concatenate([wh_gen.gen_moves(6, 0, inst, 16), wh_gen.gen_relocations(7, 0, inst, 32)], axis=1)
+    mv[..., 3] = np.arange(4)[:, None]
+    mv = mv.reshape(-1, 4)
+    d, st = oracle.eval_moves(inst, mv, 8, 0, slot_map=maps.ravel(), slot_map_stride=inst.n_sku)
+    to, seq, smap, applied = oracle.ls_step(inst, mv, M, 8, 0, slot_map=maps.ravel(), slot_map_stride=inst.n_sku)
+    smap = smap.reshape(4, -1)
+    n_reloc = 0
+    for p in range(4):
+        k = np.arange(p * M, (p + 1) * M)
+        ok = (st[k] == 0) & (d[k, 1] < 0)
+        want = -1 if not ok.any() else int(np.flatnonzero(ok)[np.argmin(d[k, 1][ok])])
+        assert applied[p] == want
+        assert len(set(smap[p].tolist())) == inst.n_sku
+        if want >= 0 and mv[p * M + want, 0] == 3:
+            n_reloc += 1
+            s, loc = mv[p * M + want, 1], mv[p * M + want, 2]
+            changed = np.flatnonzero(smap[p] != maps[p])
+            assert changed.tolist() == [s] and smap[p, s] == loc
+    assert n_reloc >= 1

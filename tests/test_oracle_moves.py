@@ -62,7 +62,7 @@ def expected(inst, move, maps=None, max_orders=0, max_lines=0):
         if (max_orders and len(tours[b]) > max_orders) or (max_lines and lines(tours[b]) > max_lines):
             return (0, 0), 1
         after = plan_cost(inst, tours, smap)
-    else:
+    elif typ == 2:
         if maps is None or not (0 <= a < inst.n_sku and 0 <= b < inst.n_sku):
             return (0, 0), 3
         if a == b:
@@ -70,6 +70,18 @@ def expected(inst, move, maps=None, max_orders=0, max_lines=0):
         m2 = smap.copy()
         m2[a], m2[b] = m2[b], m2[a]
         after = plan_cost(inst, tours, m2)
+    elif typ == 3:
+        if maps is None or not (0 <= a < inst.n_sku and 0 <= b < inst.layout.n_loc):
+            return (0, 0), 3
+        if smap[a] == b:
+            return (0, 0), 2
+        if b in set(smap.tolist()):
+            return (0, 0), 3                  # the target holds another SKU
+        m2 = smap.copy()
+        m2[a] = b
+        after = plan_cost(inst, tours, m2)
+    else:
+        return (0, 0), 3
     return (after[0] - before[0], after[1] - before[1]), 0
 
 
@@ -98,6 +110,33 @@ def test_sku_swaps_with_per_plan_slottings():
         want_d, want_st = expected(inst, tuple(mv[m]), maps=maps)
         assert st[m] == want_st and tuple(d[m]) == want_d, (m, mv[m])
     assert ((mv[:, 0] == 2) & (st == 0)).sum() > 5
+
+
+def half_full(seed, n_plans):
+    """tiny's orders on a 20 x 30 layout (1,200 locations for 600 SKUs): every
+    plan its own random slotting, half the locations empty."""
+    inst = wh_gen.tiny(seed=seed, n_plans=n_plans)
+    lay = wh_gen.Layout(20, 30)
+    rng = np.random.default_rng(seed)
+    maps = np.stack([rng.permutation(lay.n_loc)[:inst.n_sku] for _ in range(n_plans)]).astype(np.int32)
+    big = wh_gen.Instance(lay, inst.n_sku, inst.order_off, inst.line_sku, maps[0], inst.plan_tour_off,
+                          inst.tour_off, inst.order_seq)
+    return big, maps
+
+
+def test_relocations_into_empty_locations():
+    inst, maps = half_full(9, 3)
+    moves = wh_gen.gen_relocations(5, 0, inst, 40).reshape(-1, 4)
+    # a few targets that are the SKU's own location (no-op)
+    moves[::13, 2] = maps[moves[::13, 3], moves[::13, 1]]
+    d, st = oracle.eval_moves(inst, moves, slot_map=maps.ravel(), slot_map_stride=inst.n_sku)
+    for m in range(moves.shape[0]):
+        want_d, want_st = expected(inst, tuple(moves[m]), maps=maps)
+        assert st[m] == want_st and tuple(d[m]) == want_d, (m, moves[m])
+    assert (st == 0).sum() > 20 and (st == 3).sum() > 20 and (st == 2).sum() >= 5
+    # under a shared slotting relocations are invalid
+    _, st = oracle.eval_moves(inst, moves[:5])
+    assert (st == 3).all()
 
 
 def test_status_cases():

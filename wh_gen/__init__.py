@@ -61,6 +61,9 @@ def _load():
             lib.gen_moves.restype = ctypes.c_int
             lib.gen_moves.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p]
+            lib.gen_relocations.restype = ctypes.c_int
+            lib.gen_relocations.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p,
+                                            ctypes.c_int32, ctypes.c_int32, i32p]
             lib.gen_instance_param.restype = ctypes.c_int32
             lib.gen_instance_param.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_int32]
@@ -226,6 +229,16 @@ def gen_moves(seed: int, step: int, inst: Instance, moves_per_plan: int) -> np.n
     out = np.zeros((inst.n_plans, moves_per_plan, 4), np.int32)
     _check(lib.gen_moves(seed, step, inst.n_plans, moves_per_plan, inst.n_orders, _p(ntours), _p(pool),
                          pool.shape[0], inst.n_sku, _p(out)), "gen_moves")
+    return out
+
+
+def gen_relocations(seed: int, step: int, inst: Instance, moves_per_plan: int) -> np.ndarray:
+    """int32 [n_plans, moves_per_plan, 4] relocation moves {3, sku, location,
+    plan} (see gen.c)."""
+    pool = np.ascontiguousarray(np.unique(inst.line_sku).astype(np.int32))
+    out = np.zeros((inst.n_plans, moves_per_plan, 4), np.int32)
+    _check(_load().gen_relocations(seed, step, inst.n_plans, moves_per_plan, _p(pool), pool.shape[0],
+                                   inst.layout.n_loc, _p(out)), "gen_relocations")
     return out
 
 

@@ -37,6 +37,7 @@
 #define TAG_INST 7u
 #define TAG_CATEGORY 8u
 #define TAG_SIGN 9u
+#define TAG_RELOC 10u
 
 typedef struct { uint64_t s; } rng_t;
 
@@ -354,6 +355,26 @@ int gen_moves(uint64_t seed, int64_t step, int32_t n_plans, int32_t moves_per_pl
                 m[1] = sku_pool[below(&r, pool_n)];
                 m[2] = below(&r, n_sku);
             }
+        }
+    }
+    return GEN_OK;
+}
+
+/* Relocation moves {3, sku, location, plan}: the SKU drawn from sku_pool
+ * (SKUs that appear in orders), the target location uniform over the n_loc
+ * locations (occupied targets are the evaluator's to reject); plan = the
+ * plan index. */
+int gen_relocations(uint64_t seed, int64_t step, int32_t n_plans, int32_t moves_per_plan,
+                    const int32_t *sku_pool, int32_t pool_n, int32_t n_loc, int32_t *moves) {
+    if (moves_per_plan <= 0 || moves_per_plan > 256 || pool_n <= 0 || n_loc <= 0) return GEN_EINVAL;
+    for (int32_t p = 0; p < n_plans; ++p) {
+        for (int32_t k = 0; k < moves_per_plan; ++k) {
+            rng_t r = stream(seed, TAG_RELOC, ((uint64_t)step << 32) ^ ((uint64_t)p << 8) ^ (uint64_t)k);
+            int32_t *m = moves + ((int64_t)p * moves_per_plan + k) * 4;
+            m[0] = 3;
+            m[1] = sku_pool[below(&r, pool_n)];
+            m[2] = below(&r, n_loc);
+            m[3] = p;
         }
     }
     return GEN_OK;
