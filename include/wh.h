@@ -119,6 +119,11 @@ typedef struct wh_plans {
     const int32_t *plan_tour_off; /* [n_plans + 1] */
     const int32_t *tour_off;      /* [n_tours + 1] */
     const int32_t *order_seq;     /* [n_seq] */
+    /* Optional (may be NULL): per-plan location occupancy, bit (l & 31) of
+     * word p * ceil(n_locations / 32) + l / 32 set when a SKU of plan p sits
+     * at location l.  Needed only by relocation moves (wh_eval_moves type 3),
+     * built by wh_occupancy and kept current by wh_ls_apply. */
+    uint32_t *loc_used;
 } wh_plans;
 
 /* Outputs, caller-owned device memory; any pointer may be NULL to skip it.
@@ -156,14 +161,18 @@ int wh_eval_plans(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  *   type 1: relocate order a into tour b of `plan` (b counted from the
  *           plan's first tour);
  *   type 2: swap the locations of SKUs a and b in `plan`'s slotting (only
- *           with per-plan slottings, slot_map_stride > 0).
+ *           with per-plan slottings, slot_map_stride > 0);
+ *   type 3: relocate SKU a to location b, which must be empty in `plan`'s
+ *           slotting (subroutine 4 weighs moves into available empty places;
+ *           per-plan slottings and plans->loc_used, see wh_occupancy).
  * delta[2m], delta[2m+1] receive (after - before) of the plan's S-shape and
  * optimal cost; only the tours the move changes are re-costed, against their
  * current costs tour_s / tour_rr (the wh_eval_plans output for `plans`).
  * status[m]: 0 evaluated, 1 infeasible (a changed tour would exceed
  * max_orders_per_tour orders or max_lines_per_tour lines; 0 = no cap), 2 no-op
- * (same tour, same SKU), 3 invalid (id out of range, order not in the plan,
- * SKU swap under a shared slotting, or a malformed tour); deltas are 0 unless
+ * (same tour, same SKU, SKU already at the target), 3 invalid (id out of
+ * range, order not in the plan, SKU move under a shared slotting, relocation
+ * onto an occupied location or without loc_used, or a malformed tour); deltas are 0 unless
  * the status is 0.  Each plan must hold every order at most once.
  * All arrays are device memory.  The call synchronises `stream` twice (to
  * size its task list, then the record matrix of the tasks of more than 64
@@ -183,7 +192,8 @@ int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * pointers of `plans` are written): an order swap exchanges two entries of
  * order_seq; a relocation removes the order from its tour and appends it to
  * the end of the target tour, shifting order_seq and tour_off between them; a
- * SKU swap exchanges two entries of the plan's slotting.  costs (may be NULL):
+ * SKU swap exchanges two entries of the plan's slotting; a relocation sets the
+ * SKU's entry and, with plans->loc_used, moves its occupancy bit.  costs (may be NULL):
  * the plans' current per-tour and per-plan costs, updated in place for the
  * applied moves from the new tour costs that the wh_eval_moves call which
  * scored exactly these moves (same `moves` pointer, the last move evaluation
@@ -198,6 +208,14 @@ int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
 int wh_ls_apply(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, const int32_t *moves,
                 int32_t moves_per_plan, const int64_t *delta, const int32_t *status, int32_t *applied,
                 const wh_costs *costs, uint8_t *tour_changed, void *stream);
+
+/* Occupancy bits of every plan's slotting, for relocation moves: writes
+ * plans->loc_used (device, caller-owned, n_plans * ceil(n_locations / 32)
+ * words) with bit l of plan p set when some SKU of plan p sits at location l.
+ * Needs per-plan slottings (slot_map_stride > 0).  wh_ls_apply keeps the bits
+ * current as it applies relocations.  Asynchronous on `stream`; allocates
+ * nothing.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_occupancy(wh_layout *layout, const wh_orders *orders, const wh_plans *plans, void *stream);
 
 /* Batch formation (Sec. 5 and Sec. 6: clustering the orders and suggesting
  * which orders are picked together): for each of n_maps slottings

@@ -47,7 +47,7 @@ class wh_plans(ctypes.Structure):
     _fields_ = [("n_plans", ctypes.c_int32), ("n_tours", ctypes.c_int32), ("n_seq", ctypes.c_int64),
                 ("slot_map", ctypes.c_void_p), ("slot_map_stride", ctypes.c_int64),
                 ("plan_tour_off", ctypes.c_void_p), ("tour_off", ctypes.c_void_p),
-                ("order_seq", ctypes.c_void_p)]
+                ("order_seq", ctypes.c_void_p), ("loc_used", ctypes.c_void_p)]
 
 
 class wh_costs(ctypes.Structure):
@@ -107,6 +107,8 @@ SIGNATURES = {
     "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_occupancy": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
+                                    ctypes.c_void_p]),
     "wh_kmeans_slotting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -282,6 +284,7 @@ class DeviceProblem:
     order_seq: object
     n_sku: int
     slot_map_stride: int = 0
+    loc_used: object = None     # per-plan occupancy bits (relocation moves), see occupancy()
 
     @property
     def n_plans(self) -> int:
@@ -298,7 +301,7 @@ class DeviceProblem:
     def plans(self) -> wh_plans:
         return wh_plans(self.n_plans, self.n_tours, int(self.order_seq.shape[0]), _ptr(self.slot_map),
                         self.slot_map_stride, _ptr(self.plan_tour_off), _ptr(self.tour_off),
-                        _ptr(self.order_seq))
+                        _ptr(self.order_seq), _ptr(self.loc_used))
 
 
 def to_device(inst, device="cuda", slot_map=None, slot_map_stride: int = 0) -> DeviceProblem:
@@ -411,6 +414,18 @@ class Layout:
         wh_batch_grow(self.handle, prob.orders(), _ptr(maps), prob.n_sku, n_maps, max_orders, max_lines,
                       _ptr(tour_off), _ptr(order_seq), _ptr(n_tours), stream)
         return tour_off, order_seq[:, :n_orders], n_tours
+
+    def occupancy(self, prob: DeviceProblem, stream=None):
+        """Build prob.loc_used (per-plan occupancy bits, int32 device tensor)
+        from prob's per-plan slottings, for relocation moves; returns it."""
+        import torch
+        words = (self.desc[0] * 2 * self.desc[1] + 31) // 32
+        if prob.loc_used is None or prob.loc_used.numel() != prob.n_plans * words:
+            prob.loc_used = torch.zeros(max(prob.n_plans * words, 1), dtype=torch.int32,
+                                        device=prob.order_off.device)
+        _check(load().wh_occupancy(self.handle, ctypes.byref(prob.orders()), ctypes.byref(prob.plans()),
+                                   _stream_ptr(stream)), "wh_occupancy")
+        return prob.loc_used
 
     def kmeans_slotting(self, prob: DeviceProblem, signs, k: int, iters: int, freq_weight: int = 64, init=None,
                         u=None, stream=None):

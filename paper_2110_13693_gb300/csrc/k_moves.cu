@@ -176,6 +176,18 @@ __global__ void k_mv_count(MoveArgs M) {
                         cnt = (M.sku_off[mv.y + 1] - M.sku_off[mv.y]) + (M.sku_off[mv.z + 1] - M.sku_off[mv.z]);
                     }
                 }
+            } else if (mv.x == 3) {
+                // relocation of SKU mv.y to location mv.z, which must be empty
+                if (a.slot_stride > 0 && a.loc_used && (unsigned)mv.y < (unsigned)a.n_sku &&
+                    (unsigned)mv.z < (unsigned)a.g.n_loc) {
+                    const int words = (a.g.n_loc + 31) >> 5;
+                    const uint32_t used = a.loc_used[(int64_t)p * words + (mv.z >> 5)] >> (mv.z & 31) & 1u;
+                    if (a.slot_map[(int64_t)p * a.slot_stride + mv.y] == mv.z) st = 2;
+                    else if (!used) {
+                        st = 0;
+                        cnt = M.sku_off[mv.y + 1] - M.sku_off[mv.y];
+                    }
+                }
             }
         }
         M.mstatus[m] = st;
@@ -270,7 +282,7 @@ __global__ void k_mv_fill(MoveArgs M) {
             out[1] = make_int4(m, tb, mv.y, -1);
         } else {
             int k = 0;
-            for (int side = 0; side < 2; ++side) {
+            for (int side = 0; side < (mv.x == 2 ? 2 : 1); ++side) {
                 const int s = side ? mv.z : mv.y;
                 for (int i = M.sku_off[s]; i < M.sku_off[s + 1]; ++i) {
                     const int o = M.sku_orders[i];
@@ -281,11 +293,16 @@ __global__ void k_mv_fill(MoveArgs M) {
     }
 }
 
-// Location of SKU s under the task's slotting (swapped pair for SKU swaps).
-__device__ __forceinline__ int task_loc(const int32_t* map, int s, bool swap, int s1, int s2) {
-    if (swap) s = s == s1 ? s2 : (s == s2 ? s1 : s);
+// Location of SKU s under the move's slotting: the swapped pair for a SKU
+// swap, the target location for the relocated SKU.
+__device__ __forceinline__ int task_loc(const int32_t* map, int s, const int4 mv) {
+    if (mv.x == 2) s = s == mv.y ? mv.z : (s == mv.z ? mv.y : s);
+    else if (mv.x == 3 && s == mv.y) return mv.z;
     return map[s];
 }
+
+// the line's SKU is one the SKU move changes
+__device__ __forceinline__ bool sku_hit(int s, const int4 mv) { return s == mv.y || (mv.x == 2 && s == mv.z); }
 
 // Walk the changed tour of task `tk`: calls emit(key) for every line, in
 // order; returns false on an invalid id.  For SKU-swap tasks also reports
@@ -294,7 +311,7 @@ template <typename Emit>
 __device__ __forceinline__ bool walk_task(const MoveArgs& M, const int4 tk, const int4 mv, bool& primary,
                                           Emit emit) {
     const EvalArgs& a = M.a;
-    const bool swap = mv.x == 2;
+    const bool swap = mv.x >= 2;   // SKU moves: swap or relocation
     const int32_t* map = a.slot_map + (int64_t)mv.w * a.slot_stride;
     const int q0 = a.tour_off[tk.y], q1 = a.tour_off[tk.y + 1];
     const int add = (!swap && tk.z >= 0) ? tk.z : -1;
@@ -333,11 +350,11 @@ __device__ __forceinline__ bool walk_task(const MoveArgs& M, const int4 tk, cons
                 if (l + j >= le) continue;
                 const int sj = sk[j];
                 if ((unsigned)sj >= (unsigned)a.n_sku) { ok = false; continue; }
-                if (swap && (sj == mv.y || sj == mv.z)) {
+                if (swap && sku_hit(sj, mv)) {
                     hit_min = min(hit_min, o);
                     if (o == tk.z && sj == mv.y) own_has_s1 = true;
                 }
-                loc[j] = task_loc(map, sj, swap, mv.y, mv.z);
+                loc[j] = task_loc(map, sj, mv);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -431,7 +448,7 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
 __device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk, const int4 mv, uint32_t* kb,
                                                int cap, int lane, int& n_out, bool& primary) {
     const EvalArgs& a = M.a;
-    const bool swap = mv.x == 2;
+    const bool swap = mv.x >= 2;   // SKU moves: swap or relocation
     const int32_t* map = a.slot_map + (int64_t)mv.w * a.slot_stride;
     const int q0 = a.tour_off[tk.y], q1 = a.tour_off[tk.y + 1];
     const int add = (!swap && tk.z >= 0) ? tk.z : -1;
@@ -454,11 +471,11 @@ __device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk,
         for (int l = lb; l < le; ++l, ++pos) {
             const int s = a.line_sku[l];
             if ((unsigned)s >= (unsigned)a.n_sku) { bad = true; break; }
-            if (swap && (s == mv.y || s == mv.z)) {
+            if (swap && sku_hit(s, mv)) {
                 hit_min = min(hit_min, o);
                 if (o == tk.z && s == mv.y) own_has_s1 = true;
             }
-            const int loc = task_loc(map, s, swap, mv.y, mv.z);
+            const int loc = task_loc(map, s, mv);
             if ((unsigned)loc >= (unsigned)a.g.n_loc) { bad = true; break; }
             if (pos < cap) kb[pos] = loc_key(a.g, loc);
         }
@@ -594,6 +611,19 @@ int grid_of(int64_t n, int threads, int cap = 8192) {
     int64_t g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
     return g < 1 ? 1 : (int)g;
+}
+
+// occupancy bits of every plan's slotting (relocation moves): bit l of plan
+// p set when a SKU of p sits at location l (ids outside the layout skipped)
+__global__ void k_occupancy(const int32_t* slot_map, int64_t stride, int32_t n_plans, int32_t n_sku, int32_t n_loc,
+                            uint32_t* used) {
+    const int64_t total = (int64_t)n_plans * n_sku;
+    const int words = (n_loc + 31) >> 5;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i / n_sku, s = i - p * n_sku;
+        const int loc = slot_map[p * stride + s];
+        if ((unsigned)loc < (unsigned)n_loc) atomicOr(&used[p * words + (loc >> 5)], 1u << (loc & 31));
+    }
 }
 
 }  // namespace
@@ -743,6 +773,16 @@ __global__ void k_ls_apply(LsArgs L) {
                 const int32_t x = smap[mv.y];
                 smap[mv.y] = smap[mv.z];
                 smap[mv.z] = x;
+            } else if (mv.x == 3 && tid == 0) {
+                // relocation: the SKU's entry and the plan's occupancy bits
+                int32_t* smap = const_cast<int32_t*>(a.slot_map) + (int64_t)p * a.slot_stride;
+                const int32_t old = smap[mv.y];
+                smap[mv.y] = mv.z;
+                if (a.loc_used) {
+                    uint32_t* used = a.loc_used + (int64_t)p * ((a.g.n_loc + 31) >> 5);
+                    if ((unsigned)old < (unsigned)a.g.n_loc) used[old >> 5] &= ~(1u << (old & 31));
+                    used[mv.z >> 5] |= 1u << (mv.z & 31);
+                }
             }
             // costs: the changed tours take their tasks' new costs, the plan its delta
             if (L.task_cost && L.applied[p] == k) {
@@ -785,7 +825,7 @@ __global__ void __launch_bounds__(TF_THREADS) k_task_features(MoveArgs M, FeatCo
         uint32_t n_lines = 0;
         if (tk.y >= 0 && tk.y < a.n_tours) {
             const int4 mv = M.moves[tk.x];
-            const bool swap = mv.x == 2;
+            const bool swap = mv.x >= 2;   // SKU moves: swap or relocation
             const int32_t* map = a.slot_map + (int64_t)mv.w * a.slot_stride;
             const int q0 = a.tour_off[tk.y], q1 = a.tour_off[tk.y + 1];
             const int add = (!swap && tk.z >= 0) ? tk.z : -1;
@@ -804,11 +844,11 @@ __global__ void __launch_bounds__(TF_THREADS) k_task_features(MoveArgs M, FeatCo
                 for (int l = lb; l < le; ++l) {
                     const int s = a.line_sku[l];
                     if ((unsigned)s >= (unsigned)a.n_sku) { bad = true; break; }
-                    if (swap && (s == mv.y || s == mv.z)) {
+                    if (swap && sku_hit(s, mv)) {
                         hit_min = min(hit_min, o);
                         if (o == tk.z && s == mv.y) own_has_s1 = true;
                     }
-                    const int loc = task_loc(map, s, swap, mv.y, mv.z);
+                    const int loc = task_loc(map, s, mv);
                     if ((unsigned)loc >= (unsigned)a.g.n_loc) { bad = true; break; }
                     over |= !wf_insert(w, loc_key(a.g, loc));
                     ++n_lines;
@@ -909,4 +949,18 @@ cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+}  // namespace wh
+
+namespace wh {
+cudaError_t launch_occupancy(const int32_t* slot_map, int64_t stride, int32_t n_plans, int32_t n_sku, int32_t n_loc,
+                             uint32_t* used, int num_sms, cudaStream_t st) {
+    const size_t words = (size_t)((n_loc + 31) >> 5) * (size_t)n_plans;
+    cudaError_t e = cudaMemsetAsync(used, 0, words * sizeof(uint32_t), st);
+    if (e != cudaSuccess || n_plans == 0 || n_sku == 0) return e;
+    const int64_t total = (int64_t)n_plans * n_sku;
+    const int64_t want = (total + 255) / 256;
+    const int grid = (int)(want < (int64_t)num_sms * 16 ? want : (int64_t)num_sms * 16);
+    k_occupancy<<<grid, 256, 0, st>>>(slot_map, stride, n_plans, n_sku, n_loc, used);
+    return cudaGetLastError();
+}
 }  // namespace wh

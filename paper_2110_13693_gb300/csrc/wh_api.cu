@@ -161,6 +161,7 @@ void fill_args(wh::EvalArgs& a, const wh::Geo& g, const wh_orders& o, const wh_p
     a.line_sku = o.line_sku;
     a.slot_map = p.slot_map;
     a.slot_stride = p.slot_map_stride;
+    a.loc_used = p.loc_used;
     a.n_plans = p.n_plans;
     a.n_tours = p.n_tours;
     a.n_seq = p.n_seq;
@@ -636,6 +637,21 @@ extern "C" int wh_batch_grow(wh_layout* h, const wh_orders* orders, const int32_
     B.order_seq = order_seq;
     B.n_tours = n_tours;
     return wh::launch_batch_grow(B, n_maps, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
+extern "C" int wh_occupancy(wh_layout* h, const wh_orders* orders, const wh_plans* plans, void* stream) {
+    if (!h || !orders || !plans) return WH_EINVAL;
+    const wh_orders o = *orders;
+    const wh_plans p = *plans;
+    if (p.n_plans < 0 || o.n_sku < 0 || p.slot_map_stride < o.n_sku || p.slot_map_stride <= 0) return WH_EINVAL;
+    if (p.n_plans == 0) return WH_OK;
+    if (!p.loc_used || (o.n_sku > 0 && !p.slot_map)) return WH_EINVAL;
+    int rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    return wh::launch_occupancy(p.slot_map, p.slot_map_stride, p.n_plans, o.n_sku, h->g.n_loc, p.loc_used,
+                                h->num_sms, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? WH_OK
+               : WH_ECUDA;
 }
 
 extern "C" int wh_kmeans_slotting(wh_layout* h, const wh_orders* orders, const int8_t* signs, int32_t freq_weight,

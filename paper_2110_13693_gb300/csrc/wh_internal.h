@@ -29,6 +29,7 @@ struct EvalArgs {
     const uint32_t* line_key;   // shared slotting: key of every line (scratch)
     const int32_t* slot_map;
     int64_t slot_stride;        // 0: shared slotting
+    uint32_t* loc_used;         // per-plan occupancy bits or null (relocation moves)
     int32_t n_plans, n_tours;
     int64_t n_seq;
     const int32_t* plan_tour_off;
@@ -155,6 +156,9 @@ struct BatchGrowArgs {
 };
 size_t batch_grow_smem_bytes(int n_orders, int n_lines, int A);
 cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s);
+
+cudaError_t launch_occupancy(const int32_t* slot_map, int64_t stride, int32_t n_plans, int32_t n_sku, int32_t n_loc,
+                             uint32_t* used, int num_sms, cudaStream_t st);
 
 // K-means slotting (k_kmeans.cu)
 constexpr int KM_DIM = 32;       // feature row: 31 sketch coordinates + the pick-count coordinate

@@ -9,11 +9,13 @@ import wh_gen
 pytestmark = pytest.mark.gpu
 
 
-def gpu_moves(wh, inst, moves, max_orders=0, max_lines=0, maps=None):
+def gpu_moves(wh, inst, moves, max_orders=0, max_lines=0, maps=None, occupancy=True):
     import torch
     lay = wh.Layout.of(inst.layout)
     stride = inst.n_sku if maps is not None else 0
     prob = wh.to_device(inst, slot_map=None if maps is None else maps.ravel(), slot_map_stride=stride)
+    if maps is not None and occupancy:
+        lay.occupancy(prob)
     costs = wh.evaluate(lay, prob)
     mv = torch.as_tensor(np.ascontiguousarray(moves.reshape(-1, 4)), dtype=torch.int32).cuda()
     delta, status = lay.eval_moves(prob, costs, mv, max_orders, max_lines)
@@ -167,3 +169,49 @@ def test_paperscale_full_size_sampled(gpu_lib):
         wd, ws = oracle.eval_moves(one, m1[None], 24, 0, slot_map=inst.slot_map, slot_map_stride=inst.n_sku)
         assert s[k] == ws[0] and (d[k] == wd[0]).all(), (k, mv[k], d[k], wd[0], s[k], ws[0])
     lay.close()
+
+
+def half_full(seed, n_plans):
+    """tiny's orders on a 20 x 30 layout: per-plan random slottings of the 600
+    SKUs over 1,200 locations (half of them empty)."""
+    inst = wh_gen.tiny(seed=seed, n_plans=n_plans)
+    lay = wh_gen.Layout(20, 30)
+    rng = np.random.default_rng(seed)
+    maps = np.stack([rng.permutation(lay.n_loc)[:inst.n_sku] for _ in range(n_plans)]).astype(np.int32)
+    return wh_gen.Instance(lay, inst.n_sku, inst.order_off, inst.line_sku, maps[0], inst.plan_tour_off,
+                           inst.tour_off, inst.order_seq), maps
+
+
+def relocation_moves(inst, maps, seed, per_plan):
+    mv = wh_gen.gen_relocations(seed, 0, inst, per_plan).reshape(-1, 4)
+    mv[::11, 2] = maps[mv[::11, 3], mv[::11, 1]]          # some onto the SKU's own location (no-op)
+    return mv
+
+
+def test_relocations_into_empty_locations(gpu_lib):
+    inst, maps = half_full(21, 6)
+    mv = np.concatenate([moves_for(inst, 5, 32), relocation_moves(inst, maps, 6, 48)])
+    s, st = check(gpu_lib, inst, mv, max_orders=8, maps=maps)
+    r = mv[:, 0] == 3
+    assert st == 0 and (s[r] == 0).sum() > 100 and (s[r] == 3).sum() > 80 and (s[r] == 2).sum() > 10
+
+
+def test_relocations_paperscale(gpu_lib):
+    """50,000 SKUs over 200,000 locations: relocations of the most popular
+    SKUs (in most tours of a plan, long tours included) and of random ones."""
+    inst = wh_gen.paperscale(seed=6, n_plans=3)
+    maps = np.tile(inst.slot_map, (3, 1)).astype(np.int32)
+    mv = relocation_moves(inst, maps, 8, 40)
+    hot = np.asarray([[3, 0, 199_999, 0], [3, 1, 150_000, 1], [3, 2, 123_457, 2], [3, 0, int(maps[0, 1]), 0]],
+                     np.int32)
+    s, st = check(gpu_lib, inst, np.concatenate([mv, hot]), max_orders=24, maps=maps)
+    assert st == 0 and (s == 0).sum() > 60
+
+
+def test_relocation_needs_occupancy_bits(gpu_lib):
+    inst, maps = half_full(22, 2)
+    mv = relocation_moves(inst, maps, 9, 16)
+    d, s, st = gpu_moves(gpu_lib, inst, mv, maps=maps, occupancy=False)
+    assert (s == 3).all() and (d == 0).all()
+    d, s, st = gpu_moves(gpu_lib, inst, mv[:4])            # shared slotting
+    assert (s == 3).all()
