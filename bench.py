@@ -595,6 +595,7 @@ def run_surrogate_ab(wh, dev, steps, train_steps):
 # -------------------------------------------------------------- our arm
 
 def run_ours(args):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -656,11 +657,15 @@ def run_ours(args):
     value = total_tours / (elapsed_ms / 1e3)
 
     # ---- end to end through the public API from pinned host memory
+    # order ids cross the host link as 16-bit values (n_orders <= 65,536) and
+    # are widened on the device (wh_widen_u16): the link, ~209 GB/s host to
+    # device on this machine, is the end-to-end bound
     host = []
     for b in batches:
+        seq = (b.order_seq.astype(np.uint16).view(np.int16) if b.n_orders <= 65536 else b.order_seq)
         hp = wh.DeviceProblem(*(torch.as_tensor(getattr(b, f)).pin_memory() for f in
-                                ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off", "order_seq")),
-                              b.n_sku)
+                                ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off")),
+                              torch.as_tensor(seq).pin_memory(), b.n_sku)
         host.append(hp)
     # every step copies its own inputs in and its plan costs back; the copy of
     # a step overlaps the evaluation of the previous one (HostPipeline: a copy

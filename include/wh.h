@@ -467,6 +467,13 @@ int wh_batch_get_status(wh_batch *b, void *stream, uint32_t *status);
 /* Release the batch (device memory and graphs).  NULL is a no-op. */
 void wh_batch_destroy(wh_batch *b);
 
+/* Widen n unsigned 16-bit values to int32, device to device (src and dst
+ * device memory, caller-owned, not overlapping).  Order ids fit 16 bits when
+ * n_orders <= 65,536, so host-resident plans can cross the host link at half
+ * the bytes and be widened on the device before wh_eval_plans.  Asynchronous
+ * on `stream`; allocates nothing.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_widen_u16(const uint16_t *src, int32_t *dst, int64_t n, void *stream);
+
 /* Read and clear the device status word of `layout` (WH_STATUS_* bits of all
  * calls since the last read).  Synchronises `stream`.  Returns WH_OK,
  * WH_EINVAL or WH_ECUDA. */

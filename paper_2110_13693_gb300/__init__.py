@@ -107,6 +107,7 @@ SIGNATURES = {
     "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_widen_u16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "wh_occupancy": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.POINTER(wh_plans),
                                     ctypes.c_void_p]),
     "wh_kmeans_slotting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p,
@@ -524,10 +525,14 @@ class HostPipeline:
         self.copy, self.compute = torch.cuda.Stream(), torch.cuda.Stream()
         self.copied = [torch.cuda.Event() for _ in self.bufs]
         self.done = [torch.cuda.Event() for _ in self.bufs]
+        self.stage16 = [None for _ in self.bufs]      # device landing buffers of 16-bit order ids
         self.k = 0
 
     def submit(self, host: DeviceProblem, host_plan_out):
-        """Enqueue one batch; returns (ticket, bytes host->device, bytes device->host)."""
+        """Enqueue one batch; returns (ticket, bytes host->device, bytes device->host).
+        host.order_seq may be int16 (order ids as unsigned 16-bit values, for
+        n_orders <= 65,536): it crosses the link at 2 bytes per id and is
+        widened on the device (wh_widen_u16) into the slot's int32 buffer."""
         import torch
         slot = self.k % len(self.bufs)
         self.k += 1
@@ -537,7 +542,15 @@ class HostPipeline:
         with torch.cuda.stream(self.copy):
             for name in ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off", "order_seq"):
                 src, dst = getattr(host, name), getattr(dev, name)
-                dst.copy_(src, non_blocking=True)
+                if name == "order_seq" and src.dtype == torch.int16:
+                    st = self.stage16[slot]
+                    if st is None or st.numel() != src.numel():
+                        st = self.stage16[slot] = torch.empty(src.numel(), dtype=torch.int16, device=dst.device)
+                    st.copy_(src, non_blocking=True)
+                    _check(load().wh_widen_u16(ctypes.c_void_p(_ptr(st)), ctypes.c_void_p(_ptr(dst)), src.numel(),
+                                               _stream_ptr(self.copy)), "wh_widen_u16")
+                else:
+                    dst.copy_(src, non_blocking=True)
                 h2d += src.numel() * src.element_size()
             self.copied[slot].record(self.copy)
         self.compute.wait_event(self.copied[slot])

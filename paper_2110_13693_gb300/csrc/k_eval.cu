@@ -806,4 +806,38 @@ cudaError_t launch_eval_long(const LongArgs& L, bool shared_map, int num_sms, cu
     return cudaGetLastError();
 }
 
+
+// 16-bit order ids (as shipped from the host when n_orders <= 65,536)
+// widened to the int32 ids the evaluator reads: eight ids per thread step
+// when both buffers are 16-byte aligned, one otherwise
+namespace {
+__global__ void k_widen_u16(const uint16_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n, bool vec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n8 = n >> 3;
+        const uint4* s8 = reinterpret_cast<const uint4*>(src);
+        int4* d4 = reinterpret_cast<int4*>(dst);
+        for (int64_t j = i; j < n8; j += stride) {
+            const uint4 v = s8[j];
+            d4[2 * j] = make_int4((int)(v.x & 0xFFFFu), (int)(v.x >> 16), (int)(v.y & 0xFFFFu), (int)(v.y >> 16));
+            d4[2 * j + 1] = make_int4((int)(v.z & 0xFFFFu), (int)(v.z >> 16), (int)(v.w & 0xFFFFu), (int)(v.w >> 16));
+        }
+        done = n8 << 3;
+    }
+    for (int64_t j = done + i; j < n; j += stride) dst[j] = (int32_t)src[j];
+}
+}  // namespace
+
+cudaError_t launch_widen_u16(const uint16_t* src, int32_t* dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    const int64_t work = vec ? (n >> 3) + 1 : n;
+    int64_t grid = (work + 255) / 256;
+    if (grid > 2048) grid = 2048;
+    k_widen_u16<<<(int)grid, 256, 0, s>>>(src, dst, n, vec);
+    return cudaGetLastError();
+}
+
 }  // namespace wh

@@ -756,6 +756,11 @@ extern "C" int wh_routes(wh_layout* h, const wh_orders* orders, const wh_plans* 
                : WH_ECUDA;
 }
 
+extern "C" int wh_widen_u16(const uint16_t* src, int32_t* dst, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!src || !dst))) return WH_EINVAL;
+    return wh::launch_widen_u16(src, dst, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
 extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) {
     if (!h || !status) return WH_EINVAL;
     if (h->device < 0) {

@@ -160,6 +160,8 @@ cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s
 cudaError_t launch_occupancy(const int32_t* slot_map, int64_t stride, int32_t n_plans, int32_t n_sku, int32_t n_loc,
                              uint32_t* used, int num_sms, cudaStream_t st);
 
+cudaError_t launch_widen_u16(const uint16_t* src, int32_t* dst, int64_t n, cudaStream_t s);
+
 // K-means slotting (k_kmeans.cu)
 constexpr int KM_DIM = 32;       // feature row: 31 sketch coordinates + the pick-count coordinate
 constexpr int KM_SKETCH = 31;

@@ -344,3 +344,37 @@ def test_host_pipeline_matches_oracle(gpu_lib):
         assert np.array_equal(out[0].numpy(), want[2]) and np.array_equal(out[1].numpy(), want[3])
     assert lay.status() == 0
     lay.close()
+
+
+def test_host_pipeline_16bit_order_ids(gpu_lib):
+    """Order ids shipped as 16 bits and widened on the device give the same
+    plan costs as the int32 path; ids above 32,767 survive the widening."""
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.midsize(seed=44, n_plans=32)
+    lay = wh.Layout.of(inst.layout)
+    fields = ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off")
+    host = wh.DeviceProblem(*(torch.as_tensor(getattr(inst, f)).pin_memory() for f in fields),
+                            torch.as_tensor(inst.order_seq.astype(np.uint16).view(np.int16)).pin_memory(),
+                            inst.n_sku)
+    prob = wh.to_device(inst)
+    out = torch.zeros((2, inst.n_plans), dtype=torch.int64).pin_memory()
+    pipe = wh.HostPipeline(lay, [(prob, wh.alloc_costs(prob.n_tours, prob.n_plans))], 3)
+    ticket, h2d, _ = pipe.submit(host, out)
+    pipe.wait(ticket)
+    assert h2d == sum(getattr(inst, f).nbytes for f in fields) + 2 * inst.order_seq.size
+    assert np.array_equal(prob.order_seq.cpu().numpy(), inst.order_seq)
+    want = oracle.eval_plans(inst)
+    assert np.array_equal(out[0].numpy(), want[2]) and np.array_equal(out[1].numpy(), want[3])
+    # the widening alone, on values across the whole 16-bit range and a ragged tail
+    vals = np.arange(0, 65536, 7, dtype=np.uint16)
+    src_all = torch.as_tensor(vals.view(np.int16)).cuda()
+    for off in (0, 1, 3):                       # 1 and 3: unaligned buffers take the scalar path
+        src = src_all[off:]
+        dst = torch.full((src.numel() + off,), -1, dtype=torch.int32, device="cuda")[off:]
+        wh._check(wh.load().wh_widen_u16(wh.ctypes.c_void_p(src.data_ptr()), wh.ctypes.c_void_p(dst.data_ptr()),
+                                         src.numel(), None), "wh_widen_u16")
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.cpu().numpy(), vals[off:].astype(np.int32))
+    assert lay.status() == 0
+    lay.close()
