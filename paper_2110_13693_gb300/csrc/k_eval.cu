@@ -271,8 +271,11 @@ __global__ void k_prep_batch(BatchArgs b) {
         prep_instance(b.insts[i], b.mask, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+// 16-bit keys: 384-thread CTAs, two per SM (24 warps; 85 registers a thread
+// fit the sort without spills, and one copy of the order book per CTA keeps
+// the shared-memory tables at two copies per SM); 32-bit keys: 256 threads
 template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
-__global__ void __launch_bounds__(256, 2) k_eval_short(EvalArgs a) {
+__global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_short(EvalArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);
@@ -770,10 +773,16 @@ cudaError_t launch_prep_batch(const BatchArgs& b, int max_work, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& t, int num_sms, cudaStream_t s, int* grid_out) {
-    if (t.threads % 32 != 0 || t.threads > 256 || t.threads < 32) return cudaErrorInvalidValue;
+cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& tune, int num_sms, cudaStream_t s, int* grid_out) {
+    const bool k16_ok = tune.key16 && key16_ok(a.g);
+    if (tune.threads % 32 != 0 || tune.threads > (k16_ok ? 384 : 256) || tune.threads < 32) return cudaErrorInvalidValue;
     if (a.n_tours == 0) return cudaSuccess;
-    if (sshape_kernel_applies(a)) return launch_sshape(a, t, num_sms, s, grid_out);
+    if (sshape_kernel_applies(a)) {
+        Tuning ts = tune;
+        if (ts.threads > 256) ts.threads = 256;
+        return launch_sshape(a, ts, num_sms, s, grid_out);
+    }
+    const Tuning& t = tune;
     const size_t smem = eval_short_smem_bytes(a, t);
     const bool shared_map = a.slot_stride == 0;
     const bool k16 = t.key16 && key16_ok(a.g);

@@ -222,10 +222,10 @@ int reserve_scratch(wh_layout* h, size_t bytes) { return grow(&h->scratch, &h->s
 
 wh::Tuning default_tuning(const wh::EvalArgs& a) {
     wh::Tuning t;
-    t.threads = 256;
     t.key16 = 1;
+    t.threads = wh::key16_ok(a.g) ? 384 : 256;
     t.smem_tables = 1;
-    // keep two 256-thread CTAs per SM; larger order books stay in global memory
+    // keep two CTAs per SM; larger order books stay in global memory
     if (wh::eval_short_smem_bytes(a, t) > 112 * 1024) t.smem_tables = 0;
     return t;
 }
