@@ -212,19 +212,28 @@ __global__ void __launch_bounds__(KM_T) k_km_pp_round(KmArgs A, int c) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // total and the block holding the draw
+    // the block holding the draw: every thread sums a contiguous run of the
+    // block sums, a block scan of the runs gives each run's start, and the
+    // thread whose run covers the target finds the block inside it
+    const int nb = (int)gridDim.x, per = (nb + KM_T - 1) / KM_T;
+    const int b0 = min((int)threadIdx.x * per, nb), b1 = min(b0 + per, nb);
     long long part = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += KM_T) part += __ldcg(A.bsum + b);
-    const long long total = block_sum_ll(part, red);
-    if (threadIdx.x == 0) {
-        s_pick = -1;
-        if (total == 0) {
-            s_pick = (int)(A.u[c] % (unsigned long long)A.n_sku);
-        } else {
-            const long long target = (long long)(A.u[c] % (unsigned long long)total);
-            long long run = 0;
-            int b = 0;
-            for (; b < (int)gridDim.x; ++b) {
+    for (int b = b0; b < b1; ++b) part += __ldcg(A.bsum + b);
+    const long long incl = block_scan_ll(part, red);
+    __shared__ long long s_total;
+    if (threadIdx.x == KM_T - 1) s_total = incl;
+    if (threadIdx.x == 0) s_pick = -1;
+    __syncthreads();
+    const long long tot = s_total;
+    if (tot == 0) {
+        if (threadIdx.x == 0) s_pick = (int)(A.u[c] % (unsigned long long)A.n_sku);
+    } else {
+        const long long target = (long long)(A.u[c] % (unsigned long long)tot);
+        const long long excl = incl - part;
+        if (part > 0 && excl <= target && target < incl) {
+            long long run = excl;
+            int b = b0;
+            for (; b < b1; ++b) {
                 const long long v = __ldcg(A.bsum + b);
                 if (run + v > target) break;
                 run += v;
