@@ -266,6 +266,15 @@ __global__ void k_km_gather(KmArgs A) {
     A.cent[i] = A.x[(int64_t)A.seeds[c] * KM_DIM + j];
 }
 
+// |c|^2 - 2 x.c: the squared distance less |x|^2, a constant per row, so the
+// nearest centroid and its ties are the same; fits int32 by the same bounds
+__device__ __forceinline__ int32_t dist_less_norm(const int32_t (&x)[KM_DIM], const int32_t* c, int32_t cn) {
+    int32_t dot = 0;
+#pragma unroll
+    for (int j = 0; j < KM_DIM; ++j) dot += x[j] * c[j];
+    return cn - 2 * dot;
+}
+
 // assignment: nearest centroid per SKU; mode 0 accumulates the member sums
 // and counts for the update, mode 1 writes the final assignment, the counts
 // and the clusters' pick weights.  Per-block partial sums in shared memory.
@@ -275,7 +284,8 @@ __global__ void __launch_bounds__(KM_T) k_km_assign(KmArgs A, int mode) {
     int32_t* cent = sm;                                       // [K][32]
     int32_t* psum = cent + K * KM_DIM;                        // [K][32] (mode 0)
     int32_t* pcnt = psum + K * KM_DIM;                        // [K]
-    unsigned long long* pw = reinterpret_cast<unsigned long long*>(pcnt + K + (K & 1));   // [K] (mode 1)
+    int32_t* cnorm = pcnt + K;                                // [K] |c|^2
+    unsigned long long* pw = reinterpret_cast<unsigned long long*>(cnorm + K);   // [K] (mode 1); 66K ints before it, 8-byte aligned
     for (int i = threadIdx.x; i < K * KM_DIM; i += KM_T) {
         cent[i] = A.cent[i];
         psum[i] = 0;
@@ -283,6 +293,12 @@ __global__ void __launch_bounds__(KM_T) k_km_assign(KmArgs A, int mode) {
     for (int i = threadIdx.x; i < K; i += KM_T) {
         pcnt[i] = 0;
         pw[i] = 0ull;
+        int32_t nn = 0;
+        for (int j = 0; j < KM_DIM; ++j) {
+            const int32_t v = A.cent[i * KM_DIM + j];
+            nn += v * v;
+        }
+        cnorm[i] = nn;
     }
     __syncthreads();
     const int s = blockIdx.x * KM_T + threadIdx.x;
@@ -290,9 +306,9 @@ __global__ void __launch_bounds__(KM_T) k_km_assign(KmArgs A, int mode) {
         int32_t x[KM_DIM];
         load_row(A.x + (int64_t)s * KM_DIM, x);
         int best = 0;
-        int32_t bd = sqdist32(x, cent);
+        int32_t bd = dist_less_norm(x, cent, cnorm[0]);
         for (int c = 1; c < K; ++c) {
-            const int32_t d = sqdist32(x, cent + c * KM_DIM);
+            const int32_t d = dist_less_norm(x, cent + c * KM_DIM, cnorm[c]);
             if (d < bd) {
                 bd = d;
                 best = c;
@@ -412,7 +428,7 @@ __global__ void __launch_bounds__(KM_T) k_km_place(KmArgs A) {
 
 }  // namespace
 
-size_t kmeans_assign_smem(int k) { return (size_t)(2 * k * KM_DIM + k + 1) * 4 + (size_t)k * 8 + 16; }
+size_t kmeans_assign_smem(int k) { return (size_t)(2 * k * KM_DIM + 2 * k) * 4 + (size_t)k * 8 + 16; }
 
 cudaError_t launch_kmeans(const KmArgs& A, cudaStream_t s) {
     const int n = A.n_sku, K = A.k;
