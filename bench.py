@@ -302,7 +302,7 @@ def run_batched(wh, dev, steps):
             "tuning": {"threads": th, "chunks_per_item": ch, "from_cache": bool(hit)}}
 
 
-def run_moves(wh, dev, steps):
+def run_moves(wh, dev, steps, cpu=True):
     """Paper-scale local search: 500 aisles x 200 slots/side, 50,000 SKUs,
     16,384 plans with their own slottings, 64 moves per plan per step."""
     import numpy as np
@@ -359,6 +359,17 @@ def run_moves(wh, dev, steps):
     n_rel_ok = int((s == 0).sum().item())
     assert lay.status() == 0
     lay.close()
+    # the CPU baseline: the oracle on the 64 relocations of the first plan
+    # (each re-scores the whole plan), single-threaded
+    o_s = None
+    if cpu:
+        import oracle
+        one_plan = inst.subset_plans([0])
+        mv0 = rel[1][:M].cpu().numpy().copy()
+        mv0[:, 3] = 0
+        t0 = time.perf_counter()
+        oracle.eval_moves(one_plan, mv0, 24, 0, slot_map=inst.slot_map, slot_map_stride=inst.n_sku)
+        o_s = time.perf_counter() - t0
     return {"workload": "paper scale: 500 aisles x 200 slots/side, 50,000 SKUs Zipf(1.0), 4,000 orders, "
                         "16,384 plans x 64 moves per step (order swap / relocate / SKU-slot swap)",
             "moves_per_step": n_plans * M, "ms_per_step": el * 1e3 / steps,
@@ -366,11 +377,14 @@ def run_moves(wh, dev, steps):
             "ls_step_ms": el2 * 1e3 / steps, "plans_improved_per_step": improved / steps, "steps": steps,
             "relocations": {"moves_per_step": n_plans * M, "ms_per_step": el3 * 1e3 / steps,
                             "move_deltas_per_s": n_plans * M * steps / el3,
-                            "into_empty_fraction": n_rel_ok / (n_plans * M)},
+                            "into_empty_fraction": n_rel_ok / (n_plans * M),
+                            "cpu_baseline": None if o_s is None else {
+                                "value": M / o_s, "unit": "move deltas/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the 64 relocations of one plan, {o_s:.3f} s"}},
             "timing": "wall clock around the calls (each call synchronises once)"}
 
 
-def run_batch_grow(wh, dev):
+def run_batch_grow(wh, dev, cpu=True):
     """Batch formation (seed and grow by exact optimal length) of the mid-size
     order book under 304 ABC slottings (each with its own 10 % of swaps), one
     CTA per slotting; quality: the formed plan's optimal cost against random
@@ -403,13 +417,40 @@ def run_batch_grow(wh, dev):
                             inst.n_sku)
     f_cost = int(wh.evaluate(lay, formed).plan_rr[0].item())
     r_cost = wh.evaluate(lay, rand).plan_rr[:inst.n_plans].double().mean().item()
+    # the CPU baseline on a bounded sample (the oracle's growth is quadratic
+    # in the book): the first 400 orders under the first slotting, and the
+    # kernel on the same 400 orders under all the slottings
+    n_s = 400
+    off_s = inst.order_off[:n_s + 1]
+    lines_s = inst.line_sku[:off_s[-1]]
+    sample = wh_gen.Instance(inst.layout, inst.n_sku, off_s, lines_s, inst.slot_map, inst.plan_tour_off,
+                             inst.tour_off, inst.order_seq)
+    o_s = None
+    if cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.batch_grow(inst.layout, off_s, lines_s, inst.n_sku, maps[0].cpu().numpy(), 20, 60)
+        o_s = time.perf_counter() - t0
+    sp = wh.to_device(sample, dev)
+    lay.batch_grow(sp, maps[:1], 20, 60)
+    torch.cuda.synchronize()
+    e0.record()
+    lay.batch_grow(sp, maps, 20, 60)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
     lay.close()
     return {"workload": f"mid-size order book (4,000 orders) under {n_maps} ABC slottings, tours of <= 20 orders / "
                         "60 lines, one launch",
             "ms": ms, "orders_per_s": n_maps * inst.n_orders / (ms / 1e3),
             "tours_per_s": float(n_tours.double().sum().item()) / (ms / 1e3),
             "formed_plan_optimal_cost": f_cost, "random_plans_mean_optimal_cost": r_cost,
-            "formed_over_random": f_cost / r_cost}
+            "formed_over_random": f_cost / r_cost,
+            "kernel_on_sample": {"sample": f"the first {n_s} orders under all {n_maps} slottings", "ms": ms_s,
+                                 "orders_per_s": n_maps * n_s / (ms_s / 1e3)},
+            "cpu_baseline": None if o_s is None else {
+                "value": n_s / o_s, "unit": "orders/s", "cores": 1, "kind": "oracle",
+                "sample": f"the first {n_s} orders under one slotting, {o_s:.2f} s"}}
 
 
 def run_layout_sweep(wh, dev):
@@ -431,7 +472,7 @@ def run_layout_sweep(wh, dev):
             "pareto": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in front]}
 
 
-def run_kmeans(wh, dev):
+def run_kmeans(wh, dev, cpu=True):
     """K-means slotting on the category workloads: one call (features,
     K-means++ seeding, Lloyd rounds, zones) timed with CUDA events after a
     warm-up, and the slotting scored by the evaluator against the ABC one on
@@ -478,12 +519,23 @@ def run_kmeans(wh, dev):
 
     mid = one(wh_gen.midsize_cat(seed=6, n_plans=256), 64, 20, 64)
     paper = one(wh_gen.paperscale_cat(seed=7, n_plans=256), 256, 20, 64)
+    # the CPU baseline: the oracle on the same mid-size call
+    if cpu:
+        import oracle
+        ic = wh_gen.midsize_cat(seed=6, n_plans=1)
+        sg = wh_gen.gen_signs(3, (ic.n_sku, 32))
+        uu = np.array([wh_gen.stream_word(5, 11, i) for i in range(64)], np.uint64)
+        t0 = time.perf_counter()
+        oracle.kmeans_slotting(ic.layout, ic.order_off, ic.line_sku, ic.n_sku, sg, 64, 64, 20, u=uu)
+        o_ms = (time.perf_counter() - t0) * 1e3
+        mid["cpu_baseline"] = {"value": o_ms, "unit": "ms per call", "cores": 1, "kind": "oracle",
+                               "sample": "the same mid-size call (k = 64, 20 rounds)"}
     return {"workload": "category order books: mid-size (8,000 SKUs, 64 categories, 40 x 100 layout, k = 64) and "
                         "paper-scale (50,000 SKUs, 256 categories, 500 x 200 layout, k = 256), 20 Lloyd rounds",
             "midsize": mid, "paperscale": paper}
 
 
-def run_routes(wh, dev):
+def run_routes(wh, dev, cpu=True):
     """Explicit optimal pick sequences for every tour of 1,024 paper-scale
     plans (one thread per tour: tracking DP, backtrack, Euler circuit), one
     launch after a warm-up; the route lengths are checked against the
@@ -506,9 +558,27 @@ def run_routes(wh, dev):
     rr = wh.evaluate(lay, prob).tour_rr[:inst.n_tours]
     assert torch.equal(length, rr)
     lay.close()
+    # the CPU baseline: the oracle's optimal length (the DP alone, no
+    # sequence) of the first 5,000 tours, single-threaded
+    n_o, o_s = 5000, None
+    if cpu:
+        import oracle
+        locs = []
+        for t in range(n_o):
+            ls = []
+            for o in inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]:
+                ls.extend(inst.slot_map[inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]]].tolist())
+            locs.append(ls)
+        t0 = time.perf_counter()
+        for ls in locs:
+            oracle.rr(inst.layout, ls)
+        o_s = time.perf_counter() - t0
     return {"workload": f"all {inst.n_tours:,} tours of 1,024 paper-scale plans, one launch",
             "ms": ms, "tours_per_s": inst.n_tours / (ms / 1e3),
-            "points_per_s": float(npt.double().sum().item()) / (ms / 1e3), "lengths_equal_optimal": True}
+            "points_per_s": float(npt.double().sum().item()) / (ms / 1e3), "lengths_equal_optimal": True,
+            "cpu_baseline": None if o_s is None else {
+                "value": n_o / o_s, "unit": "tours/s", "cores": 1, "kind": "oracle",
+                "sample": f"optimal length (the DP alone, no sequence) of the first {n_o} tours, {o_s:.2f} s"}}
 
 
 def run_surrogate_ab(wh, dev, steps, train_steps):
@@ -717,12 +787,12 @@ def run_ours(args):
         extra["sshape_only"] = run_sshape(wh, lay, probs, batches, costs, stream, min(args.steps, 200))
     if not args.no_extra and world == 1:
         extra["batched"] = run_batched(wh, dev, args.extra_steps)
-        extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4))
+        extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4), cpu=not args.no_cpu_baseline)
         extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps)
-        extra["batch_formation"] = run_batch_grow(wh, dev)
+        extra["batch_formation"] = run_batch_grow(wh, dev, cpu=not args.no_cpu_baseline)
         extra["layout_sweep"] = run_layout_sweep(wh, dev)
-        extra["routes"] = run_routes(wh, dev)
-        extra["kmeans_slotting"] = run_kmeans(wh, dev)
+        extra["routes"] = run_routes(wh, dev, cpu=not args.no_cpu_baseline)
+        extra["kmeans_slotting"] = run_kmeans(wh, dev, cpu=not args.no_cpu_baseline)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
