@@ -84,3 +84,61 @@ def test_status_without_device_use(lib):
     assert lib.wh_get_last_status(h, None, ctypes.byref(v)) == wh.WH_OK and v.value == 0
     assert lib.wh_get_last_status(h, None, None) == wh.WH_EINVAL
     lib.wh_destroy(h)
+
+
+def test_next_row_entry_points_host_checks(lib):
+    """Explicit routes, K-means slotting, occupancy bits, 16-bit widening and
+    batch formation reject bad arguments (and do nothing for empty work)
+    before any device call."""
+    h = ctypes.c_void_p()
+    assert lib.wh_create_layout(ctypes.byref(wh.wh_layout_desc(10, 30, 3, 1, 2)), ctypes.byref(h)) == 0
+    big = ctypes.c_void_p()
+    assert lib.wh_create_layout(ctypes.byref(wh.wh_layout_desc(300, 30, 3, 1, 2)), ctypes.byref(big)) == 0
+    o = wh.wh_orders(2, 4, 600, 16, 32)          # pointer values only: nothing is dereferenced
+    p = wh.wh_plans(1, 2, 4, 48, 0, 64, 80, 96)
+    P = ctypes.c_void_p
+    # routes
+    r = lambda hh, n, tours, pts, npt, ln: lib.wh_routes(hh, ctypes.byref(o), ctypes.byref(p), P(tours), n, 256,
+                                                        P(pts), P(npt), P(ln), None)
+    assert r(None, 1, 16, 16, 16, 16) == wh.WH_EINVAL
+    assert r(h, -1, 16, 16, 16, 16) == wh.WH_EINVAL
+    assert r(h, 0, 0, 0, 0, 0) == wh.WH_OK
+    assert r(h, 3, 0, 16, 16, 16) == wh.WH_EINVAL   # NULL tour list
+    assert r(h, 3, 16, 16, 0, 16) == wh.WH_EINVAL   # NULL counts
+    # K-means slotting
+    def km(hh, signs, fw, k, init, u, iters, x_out=0):
+        return lib.wh_kmeans_slotting(hh, ctypes.byref(o), P(signs), fw, k, P(init), P(u), iters, P(x_out), None,
+                                      P(16), P(16), P(16), None)
+    assert km(None, 16, 64, 8, 16, 0, 5) == wh.WH_EINVAL
+    assert km(h, 0, 64, 8, 16, 0, 5) == wh.WH_EINVAL          # NULL signs
+    assert km(h, 16, 64, 8, 0, 0, 5) == wh.WH_EINVAL          # neither seeds nor draws
+    assert km(h, 16, 64, 0, 16, 0, 5) == wh.WH_EINVAL         # k = 0
+    assert km(h, 16, 64, 8, 16, 0, -1) == wh.WH_EINVAL        # negative rounds
+    assert km(h, 16, -1, 8, 16, 0, 5) == wh.WH_EINVAL
+    assert km(h, 8, 64, 8, 16, 0, 5) == wh.WH_EINVAL          # signs not 16-byte aligned
+    assert km(h, 16, 64, 8, 16, 0, 5, x_out=24) == wh.WH_EINVAL
+    assert km(h, 16, 64, 257, 16, 0, 5) == wh.WH_ERANGE       # more than 256 clusters
+    assert km(h, 16, 257, 8, 16, 0, 5) == wh.WH_ERANGE        # frequency weight above 256
+    small = ctypes.c_void_p()
+    assert lib.wh_create_layout(ctypes.byref(wh.wh_layout_desc(2, 10, 3, 1, 2)), ctypes.byref(small)) == 0
+    assert km(small, 16, 64, 8, 16, 0, 5) == wh.WH_ERANGE     # 600 SKUs, 40 locations
+    lib.wh_destroy(small)
+    # occupancy bits
+    occ = lambda plans: lib.wh_occupancy(h, ctypes.byref(o), ctypes.byref(plans), None)
+    assert occ(wh.wh_plans(1, 2, 4, 48, 0, 64, 80, 96, 112)) == wh.WH_EINVAL      # shared slotting
+    assert occ(wh.wh_plans(1, 2, 4, 48, 600, 64, 80, 96, 0)) == wh.WH_EINVAL      # no bit array
+    assert occ(wh.wh_plans(0, 0, 0, 48, 600, 64, 80, 96, 0)) == wh.WH_OK          # no plans
+    assert lib.wh_occupancy(None, ctypes.byref(o), ctypes.byref(p), None) == wh.WH_EINVAL
+    # widening
+    assert lib.wh_widen_u16(P(16), P(16), -1, None) == wh.WH_EINVAL
+    assert lib.wh_widen_u16(None, P(16), 8, None) == wh.WH_EINVAL
+    assert lib.wh_widen_u16(None, None, 0, None) == wh.WH_OK
+    # batch formation: 16-bit keys need at most 255 aisles
+    bg = lambda hh, n_maps, mo: lib.wh_batch_grow(hh, ctypes.byref(o), P(48), 0, n_maps, mo, 0, P(16), P(16),
+                                                  P(16), None)
+    assert bg(big, 1, 8) == wh.WH_ERANGE
+    assert bg(h, -1, 8) == wh.WH_EINVAL
+    assert bg(h, 1, -1) == wh.WH_EINVAL
+    assert bg(h, 0, 8) == wh.WH_OK
+    lib.wh_destroy(big)
+    lib.wh_destroy(h)
