@@ -33,6 +33,8 @@ struct BgShared {
     uint32_t* rec;       // [A] lo << 16 | hi << 8 | gap of the tour's aisles
     uint16_t* alist;     // [A] the tour's aisles, ascending
     int* n_aisles;       // entries of alist
+    uint16_t* rem;       // [n_orders] the unassigned orders, compacted (any order)
+    uint16_t* pos;       // [n_orders] position of an unassigned order in rem
 };
 
 // shallowest / deepest set slot and the largest gap between consecutive set
@@ -111,7 +113,7 @@ __device__ __forceinline__ unsigned long long block_min_u64(unsigned long long x
 __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long red[BG_THREADS / 32];
-    __shared__ int s_na;
+    __shared__ int s_na, s_nrem;
     const EvalArgs& a = B.a;
     const Geo& g = a.g;
     const int tid = threadIdx.x, T = blockDim.x;
@@ -132,6 +134,10 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
     q += 2 * (size_t)n_lines;
     S.alist = reinterpret_cast<uint16_t*>(q);
     q += 2 * (size_t)A;
+    S.rem = reinterpret_cast<uint16_t*>(q);
+    q += 2 * (size_t)n_orders;
+    S.pos = reinterpret_cast<uint16_t*>(q);
+    q += 2 * (size_t)n_orders;
     S.used = q;
     S.n_aisles = &s_na;
 
@@ -151,8 +157,15 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
         }
     }
     for (int i = tid; i < 8 * A; i += T) S.mask[i] = 0u;
-    for (int o = tid; o < n_orders; o += T) S.used[o] = 0;
-    if (tid == 0) s_na = 0;
+    for (int o = tid; o < n_orders; o += T) {
+        S.used[o] = 0;
+        S.rem[o] = (uint16_t)o;
+        S.pos[o] = (uint16_t)o;
+    }
+    if (tid == 0) {
+        s_na = 0;
+        s_nrem = n_orders;
+    }
     if (__syncthreads_or(bad)) {
         if (tid == 0) {
             flag(a.status, WH_STATUS_BAD_LOC);
@@ -183,8 +196,11 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
     while (done < n_orders) {
         // seed: the longest order alone (max alone, then lowest id)
         unsigned long long best = ~0ull;
-        for (int o = tid; o < n_orders; o += T)
-            if (!S.used[o]) best = min(best, ((unsigned long long)(0x7fffffff - S.alone[o]) << 32) | (uint32_t)o);
+        const int nr = s_nrem;
+        for (int i = tid; i < nr; i += T) {
+            const int o = S.rem[i];
+            best = min(best, ((unsigned long long)(0x7fffffff - S.alone[o]) << 32) | (uint32_t)o);
+        }
         best = block_min_u64(best, red);
         int o_add = (int)(best & 0xFFFFFFFFull);
         int cost = S.alone[o_add];
@@ -195,6 +211,10 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
             if (tid == 0) {
                 S.used[o_add] = 1;
                 order_seq[done] = o_add;
+                // out of the unassigned list: the last entry takes its place
+                const int at = S.pos[o_add], last = S.rem[--s_nrem];
+                S.rem[at] = (uint16_t)last;
+                S.pos[last] = (uint16_t)at;
                 for (int l = S.off[o_add]; l < S.off[o_add + 1]; ++l) {
                     const int ai = S.key[l] >> 8, k = S.key[l] & 0xFF;
                     uint32_t* m = S.mask + ai * 8;
@@ -225,10 +245,12 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
             lines += S.off[o_add + 1] - S.off[o_add];
             __syncthreads();
             if (B.max_orders > 0 && count >= B.max_orders) break;
-            // grow: the fitting order that lengthens the tour least
+            // grow: the fitting order that lengthens the tour least (the
+            // minimum of (increase, id) does not depend on the list's order)
             best = ~0ull;
-            for (int o = tid; o < n_orders; o += T) {
-                if (S.used[o]) continue;
+            const int nrg = s_nrem;
+            for (int i = tid; i < nrg; i += T) {
+                const int o = S.rem[i];
                 if (B.max_lines > 0 && lines + (S.off[o + 1] - S.off[o]) > B.max_lines) continue;
                 const int c = cost_with(S, g, o);
                 best = min(best, ((unsigned long long)(uint32_t)(c - cost) << 32) | (uint32_t)o);
@@ -254,7 +276,7 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
 
 size_t batch_grow_smem_bytes(int n_orders, int n_lines, int A) {
     return 4 * (size_t)(n_orders + 1) + 4 * (size_t)n_orders + 32 * (size_t)A + 4 * (size_t)A + 2 * (size_t)n_lines +
-           2 * (size_t)A + (size_t)n_orders + 16;
+           2 * (size_t)A + 4 * (size_t)n_orders + (size_t)n_orders + 16;
 }
 
 cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s) {

@@ -618,6 +618,7 @@ extern "C" int wh_batch_grow(wh_layout* h, const wh_orders* orders, const int32_
         return WH_EINVAL;
     if (slot_map_stride != 0 && slot_map_stride < o.n_sku) return WH_EINVAL;
     if (h->g.A > 255 || h->g.L > 256) return WH_ERANGE;   // 16-bit keys, 256-bit depth masks
+    if (o.n_orders > 65535) return WH_ERANGE;   // 16-bit order ids in the unassigned list
     if (wh::batch_grow_smem_bytes(o.n_orders, o.n_lines, h->g.A) > 200 * 1024) return WH_ERANGE;
     int rc = bind_device(h);
     if (rc != WH_OK) return rc;
