@@ -231,9 +231,9 @@ int wh_occupancy(wh_layout *layout, const wh_orders *orders, const wh_plans *pla
  * slotting p: tour_off[p * (n_orders + 1) ...] (tour offsets into order_seq),
  * order_seq[p * n_orders ...] (tours in order of formation, orders in order
  * of insertion), n_tours[p] (-1 when the slotting maps a line outside the
- * layout: status bit WH_STATUS_BAD_LOC).  Needs A <= 255 and L <= 256
- * (WH_ERANGE otherwise) and the
- * order book in shared memory (about 9 B per order + 2 B per line + 38 B per
+ * layout: status bit WH_STATUS_BAD_LOC).  Needs A <= 255, L <= 256 and
+ * n_orders <= 65,535 (WH_ERANGE otherwise) and the
+ * order book in shared memory (about 12 B per order + 2 B per line + 38 B per
  * aisle <= 200 KB, WH_ERANGE otherwise).  Asynchronous on `stream`; allocates
  * nothing.  Returns WH_OK, WH_EINVAL, WH_ERANGE or WH_ECUDA. */
 int wh_batch_grow(wh_layout *layout, const wh_orders *orders, const int32_t *slot_map, int64_t slot_map_stride,

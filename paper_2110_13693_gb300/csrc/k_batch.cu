@@ -27,7 +27,6 @@ constexpr int BG_THREADS = 256;
 struct BgShared {
     uint16_t* key;       // [n_lines] aisle << 8 | slot under this slotting
     int32_t* off;        // [n_orders + 1]
-    uint8_t* used;       // [n_orders]
     int32_t* alone;      // [n_orders] length of the order's tour alone
     uint32_t* mask;      // [A][8] the tour's pick-depth bits per aisle
     uint32_t* rec;       // [A] lo << 16 | hi << 8 | gap of the tour's aisles
@@ -138,7 +137,6 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
     q += 2 * (size_t)n_orders;
     S.pos = reinterpret_cast<uint16_t*>(q);
     q += 2 * (size_t)n_orders;
-    S.used = q;
     S.n_aisles = &s_na;
 
     const int32_t* map = a.slot_map + (int64_t)p * a.slot_stride;
@@ -158,7 +156,6 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
     }
     for (int i = tid; i < 8 * A; i += T) S.mask[i] = 0u;
     for (int o = tid; o < n_orders; o += T) {
-        S.used[o] = 0;
         S.rem[o] = (uint16_t)o;
         S.pos[o] = (uint16_t)o;
     }
@@ -209,7 +206,6 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
             // add o_add to the tour (thread 0), emit it
             __syncthreads();
             if (tid == 0) {
-                S.used[o_add] = 1;
                 order_seq[done] = o_add;
                 // out of the unassigned list: the last entry takes its place
                 const int at = S.pos[o_add], last = S.rem[--s_nrem];
@@ -276,7 +272,7 @@ __global__ void __launch_bounds__(BG_THREADS) k_batch_grow(BatchGrowArgs B) {
 
 size_t batch_grow_smem_bytes(int n_orders, int n_lines, int A) {
     return 4 * (size_t)(n_orders + 1) + 4 * (size_t)n_orders + 32 * (size_t)A + 4 * (size_t)A + 2 * (size_t)n_lines +
-           2 * (size_t)A + 4 * (size_t)n_orders + (size_t)n_orders + 16;
+           2 * (size_t)A + 4 * (size_t)n_orders + 16;
 }
 
 cudaError_t launch_batch_grow(const BatchGrowArgs& B, int n_maps, cudaStream_t s) {
