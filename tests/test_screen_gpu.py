@@ -61,9 +61,14 @@ def moved_tours(inst, smap, mv):
         ta, tb = where[x], t0 + y
         return [(lines([o for o in tours[ta] if o != x], smap), ta), (lines(tours[tb] + [x], smap), tb)]
     m2 = smap.copy()
-    m2[x], m2[y] = m2[y], m2[x]
+    if typ == 2:
+        m2[x], m2[y] = m2[y], m2[x]
+        skus = {x, y}
+    else:                                   # relocation of SKU x to the empty location y
+        m2[x] = y
+        skus = {x}
     hit = {where[o] for o in range(inst.n_orders) if o in where and
-           (set(inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]].tolist()) & {x, y})}
+           (set(inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]].tolist()) & skus)}
     return [(lines(tours[t], m2), t) for t in sorted(hit)]
 
 
@@ -166,3 +171,74 @@ def test_prediction_cache_matches_full_recompute(gpu_lib):
     sg.close()
     lay.close()
     lay2.close()
+
+
+def test_screen_and_search_with_relocations(gpu_lib):
+    """Relocations into empty locations mixed into the screened moves (tiny's
+    orders on a half-empty 20 x 30 layout): the kept moves are the lowest
+    predicted deltas, and screened steps keep exact costs and occupancy bits."""
+    import torch
+    wh = gpu_lib
+    base = wh_gen.tiny(seed=24, n_plans=4)
+    lay_d = wh_gen.Layout(20, 30)
+    rng = np.random.default_rng(24)
+    smap = rng.permutation(lay_d.n_loc)[:base.n_sku].astype(np.int32)
+    inst = wh_gen.Instance(lay_d, base.n_sku, base.order_off, base.line_sku, smap, base.plan_tour_off,
+                           base.tour_off, base.order_seq)
+    lay, prob, costs = setup(wh, inst)
+    lay.occupancy(prob)
+    sg = wh.Surrogate(5)
+    X, t = search.training_set(wh, lay, prob, costs, inst.layout)
+    search.train(sg, X, t, 60, 256, 3e-3)
+    M, keep = 32, 4
+
+    def mixed(step):
+        mv = np.concatenate([wh_gen.gen_moves(6, step, inst, M // 2), wh_gen.gen_relocations(7, step, inst, M // 2)],
+                            axis=1)
+        mv[..., 3] = np.arange(inst.n_plans)[:, None]
+        return torch.as_tensor(mv.reshape(-1, 4)).cuda()
+
+    mv = mixed(0)
+    kept = lay.screen(sg, prob, mv, M, keep, 8).cpu().numpy().reshape(inst.n_plans, keep, 4)
+    params = wh.unpack_params(sg.params()[0])
+    w = {k: (oracle.bf16(v) if k in ("w1", "w2") else v) for k, v in params.items()}
+    pred = lambda locs: oracle.mlp_forward(w, oracle.bf16(oracle.features(inst.layout, locs))[None])[0]
+    maps = np.tile(smap, (inst.n_plans, 1))
+    d, st = oracle.eval_moves(inst, mv.cpu().numpy(), 8, 0, slot_map=maps.ravel(), slot_map_stride=inst.n_sku)
+    assert ((mv[:, 0].cpu().numpy() == 3) & (st == 0)).sum() > 10
+    old = {}
+    for p in range(inst.n_plans):
+        scores = {}
+        for k in range(M):
+            m = p * M + k
+            if st[m] != 0:
+                continue
+            sc = 0.0
+            for locs, t_old in moved_tours(inst, smap, mv[m].cpu().numpy()):
+                if t_old not in old:
+                    orig = [smap[s] for o in inst.order_seq[inst.tour_off[t_old]:inst.tour_off[t_old + 1]]
+                            for s in inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]]]
+                    old[t_old] = pred(orig)
+                sc += pred(locs) - old[t_old]
+            scores[k] = sc
+        kth = sorted(scores.values())[keep - 1]
+        moves_p = mv[p * M:(p + 1) * M].cpu().numpy().tolist()
+        for j in range(keep):
+            k = moves_p.index(kept[p, j].tolist())
+            assert scores[k] <= kth + 1e-3 * max(1.0, abs(kth)), (p, j, scores[k], kth)
+    # screened steps: exact costs and occupancy after every applied move
+    search.run_search(wh, lay, prob, costs, mixed, 4, M, 8, 0, sg=sg, keep=keep)
+    cur_maps = prob.slot_map.cpu().numpy().reshape(inst.n_plans, -1)
+    cur = wh_gen.Instance(inst.layout, inst.n_sku, inst.order_off, inst.line_sku, cur_maps.ravel(),
+                          inst.plan_tour_off, prob.tour_off.cpu().numpy(), prob.order_seq.cpu().numpy())
+    want = oracle.eval_plans(cur, slot_map=cur_maps.ravel(), slot_map_stride=inst.n_sku)
+    assert np.array_equal(costs.plan_rr[:inst.n_plans].cpu().numpy(), want[3])
+    words = (inst.layout.n_loc + 31) // 32
+    bits = np.zeros((inst.n_plans, words), np.uint32)
+    for p in range(inst.n_plans):
+        for loc in cur_maps[p]:
+            bits[p, loc >> 5] |= np.uint32(1 << (int(loc) & 31))
+    assert np.array_equal(prob.loc_used.cpu().numpy().view(np.uint32).reshape(inst.n_plans, words), bits)
+    assert lay.status() == 0
+    sg.close()
+    lay.close()
