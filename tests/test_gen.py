@@ -93,3 +93,36 @@ def test_moves_in_range():
                 assert 0 <= a < inst.n_sku and 0 <= b < inst.n_sku
     assert np.array_equal(mv, wh_gen.gen_moves(7, 0, inst, 64))
     assert not np.array_equal(mv, wh_gen.gen_moves(7, 1, inst, 64))
+
+
+def test_category_orders():
+    """Category order books: sizes in range, SKUs distinct within an order and
+    about 80 % of the lines from the order's category (s mod n_cat)."""
+    inst = wh_gen.midsize_cat(seed=6, n_plans=2)
+    off, lines = inst.order_off, inst.line_sku
+    sizes = np.diff(off)
+    assert sizes.min() >= 1 and sizes.max() <= 12 and inst.n_sku == 8000
+    check_partition(inst, 20, 60)
+    share = []
+    for o in range(inst.n_orders):
+        ls = lines[off[o]:off[o + 1]]
+        assert len(set(ls.tolist())) == len(ls)
+        share.append(np.bincount(ls % 64).max() / len(ls))
+    assert 0.8 < float(np.mean(share)) < 0.97
+    a = wh_gen.gen_orders_cat(3, 100, 1000, 8, 0.4, 1.0, 10, 0.0)
+    b = wh_gen.gen_orders_cat(3, 100, 1000, 8, 0.4, 1.0, 10, 1.0)
+    assert np.array_equal(np.diff(a[0]), np.diff(b[0]))          # sizes drawn from their own stream
+    for o in range(100):                                          # p_in = 1: one category per order
+        assert len(set((b[1][b[0][o]:b[0][o + 1]] % 10).tolist())) == 1
+
+
+def test_sign_rows_and_relocations():
+    s = wh_gen.gen_signs(9, (500, 32))
+    assert s.dtype == np.int8 and set(np.unique(s).tolist()) == {-1, 1}
+    assert abs(float(s.mean())) < 0.05 and np.array_equal(s, wh_gen.gen_signs(9, (500, 32)))
+    inst = wh_gen.tiny(seed=3, n_plans=4)
+    mv = wh_gen.gen_relocations(2, 0, inst, 16)
+    assert (mv[..., 0] == 3).all()
+    assert np.isin(mv[..., 1], np.unique(inst.line_sku)).all()
+    assert ((mv[..., 2] >= 0) & (mv[..., 2] < inst.layout.n_loc)).all()
+    assert (mv[..., 3] == np.arange(4)[:, None]).all()
