@@ -431,10 +431,10 @@ class Layout:
     def kmeans_slotting(self, prob: DeviceProblem, signs, k: int, iters: int, freq_weight: int = 64, init=None,
                         u=None, stream=None):
         """K-means slotting of prob's SKUs (see wh_kmeans_slotting): signs int8
-        [n_sku, 32] of +-1 and either init (int32 [k] SKU ids) or u (uint64
-        draws [k], K-means++), device tensors.  Returns (x [n_sku, 32], seeds
-        [k], centroids [k, 32], assign [n_sku], slot_map [n_sku]) device
-        tensors."""
+        [n_sku, 32] of +-1 and either init (int32 [k] SKU ids) or u (the k
+        uint64 K-means++ draws, held as the bits of an int64 tensor), device
+        tensors.  Returns (x [n_sku, 32], seeds [k], centroids [k, 32], assign
+        [n_sku], slot_map [n_sku]) device tensors."""
         import torch
         dev = prob.order_off.device
         n_sku = prob.n_sku
