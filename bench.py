@@ -330,6 +330,16 @@ def run_moves(wh, dev, steps, cpu=True):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     n_ok = int((s == 0).sum().item())
+    o_mv = None
+    if cpu:
+        # the CPU baseline: the oracle on the first plan's 64 moves (each
+        # re-scores the whole plan), single-threaded
+        import oracle
+        mv_c = moves[2][:M].cpu().numpy().copy()
+        mv_c[:, 3] = 0
+        tc = time.perf_counter()
+        oracle.eval_moves(inst.subset_plans([0]), mv_c, 24, 0, slot_map=inst.slot_map, slot_map_stride=inst.n_sku)
+        o_mv = time.perf_counter() - tc
     # full local-search steps (evaluate, apply, re-score) on the same population,
     # after one untimed step (first use of every kernel on the way)
     applied = lay.ls_step(prob, costs, moves[0], M, 24)
@@ -375,6 +385,9 @@ def run_moves(wh, dev, steps, cpu=True):
             "moves_per_step": n_plans * M, "ms_per_step": el * 1e3 / steps,
             "move_deltas_per_s": n_plans * M * steps / el, "evaluated_fraction": n_ok / (n_plans * M),
             "ls_step_ms": el2 * 1e3 / steps, "plans_improved_per_step": improved / steps, "steps": steps,
+            "cpu_baseline": None if o_mv is None else {
+                "value": M / o_mv, "unit": "move deltas/s", "cores": 1, "kind": "oracle",
+                "sample": f"the 64 moves of one plan, {o_mv:.3f} s"},
             "relocations": {"moves_per_step": n_plans * M, "ms_per_step": el3 * 1e3 / steps,
                             "move_deltas_per_s": n_plans * M * steps / el3,
                             "into_empty_fraction": n_rel_ok / (n_plans * M),
@@ -581,7 +594,7 @@ def run_routes(wh, dev, cpu=True):
                 "sample": f"optimal length (the DP alone, no sequence) of the first {n_o} tours, {o_s:.2f} s"}}
 
 
-def run_surrogate_ab(wh, dev, steps, train_steps):
+def run_surrogate_ab(wh, dev, steps, train_steps, cpu=True):
     """Config 5: the MLP prescreen on the paper-scale population.  Trained on
     ~10M exactly scored tours of the paper-scale generator (four random
     populations), judged on a held-out one, then plain exact search and
@@ -611,6 +624,34 @@ def run_surrogate_ab(wh, dev, steps, train_steps):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     mean_err, p99_err = search.errors(sg, X_held, t_held)
+    # inference on its own: the 500,000 held-out rows in one prediction
+    sg.predict(X_held[:4096])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sg.predict(X_held)
+    e1.record()
+    torch.cuda.synchronize()
+    infer = {"rows": int(X_held.shape[0]), "ms": e0.elapsed_time(e1),
+             "rows_per_s": X_held.shape[0] / (e0.elapsed_time(e1) / 1e3)}
+    if cpu:
+        # the CPU baseline: the oracle's features and MLP forward (float64,
+        # the same bf16 rounding points) of the first 2,000 tours, one core
+        import oracle
+        n_c = 2000
+        w = {k: (oracle.bf16(v) if k in ("w1", "w2") else v) for k, v in wh.unpack_params(sg.params()[0]).items()}
+        locs = []
+        for t_i in range(n_c):
+            ls = []
+            for o in inst0.order_seq[inst0.tour_off[t_i]:inst0.tour_off[t_i + 1]]:
+                ls.extend(inst0.slot_map[inst0.line_sku[inst0.order_off[o]:inst0.order_off[o + 1]]].tolist())
+            locs.append(ls)
+        tc = time.perf_counter()
+        Xc = np.stack([oracle.bf16(oracle.features(inst0.layout, ls)) for ls in locs])
+        oracle.mlp_forward(w, Xc)
+        o_s = time.perf_counter() - tc
+        infer["cpu_baseline"] = {"value": n_c / o_s, "unit": "tours/s (features + MLP forward)", "cores": 1,
+                                 "kind": "oracle", "sample": f"the first {n_c} tours, {o_s:.2f} s"}
     del Xs, ts, X_train, t_train
 
     def population():
@@ -651,7 +692,7 @@ def run_surrogate_ab(wh, dev, steps, train_steps):
     lay.close()
     return {"workload": "paper scale, 16,384 plans with their own slottings, 64 moves per plan per step; "
                         f"surrogate trained on {4 * inst0.n_tours} exactly scored tours of the same generator",
-            "surrogate_mean_rel_error": mean_err, "surrogate_p99_rel_error": p99_err,
+            "surrogate_mean_rel_error": mean_err, "surrogate_p99_rel_error": p99_err, "inference": infer,
             "held_out_tours": 500000, "train_steps": train_steps, "batch": 4096, "train_seconds": train_s,
             "data_seconds": data_s, "keep_per_plan": keep, "start_best": start_best,
             "plain": {"steps": len(plain), "seconds": plain[-1][0], "best": plain[-1][1], "mean": plain[-1][2],
@@ -788,7 +829,7 @@ def run_ours(args):
     if not args.no_extra and world == 1:
         extra["batched"] = run_batched(wh, dev, args.extra_steps)
         extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4), cpu=not args.no_cpu_baseline)
-        extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps)
+        extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps, cpu=not args.no_cpu_baseline)
         extra["batch_formation"] = run_batch_grow(wh, dev, cpu=not args.no_cpu_baseline)
         extra["layout_sweep"] = run_layout_sweep(wh, dev)
         extra["routes"] = run_routes(wh, dev, cpu=not args.no_cpu_baseline)
