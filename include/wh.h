@@ -357,6 +357,29 @@ int wh_surrogate_get_status(wh_surrogate *s, uint32_t *out);
 int wh_surrogate_train_step(wh_surrogate *s, const uint16_t *X, const float *target, int32_t n, float lr,
                             float *loss_out, void *stream);
 
+/* Intermediates of the last wh_surrogate_train_step (a check of the
+ * training step layer by layer against a reference; Sec. 1 / Fig. 1,
+ * config 5's bf16 weights and activations with fp32 accumulation): copy the
+ * first n_rows rows (n_rows <= that step's n) of one saved buffer to dst
+ * (device, caller-owned), enqueued on `stream`:
+ *   WH_TRACE_Z1, WH_TRACE_Z2   fp32 [n_rows][256] pre-activations;
+ *   WH_TRACE_H1, WH_TRACE_H2   bf16 [n_rows][256] activations;
+ *   WH_TRACE_Y, WH_TRACE_DY    fp32 [n_rows] outputs and (y - target) / n;
+ *   WH_TRACE_DZ2, WH_TRACE_DZ1 bf16 [n_rows][256] back-propagated gradients
+ *                              of the pre-activations (the backward GEMMs'
+ *                              operands).
+ * The buffers hold the last step's values until the next training step.
+ * Returns WH_OK or WH_EINVAL (unknown buffer, rows beyond the last step). */
+#define WH_TRACE_Z1 0
+#define WH_TRACE_H1 1
+#define WH_TRACE_Z2 2
+#define WH_TRACE_H2 3
+#define WH_TRACE_Y 4
+#define WH_TRACE_DY 5
+#define WH_TRACE_DZ2 6
+#define WH_TRACE_DZ1 7
+int wh_surrogate_get_trace(wh_surrogate *s, int32_t which, void *dst, int64_t n_rows, void *stream);
+
 /* Prescreen of local-search moves: for plan p's moves [p*moves_per_plan,
  * (p+1)*moves_per_plan) the surrogate predicts each move's change of the
  * plan's optimal cost (sum over the tours the move changes of predicted new
@@ -397,7 +420,10 @@ void wh_surrogate_destroy(wh_surrogate *s);
  *   - Limits: orders->n_lines <= WH_NOALLOC_MAX_LINES and
  *     plans->n_tours <= WH_NOALLOC_MAX_TOURS, else WH_ERANGE before any work.
  *   - status: optional caller-owned device word; the call zeroes it on
- *     `stream` and the kernels OR WH_STATUS_* bits into it.  NULL: no status.
+ *     `stream` and the kernels OR WH_STATUS_* bits into it.  NULL: the bits
+ *     go to a word inside the library's array, cleared by each call and
+ *     reported nowhere (errors found on the device then show only as tour
+ *     costs of -1).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

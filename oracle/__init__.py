@@ -33,6 +33,9 @@ Functions and the independent checks that pin them (all in ``tests/``):
                         with the same bf16 rounding points, backward by
                         finite differences and by torch autograd, Adam by
                         torch.optim.Adam.
+* ``mlp_train_trace`` -- one training step with every intermediate and the
+                        backward's bf16 rounding points; pinned by torch
+                        autograd with the same roundings as gradient hooks.
 * ``kmeans_features`` / ``kmeans_slotting`` -- K-means slotting; features
                         pinned by the dense co-occurrence matrix times the
                         sign matrix (numpy) and exact integer square roots;
@@ -131,6 +134,8 @@ def _load():
             lib.or_mlp_forward.argtypes = [f32p] * 7 + [ctypes.c_int32, f64p]
             lib.or_mlp_backward.restype = ctypes.c_double
             lib.or_mlp_backward.argtypes = [f32p] * 7 + [f64p, ctypes.c_int32] + [f64p] * 6
+            lib.or_mlp_train_trace.restype = ctypes.c_double
+            lib.or_mlp_train_trace.argtypes = [f32p] * 7 + [f64p, ctypes.c_int32] + [f64p] * 17
             lib.or_adam.restype = None
             lib.or_adam.argtypes = [f64p, f64p, f64p, f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_int32]
@@ -361,6 +366,30 @@ def mlp_backward(params, X, t):
                                    _ptr(t, ctypes.c_double), n,
                                    *[_ptr(g[k], ctypes.c_double) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
     return float(loss), g
+
+
+TRACE_ROWS = ("z1", "h1", "z2", "h2", "d2pre", "d2", "s1", "d1pre", "d1")
+
+
+def mlp_train_trace(params, X, t):
+    """(loss, trace dict, grads dict) of one training step with the bf16
+    rounding points of the tensor-core contract: activations h1, h2 and the
+    back-propagated d2 = dL/dz2, d1 = dL/dz1 rounded to bf16 before use.
+    trace: z1, h1, z2, h2, d2pre, d2, s1, d1pre, d1 [n, 256]; y, dy [n]."""
+    X = _f32(X)
+    t = np.ascontiguousarray(np.asarray(t, np.float64))
+    n = X.shape[0]
+    tr = {k: np.zeros((n, MLP_H)) for k in TRACE_ROWS}
+    tr["y"], tr["dy"] = np.zeros(n), np.zeros(n)
+    g = {"w1": np.zeros((MLP_IN, MLP_H)), "b1": np.zeros(MLP_H), "w2": np.zeros((MLP_H, MLP_H)),
+         "b2": np.zeros(MLP_H), "w3": np.zeros(MLP_H), "b3": np.zeros(1)}
+    ps = [_f32(params[k]) for k in ("w1", "b1", "w2", "b2", "w3", "b3")]
+    order = ("z1", "h1", "z2", "h2", "y", "dy", "d2pre", "d2", "s1", "d1pre", "d1")
+    loss = _load().or_mlp_train_trace(*[_ptr(p, ctypes.c_float) for p in ps], _ptr(X, ctypes.c_float),
+                                      _ptr(t, ctypes.c_double), n,
+                                      *[_ptr(tr[k], ctypes.c_double) for k in order],
+                                      *[_ptr(g[k], ctypes.c_double) for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    return float(loss), tr, g
 
 
 def adam(p, m, v, g, lr, step, b1=0.9, b2=0.999, eps=1e-8):

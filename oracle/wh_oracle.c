@@ -880,6 +880,59 @@ double or_mlp_backward(const float *w1, const float *b1, const float *w2, const 
     return loss / n;
 }
 
+/* One training step's every intermediate, row by row, with the rounding
+ * points of the bf16-operand contract (bf16 weights and activations on the
+ * tensor cores, fp32 accumulation; config 5 of the learned prescreen, the
+ * paper's machine learning in the loop, Sec. 1 / Fig. 1): every operand of a
+ * product is a bf16 value, so the forward's activations h1, h2 and the
+ * backward's back-propagated pre-activation gradients d2 = dL/dz2 and
+ * d1 = dL/dz1 are rounded to bf16 (through float, as the forward's
+ * activations) before they are used; everything else is double.  The
+ * gradients are the chain rule through that computation (each rounding
+ * point passes the gradient through unchanged). */
+double or_mlp_train_trace(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                          const float *b3, const float *X, const double *t, int32_t n, double *z1, double *h1,
+                          double *z2, double *h2, double *y, double *dy, double *d2pre, double *d2, double *s1,
+                          double *d1pre, double *d1, double *g1, double *gb1, double *g2, double *gb2, double *g3,
+                          double *gb3) {
+    memset(g1, 0, sizeof(double) * MLP_IN * MLP_H);
+    memset(gb1, 0, sizeof(double) * MLP_H);
+    memset(g2, 0, sizeof(double) * MLP_H * MLP_H);
+    memset(gb2, 0, sizeof(double) * MLP_H);
+    memset(g3, 0, sizeof(double) * MLP_H);
+    gb3[0] = 0.0;
+    double loss = 0.0;
+    for (int32_t r = 0; r < n; ++r) {
+        const int64_t o = (int64_t)r * MLP_H;
+        const float *x = X + (int64_t)r * MLP_IN;
+        y[r] = mlp_row(w1, b1, w2, b2, w3, b3, x, z1 + o, h1 + o, z2 + o, h2 + o);
+        const double e = y[r] - t[r];
+        loss += 0.5 * e * e;
+        dy[r] = e / n;
+        gb3[0] += dy[r];
+        for (int i = 0; i < MLP_H; ++i) {
+            g3[i] += dy[r] * h2[o + i];
+            d2pre[o + i] = dy[r] * (double)w3[i] * gelu_grad(z2[o + i]);
+            d2[o + i] = (double)or_bf16((float)d2pre[o + i]);
+        }
+        for (int j = 0; j < MLP_H; ++j) gb2[j] += d2[o + j];
+        for (int i = 0; i < MLP_H; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < MLP_H; ++j) {
+                g2[i * MLP_H + j] += h1[o + i] * d2[o + j];
+                acc += (double)w2[i * MLP_H + j] * d2[o + j];
+            }
+            s1[o + i] = acc;
+            d1pre[o + i] = acc * gelu_grad(z1[o + i]);
+            d1[o + i] = (double)or_bf16((float)d1pre[o + i]);
+        }
+        for (int j = 0; j < MLP_H; ++j) gb1[j] += d1[o + j];
+        for (int i = 0; i < MLP_IN; ++i)
+            for (int j = 0; j < MLP_H; ++j) g1[i * MLP_H + j] += (double)x[i] * d1[o + j];
+    }
+    return loss / n;
+}
+
 void or_adam(double *p, double *m, double *v, const double *g, int64_t n, double lr, double b1, double b2,
              double eps, int32_t step) {
     const double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);

@@ -210,6 +210,20 @@ double or_mlp_backward(const float *w1, const float *b1, const float *w2, const 
                        const float *b3, const float *X, const double *t, int32_t n, double *g1, double *gb1,
                        double *g2, double *gb2, double *g3, double *gb3);
 
+/* One training step with every intermediate kept ([n][256] row-major unless
+ * noted): pre-activations z1, z2 and bf16 activations h1, h2 as in
+ * or_mlp_forward; outputs y[n]; dy[n] = (y - t) / n; d2pre = dy * w3 *
+ * gelu'(z2) and d2 = bf16(d2pre); s1 = d2 W2^T; d1pre = s1 * gelu'(z1) and
+ * d1 = bf16(d1pre).  The back-propagated gradients are rounded to bf16 where
+ * they become operands of a product (the bf16-operand contract of the
+ * tensor-core training step); gradients g* as in or_mlp_backward but from
+ * the rounded d2, d1.  Returns the loss 0.5 * mean((y - t)^2). */
+double or_mlp_train_trace(const float *w1, const float *b1, const float *w2, const float *b2, const float *w3,
+                          const float *b3, const float *X, const double *t, int32_t n, double *z1, double *h1,
+                          double *z2, double *h2, double *y, double *dy, double *d2pre, double *d2, double *s1,
+                          double *d1pre, double *d1, double *g1, double *gb1, double *g2, double *gb2, double *g3,
+                          double *gb3);
+
 /* One Adam step (Kingma & Ba 2015) on n parameters: m = b1 m + (1-b1) g,
  * v = b2 v + (1-b2) g^2, p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
 void or_adam(double *p, double *m, double *v, const double *g, int64_t n, double lr, double b1, double b2,

@@ -104,6 +104,8 @@ SIGNATURES = {
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_surrogate_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_void_p]),
     "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
@@ -120,6 +122,8 @@ SIGNATURES = {
     "wh_surrogate_destroy": (None, [ctypes.c_void_p]),
 }
 WH_MLP_NPARAM, WH_FEATURES = 115457, 192
+(WH_TRACE_Z1, WH_TRACE_H1, WH_TRACE_Z2, WH_TRACE_H2, WH_TRACE_Y, WH_TRACE_DY, WH_TRACE_DZ2,
+ WH_TRACE_DZ1) = range(8)
 
 
 def library_path() -> str:
@@ -673,6 +677,11 @@ def wh_surrogate_train_step(s, X, target, n: int, lr: float, loss=0, stream=None
            "wh_surrogate_train_step")
 
 
+def wh_surrogate_get_trace(s, which: int, dst, n_rows: int, stream=None) -> None:
+    _check(load().wh_surrogate_get_trace(s, which, ctypes.c_void_p(dst), n_rows, _stream_ptr(stream)),
+           "wh_surrogate_get_trace")
+
+
 def wh_surrogate_screen(layout, s, orders: wh_orders, plans: wh_plans, moves, moves_per_plan: int, keep: int,
                         max_orders: int, max_lines: int, kept, y_tour=None, tour_changed=None, stream=None) -> None:
     _check(load().wh_surrogate_screen(layout, s, ctypes.byref(orders), ctypes.byref(plans), ctypes.c_void_p(moves),
@@ -733,6 +742,22 @@ class Surrogate:
         wh_surrogate_train_step(self.handle, X.data_ptr(), target.data_ptr(), int(X.shape[0]), lr,
                                 loss.data_ptr(), stream)
         return loss
+
+    def trace(self, n_rows: int, stream=None) -> dict:
+        """The last training step's intermediates (first n_rows rows): z1, h1,
+        z2, h2 [n_rows, 256], y, dy [n_rows], dz2, dz1 [n_rows, 256]."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        spec = (("z1", WH_TRACE_Z1, torch.float32, 256), ("h1", WH_TRACE_H1, torch.bfloat16, 256),
+                ("z2", WH_TRACE_Z2, torch.float32, 256), ("h2", WH_TRACE_H2, torch.bfloat16, 256),
+                ("y", WH_TRACE_Y, torch.float32, 0), ("dy", WH_TRACE_DY, torch.float32, 0),
+                ("dz2", WH_TRACE_DZ2, torch.bfloat16, 256), ("dz1", WH_TRACE_DZ1, torch.bfloat16, 256))
+        out = {}
+        for name, which, dt, cols in spec:
+            t = torch.empty((max(n_rows, 1), cols) if cols else (max(n_rows, 1),), dtype=dt, device=dev)
+            wh_surrogate_get_trace(self.handle, which, t.data_ptr(), n_rows, stream)
+            out[name] = t[:n_rows]
+        return out
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -120,7 +120,8 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
     a.plan_rr = out->plan_rr;
     a.mask = routing_mask;
     a.max_rec = d.n_aisles < wh::SHORT_MAX ? d.n_aisles : wh::SHORT_MAX;
-    // status bits go to the caller's word when given, else to the array's own
+    // status bits go to the caller's word when given, else to a word inside
+    // the array that this call clears and nothing reports
     a.status = status ? status : reinterpret_cast<uint32_t*>(base);
     a.long_count = reinterpret_cast<int32_t*>(base) + 1;
     a.long_cap = p.n_tours;
@@ -137,8 +138,9 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
     a.long_list = reinterpret_cast<int32_t*>(base + kHeaderBytes + kKeyBytes);
 
     // the array keeps the previous call's contents: zero what must start at 0
-    // (the caller's status word here; the long-tour counter in k_prep)
-    if (status && cudaMemsetAsync(status, 0, sizeof(uint32_t), s) != cudaSuccess) return WH_ECUDA;
+    // (the status word in use, the caller's or the array's own, here; the
+    // long-tour counter in k_prep)
+    if (cudaMemsetAsync(a.status, 0, sizeof(uint32_t), s) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_prep(a, s) != cudaSuccess) return WH_ECUDA;
     if (wh::launch_eval_short(a, t, num_sms, s, nullptr) != cudaSuccess) return WH_ECUDA;
     if (p.n_tours > 0) {

@@ -25,6 +25,7 @@ struct wh_surrogate {
     __nv_bfloat16* w2b = nullptr;
     int step = 0;
     int64_t cap = 0;       // rows of training scratch
+    int64_t last_n = 0;    // rows of the last training step (its saved intermediates)
     float *Z1 = nullptr, *Z2 = nullptr, *y = nullptr, *dy = nullptr, *loss = nullptr;
     float* part = nullptr; // split partials of the weight gradients and column sums
     __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
@@ -298,11 +299,34 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     gw1.Cf = s->G;
     gw1.ldc = 256;
     if (wh::launch_gemm_splitk(gw1, splits_for(n), st) != cudaSuccess) return WH_ECUDA;
+    s->last_n = n;
     s->step += 1;
     if (wh::launch_adam(s->P, s->Mo, s->Ve, s->G, wh::MLP_NPARAM, lr, s->step, s->w1b, s->w2b, st) != cudaSuccess)
         return WH_ECUDA;
     s->t_stale = true;
     if (loss_out && cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return WH_ECUDA;
+    return WH_OK;
+}
+
+extern "C" int wh_surrogate_get_trace(wh_surrogate* s, int32_t which, void* dst, int64_t n_rows, void* stream) {
+    if (!s || !dst || n_rows < 0 || n_rows > s->last_n) return WH_EINVAL;
+    const void* src = nullptr;
+    size_t row_bytes = 0;
+    switch (which) {
+        case WH_TRACE_Z1: src = s->Z1; row_bytes = 256 * sizeof(float); break;
+        case WH_TRACE_H1: src = s->H1; row_bytes = 256 * sizeof(__nv_bfloat16); break;
+        case WH_TRACE_Z2: src = s->Z2; row_bytes = 256 * sizeof(float); break;
+        case WH_TRACE_H2: src = s->H2; row_bytes = 256 * sizeof(__nv_bfloat16); break;
+        case WH_TRACE_Y: src = s->y; row_bytes = sizeof(float); break;
+        case WH_TRACE_DY: src = s->dy; row_bytes = sizeof(float); break;
+        case WH_TRACE_DZ2: src = s->dZ2; row_bytes = 256 * sizeof(__nv_bfloat16); break;
+        case WH_TRACE_DZ1: src = s->dZ1; row_bytes = 256 * sizeof(__nv_bfloat16); break;
+        default: return WH_EINVAL;
+    }
+    if (n_rows == 0) return WH_OK;
+    if (cudaMemcpyAsync(dst, src, row_bytes * (size_t)n_rows, cudaMemcpyDeviceToDevice,
+                        static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return WH_ECUDA;
     return WH_OK;
 }

@@ -104,6 +104,57 @@ def test_backward_matches_autograd_and_finite_differences():
         assert abs((up - dn) / (2 * eps) - g[k].reshape(-1)[idx]) < 1e-6
 
 
+def test_train_trace_matches_autograd_with_rounded_gradients():
+    """The training trace against torch float64 autograd in which the forward
+    rounds h1, h2 to bf16 (straight through) and gradient hooks round
+    dL/dz2 and dL/dz1 to bf16: the same rounding points, computed
+    independently.  With the roundings made identity the gradients reduce
+    to or_mlp_backward's."""
+    p, X = rand_params(9), rand_x(10, 48)
+    tgt = np.random.default_rng(11).normal(size=48) * 0.1
+    loss, tr, g = oracle.mlp_train_trace(p, X, tgt)
+    t = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in p.items()}
+    x = torch.tensor(X, dtype=torch.float64)
+    rnd = lambda v: v.detach().to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    ste = lambda h: h + (rnd(h) - h).detach()
+    gel = lambda z: 0.5 * z * (1 + torch.erf(z / np.sqrt(2.0)))
+    seen = {}
+
+    def hook(name):
+        def f(grad):
+            seen[name + "pre"] = grad.detach().clone()
+            seen[name] = rnd(grad)
+            return seen[name]
+        return f
+
+    z1 = x @ t["w1"] + t["b1"]
+    z1.register_hook(hook("d1"))
+    h1 = ste(gel(z1))
+    z2 = h1 @ t["w2"] + t["b2"]
+    z2.register_hook(hook("d2"))
+    h2 = ste(gel(z2))
+    y = h2 @ t["w3"] + t["b3"]
+    tl = 0.5 * ((y - torch.tensor(tgt)) ** 2).mean()
+    tl.backward()
+    assert abs(loss - tl.item()) < 1e-12
+    for k, v in (("z1", z1), ("h1", h1), ("z2", z2), ("h2", h2)):
+        np.testing.assert_allclose(tr[k], v.detach().numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(tr["y"], y.detach().numpy(), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(tr["dy"], (y.detach().numpy() - tgt) / 48, rtol=1e-12, atol=1e-15)
+    for k in ("d2pre", "d2", "d1pre", "d1"):
+        np.testing.assert_allclose(tr[k], seen[k].numpy(), rtol=1e-9, atol=1e-18)
+    # the rounded gradients are bf16 values; about half their entries moved
+    assert np.array_equal(tr["d2"], oracle.bf16(tr["d2"]).astype(np.float64))
+    assert (tr["d1"] != tr["d1pre"]).mean() > 0.5
+    for k in p:
+        np.testing.assert_allclose(g[k].reshape(-1), t[k].grad.numpy().reshape(-1), rtol=1e-9, atol=1e-15)
+    # without the gradient roundings: the plain backward
+    _, g0 = oracle.mlp_backward(p, X, tgt)
+    for k in ("w3", "b3"):
+        np.testing.assert_allclose(g[k], g0[k], rtol=1e-12, atol=1e-18)
+    assert not np.allclose(g["w1"], g0["w1"], rtol=1e-6, atol=0)
+
+
 def test_adam_matches_torch():
     rng = np.random.default_rng(8)
     p0 = rng.normal(size=50)
