@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: exact tour evaluations per second on one GB300 (or N, weak scaling).
 
-One step = one call of wh_eval_plans on a batch of 4,096 candidate plans of
-the mid-size warehouse (40 aisles x 100 slots per side, 8,000 SKUs with
-Zipf(1.1) popularity slotted ABC with 10% swapped, 4,000 orders of 1..12
-lines, tours of at most 20 orders / 60 lines), scoring every tour under both
+One step = one persistent launch, replayed as a CUDA graph, that scores 1,024
+independent warehouse instances of uneven size (aisles U[8,64], slots per side
+U[20,200], orders U[100,5000] of 1..12 lines, as many SKUs as locations with
+Zipf(1.1) popularity slotted ABC with 10% swapped) with 256 random candidate
+plans each (tours of at most 20 orders / 60 lines): every tour under both
 routing rules (S-shape and optimal) and every plan's int64 sums.  Inputs are
-synthetic (seeded generator) and resident in HBM when timing starts; steps
-rotate over several plan batches whose combined size exceeds the L2 cache.
+synthetic (seeded generator) and resident in HBM when timing starts (about
+3 GB of plan arrays, far above the L2 cache).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line on rank 0.  Under torchrun each rank scores its own
-batches (no collective on the data path); the timing is the max over ranks.
+1,024 instances (no collective on the data path); the timing is the max over
+ranks.  Extra fields measure the other rows: the mid-size single-instance
+launch, the paper-scale population, move deltas, the surrogate prescreen and
+the next rows.
 """
 import argparse
 import hashlib
@@ -29,21 +33,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exact tour evals/s (RR DP, S-shape) and surrogate-screened vs plain, 1 GB300"
 UNIT = "tours/s"
-PLANS_PER_STEP = 4096
-WORKLOAD = ("midsize warehouse: 40 aisles x 100 slots/side (8,000 locations), 8,000 SKUs Zipf(1.1) "
-            "ABC-slotted with 10% swapped, 4,000 orders of 1-12 lines, 4,096 plans per step in tours "
-            "of <= 20 orders / 60 lines; S-shape + optimal (Ratliff-Rosenthal) cost of every tour, "
-            "int64 sum per plan")
+N_INST, PLANS_PER_INST = 1024, 256
+INST_SEED = 3
+WORKLOAD = ("batched: 1,024 independent warehouse instances of uneven size (aisles U[8,64], slots/side "
+            "U[20,200], orders U[100,5000] of 1-12 lines, SKUs = locations, Zipf(1.1) ABC-slotted with 10% "
+            "swapped) x 256 random plans each (tours <= 20 orders / 60 lines), one persistent launch replayed "
+            "as a CUDA graph; S-shape + optimal (Ratliff-Rosenthal) cost of every tour, int64 sum per plan")
+PLANS_PER_STEP = 4096          # the mid-size launch (extra field "midsize")
+MIDSIZE_WORKLOAD = ("midsize warehouse: 40 aisles x 100 slots/side (8,000 locations), 8,000 SKUs Zipf(1.1) "
+                    "ABC-slotted with 10% swapped, 4,000 orders of 1-12 lines, 4,096 plans per step in tours "
+                    "of <= 20 orders / 60 lines; S-shape + optimal (Ratliff-Rosenthal) cost of every tour, "
+                    "int64 sum per plan")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--batches", type=int, default=4, help="plan batches rotated across steps")
-    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--batches", type=int, default=4, help="mid-size plan batches rotated across steps")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--midsize-steps", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and move-delta measurements")
@@ -266,41 +277,6 @@ def cpu_oracle_rate_all_cores(seconds, cores):
 
 
 # ------------------------------------------------- other hot-path rows
-
-def run_batched(wh, dev, steps):
-    """1,024 uneven instances x 256 plans in one persistent launch replayed
-    as a CUDA graph, launch shape from the autotuner (JSON cache)."""
-    import torch
-    import wh_gen
-    insts = [wh_gen.batched_instance(3, i, n_plans=256) for i in range(1024)]
-    items = []
-    for inst in insts:
-        lay = inst.layout
-        prob = wh.to_device(inst, dev)
-        items.append(((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width),
-                      prob, wh.alloc_costs(prob.n_tours, prob.n_plans, dev)))
-    tours = sum(p.n_tours for _, p, _ in items)
-    batch = wh.Batch(items)
-    cache = os.path.join(ROOT, "paper_2110_13693_gb300", "autotune_cache.json")
-    th, ch, hit = batch.autotune(3, cache)
-    stream = torch.cuda.current_stream(dev)
-    for _ in range(3):
-        batch.eval(3, stream, graph=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        batch.eval(3, stream, graph=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    assert batch.status() == 0
-    batch.close()
-    return {"workload": "1,024 instances (aisles U[8,64], slots/side U[20,200], orders U[100,5000]) x 256 plans, "
-                        "one persistent launch replayed as a CUDA graph",
-            "tours_per_step": tours, "ms_per_step": ms, "tours_per_s": tours / (ms / 1e3), "steps": steps,
-            "tuning": {"threads": th, "chunks_per_item": ch, "from_cache": bool(hit)}}
-
 
 def run_moves(wh, dev, steps, cpu=True):
     """Paper-scale local search: 500 aisles x 200 slots/side, 50,000 SKUs,
@@ -703,10 +679,211 @@ def run_surrogate_ab(wh, dev, steps, train_steps, cpu=True):
             "screened_reaches_plain_best_faster": hit is not None and hit < plain[-1][0]}
 
 
+# ----------------------------------------------- batched workload helpers
+
+def make_instances(rank):
+    """This rank's 1,024 instances (rank r takes generator indices
+    r*1024 .. r*1024+1023, so ranks score different instances)."""
+    import wh_gen
+    return [wh_gen.batched_instance(INST_SEED, rank * N_INST + i, n_plans=PLANS_PER_INST) for i in range(N_INST)]
+
+
+_WORKER_BATCHED = {}
+
+
+def _oracle_batched(job):
+    """One host core (a spawned worker): the oracle on plan chunks of the
+    batched instances `ids` (taken in turn, `per_chunk` plans at a time) for
+    `seconds` of wall time, or exactly one chunk of each id when seconds is
+    0; returns (tours, plans, seconds)."""
+    ids, seconds, per_chunk = job
+    import oracle
+    import wh_gen
+    oracle.build()
+    tours = plans = 0
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        i = ids[k % len(ids)]
+        if i not in _WORKER_BATCHED:
+            _WORKER_BATCHED.clear()          # one instance held at a time
+            _WORKER_BATCHED[i] = wh_gen.batched_instance(INST_SEED, i, n_plans=PLANS_PER_INST)
+        inst = _WORKER_BATCHED[i]
+        p0 = (k // len(ids)) * per_chunk % inst.n_plans
+        sub = inst.subset_plans(range(p0, min(p0 + per_chunk, inst.n_plans)))
+        oracle.eval_plans(sub)
+        tours += sub.n_tours
+        plans += sub.n_plans
+        k += 1
+        el = time.perf_counter() - t0
+        if (seconds <= 0 and k >= len(ids)) or (seconds > 0 and el >= seconds):
+            return tours, plans, el
+
+
+def cpu_oracle_batched(seconds, cores, per_chunk=4):
+    """The oracle on every host core over the batched workload: one spawned
+    process per core, core c scoring plan chunks of instances c, c + cores,
+    ... for `seconds`; tours per second of wall time."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    jobs = [(list(range(c, N_INST, cores))[:8], seconds, per_chunk) for c in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_batched, jobs)
+    tours = sum(r[0] for r in res)
+    plans = sum(r[1] for r in res)
+    el = max(r[2] for r in res)
+    return tours / el, tours, plans, el
+
+
+def batched_profile(tours_per_launch):
+    """The committed ncu summary of k_eval_batch (DRAM bytes of one launch
+    on a smaller batch of the same generator), scaled to a full launch by
+    the tours processed, only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_eval_batch_batched.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha") == kernel_source_hash():
+            scale = tours_per_launch / float(d["tours_per_launch"])
+            return d, float(d["dram_bytes_per_launch"]) * scale
+    except Exception:
+        pass
+    return None, None
+
+
 # -------------------------------------------------------------- our arm
 
-def run_ours(args):
+def run_midsize(wh, dev, rank, args):
+    """The mid-size single-instance launch (4,096 plans per wh_eval_plans
+    call, 4 rotated batches): kernel roofline, the S-shape streaming path,
+    end to end from host memory, and the oracle on all host cores."""
     import numpy as np
+    import torch
+    batches = make_batches(args.batches, rank)
+    lay = wh.Layout.of(batches[0].layout)
+    probs = [wh.to_device(b, dev) for b in batches]
+    tours = [p.n_tours for p in probs]
+    costs = wh.alloc_costs(max(tours), PLANS_PER_STEP, dev)
+    stream = torch.cuda.current_stream(dev)
+    mask = wh.WH_ROUTE_SSHAPE | wh.WH_ROUTE_OPTIMAL
+    steps = args.midsize_steps
+    for i in range(max(3, args.warmup)):
+        lay.eval_plans(probs[i % len(probs)], costs, mask, stream)
+    torch.cuda.synchronize()
+    assert lay.status() == 0, "device status flagged an input error"
+    lay.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    n_tours = 0
+    for i in range(steps):
+        b = i % len(probs)
+        lay.eval_plans(probs[b], costs, mask, stream)
+        n_tours += tours[b]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ktime = lay.timing()
+    lay.set_timing(False)
+    assert lay.status() == 0
+    dom_name, (dom_launches, dom_ms) = max(ktime.items(), key=lambda kv: kv[1][1])
+    per_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
+    alg = sum(algorithmic_bytes(batches[i % len(batches)]) for i in range(steps)) / steps
+    peak, peak_kind = measured_peaks()
+    achieved = alg / per_launch_s / 1e9
+    prof = recorded_profile()
+    out = {"workload": MIDSIZE_WORKLOAD, "steps": steps, "ms_per_step": ms / steps,
+           "tours_per_s": n_tours / (ms / 1e3), "plans_per_s": PLANS_PER_STEP * steps / (ms / 1e3),
+           "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in ktime.items()},
+           "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
+                        "launch_ms": per_launch_s * 1e3,
+                        "traffic": float(prof["dram_bytes_per_launch"]) if prof else None,
+                        "issue_active_frac": prof.get("issue_active_frac") if prof else None,
+                        "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None}}
+    out["sshape_only"] = run_sshape(wh, lay, probs, batches, costs, stream, min(steps, 200))
+    # end to end from pinned host memory: 16-bit order ids widened on the device
+    host = []
+    for b in batches:
+        seq = b.order_seq.astype(np.uint16).view(np.int16)
+        host.append(wh.DeviceProblem(*(torch.as_tensor(getattr(b, f)).pin_memory() for f in
+                                       ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off")),
+                                     torch.as_tensor(seq).pin_memory(), b.n_sku))
+    plan_outs = [torch.empty((2, PLANS_PER_STEP), dtype=torch.int64).pin_memory() for _ in probs]
+    pipe = wh.HostPipeline(lay, [(p, costs) for p in probs], mask)
+    for i in range(len(probs)):
+        pipe.wait(pipe.submit(host[i], plan_outs[i])[0])
+    torch.cuda.synchronize()
+    e_steps = 40
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(pipe.copy)
+    e_tours, h2d, d2h, prev = 0, 0, 0, None
+    for i in range(e_steps):
+        b = i % len(probs)
+        ticket, h2d, d2h = pipe.submit(host[b], plan_outs[b])
+        if prev is not None:
+            pipe.wait(prev)
+        prev = ticket
+        e_tours += tours[b]
+    e1.record(pipe.compute)
+    pipe.wait(prev)
+    torch.cuda.synchronize()
+    out["e2e"] = {"value": e_tours / (e0.elapsed_time(e1) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h, "steps": e_steps}
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, ct, cp, el = cpu_oracle_rate_all_cores(args.cpu_seconds / 2, cores)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{cp} plans ({ct} tours) of the mid-size workload, {el:.1f} s on "
+                                         f"{cores} host cores (one process per core)"}
+    lay.close()
+    return out
+
+
+def run_paperscale_eval(wh, dev, steps):
+    """Config 4's whole population scored in one call: 16,384 paper-scale
+    plans (500 aisles x 200 slots/side, 50,000 SKUs, tours of <= 24 orders,
+    30 % of them longer than 64 lines), each plan with its own slotting
+    (16,384 slot maps), both rules."""
+    import torch
+    import wh_gen
+    n_plans = 16384
+    inst = wh_gen.paperscale(seed=4, n_plans=n_plans)
+    lay = wh.Layout.of(inst.layout)
+    base = wh.to_device(inst, dev)
+    prob = wh.DeviceProblem(base.order_off, base.line_sku, base.slot_map.repeat(n_plans), base.plan_tour_off,
+                            base.tour_off, base.order_seq, inst.n_sku, inst.n_sku)
+    costs = wh.alloc_costs(prob.n_tours, n_plans, dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        lay.eval_plans(prob, costs, 3, stream)
+    torch.cuda.synchronize()
+    lay.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        lay.eval_plans(prob, costs, 3, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kt = lay.timing()
+    lay.set_timing(False)
+    assert lay.status() == 0
+    long_frac = float((inst.tour_lines() > 64).mean())
+    lay.close()
+    alg = algorithmic_bytes(inst) + 4 * inst.n_sku * (n_plans - 1)   # one slotting table per plan
+    peak, kind = measured_peaks()
+    return {"workload": "paper scale: 500 aisles x 200 slots/side, 50,000 SKUs Zipf(1.0), 4,000 orders, 16,384 "
+                        "plans with their own slottings, tours <= 24 orders; both rules",
+            "tours_per_step": inst.n_tours, "ms_per_step": ms, "tours_per_s": inst.n_tours / (ms / 1e3),
+            "plans_per_s": n_plans / (ms / 1e3), "long_tour_fraction": long_frac, "steps": steps,
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in kt.items()},
+            "step_roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_kind": kind,
+                              "algorithmic_bytes_per_step": alg}}
+
+
+def run_ours(args):
     import torch
     import torch.distributed as dist
 
@@ -724,110 +901,107 @@ def run_ours(args):
         dist.barrier()
     wh.load()
     dev = torch.device("cuda", local)
-
-    batches = make_batches(args.batches, rank)
-    lay = wh.Layout.of(batches[0].layout)
-    probs = [wh.to_device(b, dev) for b in batches]
-    tours = [p.n_tours for p in probs]
-    costs = wh.alloc_costs(max(tours), PLANS_PER_STEP, dev)
-    stream = torch.cuda.current_stream(dev)
     mask = wh.WH_ROUTE_SSHAPE | wh.WH_ROUTE_OPTIMAL
 
-    for i in range(args.warmup):
-        lay.eval_plans(probs[i % len(probs)], costs, mask, stream)
+    insts = make_instances(rank)
+    packed = wh.PackedInstances(insts)
+    alg = sum(algorithmic_bytes(i) for i in insts)
+    tours_step = packed.total_tours
+    lines_step = sum(int(i.tour_lines().sum()) for i in insts)
+    del insts
+    dset = packed.device_set(dev)
+    stream = torch.cuda.current_stream(dev)
+    dset.load(stream)
     torch.cuda.synchronize()
-    assert lay.status() == 0, "device status flagged an input error"
+    batch = dset.batch
+    cache = os.path.join(ROOT, "paper_2110_13693_gb300", "autotune_cache.json")
+    th, ch, hit = batch.autotune(mask, cache, stream)
+    for _ in range(max(3, args.warmup)):
+        batch.eval(mask, stream, graph=True)
+    torch.cuda.synchronize()
+    assert batch.status() == 0, "device status flagged an input error"
 
-    # ---- timed region: exactly K steps
+    # ---- timed region: exactly K graph replays
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.15)   # let the sampler's first line land
-    lay.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    n_tours = 0
-    for i in range(args.steps):
-        b = i % len(probs)
-        lay.eval_plans(probs[b], costs, mask, stream)
-        n_tours += tours[b]
+    for _ in range(args.steps):
+        batch.eval(mask, stream, graph=True)
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
-    ktime = lay.timing()
-    lay.set_timing(False)
-    assert lay.status() == 0
+    assert batch.status() == 0
+
+    # ---- the same steps launched eagerly with CUDA events around each kernel
+    k_steps = min(args.steps, 50)
+    batch.set_timing(True)
+    for _ in range(k_steps):
+        batch.eval(mask, stream)
+    ktime = batch.timing()
+    batch.set_timing(False)
+    torch.cuda.synchronize()
+    assert batch.status() == 0
 
     from paper_2110_13693_gb300.shard import combine
-    elapsed_ms, total_tours = combine(elapsed_ms, n_tours, dev)
+    elapsed_ms, total_tours = combine(elapsed_ms, tours_step * args.steps, dev)
     value = total_tours / (elapsed_ms / 1e3)
 
-    # ---- end to end through the public API from pinned host memory
-    # order ids cross the host link as 16-bit values (n_orders <= 65,536) and
-    # are widened on the device (wh_widen_u16): the link, ~209 GB/s host to
-    # device on this machine, is the end-to-end bound
-    host = []
-    for b in batches:
-        seq = (b.order_seq.astype(np.uint16).view(np.int16) if b.n_orders <= 65536 else b.order_seq)
-        hp = wh.DeviceProblem(*(torch.as_tensor(getattr(b, f)).pin_memory() for f in
-                                ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off")),
-                              torch.as_tensor(seq).pin_memory(), b.n_sku)
-        host.append(hp)
-    # every step copies its own inputs in and its plan costs back; the copy of
-    # a step overlaps the evaluation of the previous one (HostPipeline: a copy
-    # stream and a compute stream, one device buffer set per rotated batch)
-    plan_outs = [torch.empty((2, PLANS_PER_STEP), dtype=torch.int64).pin_memory() for _ in probs]
-    pipe = wh.HostPipeline(lay, [(p, costs) for p in probs], mask)
-    e2e_steps = max(1, min(args.e2e_steps, args.steps))
-    for i in range(len(probs)):
-        pipe.wait(pipe.submit(host[i], plan_outs[i])[0])
+    # ---- end to end from pinned host memory through the same public API:
+    # every step copies all instances' inputs in (order ids as 16-bit values,
+    # widened on the device) and every plan's costs back; the copy of a step
+    # overlaps the evaluation of the previous one
+    packed.pin()
+    pipe = wh.PackedPipeline(packed, mask, tuning=batch.tuning())
+    for _ in range(2):
+        pipe.wait(pipe.submit()[0])
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.e2e_steps, args.steps))
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(pipe.copy)
-    e_tours, h2d, d2h, prev = 0, 0, 0, None
-    for i in range(e2e_steps):
-        b = i % len(probs)
-        ticket, hb, db = pipe.submit(host[b], plan_outs[b])
+    prev, h2d, d2h = None, 0, 0
+    for _ in range(e_steps):
+        ticket, h2d, d2h = pipe.submit()
         if prev is not None:
             pipe.wait(prev)            # the previous step's plan costs are on the host now
         prev = ticket
-        e_tours += tours[b]
-        h2d, d2h = hb, db
-    e1.record(pipe.compute)          # after the last step's copy back
+    e1.record(pipe.compute)
     pipe.wait(prev)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_ms, e_tours = combine(e2e_ms, e_tours, dev)
+    e2e_ms, e_tours = combine(e0.elapsed_time(e1), tours_step * e_steps, dev)
     e2e_value = e_tours / (e2e_ms / 1e3)
+    for d in pipe.sets:
+        assert d.batch.status() == 0
+    pipe.close()
 
     if rank != 0:
+        dset.close()
         dist.destroy_process_group()
         return
 
     # ---- roofline of the dominant kernel
-    dom = max(ktime.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_launches, dom_ms) = dom
+    dom_name, (dom_launches, dom_ms) = max(ktime.items(), key=lambda kv: kv[1][1])
     per_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
-    alg = sum(algorithmic_bytes(b) * (args.steps // len(batches) + (1 if i < args.steps % len(batches) else 0))
-              for i, b in enumerate(batches)) / args.steps
     peak, peak_kind = measured_peaks()
     achieved = alg / per_launch_s / 1e9
-    prof = recorded_profile()
-    traffic = float(prof["dram_bytes_per_launch"]) if prof else None
-    launches = sum(v[0] for v in ktime.values())
+    prof, traffic = batched_profile(tours_step)
+    launches_per_step = len(ktime)
+    step_s = elapsed_ms / 1e3 / args.steps
 
     extra = {}
     if world == 1:
-        extra["sshape_only"] = run_sshape(wh, lay, probs, batches, costs, stream, min(args.steps, 200))
+        extra["midsize"] = run_midsize(wh, dev, rank, args)
     if not args.no_extra and world == 1:
-        extra["batched"] = run_batched(wh, dev, args.extra_steps)
+        extra["paperscale_eval"] = run_paperscale_eval(wh, dev, max(3, args.extra_steps // 2))
         extra["moves"] = run_moves(wh, dev, max(2, args.extra_steps // 4), cpu=not args.no_cpu_baseline)
         extra["surrogate"] = run_surrogate_ab(wh, dev, args.ab_steps, args.train_steps, cpu=not args.no_cpu_baseline)
         extra["batch_formation"] = run_batch_grow(wh, dev, cpu=not args.no_cpu_baseline)
@@ -838,34 +1012,36 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
-        rate, ct, cp, el = cpu_oracle_rate_all_cores(args.cpu_seconds, cores)
-        r1, ct1, cp1, el1 = cpu_oracle_rate(batches[0], max(2.0, args.cpu_seconds / 4))
+        rate, ct, cp, el = cpu_oracle_batched(args.cpu_seconds, cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{cp} plans ({ct} tours) of the same workload, {el:.1f} s on {cores} host cores "
-                         "(one process per core, each on its own plan chunks)",
-               "single_core": {"value": r1, "sample": f"{cp1} plans ({ct1} tours), {el1:.1f} s on one core"}}
+               "sample": f"{cp} plans ({ct} tours) of the same 1,024 instances, {el:.1f} s on {cores} host cores "
+                         "(one process per core, each on plan chunks of its own instances)"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "plans_per_step": PLANS_PER_STEP,
-                   "tours_per_step": round(sum(tours) / len(tours)), "routing": "S-shape + optimal",
-                   "l2": f"inputs larger than L2: {len(batches)} plan batches rotated, "
-                         f"{sum(4 * (b.order_seq.size + b.tour_off.size) for b in batches) / 1e6:.0f} MB of "
-                         "plan arrays resident (> 129 MB L2)",
-                   "parallelism": f"dp{world} (independent plan batches per GPU)"},
-        "plans_per_s": world * PLANS_PER_STEP * args.steps / (elapsed_ms / 1e3),
+        "config": {"workload": WORKLOAD, "instances": N_INST, "plans_per_step": packed.total_plans,
+                   "tours_per_step": tours_step, "lines_per_step": lines_step, "routing": "S-shape + optimal",
+                   "launch": f"CUDA graph replay of one persistent launch (autotuned: {th} threads, "
+                             f"{ch} chunks per work item{', from cache' if hit else ''})",
+                   "l2": f"inputs larger than L2: {packed.h2d_bytes / 1e9:.2f} GB of packed instance arrays "
+                         f"({4 * packed.seq16.numel() / 1e9:.2f} GB of int32 order ids) resident (> 129 MB L2)",
+                   "parallelism": f"dp{world} (independent instances per GPU)"},
+        "plans_per_s": world * packed.total_plans * args.steps / (elapsed_ms / 1e3),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
-        "gpu_launches": launches,
+        "gpu_launches": launches_per_step * args.steps,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
                         "share": round(v[1] / max(sum(x[1] for x in ktime.values()), 1e-12), 4)}
                     for k, v in ktime.items()},
         "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_s * 1e3,
+                     "launch_timing": f"CUDA events around each launch of {k_steps} eager steps "
+                                      "(graph replays carry no per-kernel events)",
+                     "step_frac": alg / step_s / 1e9 / peak,
                      "traffic": traffic,
                      "issue_active_frac": prof.get("issue_active_frac") if prof else None,
                      "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None},
@@ -873,6 +1049,7 @@ def run_ours(args):
     }
     out.update(extra)
     print(json.dumps(out))
+    dset.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -880,6 +1057,9 @@ def run_ours(args):
 # --------------------------------------------------------- reference arm
 
 def run_reference(args):
+    """The oracle as it stands on every host core, on the same workload and
+    metric: each step, core c scores a bounded sample of plans of its own
+    batched instances (the whole run is sized to end within minutes)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -887,14 +1067,12 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    # every step: each host core scores `per_core` plans of the same workload
-    # (a bounded sample sized so that the whole run ends within minutes)
-    per_plan_s = 0.008
+    per_plan_s = 0.004
     per_core = int(max(1, min(64, 120.0 / max(1, args.steps + args.warmup) / per_plan_s)))
     with mp.get_context("spawn").Pool(cores) as pool:
         def step(i):
-            jobs = [(2, PLANS_PER_STEP, (i * cores + c) * per_core, 0.0, per_core) for c in range(cores)]
-            return sum(r[0] for r in pool.map(_oracle_chunks, jobs))
+            jobs = [([(i * cores + c) % N_INST], 0.0, per_core) for c in range(cores)]
+            return sum(r[0] for r in pool.map(_oracle_batched, jobs))
         for i in range(args.warmup):
             step(i)
         t0 = time.perf_counter()
@@ -907,11 +1085,11 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "plans_per_step": per_core * cores,
-                      "note": "each step scores a bounded sample of the same workload with the CPU oracle, "
-                              f"{per_core} plans on each of {cores} host cores"},
+           "config": {"workload": WORKLOAD, "instances": N_INST, "plans_per_step": per_core * cores,
+                      "note": "each step scores a bounded sample of the same workload with the CPU oracle: "
+                              f"{per_core} plans of one instance on each of {cores} host cores"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{per_core} plans per core per step of the same workload, "
+                            "sample": f"{per_core} plans of one batched instance per core per step, "
                                       f"{cores} processes"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

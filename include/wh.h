@@ -505,6 +505,16 @@ int wh_widen_u16(const uint16_t *src, int32_t *dst, int64_t n, void *stream);
  * WH_EINVAL or WH_ECUDA. */
 int wh_get_last_status(wh_layout *layout, void *stream, uint32_t *status);
 
+/* Kernel timing of a batch (tracing aid; no counterpart in the paper), as
+ * wh_set_timing / wh_get_timing for a layout: while enabled, every kernel that
+ * wh_batch_eval launches (k_prep_batch, k_eval_batch, k_eval_long) is
+ * bracketed by two CUDA events on the launch's stream.  Graph replays
+ * (wh_batch_eval_graph) carry no events and are not counted.  Enabling
+ * resets the totals.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_batch_set_timing(wh_batch *b, int enable);
+int wh_batch_get_timing(wh_batch *b, int32_t *n_kernels, const char **names, int32_t *launches,
+                        double *total_ms, int32_t cap);
+
 /* Kernel timing (tracing aid; no counterpart in the paper).  While enabled,
  * every kernel this handle launches is bracketed by two CUDA events recorded
  * on the launch's stream; wh_get_timing synchronises on those events and

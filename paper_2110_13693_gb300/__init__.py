@@ -80,6 +80,10 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "wh_destroy": (None, [ctypes.c_void_p]),
+    "wh_batch_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "wh_batch_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "wh_batch_create": (ctypes.c_int, [ctypes.POINTER(wh_instance), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "wh_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "wh_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int32)] * 3),
@@ -220,6 +224,22 @@ def wh_get_timing(layout) -> dict:
     launches = (ctypes.c_int32 * cap)()
     ms = (ctypes.c_double * cap)()
     _check(load().wh_get_timing(layout, ctypes.byref(n), names, launches, ms, cap), "wh_get_timing")
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n.value, cap))}
+
+
+def wh_batch_set_timing(batch, enable: bool) -> None:
+    _check(load().wh_batch_set_timing(batch, 1 if enable else 0), "wh_batch_set_timing")
+
+
+def wh_batch_get_timing(batch) -> dict:
+    """{kernel name: (launches, total ms)} of the batch's eager launches since
+    timing was enabled."""
+    cap = 16
+    n = ctypes.c_int32(0)
+    names = (ctypes.c_char_p * cap)()
+    launches = (ctypes.c_int32 * cap)()
+    ms = (ctypes.c_double * cap)()
+    _check(load().wh_batch_get_timing(batch, ctypes.byref(n), names, launches, ms, cap), "wh_batch_get_timing")
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n.value, cap))}
 
 
@@ -595,6 +615,12 @@ class Batch:
     def status(self, stream=None) -> int:
         return wh_batch_get_status(self.handle, stream)
 
+    def set_timing(self, enable: bool) -> None:
+        wh_batch_set_timing(self.handle, enable)
+
+    def timing(self) -> dict:
+        return wh_batch_get_timing(self.handle)
+
     def close(self):
         if self.handle is not None and self.handle.value:
             wh_batch_destroy(self.handle)
@@ -605,6 +631,161 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class PackedInstances:
+    """Many instances packed into two flat arrays, ready for one copy each
+    across the host link: int32 ``flat`` holds, per instance, order_off,
+    line_sku, slot_map, plan_tour_off and tour_off; ``seq16`` holds every
+    instance's order ids as unsigned 16-bit values (each instance must have
+    at most 65,536 orders).  Segments start on 16-byte boundaries (int32
+    segments on multiples of 4 elements, the 16-bit order ids on multiples of
+    8, so that their int32 widening starts on 32 bytes).  ``pin()`` moves
+    both arrays to pinned host memory; ``device_set()`` makes a device copy
+    with per-instance DeviceProblem / Costs views and a Batch over them."""
+
+    FIELDS = ("order_off", "line_sku", "slot_map", "plan_tour_off", "tour_off")
+
+    def __init__(self, insts):
+        import numpy as np
+        import torch
+        self.geo, self.offsets, self.seq_off, self.n_sku = [], [], [], []
+        self.n_tours, self.n_plans = [], []
+        parts, seqs, pos, spos = [], [], 0, 0
+        for inst in insts:
+            if inst.n_orders > 65536:
+                raise ValueError("16-bit order ids need at most 65,536 orders")
+            lay = inst.layout
+            self.geo.append((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch,
+                             lay.cross_aisle_width))
+            offs = []
+            for f in self.FIELDS:
+                a = np.asarray(getattr(inst, f), np.int32)
+                offs.append((pos, a.size))
+                pad = (-a.size) % 4
+                parts.append(a)
+                if pad:
+                    parts.append(np.zeros(pad, np.int32))
+                pos += a.size + pad
+            self.offsets.append(offs)
+            q = np.asarray(inst.order_seq).astype(np.uint16)
+            self.seq_off.append((spos, q.size))
+            pad = (-q.size) % 8
+            seqs.append(q)
+            if pad:
+                seqs.append(np.zeros(pad, np.uint16))
+            spos += q.size + pad
+            self.n_sku.append(int(inst.n_sku))
+            self.n_tours.append(int(inst.n_tours))
+            self.n_plans.append(int(inst.n_plans))
+        self.flat = torch.from_numpy(np.concatenate(parts) if parts else np.zeros(4, np.int32))
+        self.seq16 = torch.from_numpy((np.concatenate(seqs) if seqs else np.zeros(8, np.uint16)).view(np.int16))
+        self.total_tours, self.total_plans = sum(self.n_tours), sum(self.n_plans)
+
+    def pin(self) -> "PackedInstances":
+        self.flat = self.flat.pin_memory()
+        self.seq16 = self.seq16.pin_memory()
+        return self
+
+    @property
+    def h2d_bytes(self) -> int:
+        return self.flat.numel() * 4 + self.seq16.numel() * 2
+
+    def device_set(self, device="cuda"):
+        return PackedDeviceSet(self, device)
+
+
+class PackedDeviceSet:
+    """Device buffers shaped like a PackedInstances (flat int32 arrays, the
+    16-bit landing buffer and the widened int32 order ids, per-instance
+    outputs) and a Batch over per-instance views of them."""
+
+    def __init__(self, packed: PackedInstances, device="cuda"):
+        import torch
+        self.packed = packed
+        self.flat = torch.empty(packed.flat.numel(), dtype=torch.int32, device=device)
+        self.seq16 = torch.empty(packed.seq16.numel(), dtype=torch.int16, device=device)
+        self.seq = torch.empty(packed.seq16.numel(), dtype=torch.int32, device=device)
+        self.tour_s = torch.empty(max(packed.total_tours, 1), dtype=torch.int32, device=device)
+        self.tour_rr = torch.empty_like(self.tour_s)
+        self.plan_s = torch.empty(max(packed.total_plans, 1), dtype=torch.int64, device=device)
+        self.plan_rr = torch.empty_like(self.plan_s)
+        items, t0, p0 = [], 0, 0
+        for i, geo in enumerate(packed.geo):
+            v = [self.flat[o:o + n] for o, n in packed.offsets[i]]
+            so, sn = packed.seq_off[i]
+            prob = DeviceProblem(v[0], v[1], v[2], v[3], v[4], self.seq[so:so + sn], packed.n_sku[i])
+            nt, npl = packed.n_tours[i], packed.n_plans[i]
+            costs = Costs(self.tour_s[t0:t0 + nt], self.tour_rr[t0:t0 + nt], self.plan_s[p0:p0 + npl],
+                          self.plan_rr[p0:p0 + npl])
+            items.append((geo, prob, costs))
+            t0 += nt
+            p0 += npl
+        self.items = items
+        self.batch = Batch(items)
+
+    def load(self, stream=None) -> None:
+        """Copy the packed host arrays in and widen the order ids, on `stream`."""
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            self.flat.copy_(self.packed.flat, non_blocking=True)
+            self.seq16.copy_(self.packed.seq16, non_blocking=True)
+            _check(load().wh_widen_u16(ctypes.c_void_p(_ptr(self.seq16)), ctypes.c_void_p(_ptr(self.seq)),
+                                       self.seq.numel(), _stream_ptr(s)), "wh_widen_u16")
+
+    def close(self):
+        self.batch.close()
+
+
+class PackedPipeline:
+    """End-to-end batched scoring from pinned host memory: every submitted
+    step copies all instances' inputs in (one copy of the int32 arrays, one
+    of the 16-bit order ids, widened on the device), scores them in one
+    persistent launch replayed as a CUDA graph, and copies every plan's two
+    costs back to a pinned host array.  Two device sets alternate, so the
+    copy of one step (copy stream) overlaps the evaluation of the previous
+    one (compute stream)."""
+
+    def __init__(self, packed: PackedInstances, mask: int = 3, tuning=None, slots: int = 2):
+        import torch
+        self.packed, self.mask = packed, mask
+        self.sets = [PackedDeviceSet(packed) for _ in range(slots)]
+        if tuning is not None:
+            for d in self.sets:
+                d.batch.set_tuning(*tuning)
+        self.copy, self.compute = torch.cuda.Stream(), torch.cuda.Stream()
+        self.copied = [torch.cuda.Event() for _ in self.sets]
+        self.done = [torch.cuda.Event() for _ in self.sets]
+        self.out = [torch.empty((2, max(packed.total_plans, 1)), dtype=torch.int64).pin_memory()
+                    for _ in self.sets]
+        self.k = 0
+
+    def submit(self):
+        """Enqueue one step; returns (ticket, bytes host->device, bytes device->host)."""
+        slot = self.k % len(self.sets)
+        self.k += 1
+        d = self.sets[slot]
+        self.copy.wait_event(self.done[slot])      # the set's previous step is finished
+        d.load(self.copy)
+        self.copied[slot].record(self.copy)
+        self.compute.wait_event(self.copied[slot])
+        import torch
+        with torch.cuda.stream(self.compute):
+            d.batch.eval(self.mask, self.compute, graph=True)
+            n = self.packed.total_plans
+            self.out[slot][0, :n].copy_(d.plan_s[:n], non_blocking=True)
+            self.out[slot][1, :n].copy_(d.plan_rr[:n], non_blocking=True)
+            self.done[slot].record(self.compute)
+        return slot, self.packed.h2d_bytes, 2 * 8 * self.packed.total_plans
+
+    def wait(self, ticket):
+        self.done[ticket].synchronize()
+        return self.out[ticket]
+
+    def close(self):
+        for d in self.sets:
+            d.close()
 
 
 # ----------------------------------------------------------------- surrogate

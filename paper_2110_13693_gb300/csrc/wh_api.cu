@@ -13,6 +13,15 @@
 
 #include "wh_internal.h"
 
+// Per-kernel CUDA-event timing of a handle's launches (wh_set_timing,
+// wh_batch_set_timing): a pool of event pairs, reused across sessions.
+struct KernelTiming {
+    bool on = false;
+    std::vector<cudaEvent_t> events;       // pairs: [2i] before, [2i+1] after launch i
+    std::vector<int> kernel;               // kernel id of each recorded pair
+    size_t n = 0;                          // pairs recorded this session
+};
+
 struct wh_layout {
     wh_layout_desc d;
     wh::Geo g;
@@ -35,11 +44,7 @@ struct wh_layout {
     const int64_t* last_task_off = nullptr;
     const int4* last_tasks = nullptr;
     const int2* last_task_cost = nullptr;
-    // kernel timing (wh_set_timing)
-    bool timing = false;
-    std::vector<cudaEvent_t> events;       // pool, reused across sessions
-    std::vector<int> event_kernel;         // kernel id of each recorded pair
-    size_t n_recorded = 0;                 // pairs recorded this session
+    KernelTiming timing;                   // wh_set_timing
 };
 
 struct wh_batch {
@@ -61,6 +66,7 @@ struct wh_batch {
     int32_t chunks_per_item = 16;
     cudaStream_t capture = nullptr;
     cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};   // per routing mask
+    KernelTiming timing;                   // wh_batch_set_timing (eager launches only)
 };
 
 namespace {
@@ -70,31 +76,58 @@ const char* const kKernelNames[K_COUNT] = {"k_prep", "k_eval_short", "k_eval_lon
 // Brackets one launch with events when timing is on.
 class LaunchTimer {
   public:
-    LaunchTimer(wh_layout* h, int kernel, cudaStream_t s) : h_(h), s_(s) {
-        if (!h_->timing) return;
-        const size_t need = 2 * (h_->n_recorded + 1);
-        while (h_->events.size() < need) {
+    LaunchTimer(KernelTiming& t, int kernel, cudaStream_t s) : t_(t), s_(s) {
+        if (!t_.on) return;
+        const size_t need = 2 * (t_.n + 1);
+        while (t_.events.size() < need) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) { ok_ = false; return; }
-            h_->events.push_back(e);
+            t_.events.push_back(e);
         }
-        if (h_->event_kernel.size() < h_->n_recorded + 1) h_->event_kernel.resize(h_->n_recorded + 1);
-        h_->event_kernel[h_->n_recorded] = kernel;
-        ok_ = cudaEventRecord(h_->events[2 * h_->n_recorded], s_) == cudaSuccess;
+        if (t_.kernel.size() < t_.n + 1) t_.kernel.resize(t_.n + 1);
+        t_.kernel[t_.n] = kernel;
+        ok_ = cudaEventRecord(t_.events[2 * t_.n], s_) == cudaSuccess;
         armed_ = ok_;
     }
     ~LaunchTimer() {
         if (!armed_) return;
-        if (cudaEventRecord(h_->events[2 * h_->n_recorded + 1], s_) == cudaSuccess) ++h_->n_recorded;
+        if (cudaEventRecord(t_.events[2 * t_.n + 1], s_) == cudaSuccess) ++t_.n;
     }
     bool ok() const { return ok_; }
 
   private:
-    wh_layout* h_;
+    KernelTiming& t_;
     cudaStream_t s_;
     bool ok_ = true;
     bool armed_ = false;
 };
+
+// Per-kernel launches and summed milliseconds of a timing session
+// (synchronises on the recorded events).
+int read_timing(const KernelTiming& t, int n_kinds, const char* const* kinds, int32_t* n_kernels,
+                const char** names, int32_t* launches, double* total_ms, int32_t cap) {
+    std::vector<double> ms(n_kinds, 0.0);
+    std::vector<int32_t> cnt(n_kinds, 0);
+    for (size_t i = 0; i < t.n; ++i) {
+        float e = 0.f;
+        if (cudaEventSynchronize(t.events[2 * i + 1]) != cudaSuccess) return WH_ECUDA;
+        if (cudaEventElapsedTime(&e, t.events[2 * i], t.events[2 * i + 1]) != cudaSuccess) return WH_ECUDA;
+        ms[t.kernel[i]] += e;
+        cnt[t.kernel[i]] += 1;
+    }
+    *n_kernels = n_kinds;
+    for (int32_t k = 0; k < n_kinds && k < cap; ++k) {
+        names[k] = kinds[k];
+        launches[k] = cnt[k];
+        total_ms[k] = ms[k];
+    }
+    return WH_OK;
+}
+
+void free_timing(KernelTiming& t) {
+    for (cudaEvent_t e : t.events) cudaEventDestroy(e);
+    t.events.clear();
+}
 
 constexpr size_t kAlign = 256;
 constexpr int32_t kBatchLongCap = 1 << 22;
@@ -281,15 +314,15 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     a.long_list = reinterpret_cast<int32_t*>(base + key_bytes + agg_bytes);
 
     {
-        LaunchTimer lt(h, K_PREP, s);
+        LaunchTimer lt(h->timing, K_PREP, s);
         if (!lt.ok() || wh::launch_prep(a, s) != cudaSuccess) return WH_ECUDA;
     }
     {
-        LaunchTimer lt(h, wh::sshape_kernel_applies(a) ? K_EVAL_SSHAPE : K_EVAL_SHORT, s);
+        LaunchTimer lt(h->timing, wh::sshape_kernel_applies(a) ? K_EVAL_SSHAPE : K_EVAL_SHORT, s);
         if (!lt.ok() || wh::launch_eval_short(a, t, h->num_sms, s, nullptr) != cudaSuccess) return WH_ECUDA;
     }
     if (p.n_tours > 0) {
-        LaunchTimer lt(h, K_EVAL_LONG, s);
+        LaunchTimer lt(h->timing, K_EVAL_LONG, s);
         wh::LongArgs L;
         L.single = a;
         L.insts = nullptr;
@@ -780,40 +813,23 @@ extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) 
 
 extern "C" int wh_set_timing(wh_layout* h, int enable) {
     if (!h) return WH_EINVAL;
-    h->timing = enable != 0;
-    h->n_recorded = 0;
+    h->timing.on = enable != 0;
+    h->timing.n = 0;
     return WH_OK;
 }
 
 extern "C" int wh_get_timing(wh_layout* h, int32_t* n_kernels, const char** names, int32_t* launches,
                              double* total_ms, int32_t cap) {
     if (!h || !n_kernels || cap < 0 || (cap > 0 && (!names || !launches || !total_ms))) return WH_EINVAL;
-    double ms[K_COUNT] = {};
-    int32_t cnt[K_COUNT] = {};
-    if (h->n_recorded > 0) {
-        DeviceGuard guard(h->device);
-        for (size_t i = 0; i < h->n_recorded; ++i) {
-            float e = 0.f;
-            if (cudaEventSynchronize(h->events[2 * i + 1]) != cudaSuccess) return WH_ECUDA;
-            if (cudaEventElapsedTime(&e, h->events[2 * i], h->events[2 * i + 1]) != cudaSuccess) return WH_ECUDA;
-            ms[h->event_kernel[i]] += e;
-            cnt[h->event_kernel[i]] += 1;
-        }
-    }
-    *n_kernels = K_COUNT;
-    for (int32_t k = 0; k < K_COUNT && k < cap; ++k) {
-        names[k] = kKernelNames[k];
-        launches[k] = cnt[k];
-        total_ms[k] = ms[k];
-    }
-    return WH_OK;
+    DeviceGuard guard(h->device);
+    return read_timing(h->timing, K_COUNT, kKernelNames, n_kernels, names, launches, total_ms, cap);
 }
 
 extern "C" void wh_destroy(wh_layout* h) {
     if (!h) return;
     if (h->device >= 0) {
         DeviceGuard guard(h->device);
-        for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+        free_timing(h->timing);
         if (h->mv_scratch) cudaFree(h->mv_scratch);
         if (h->mv_tasks) cudaFree(h->mv_tasks);
         if (h->mv_long) cudaFree(h->mv_long);
@@ -888,10 +904,23 @@ wh::BatchArgs batch_args(const wh_batch* b, uint32_t mask) {
     return B;
 }
 
-int launch_batch(wh_batch* b, uint32_t mask, cudaStream_t s) {
+enum BatchKernelId { KB_PREP = 0, KB_EVAL = 1, KB_LONG = 2, KB_COUNT = 3 };
+const char* const kBatchKernelNames[KB_COUNT] = {"k_prep_batch", "k_eval_batch", "k_eval_long"};
+
+// The batch's launch sequence; `timed`: bracket each launch with the batch's
+// timing events when its timing is on (never while capturing a graph)
+int launch_batch(wh_batch* b, uint32_t mask, cudaStream_t s, bool timed = false) {
+    KernelTiming off;
+    KernelTiming& tm = timed ? b->timing : off;
     const wh::BatchArgs B = batch_args(b, mask);
-    if (wh::launch_prep_batch(B, b->max_work, s) != cudaSuccess) return WH_ECUDA;
-    if (wh::launch_eval_batch(B, b->tune, b->key16, b->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    {
+        LaunchTimer lt(tm, KB_PREP, s);
+        if (wh::launch_prep_batch(B, b->max_work, s) != cudaSuccess) return WH_ECUDA;
+    }
+    {
+        LaunchTimer lt(tm, KB_EVAL, s);
+        if (wh::launch_eval_batch(B, b->tune, b->key16, b->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    }
     wh::LongArgs L;
     std::memset(&L, 0, sizeof(L));
     L.insts = b->d_args;
@@ -899,6 +928,7 @@ int launch_batch(wh_batch* b, uint32_t mask, cudaStream_t s) {
     L.count = B.long_count;
     L.cap = b->long_cap;
     L.mask = mask;
+    LaunchTimer lt(tm, KB_LONG, s);
     if (wh::launch_eval_long(L, true, b->num_sms, s) != cudaSuccess) return WH_ECUDA;
     return WH_OK;
 }
@@ -1009,7 +1039,21 @@ extern "C" int wh_batch_eval(wh_batch* b, uint32_t routing_mask, void* stream) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return WH_ECUDA;
     if (dev != b->device) return WH_EINVAL;
-    return launch_batch(b, routing_mask, static_cast<cudaStream_t>(stream));
+    return launch_batch(b, routing_mask, static_cast<cudaStream_t>(stream), true);
+}
+
+extern "C" int wh_batch_set_timing(wh_batch* b, int enable) {
+    if (!b) return WH_EINVAL;
+    b->timing.on = enable != 0;
+    b->timing.n = 0;
+    return WH_OK;
+}
+
+extern "C" int wh_batch_get_timing(wh_batch* b, int32_t* n_kernels, const char** names, int32_t* launches,
+                                   double* total_ms, int32_t cap) {
+    if (!b || !n_kernels || cap < 0 || (cap > 0 && (!names || !launches || !total_ms))) return WH_EINVAL;
+    DeviceGuard guard(b->device);
+    return read_timing(b->timing, KB_COUNT, kBatchKernelNames, n_kernels, names, launches, total_ms, cap);
 }
 
 extern "C" int wh_batch_eval_graph(wh_batch* b, uint32_t routing_mask, void* stream) {
@@ -1196,6 +1240,7 @@ extern "C" void wh_batch_destroy(wh_batch* b) {
     if (b->device >= 0) {
         DeviceGuard guard(b->device);
         drop_graphs(b);
+        free_timing(b->timing);
         if (b->capture) cudaStreamDestroy(b->capture);
         if (b->d_items) cudaFree(b->d_items);
         if (b->d_args) cudaFree(b->d_args);

@@ -174,3 +174,45 @@ def test_batched_full_size_sampled(gpu_lib):
         assert np.array_equal(tr[idx], sub[1]) and np.array_equal(ts[idx], sub[0])
         assert np.array_equal(pr[plans], sub[3]) and np.array_equal(ps[plans], sub[2])
     batch.close()
+
+
+def test_packed_instances_device_set_and_host_pipeline(gpu_lib):
+    """The benchmark's packed layout: all instances' int32 arrays in one flat
+    buffer and the order ids as 16-bit values widened on the device.  The
+    device set scores every instance exactly as the oracle does; the host
+    pipeline (two device sets, copies overlapping evaluation) returns the same
+    plan costs on every submitted step; per-kernel timing counts the eager
+    launches only."""
+    import torch
+    wh = gpu_lib
+    insts = [wh_gen.batched_instance(9, i, n_plans=5) for i in range(20)]
+    want = [oracle.eval_plans(inst) for inst in insts]
+    packed = wh.PackedInstances(insts)
+    d = packed.device_set()
+    d.load()
+    d.batch.set_timing(True)
+    d.batch.eval(3)
+    d.batch.eval(3, graph=True)
+    kt = d.batch.timing()
+    d.batch.set_timing(False)
+    torch.cuda.synchronize()
+    assert d.batch.status() == 0
+    assert kt["k_eval_batch"][0] == 1 and kt["k_prep_batch"][0] == 1 and kt["k_eval_batch"][1] > 0
+    for i, (_, prob, c) in enumerate(d.items):
+        got = (c.tour_s[:prob.n_tours].cpu().numpy(), c.tour_rr[:prob.n_tours].cpu().numpy(),
+               c.plan_s[:prob.n_plans].cpu().numpy(), c.plan_rr[:prob.n_plans].cpu().numpy())
+        assert_same(got, want[i], f"packed instance {i}")
+    all_s = np.concatenate([w[2] for w in want])
+    all_r = np.concatenate([w[3] for w in want])
+    packed.pin()
+    pipe = wh.PackedPipeline(packed, 3, tuning=d.batch.tuning())
+    tickets = [pipe.submit() for _ in range(3)]
+    assert tickets[0][1] == packed.h2d_bytes and tickets[0][2] == 16 * packed.total_plans
+    for tk, _, _ in tickets[-2:]:
+        out = pipe.wait(tk)
+        assert np.array_equal(out[0, :packed.total_plans].numpy(), all_s)
+        assert np.array_equal(out[1, :packed.total_plans].numpy(), all_r)
+    for s in pipe.sets:
+        assert s.batch.status() == 0
+    pipe.close()
+    d.close()
