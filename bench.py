@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--extra-steps", type=int, default=20)
     ap.add_argument("--ab-steps", type=int, default=100, help="plain local-search steps of the prescreen A/B")
     ap.add_argument("--train-steps", type=int, default=2500)
-    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small"], default=None,
+    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small", "sshape-small"], default=None,
                     help="run a small case of one kernel three times (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -141,13 +141,14 @@ def algorithmic_bytes_one_rule(inst):
 
 def run_sshape(wh, lay, probs, batches, costs, stream, steps):
     """The streaming path: the same plan batches scored under the S-shape
-    rule alone (its own sort-free kernel), with the HBM roofline of that
-    kernel from CUDA events around each launch."""
+    rule alone (per-order aggregates built by k_prep on every call, then the
+    sort-free streaming kernel).  Two rooflines: the streaming kernel alone
+    (CUDA events around each launch) and the whole step (prep + kernel,
+    back-to-back calls timed by two events, no per-kernel events)."""
     import torch
     for i in range(3):
         lay.eval_plans(probs[i % len(probs)], costs, 1, stream)
     torch.cuda.synchronize()
-    lay.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     n_tours = 0
@@ -156,20 +157,29 @@ def run_sshape(wh, lay, probs, batches, costs, stream, steps):
         n_tours += batches[i % len(batches)].n_tours
     e1.record(stream)
     torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lay.set_timing(True)
+    for i in range(steps):
+        lay.eval_plans(probs[i % len(probs)], costs, 1, stream)
     kt = lay.timing()
     lay.set_timing(False)
+    torch.cuda.synchronize()
     assert lay.status() == 0
-    ms = e0.elapsed_time(e1)
     name, (launches, kms) = max(kt.items(), key=lambda kv: kv[1][1])
     per_launch_s = kms / 1e3 / max(launches, 1)
     alg = sum(algorithmic_bytes_one_rule(batches[i % len(batches)]) for i in range(steps)) / steps
     peak, kind = measured_peaks()
     achieved = alg / per_launch_s / 1e9
-    return {"workload": "the headline plan batches, S-shape rule only", "tours_per_s": n_tours / (ms / 1e3),
+    step_s = ms / 1e3 / steps
+    return {"workload": "the mid-size plan batches, S-shape rule only", "tours_per_s": n_tours / (ms / 1e3),
             "ms_per_step": ms / steps, "steps": steps,
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in kt.items()},
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_launch": alg,
-                         "launch_ms": per_launch_s * 1e3}}
+                         "launch_ms": per_launch_s * 1e3},
+            "step_roofline": {"bound": "hbm", "achieved": alg / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": alg / step_s / 1e9 / peak, "peak_kind": kind,
+                              "note": "whole wh_eval_plans call: per-order aggregates (k_prep) + streaming kernel"}}
 
 
 def measured_peaks():
@@ -306,6 +316,14 @@ def run_moves(wh, dev, steps, cpu=True):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     n_ok = int((s == 0).sum().item())
+    walked, walked_lines = lay.move_stats()
+    # algorithmic bytes of one call: per move its record (16 B), both deltas
+    # (16 B) and its status (4 B); per changed tour walked its task record
+    # (16 B), its two tour offsets and two current costs (16 B), and per line
+    # of it the SKU and the SKU's location under the plan's slotting (8 B)
+    mv_bytes = n_plans * M * 36 + walked * 32 + walked_lines * 8
+    peak, kind = measured_peaks()
+    mv_ach = mv_bytes / (el / steps) / 1e9
     o_mv = None
     if cpu:
         # the CPU baseline: the oracle on the first plan's 64 moves (each
@@ -360,6 +378,10 @@ def run_moves(wh, dev, steps, cpu=True):
                         "16,384 plans x 64 moves per step (order swap / relocate / SKU-slot swap)",
             "moves_per_step": n_plans * M, "ms_per_step": el * 1e3 / steps,
             "move_deltas_per_s": n_plans * M * steps / el, "evaluated_fraction": n_ok / (n_plans * M),
+            "changed_tours_per_step": walked, "changed_tour_lines_per_step": walked_lines,
+            "roofline": {"bound": "hbm", "achieved": mv_ach, "peak": peak, "unit": "GB/s", "frac": mv_ach / peak,
+                         "peak_kind": kind, "algorithmic_bytes_per_step": mv_bytes,
+                         "note": "whole wh_eval_moves call (wall clock, one synchronisation per call)"},
             "ls_step_ms": el2 * 1e3 / steps, "plans_improved_per_step": improved / steps, "steps": steps,
             "cpu_baseline": None if o_mv is None else {
                 "value": M / o_mv, "unit": "move deltas/s", "cores": 1, "kind": "oracle",
@@ -630,6 +652,11 @@ def run_surrogate_ab(wh, dev, steps, train_steps, cpu=True):
                                  "kind": "oracle", "sample": f"the first {n_c} tours, {o_s:.2f} s"}
     del Xs, ts, X_train, t_train
 
+    def moves_fn0(step):
+        mv = wh_gen.gen_moves(22, step, inst0, M)
+        mv[..., 3] = np.arange(n_plans)[:, None]
+        return torch.as_tensor(mv.reshape(-1, 4)).to(dev)
+
     def population():
         base = wh.to_device(inst0, dev)
         smap = base.slot_map.repeat(n_plans)
@@ -637,46 +664,81 @@ def run_surrogate_ab(wh, dev, steps, train_steps, cpu=True):
                                 base.order_seq.clone(), inst0.n_sku, inst0.n_sku)
         return prob, wh.evaluate(lay, prob)
 
-    moves = {}
-
-    def moves_fn(step):
-        if step not in moves:
-            mv = wh_gen.gen_moves(23, step, inst0, M)
-            mv[..., 3] = np.arange(n_plans)[:, None]
-            moves[step] = torch.as_tensor(mv.reshape(-1, 4)).to(dev)
-        return moves[step]
-
-    for s in range(steps * 2):
-        moves_fn(s)                       # generated outside the timed searches
     keep = search.keep_count(M)
-    # untimed warm-up of both arms on a throwaway population: the first use
+
+    def ab(seed):
+        """Plain exact search (`steps` steps) and, from the same start over the
+        same sequence of move sets, screened search with the trained network
+        and screened search keeping a seeded random `keep` of the moves (the
+        same exact re-scores without the network), both for twice as many
+        steps; wall clock of every step."""
+        moves = {}
+
+        def moves_fn(step):
+            if step not in moves:
+                mv = wh_gen.gen_moves(seed, step, inst0, M)
+                mv[..., 3] = np.arange(n_plans)[:, None]
+                moves[step] = torch.as_tensor(mv.reshape(-1, 4)).to(dev)
+            return moves[step]
+
+        for st in range(steps * 2):
+            moves_fn(st)                  # generated outside the timed searches
+        gen = torch.Generator(device=dev).manual_seed(seed)
+        rand_idx = {}
+
+        def random_fn(step):
+            if step not in rand_idx:
+                rand_idx[step] = torch.argsort(torch.rand((n_plans, M), device=dev, generator=gen), dim=1)[:, :keep]
+            mv = moves_fn(step).view(n_plans, M, 4)
+            return mv[torch.arange(n_plans, device=dev)[:, None], rand_idx[step]].reshape(-1, 4).contiguous()
+
+        for st in range(steps * 2):
+            random_fn(st)
+        prob, costs = population()
+        start_best = int(costs.plan_rr[:n_plans].min().item())
+        plain = search.run_search(wh, lay, prob, costs, moves_fn, steps, M, 24, 0)
+        target = plain[-1][1]
+        prob, costs = population()
+        screened = search.run_search(wh, lay, prob, costs, moves_fn, steps * 2, M, 24, 0, sg=sg, keep=keep)
+        prob, costs = population()
+        rand = search.run_search(wh, lay, prob, costs, random_fn, steps * 2, keep, 24, 0)
+        hit = next((tr[0] for tr in screened if tr[1] <= target), None)
+        t_eq = plain[-1][0]
+        best_at_eq = min((tr[1] for tr in screened if tr[0] <= t_eq), default=start_best)
+        rand_at_eq = min((tr[1] for tr in rand if tr[0] <= t_eq), default=start_best)
+        return {"move_seed": seed, "start_best": start_best,
+                "plain": {"steps": len(plain), "seconds": plain[-1][0], "best": plain[-1][1], "mean": plain[-1][2],
+                          "ms_per_step": plain[-1][0] * 1e3 / len(plain)},
+                "screened": {"steps": len(screened), "seconds": screened[-1][0], "best": screened[-1][1],
+                             "mean": screened[-1][2], "ms_per_step": screened[-1][0] * 1e3 / len(screened),
+                             "seconds_to_plain_best": hit, "best_at_plain_wall_time": best_at_eq,
+                             "mean_after_plain_steps": screened[steps - 1][2]},
+                "random_keep": {"steps": len(rand), "seconds": rand[-1][0], "best": rand[-1][1], "mean": rand[-1][2],
+                                "ms_per_step": rand[-1][0] * 1e3 / len(rand), "best_at_plain_wall_time": rand_at_eq,
+                                "mean_after_plain_steps": rand[steps - 1][2]},
+                "screened_reaches_plain_best_faster": hit is not None and hit < plain[-1][0]}
+
+    # untrained warm-up of every arm on a throwaway population: the first use
     # of every kernel (ours and torch's) stays out of the timed searches
     prob, costs = population()
-    search.run_search(wh, lay, prob, costs, moves_fn, 2, M, 24, 0)
-    search.run_search(wh, lay, prob, costs, moves_fn, 2, M, 24, 0, sg=sg, keep=keep)
-    prob, costs = population()
-    start_best = int(costs.plan_rr[:n_plans].min().item())
-    plain = search.run_search(wh, lay, prob, costs, moves_fn, steps, M, 24, 0)
-    target = plain[-1][1]
-    prob, costs = population()
-    screened = search.run_search(wh, lay, prob, costs, moves_fn, steps * 2, M, 24, 0, sg=sg, keep=keep)
-    hit = next((tr[0] for tr in screened if tr[1] <= target), None)
-    t_eq = plain[-1][0]
-    best_at_eq = min((tr[1] for tr in screened if tr[0] <= t_eq), default=start_best)
+    search.run_search(wh, lay, prob, costs, lambda st: moves_fn0(st), 2, M, 24, 0)
+    search.run_search(wh, lay, prob, costs, lambda st: moves_fn0(st), 2, M, 24, 0, sg=sg, keep=keep)
+    runs = [ab(seed) for seed in (23, 24, 25)]
     assert lay.status() == 0
     sg.close()
     lay.close()
+    first = runs[0]
     return {"workload": "paper scale, 16,384 plans with their own slottings, 64 moves per plan per step; "
                         f"surrogate trained on {4 * inst0.n_tours} exactly scored tours of the same generator",
             "surrogate_mean_rel_error": mean_err, "surrogate_p99_rel_error": p99_err, "inference": infer,
             "held_out_tours": 500000, "train_steps": train_steps, "batch": 4096, "train_seconds": train_s,
-            "data_seconds": data_s, "keep_per_plan": keep, "start_best": start_best,
-            "plain": {"steps": len(plain), "seconds": plain[-1][0], "best": plain[-1][1], "mean": plain[-1][2],
-                      "ms_per_step": plain[-1][0] * 1e3 / len(plain)},
-            "screened": {"steps": len(screened), "seconds": screened[-1][0], "best": screened[-1][1],
-                         "mean": screened[-1][2], "ms_per_step": screened[-1][0] * 1e3 / len(screened),
-                         "seconds_to_plain_best": hit, "best_at_plain_wall_time": best_at_eq},
-            "screened_reaches_plain_best_faster": hit is not None and hit < plain[-1][0]}
+            "data_seconds": data_s, "keep_per_plan": keep, "start_best": first["start_best"],
+            "plain": first["plain"], "screened": first["screened"], "random_keep": first["random_keep"],
+            "screened_reaches_plain_best_faster": first["screened_reaches_plain_best_faster"],
+            "seeds": runs,
+            "screened_faster_all_seeds": all(r["screened_reaches_plain_best_faster"] for r in runs),
+            "screened_beats_random_keep_all_seeds": all(
+                r["screened"]["mean_after_plain_steps"] < r["random_keep"]["mean_after_plain_steps"] for r in runs)}
 
 
 # ----------------------------------------------- batched workload helpers
@@ -1031,7 +1093,7 @@ def run_ours(args):
         "plans_per_s": world * packed.total_plans * args.steps / (elapsed_ms / 1e3),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps},
+                "steps": e_steps},
         "gpu_launches": launches_per_step * args.steps,
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
                         "share": round(v[1] / max(sum(x[1] for x in ktime.values()), 1e-12), 4)}
@@ -1106,7 +1168,18 @@ def run_case(name):
     from paper_2110_13693_gb300 import build as whbuild
     whbuild.build()
     wh.load()
-    if name == "batched-small":
+    if name == "sshape-small":
+        # one mid-size batch (4,096 plans) under the S-shape rule alone, three calls
+        inst = wh_gen.midsize(seed=2, n_plans=PLANS_PER_STEP)
+        lay = wh.Layout.of(inst.layout)
+        prob = wh.to_device(inst)
+        costs = wh.alloc_costs(prob.n_tours, prob.n_plans)
+        for _ in range(3):
+            lay.eval_plans(prob, costs, 1)
+        torch.cuda.synchronize()
+        assert lay.status() == 0
+        lay.close()
+    elif name == "batched-small":
         items = []
         for i in range(128):
             inst = wh_gen.batched_instance(3, i, n_plans=64)

@@ -347,6 +347,18 @@ int wh_surrogate_get_params(wh_surrogate *s, float *host_params, float *host_gra
  * WH_ECUDA. */
 int wh_surrogate_predict(wh_surrogate *s, const uint16_t *X, int64_t n, float *y, void *stream);
 
+/* Test of the prediction kernel's failure handling (no counterpart in the
+ * paper): the same launch as wh_surrogate_predict, but the kernel's producer
+ * stops before 128-row tile `skip_tile` (0 <= skip_tile < ceil(n / 128)) and
+ * every barrier wait gives up after wait_ns nanoseconds (1,000 ..
+ * 2,000,000,000).  The wait for that tile's features then runs out: the CTA
+ * sets WH_STATUS_TIMEOUT in the surrogate's status word, its other roles leave
+ * their loops, copies and MMAs in flight are waited for and the tensor memory
+ * is freed, so the context stays usable; y is incomplete.  Read the status
+ * with wh_surrogate_get_status.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_surrogate_predict_timeout_test(wh_surrogate *s, const uint16_t *X, int64_t n, float *y, int64_t skip_tile,
+                                      uint64_t wait_ns, void *stream);
+
 /* Read and clear the surrogate's device status word (WH_STATUS_* bits of the
  * prediction kernels).  Synchronises the device. */
 int wh_surrogate_get_status(wh_surrogate *s, uint32_t *out);
@@ -477,8 +489,9 @@ int wh_batch_eval(wh_batch *b, uint32_t routing_mask, void *stream);
  * routing_mask captures (on a private stream) and instantiates. */
 int wh_batch_eval_graph(wh_batch *b, uint32_t routing_mask, void *stream);
 
-/* Autotuner: time candidate launch shapes (CTA size x chunks per item) on
- * this batch with the given mask, keep the fastest and report it.  When
+/* Autotuner: time candidate launch shapes (CTA size 128 or 256 x 2 to 4,096
+ * chunks of 32 tours per work item) on this batch with the given mask, keep
+ * the fastest and report it.  When
  * cache_path is not NULL the choice is looked up first, and stored after, in
  * that JSON file under a key built from the batch's size bucket (key width,
  * instance count, total tours, largest order book, mask).  Synchronises
@@ -504,6 +517,12 @@ int wh_widen_u16(const uint16_t *src, int32_t *dst, int64_t n, void *stream);
  * calls since the last read).  Synchronises `stream`.  Returns WH_OK,
  * WH_EINVAL or WH_ECUDA. */
 int wh_get_last_status(wh_layout *layout, void *stream, uint32_t *status);
+
+/* Work of the last wh_eval_moves call on this handle (measurement aid; no
+ * counterpart in the paper): *tours = changed tours walked (one per task of
+ * the moves: the tours a move rewrites), *lines = their order lines.
+ * Synchronises `stream`.  Returns WH_OK, WH_EINVAL or WH_ECUDA. */
+int wh_get_move_stats(wh_layout *layout, void *stream, int64_t *tours, int64_t *lines);
 
 /* Kernel timing of a batch (tracing aid; no counterpart in the paper), as
  * wh_set_timing / wh_get_timing for a layout: while enabled, every kernel that

@@ -76,6 +76,8 @@ SIGNATURES = {
                                              ctypes.POINTER(wh_plans), ctypes.c_uint32,
                                              ctypes.POINTER(wh_costs), ctypes.c_void_p, ctypes.c_void_p]),
     "wh_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "wh_get_move_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int64)]),
     "wh_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
@@ -108,6 +110,9 @@ SIGNATURES = {
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "wh_surrogate_predict_timeout_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                                         ctypes.c_void_p]),
     "wh_surrogate_get_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.c_void_p]),
     "wh_batch_grow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(wh_orders), ctypes.c_void_p, ctypes.c_int64,
@@ -210,6 +215,14 @@ def wh_get_last_status(layout, stream=None) -> int:
     v = ctypes.c_uint32(0)
     _check(load().wh_get_last_status(layout, _stream_ptr(stream), ctypes.byref(v)), "wh_get_last_status")
     return int(v.value)
+
+
+def wh_get_move_stats(layout, stream=None):
+    """(changed tours walked, their lines) of the last wh_eval_moves call."""
+    t, l = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().wh_get_move_stats(layout, _stream_ptr(stream), ctypes.byref(t), ctypes.byref(l)),
+           "wh_get_move_stats")
+    return int(t.value), int(l.value)
 
 
 def wh_set_timing(layout, enable: bool) -> None:
@@ -495,6 +508,9 @@ class Layout:
 
     def timing(self) -> dict:
         return wh_get_timing(self.handle)
+
+    def move_stats(self, stream=None):
+        return wh_get_move_stats(self.handle, stream)
 
     def close(self):
         if self.handle is not None and self.handle.value:
@@ -850,6 +866,12 @@ def wh_surrogate_get_status(s) -> int:
 def wh_surrogate_predict(s, X, n: int, y, stream=None) -> None:
     _check(load().wh_surrogate_predict(s, ctypes.c_void_p(X), n, ctypes.c_void_p(y), _stream_ptr(stream)),
            "wh_surrogate_predict")
+
+
+def wh_surrogate_predict_timeout_test(s, X, n: int, y, skip_tile: int, wait_ns: int, stream=None) -> None:
+    _check(load().wh_surrogate_predict_timeout_test(s, ctypes.c_void_p(X), n, ctypes.c_void_p(y), skip_tile,
+                                                    wait_ns, _stream_ptr(stream)),
+           "wh_surrogate_predict_timeout_test")
 
 
 def wh_surrogate_train_step(s, X, target, n: int, lr: float, loss=0, stream=None) -> None:

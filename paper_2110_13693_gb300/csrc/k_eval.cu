@@ -220,23 +220,36 @@ __device__ __forceinline__ void prep_instance(const EvalArgs& a, uint32_t mask, 
                 flag(a.status, WH_STATUS_BAD_OFFSET);
                 fl = 4u;
             } else {
-                for (int l = lb; l < le; ++l) {
-                    const int sku = a.line_sku[l];
-                    if ((unsigned)sku >= (unsigned)a.n_sku) {
-                        flag(a.status, WH_STATUS_BAD_SKU);
-                        fl |= 1u;
-                        continue;
+                // four lines a step: their SKU loads, then their slot loads,
+                // in flight together
+                for (int l0 = lb; l0 < le; l0 += 4) {
+                    int sku[4], loc[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sku[j] = l0 + j < le ? a.line_sku[l0 + j] : -1;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        loc[j] = -1;
+                        if (l0 + j >= le) continue;
+                        if ((unsigned)sku[j] >= (unsigned)a.n_sku) {
+                            flag(a.status, WH_STATUS_BAD_SKU);
+                            fl |= 1u;
+                            continue;
+                        }
+                        loc[j] = a.slot_map[sku[j]];
+                        if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) {
+                            flag(a.status, WH_STATUS_BAD_LOC);
+                            fl |= 1u;
+                            loc[j] = -1;
+                        }
                     }
-                    const int loc = a.slot_map[sku];
-                    if ((unsigned)loc >= (unsigned)a.g.n_loc) {
-                        flag(a.status, WH_STATUS_BAD_LOC);
-                        fl |= 1u;
-                        continue;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (loc[j] < 0) continue;
+                        const uint32_t key = loc_key(a.g, loc[j]);
+                        bits |= 1ull << (key >> 16);
+                        kmax = max(kmax, key);
+                        fl |= 2u;
                     }
-                    const uint32_t key = loc_key(a.g, loc);
-                    bits |= 1ull << (key >> 16);
-                    kmax = max(kmax, key);
-                    fl |= 2u;
                 }
             }
             a.order_agg[o] = make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), kmax, fl);
@@ -519,8 +532,10 @@ __global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs
 // Persistent batch kernel: CTAs pop work items (instance, chunk range) from
 // a queue ordered largest first, stage that instance's order book once, and
 // split the item's chunks among their warps.
+// 16-bit keys: up to 384-thread CTAs, two per SM (85 registers a thread, as
+// k_eval_short); 32-bit keys: up to 256 threads
 template <bool KEY16, bool SMEM_TABLES>
-__global__ void __launch_bounds__(256, 2) k_eval_batch(BatchArgs b) {
+__global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     __shared__ __align__(16) EvalArgs s_a;
@@ -798,7 +813,7 @@ cudaError_t launch_eval_short(const EvalArgs& a, const Tuning& tune, int num_sms
 }
 
 cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int num_sms, cudaStream_t s) {
-    if (t.threads % 32 != 0 || t.threads > 256 || t.threads < 32) return cudaErrorInvalidValue;
+    if (t.threads % 32 != 0 || t.threads > (k16 ? 384 : 256) || t.threads < 32) return cudaErrorInvalidValue;
     if (b.n_items == 0) return cudaSuccess;
     const size_t smem = eval_batch_smem_bytes(b, t, k16);
     const bool sm = t.smem_tables != 0;

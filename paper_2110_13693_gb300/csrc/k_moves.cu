@@ -196,6 +196,7 @@ __global__ void k_mv_count(MoveArgs M) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         M.task_off[M.n_moves] = 0;
         *M.long_count = 0;
+        if (M.stats) M.stats[0] = M.stats[1] = 0;
     }
 }
 
@@ -401,6 +402,14 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
             if (!ok) {
                 flag(a.status, WH_STATUS_BAD_ORDER);
                 M.mstatus[tk.x] = 3;
+            }
+        }
+        if (M.stats) {   // changed tours walked and their lines (the moves' roofline)
+            const unsigned walked = __reduce_add_sync(0xffffffffu, active && ok ? 1u : 0u);
+            const unsigned lines = __reduce_add_sync(0xffffffffu, active && ok ? (unsigned)n : 0u);
+            if (lane == 0 && walked) {
+                atomicAdd(M.stats, (unsigned long long)walked);
+                atomicAdd(M.stats + 1, (unsigned long long)lines);
             }
         }
         bool run = active && ok && primary;
@@ -812,12 +821,24 @@ __global__ void k_ls_apply(LsArgs L) {
 // (rows of non-counted tasks are written too and ignored by the selection).
 constexpr int TF_THREADS = 256;
 
+// One changed tour per warp.  Its orders are taken 32 at a time (one per
+// lane: id, line range); then the lanes walk the round's lines flat, 32 at a
+// time, each lane finding its line's order from the orders' start offsets (a
+// bitmask of order starts within the 32-line window), so all lanes gather
+// slot-map entries together whatever the orders' sizes.
 __global__ void __launch_bounds__(TF_THREADS) k_task_features(MoveArgs M, FeatConst c, uint4* X) {
     __shared__ WarpFeat ws[TF_THREADS / 32];
+    __shared__ int s_lb[TF_THREADS / 32][32], s_off[TF_THREADS / 32][33], s_o[TF_THREADS / 32][32],
+        s_rank[TF_THREADS / 32][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpFeat& w = ws[wid];
+    int* lbs = s_lb[wid];
+    int* offs = s_off[wid];
+    int* ords = s_o[wid];
+    int* rank_to_k = s_rank[wid];
     wf_init(w, lane);
     const EvalArgs& a = M.a;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n_warps = (int64_t)gridDim.x * (TF_THREADS / 32);
     for (int64_t i = (int64_t)blockIdx.x * (TF_THREADS / 32) + wid; i < M.n_tasks; i += n_warps) {
         const int4 tk = M.tasks[i];
@@ -835,24 +856,60 @@ __global__ void __launch_bounds__(TF_THREADS) k_task_features(MoveArgs M, FeatCo
             bool own_has_s1 = false;
             const int q_end = bad ? q0 : (add >= 0 ? q1 + 1 : q1);
             for (int qb = q0; qb < q_end; qb += 32) {
+                // this round's orders, one per lane (none: count 0)
                 const int q = qb + lane;
-                if (bad || q >= q_end) continue;
-                const int o = q < q1 ? a.order_seq[q] : add;
-                if (q < q1 && o == rem) continue;
-                int lb, le;
-                if (order_lines_checked(a, o, lb, le) < 0) { bad = true; continue; }
-                for (int l = lb; l < le; ++l) {
-                    const int s = a.line_sku[l];
-                    if ((unsigned)s >= (unsigned)a.n_sku) { bad = true; break; }
-                    if (swap && sku_hit(s, mv)) {
-                        hit_min = min(hit_min, o);
-                        if (o == tk.z && s == mv.y) own_has_s1 = true;
+                int o = -1, lb = 0, cnt = 0;
+                if (q < q_end) {
+                    o = q < q1 ? a.order_seq[q] : add;
+                    if (q < q1 && o == rem) {
+                        o = -1;
+                    } else {
+                        int le;
+                        const int cc = order_lines_checked(a, o, lb, le);
+                        if (cc < 0) bad = true;
+                        else cnt = cc;
                     }
-                    const int loc = task_loc(map, s, mv);
-                    if ((unsigned)loc >= (unsigned)a.g.n_loc) { bad = true; break; }
-                    over |= !wf_insert(w, loc_key(a.g, loc));
-                    ++n_lines;
                 }
+                const int incl = warp_inclusive_scan(cnt);
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const unsigned nonempty = __ballot_sync(0xffffffffu, cnt > 0);
+                lbs[lane] = lb;
+                offs[lane] = incl - cnt;
+                ords[lane] = o;
+                if (cnt > 0) rank_to_k[__popc(nonempty & lt_mask)] = lane;
+                __syncwarp();
+                // the round's lines, 32 at a time: line p belongs to the
+                // nonempty order whose start is the last one <= p
+                int before = 0;   // nonempty orders starting before this window
+                for (int p0 = 0; p0 < total; p0 += 32) {
+                    const int start = offs[lane];
+                    const bool head = cnt > 0 && start >= p0 && start < p0 + 32;
+                    const unsigned hm = __reduce_or_sync(0xffffffffu, head ? 1u << (start - p0) : 0u);
+                    const int p = p0 + lane;
+                    if (p < total && !bad) {
+                        const int r = before + __popc(hm & (lt_mask | (1u << lane))) - 1;
+                        const int k = rank_to_k[r];
+                        const int ok_ = ords[k];
+                        const int l = lbs[k] + (p - offs[k]);
+                        const int sk = a.line_sku[l];
+                        if ((unsigned)sk >= (unsigned)a.n_sku) {
+                            bad = true;
+                        } else {
+                            if (swap && sku_hit(sk, mv)) {
+                                hit_min = min(hit_min, ok_);
+                                if (ok_ == tk.z && sk == mv.y) own_has_s1 = true;
+                            }
+                            const int loc = task_loc(map, sk, mv);
+                            if ((unsigned)loc >= (unsigned)a.g.n_loc) bad = true;
+                            else {
+                                over |= !wf_insert(w, loc_key(a.g, loc));
+                                ++n_lines;
+                            }
+                        }
+                    }
+                    before += __popc(hm);
+                }
+                __syncwarp();
             }
             ok = !__any_sync(0xffffffffu, bad);
             hit_min = __reduce_min_sync(0xffffffffu, hit_min);

@@ -1,0 +1,197 @@
+// tcgen05 / TMA / mbarrier building blocks for sm_103a shared by the
+// tensor-core kernels (the surrogate's forward and backward passes): the
+// instruction and shared-memory descriptors of kind::f16 MMAs on K-major
+// bf16 operands in the 128-byte swizzled layout that TMA writes, bounded
+// mbarrier waits, TMEM loads and packed fp32x2 arithmetic.  Everything lives
+// in an unnamed namespace, so each translation unit gets its own copy.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "wh_internal.h"
+
+namespace wh {
+namespace {
+
+// instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator (bits
+// 4-5), A and B bf16 (bits 7-9, 10-12), both K-major (bits 15, 16 clear),
+// N/8 at bits 17-22, M/16 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete.  Gives up when the CTA's abort
+// flag is set or after wait_ns (default WAIT_NS), setting the flag and the
+// status word.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* status,
+                                       unsigned long long wait_ns = WAIT_NS) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (*abort) return false;
+            if (globaltimer() - t0 > wait_ns || i > (1u << 30)) {
+                *abort = 1;
+                atomicOr(status, (int)WH_STATUS_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// used after an abort: wait for a phase without giving up on the flag
+__device__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 0; !mbar_try(bar, parity); ++i)
+        if ((i & 63) == 0 && globaltimer() - t0 > WAIT_NS) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout that TMA writes: 8-row groups 1024 bytes apart (stride
+// byte offset), descriptor version 1 (bit 46), swizzle mode 2 (bits 61-63).
+// Advancing K by 16 bf16 inside a 1024-byte aligned atom adds 32 bytes to
+// the start address.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// 32 TMEM lanes x 32 fp32 columns: lane i of the warp receives its lane's
+// columns [col, col + 32).  The wait names the registers so that no use of
+// them is scheduled before the load has landed.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Pairs of fp32 values in one 64-bit register for the packed fp32x2
+// arithmetic of sm_100 and later (add / mul / fma .f32x2, element-wise,
+// round to nearest): the epilogue's FMA-pipe work in half the instructions.
+__device__ __forceinline__ uint64_t pk(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(uint64_t r, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t dup2(float x) { return pk(x, x); }
+
+// gelu(z) = z/2 (1 + erf(z / sqrt 2)) of both halves of z.  erf by the
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.28 (after Hastings): for x >= 0,
+// erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16, |error| <= 3e-7; odd
+// in x (large x: the power overflows to inf and erf to 1).  Far below the
+// bf16 resolution (2^-8) of the activations it feeds; one reciprocal per
+// value and FMAs, all but the reciprocal on packed pairs.
+__device__ __forceinline__ uint64_t gelu2(uint64_t z) {
+    float x0, x1;
+    upk(mul2(z, dup2(0.70710678118654752f)), x0, x1);
+    const uint64_t ax = pk(fabsf(x0), fabsf(x1));
+    uint64_t p = fma2(dup2(0.0000430638f), ax, dup2(0.0002765672f));
+    p = fma2(p, ax, dup2(0.0001520143f));
+    p = fma2(p, ax, dup2(0.0092705272f));
+    p = fma2(p, ax, dup2(0.0422820123f));
+    p = fma2(p, ax, dup2(0.0705230784f));
+    p = fma2(p, ax, dup2(1.0f));
+    p = mul2(p, p);   // ^2
+    p = mul2(p, p);   // ^4
+    p = mul2(p, p);   // ^8
+    p = mul2(p, p);   // ^16
+    float p0, p1;
+    upk(p, p0, p1);
+    const float m0 = 1.0f - 1.0f / p0, m1 = 1.0f - 1.0f / p1;   // |erf|
+    const uint64_t er = pk(copysignf(m0, x0), copysignf(m1, x1));
+    const uint64_t hz = mul2(z, dup2(0.5f));
+    return fma2(hz, er, hz);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&p);
+}
+
+}  // namespace
+}  // namespace wh

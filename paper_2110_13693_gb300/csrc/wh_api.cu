@@ -321,7 +321,8 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
         LaunchTimer lt(h->timing, wh::sshape_kernel_applies(a) ? K_EVAL_SSHAPE : K_EVAL_SHORT, s);
         if (!lt.ok() || wh::launch_eval_short(a, t, h->num_sms, s, nullptr) != cudaSuccess) return WH_ECUDA;
     }
-    if (p.n_tours > 0) {
+    // the S-shape-only kernels keep every tour in its thread: no long-tour pass
+    if (p.n_tours > 0 && !wh::sshape_kernel_applies(a)) {
         LaunchTimer lt(h->timing, K_EVAL_LONG, s);
         wh::LongArgs L;
         L.single = a;
@@ -354,6 +355,7 @@ int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int
     M.delta = delta;
     M.mstatus = status;
     M.long_count = reinterpret_cast<int32_t*>(h->meta + 2);
+    M.stats = reinterpret_cast<unsigned long long*>(h->meta + 4);
 
     const size_t n_ot = (size_t)p.n_plans * (size_t)o.n_orders;
     const size_t nb = ((size_t)n_moves + 1 + 1023) / 1024;
@@ -811,6 +813,23 @@ extern "C" int wh_get_last_status(wh_layout* h, void* stream, uint32_t* status) 
     return WH_OK;
 }
 
+extern "C" int wh_get_move_stats(wh_layout* h, void* stream, int64_t* tours, int64_t* lines) {
+    if (!h || !tours || !lines) return WH_EINVAL;
+    if (!h->meta) {
+        *tours = *lines = 0;
+        return WH_OK;
+    }
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long v[2] = {0, 0};
+    if (cudaMemcpyAsync(v, h->meta + 4, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return WH_ECUDA;
+    *tours = (int64_t)v[0];
+    *lines = (int64_t)v[1];
+    return WH_OK;
+}
+
 extern "C" int wh_set_timing(wh_layout* h, int enable) {
     if (!h) return WH_EINVAL;
     h->timing.on = enable != 0;
@@ -1009,7 +1028,8 @@ extern "C" int wh_batch_create(const wh_instance* insts, int32_t n, wh_batch** o
 }
 
 extern "C" int wh_batch_set_tuning(wh_batch* b, int32_t threads, int32_t chunks_per_item, int32_t smem_tables) {
-    if (!b || threads < 32 || threads > 256 || (threads % 32) || chunks_per_item < 1 || smem_tables < 0 ||
+    if (!b || threads < 32 || threads > (b->key16 ? 384 : 256) || (threads % 32) || chunks_per_item < 1 ||
+        smem_tables < 0 ||
         smem_tables > 1)
         return WH_EINVAL;
     DeviceGuard guard(b->device);
@@ -1176,8 +1196,8 @@ extern "C" int wh_batch_autotune(wh_batch* b, uint32_t routing_mask, const char*
     } else {
         if (from_cache) *from_cache = 0;
         const int32_t smem = b->tune.smem_tables;
-        const int thread_opts[] = {128, 256};
-        const int chunk_opts[] = {2, 4, 8, 16, 32, 64};
+        const int thread_opts[] = {128, 256, 384};
+        const int chunk_opts[] = {2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096};
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess) return WH_ECUDA;
         if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1187,6 +1207,7 @@ extern "C" int wh_batch_autotune(wh_batch* b, uint32_t routing_mask, const char*
         TuneEntry best;
         best.ms = 1e30;
         for (int th : thread_opts) {
+            if (th > 256 && !b->key16) continue;
             for (int ch : chunk_opts) {
                 rc = wh_batch_set_tuning(b, th, ch, smem);
                 if (rc != WH_OK) break;

@@ -112,6 +112,7 @@ struct MoveArgs {
     int32_t* long_m;
     uint32_t* long_key;
     int32_t long_rec_cap;
+    unsigned long long* stats;  // [0] changed tours walked, [1] their lines (zeroed by the count pass)
 };
 
 struct LsArgs {
@@ -229,24 +230,37 @@ constexpr int64_t MLP_W3_OFF = MLP_B2_OFF + 256;
 constexpr int64_t MLP_B3_OFF = MLP_W3_OFF + 256;
 constexpr int64_t MLP_NPARAM = MLP_B3_OFF + 1;
 
-struct GemmArgs {
-    int64_t M;
-    int N, K;
-    const __nv_bfloat16* A;
-    int64_t lda;
-    int transA;
-    const __nv_bfloat16* B;
-    int64_t ldb;
-    int transB;
-    float* Z;
-    int64_t ldz;
-    __nv_bfloat16* Cb;
-    float* Cf;
-    int64_t ldc;
-    // fp32 output in splits of K (gridDim.z > 1): split z writes
-    // Cpart[z][M][ldc], then launch_split_reduce adds them in a fixed order
-    float* Cpart;
+// Training backward on the tensor cores (k_mlp_bwd.cu).  Row-major [n][256]
+// buffers unless noted; the transposed copies are [features][ldt] bf16 with
+// ldt a multiple of 64 (columns n .. ldt-1 unused: the tensor maps end at n).
+struct BwdArgs {
+    int64_t n;                  // rows of the batch
+    int64_t ldt;                // row stride (elements) of the transposed copies
+    const float* y;             // [n] outputs of the training forward
+    const float* t;             // [n] targets
+    const float* Z1;
+    const float* Z2;
+    const __nv_bfloat16* H2;
+    const __nv_bfloat16* X;     // [n][192]
+    const float* P;             // fp32 master parameters
+    float* dy;                  // [n] (y - t) / n
+    __nv_bfloat16* dZ2;
+    __nv_bfloat16* dZ2T;        // [256][ldt]
+    __nv_bfloat16* XT;          // [193][ldt]: X transposed, row 192 = 1
+    __nv_bfloat16* dZ1;
+    __nv_bfloat16* dZ1T;        // [256][ldt]
+    float* part_t;              // per 32-row block: b2[256], w3[256], b3, loss partial sums
+    float* part_w;              // [2][splits][256][256]: dW2 and [dW1; db1] partial products
+    int32_t splits;             // batch ranges of the weight gradients
+    int64_t split_rows;         // rows per range (a multiple of 64)
+    int* status;                // WH_STATUS_* bits (bounded waits)
 };
+int bwd_tail_part_floats(int64_t n);
+cudaError_t launch_bwd(const BwdArgs& b, const CUtensorMap& mdz2, const CUtensorMap& mw2, const CUtensorMap& mh1t,
+                       const CUtensorMap& mdz2t, const CUtensorMap& mxt, const CUtensorMap& mdz1t, int num_sms,
+                       cudaStream_t s);
+cudaError_t launch_adam_parts(const BwdArgs& b, float* p, float* m, float* v, float* G, float lr, int step, void* w1b,
+                              void* w2b, float* loss, cudaStream_t s);
 
 struct FeatConst {
     int32_t A, L;
@@ -260,26 +274,17 @@ cudaError_t launch_features(const EvalArgs& a, const FeatConst& c, void* X, cons
 cudaError_t launch_compact_flags(const uint8_t* flag, int64_t n, int32_t* list, int32_t* count, cudaStream_t s);
 cudaError_t launch_scatter_pred(const int32_t* list, const float* y, int64_t n, float* y_tour, uint8_t* flag,
                                 cudaStream_t s);
-cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s);   // epi: 1 fp32, 2 GELU grad
-cudaError_t launch_train_tail(const float* y, const float* t, int n, float* dy, float* loss, const float* w3,
-                              const float* Z2, void* dZ2, cudaStream_t s);
-// out[i] = sum over z < splits of part[z * n + i], in order of z
-cudaError_t launch_split_reduce(const float* part, int splits, int64_t n, float* out, cudaStream_t s);
-cudaError_t launch_gemm_splitk(const GemmArgs& g, int splits, cudaStream_t s);
-cudaError_t launch_colsum(const void* X, int64_t n, int cols, const float* scale, float* out, cudaStream_t s,
-                          float* part = nullptr);
-cudaError_t launch_sum(const float* v, int n, float* out, cudaStream_t s);
-cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int64_t n, float lr, int step, void* w1b,
-                        void* w2b, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* p, int64_t n, void* out, cudaStream_t s);
 // fused tcgen05 inference (k_mlp_tc.cu): W1t [256][192] and W2t [256][256]
 // are the transposed bf16 weights the tensor maps mw1 / mw2 describe
 cudaError_t launch_transpose_bf16(const float* p, int K, int N, void* out, cudaStream_t s);
-// Z1 / H1 / Z2 / H2 (all or none): the training forward's saved pre-
-// activations (fp32) and activations (bf16), [n][256]
+// Z1 / H1 / Z2 / H2 / H1T (all or none): the training forward's saved pre-
+// activations (fp32) and activations (bf16), [n][256], and H1 transposed,
+// [256][ldt] (ldt >= n)
 cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const CUtensorMap& mw2, const float* P,
                           int64_t n, float* y, int* status, int num_sms, cudaStream_t s, float* Z1 = nullptr,
-                          void* H1 = nullptr, float* Z2 = nullptr, void* H2 = nullptr);
+                          void* H1 = nullptr, float* Z2 = nullptr, void* H2 = nullptr, void* H1T = nullptr,
+                          int64_t ldt = 0, int64_t skip_tile = -1, unsigned long long wait_ns = 0);
 size_t mlp_tc_smem_bytes();
 
 struct Tuning {

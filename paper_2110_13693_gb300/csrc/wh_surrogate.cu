@@ -3,8 +3,9 @@
 // enqueued on the caller's stream.  Forward passes (prediction, and the
 // training forward with its saved activations) run the fused tcgen05 kernel
 // (k_mlp_tc.cu) on transposed bf16 weights that are refreshed on the stream
-// whenever the parameters have changed; the backward GEMMs run on mma.sync
-// (k_surrogate.cu), the weight gradients split along the batch.
+// whenever the parameters have changed; the backward runs on the tcgen05
+// tensor cores too (k_mlp_bwd.cu), the weight gradients in batch ranges whose
+// partials Adam sums in a fixed order.
 #include <cudaTypedefs.h>
 
 #include <cmath>
@@ -27,10 +28,14 @@ struct wh_surrogate {
     int64_t cap = 0;       // rows of training scratch
     int64_t last_n = 0;    // rows of the last training step (its saved intermediates)
     float *Z1 = nullptr, *Z2 = nullptr, *y = nullptr, *dy = nullptr, *loss = nullptr;
-    float* part = nullptr; // split partials of the weight gradients and column sums
+    float* part_w = nullptr;   // [2][kMaxSplits][256][256] weight-gradient partials
+    float* part_t = nullptr;   // per 32-row block column sums (b2, w3, b3, loss)
     __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    // transposed copies [features][ldt] for the backward's K-major operands
+    __nv_bfloat16 *H1T = nullptr, *dZ2T = nullptr, *XT = nullptr, *dZ1T = nullptr;
     __nv_bfloat16 *w1t = nullptr, *w2t = nullptr;   // [256][192], [256][256]: K contiguous
     CUtensorMap mw1, mw2;
+    CUtensorMap mw2r;      // w2b [256][256] row-major: the dZ1 product's B operand
     bool t_stale = true;   // w1t / w2t lag the parameters
     int* status = nullptr; // WH_STATUS_* bits of the inference kernel
     int num_sms = 0;
@@ -57,19 +62,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
     return fn;
 }
 
-// 2-D bf16 tensor map of a row-major [rows][cols] matrix, box [box_rows][64]
-// (128 bytes wide, the 128-byte swizzle), rows past the end read as zero
-int encode_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+// 2-D bf16 tensor map of a row-major matrix of `rows` rows whose first
+// `cols` elements are read (row stride `ld` elements, a multiple of 8), box
+// [box_rows][64] (128 bytes wide, the 128-byte swizzle); elements past the
+// ends read as zero
+int encode_map_ld(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
     if (!fn) return WH_ECUDA;
     const cuuint64_t dim[2] = {cols, rows};
-    const cuuint64_t stride[1] = {cols * 2};
+    const cuuint64_t stride[1] = {ld * 2};
     const cuuint32_t box[2] = {64, box_rows};
     const cuuint32_t estride[2] = {1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dim, stride, box, estride,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? WH_OK : WH_EINVAL;
+}
+
+// a dense row-major [rows][cols] matrix
+int encode_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    return encode_map_ld(m, base, rows, cols, cols, box_rows);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014)
@@ -81,8 +93,9 @@ uint64_t sm64(uint64_t& s) {
 }
 
 void free_all(wh_surrogate* s) {
-    void* ptrs[] = {s->P, s->Mo, s->Ve, s->G, s->w1b, s->w2b, s->Z1, s->Z2, s->y, s->dy, s->loss,
-                    s->H1, s->H2, s->dZ2, s->dZ1, s->w1t, s->w2t, s->status, s->part};
+    void* ptrs[] = {s->P,   s->Mo,  s->Ve,   s->G,   s->w1b,  s->w2b,    s->Z1,     s->Z2,
+                    s->y,   s->dy,  s->loss, s->H1,  s->H2,   s->dZ2,    s->dZ1,    s->w1t,
+                    s->w2t, s->status, s->part_w, s->part_t, s->H1T, s->dZ2T, s->XT, s->dZ1T};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -104,43 +117,37 @@ int dalloc(T** p, size_t n) {
     return WH_OK;
 }
 
-constexpr int kMaxSplits = 32;   // K splits of a weight gradient (K = the batch)
+constexpr int kMaxSplits = 16;   // batch ranges of a weight gradient
 
-int splits_for(int64_t n) {
-    const int64_t k = (n + 127) / 128;
-    return (int)(k < 1 ? 1 : (k > kMaxSplits ? kMaxSplits : k));
+// rows per batch range of the weight gradients: at least 512, a multiple of
+// 64, at most kMaxSplits ranges
+int64_t split_rows_for(int64_t n) {
+    int64_t r = (n + kMaxSplits - 1) / kMaxSplits;
+    r = (r + 63) / 64 * 64;
+    return r < 512 ? 512 : r;
 }
 
+int64_t ldt_for(int64_t n) { return (n + 63) / 64 * 64; }
+
 int reserve_train(wh_surrogate* s, int64_t n) {
-    if (!s->part && dalloc(&s->part, (size_t)kMaxSplits * 256 * 256)) return WH_ENOMEM;
+    if (!s->part_w && dalloc(&s->part_w, (size_t)2 * kMaxSplits * 256 * 256)) return WH_ENOMEM;
     if (n <= s->cap) return WH_OK;
-    void* old[] = {s->Z1, s->Z2, s->y, s->dy, s->H1, s->H2, s->dZ2, s->dZ1};
+    void* old[] = {s->Z1, s->Z2, s->y, s->dy, s->H1, s->H2, s->dZ2, s->dZ1, s->H1T, s->dZ2T, s->XT, s->dZ1T, s->part_t};
     for (void* p : old)
         if (p) cudaFree(p);
+    s->Z1 = s->Z2 = s->y = s->dy = s->part_t = nullptr;
+    s->H1 = s->H2 = s->dZ2 = s->dZ1 = s->H1T = s->dZ2T = s->XT = s->dZ1T = nullptr;
     s->cap = 0;
-    const size_t r = (size_t)n;
+    const size_t r = (size_t)n, t = (size_t)ldt_for(n);
     if (dalloc(&s->Z1, r * 256) || dalloc(&s->Z2, r * 256) || dalloc(&s->y, r) || dalloc(&s->dy, r) ||
-        dalloc(&s->H1, r * 256) || dalloc(&s->H2, r * 256) || dalloc(&s->dZ2, r * 256) || dalloc(&s->dZ1, r * 256))
+        dalloc(&s->H1, r * 256) || dalloc(&s->H2, r * 256) || dalloc(&s->dZ2, r * 256) || dalloc(&s->dZ1, r * 256) ||
+        dalloc(&s->H1T, 256 * t) || dalloc(&s->dZ2T, 256 * t) || dalloc(&s->XT, 193 * t) ||
+        dalloc(&s->dZ1T, 256 * t) || dalloc(&s->part_t, (size_t)wh::bwd_tail_part_floats(n)))
         return WH_ENOMEM;
     s->cap = n;
     return WH_OK;
 }
 
-wh::GemmArgs gemm(int64_t M, int N, int K, const __nv_bfloat16* A, int64_t lda, int ta, const __nv_bfloat16* B,
-                  int64_t ldb, int tb) {
-    wh::GemmArgs g;
-    std::memset(&g, 0, sizeof(g));
-    g.M = M;
-    g.N = N;
-    g.K = K;
-    g.A = A;
-    g.lda = lda;
-    g.transA = ta;
-    g.B = B;
-    g.ldb = ldb;
-    g.transB = tb;
-    return g;
-}
 
 // the transposed bf16 weights the tensor maps describe, when stale
 int refresh_transposed(wh_surrogate* s, cudaStream_t st) {
@@ -186,6 +193,7 @@ extern "C" int wh_surrogate_create(uint64_t seed, wh_surrogate** out) {
                                                                                                          : WH_ECUDA;
     if (rc == WH_OK) rc = encode_map(&s->mw1, s->w1t, 256, 192, 256);
     if (rc == WH_OK) rc = encode_map(&s->mw2, s->w2t, 256, 256, 256);
+    if (rc == WH_OK) rc = encode_map(&s->mw2r, s->w2b, 256, 256, 256);
     if (rc == WH_OK) rc = upload_params(s, h.data());
     if (rc == WH_OK && (cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess ||
                         cudaMemset(s->Mo, 0, sizeof(float) * wh::MLP_NPARAM) != cudaSuccess ||
@@ -241,6 +249,22 @@ extern "C" int wh_surrogate_predict(wh_surrogate* s, const uint16_t* X, int64_t 
     return WH_OK;
 }
 
+extern "C" int wh_surrogate_predict_timeout_test(wh_surrogate* s, const uint16_t* X, int64_t n, float* y,
+                                                 int64_t skip_tile, uint64_t wait_ns, void* stream) {
+    if (!s || n < 1 || !X || !y || skip_tile < 0 || wait_ns < 1000 || wait_ns > 2000000000ull) return WH_EINVAL;
+    if (n > kInferChunk || reinterpret_cast<uintptr_t>(X) % 16 != 0) return WH_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = refresh_transposed(s, st);
+    if (rc != WH_OK) return rc;
+    CUtensorMap mx;
+    rc = encode_map(&mx, X, (uint64_t)n, wh::MLP_IN, 128);
+    if (rc != WH_OK) return rc;
+    if (wh::launch_mlp_tc(mx, s->mw1, s->mw2, s->P, n, y, s->status, s->num_sms, st, nullptr, nullptr, nullptr,
+                          nullptr, nullptr, 0, skip_tile, (unsigned long long)wait_ns) != cudaSuccess)
+        return WH_ECUDA;
+    return WH_OK;
+}
+
 extern "C" int wh_surrogate_get_status(wh_surrogate* s, uint32_t* out) {
     if (!s || !out) return WH_EINVAL;
     int v = 0;
@@ -257,8 +281,9 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     int rc = reserve_train(s, n);
     if (rc != WH_OK) return rc;
     const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
+    const int64_t ldt = ldt_for(n);
     // forward on the tensor cores, keeping both layers' pre-activations and
-    // activations for the backward pass
+    // activations (and H1 transposed) for the backward pass
     if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return WH_EINVAL;
     rc = refresh_transposed(s, st);
     if (rc != WH_OK) return rc;
@@ -267,41 +292,44 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
         rc = encode_map(&mx, X, (uint64_t)n, wh::MLP_IN, 128);
         if (rc != WH_OK) return rc;
         if (wh::launch_mlp_tc(mx, s->mw1, s->mw2, s->P, n, s->y, s->status, s->num_sms, st, s->Z1, s->H1, s->Z2,
-                              s->H2) != cudaSuccess)
+                              s->H2, s->H1T, ldt) != cudaSuccess)
             return WH_ECUDA;
     }
-    if (cudaMemsetAsync(s->loss, 0, sizeof(float), st) != cudaSuccess) return WH_ECUDA;
-    if (wh::launch_train_tail(s->y, target, n, s->dy, s->loss, s->P + wh::MLP_W3_OFF, s->Z2, s->dZ2, st) !=
-        cudaSuccess)
-        return WH_ECUDA;
-    // output layer
-    if (wh::launch_colsum(s->H2, n, 256, s->dy, s->G + wh::MLP_W3_OFF, st, s->part) != cudaSuccess) return WH_ECUDA;
-    if (wh::launch_sum(s->dy, n, s->G + wh::MLP_B3_OFF, st) != cudaSuccess) return WH_ECUDA;
-    // layer 2: dW2 = H1^T dZ2, db2 = colsum dZ2, dZ1 = (dZ2 W2^T) * gelu'(Z1)
-    if (wh::launch_colsum(s->dZ2, n, 256, nullptr, s->G + wh::MLP_B2_OFF, st, s->part) != cudaSuccess)
-        return WH_ECUDA;
-    wh::GemmArgs gw2 = gemm(256, 256, n, s->H1, 256, 1, s->dZ2, 256, 0);
-    gw2.Cpart = s->part;
-    gw2.Cf = s->G + wh::MLP_W2_OFF;
-    gw2.ldc = 256;
-    if (wh::launch_gemm_splitk(gw2, splits_for(n), st) != cudaSuccess) return WH_ECUDA;
-    wh::GemmArgs gd1 = gemm(n, 256, 256, s->dZ2, 256, 0, s->w2b, 256, 1);
-    gd1.Z = s->Z1;
-    gd1.ldz = 256;
-    gd1.Cb = s->dZ1;
-    gd1.ldc = 256;
-    if (wh::launch_gemm(gd1, 2, st) != cudaSuccess) return WH_ECUDA;
-    // layer 1: dW1 = X^T dZ1, db1 = colsum dZ1
-    if (wh::launch_colsum(s->dZ1, n, 256, nullptr, s->G + wh::MLP_B1_OFF, st, s->part) != cudaSuccess)
-        return WH_ECUDA;
-    wh::GemmArgs gw1 = gemm(192, 256, n, Xb, 192, 1, s->dZ1, 256, 0);
-    gw1.Cpart = s->part;
-    gw1.Cf = s->G;
-    gw1.ldc = 256;
-    if (wh::launch_gemm_splitk(gw1, splits_for(n), st) != cudaSuccess) return WH_ECUDA;
+    // backward on the tensor cores: dy, dZ2 and the transposed operands; dZ1;
+    // the weight gradients in batch ranges; Adam over their fixed-order sums
+    wh::BwdArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.n = n;
+    b.ldt = ldt;
+    b.y = s->y;
+    b.t = target;
+    b.Z1 = s->Z1;
+    b.Z2 = s->Z2;
+    b.H2 = s->H2;
+    b.X = Xb;
+    b.P = s->P;
+    b.dy = s->dy;
+    b.dZ2 = s->dZ2;
+    b.dZ2T = s->dZ2T;
+    b.XT = s->XT;
+    b.dZ1 = s->dZ1;
+    b.dZ1T = s->dZ1T;
+    b.part_t = s->part_t;
+    b.part_w = s->part_w;
+    b.split_rows = split_rows_for(n);
+    b.splits = (int32_t)((n + b.split_rows - 1) / b.split_rows);
+    b.status = s->status;
+    CUtensorMap mdz2, mh1t, mdz2t, mxt, mdz1t;
+    rc = encode_map(&mdz2, s->dZ2, (uint64_t)n, 256, 128);
+    if (rc == WH_OK) rc = encode_map_ld(&mh1t, s->H1T, 256, (uint64_t)n, (uint64_t)ldt, 128);
+    if (rc == WH_OK) rc = encode_map_ld(&mdz2t, s->dZ2T, 256, (uint64_t)n, (uint64_t)ldt, 256);
+    if (rc == WH_OK) rc = encode_map_ld(&mxt, s->XT, 193, (uint64_t)n, (uint64_t)ldt, 128);
+    if (rc == WH_OK) rc = encode_map_ld(&mdz1t, s->dZ1T, 256, (uint64_t)n, (uint64_t)ldt, 256);
+    if (rc != WH_OK) return rc;
+    if (wh::launch_bwd(b, mdz2, s->mw2r, mh1t, mdz2t, mxt, mdz1t, s->num_sms, st) != cudaSuccess) return WH_ECUDA;
     s->last_n = n;
     s->step += 1;
-    if (wh::launch_adam(s->P, s->Mo, s->Ve, s->G, wh::MLP_NPARAM, lr, s->step, s->w1b, s->w2b, st) != cudaSuccess)
+    if (wh::launch_adam_parts(b, s->P, s->Mo, s->Ve, s->G, lr, s->step, s->w1b, s->w2b, s->loss, st) != cudaSuccess)
         return WH_ECUDA;
     s->t_stale = true;
     if (loss_out && cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)

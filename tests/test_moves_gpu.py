@@ -215,3 +215,49 @@ def test_relocation_needs_occupancy_bits(gpu_lib):
     assert (s == 3).all() and (d == 0).all()
     d, s, st = gpu_moves(gpu_lib, inst, mv[:4])            # shared slotting
     assert (s == 3).all()
+
+
+def test_move_stats_count_the_changed_tours(gpu_lib):
+    """wh_get_move_stats after a call: the changed tours the moves rewrite
+    (two per accepted order swap or relocation, one per order holding a
+    swapped SKU) and their line counts, recounted here from the plans."""
+    import torch
+    wh = gpu_lib
+    inst = wh_gen.paperscale(seed=8, n_plans=6)
+    maps = np.tile(inst.slot_map, (inst.n_plans, 1)).astype(np.int32)
+    mv = moves_for(inst, 9, 64)
+    lay = wh.Layout.of(inst.layout)
+    prob = wh.to_device(inst, slot_map=maps.ravel(), slot_map_stride=inst.n_sku)
+    costs = wh.evaluate(lay, prob)
+    _, status = lay.eval_moves(prob, costs, torch.as_tensor(mv).cuda(), 24, 0)
+    tours, lines = lay.move_stats()
+    status = status.cpu().numpy()
+    assert lay.status() == 0
+    lay.close()
+    ol = np.diff(inst.order_off)                        # lines per order
+    line_order = np.repeat(np.arange(inst.n_orders), ol)
+    orders_of = {}
+    for l, sku in enumerate(inst.line_sku):
+        orders_of.setdefault(int(sku), []).append(int(line_order[l]))
+    want_t = want_l = 0
+    for m, (typ, a, b, p) in enumerate(mv):
+        if status[m] != 0:
+            continue
+        t0, t1 = inst.plan_tour_off[p], inst.plan_tour_off[p + 1]
+        tour_of = {}
+        for t in range(t0, t1):
+            for o in inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]:
+                tour_of[int(o)] = t
+        tl = lambda t: int(ol[inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]].sum())
+        if typ == 0:
+            want_t += 2
+            want_l += tl(tour_of[a]) - ol[a] + ol[b] + tl(tour_of[b]) - ol[b] + ol[a]
+        elif typ == 1:
+            want_t += 2
+            want_l += tl(tour_of[a]) - ol[a] + tl(t0 + b) + ol[a]
+        else:
+            for sku in (a, b):
+                for o in orders_of.get(int(sku), []):
+                    want_t += 1
+                    want_l += tl(tour_of[o])
+    assert (tours, lines) == (want_t, int(want_l))

@@ -254,3 +254,33 @@ def test_features_full_paperscale_sampled(gpu_lib):
         want = oracle.bf16(oracle.features(inst.layout, tour_locs(inst, int(t), inst.slot_map)))
         assert np.array_equal(got[r], torch.from_numpy(want).to(torch.bfloat16).view(torch.int16).numpy()), t
     lay.close()
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable(gpu_lib):
+    """The tensor-core kernel's failure path: with the producer stopped
+    before one tile and a 200-microsecond wait limit, the wait for that tile
+    runs out; the kernel returns, the status word reports WH_STATUS_TIMEOUT,
+    and the next normal predictions on the same context are exact again."""
+    import torch
+    wh = gpu_lib
+    sms = torch.cuda.get_device_properties(0).multi_processor_count   # one CTA per SM
+    n = sms * 128 * 2 + 5
+    Xh = rand_features(7, n)
+    X = torch.from_numpy(Xh).to(torch.bfloat16).cuda()
+    s = wh.Surrogate(0)
+    s.set_params(wh.pack_params(bf16_params(5)))
+    y0 = s.predict(X).clone()
+    assert s.status() == 0
+    for skip in (0, sms + 1):      # the first tile of CTA 0; the second tile of CTA 1
+        y = torch.zeros(n, dtype=torch.float32, device="cuda")
+        wh.wh_surrogate_predict_timeout_test(s.handle, X.data_ptr(), n, y.data_ptr(), skip, 200000)
+        torch.cuda.synchronize()
+        assert s.status() & wh.WH_STATUS_TIMEOUT
+        # tiles of the other CTAs were scored as usual
+        other = torch.arange(n, device="cuda") // 128 % sms != skip % sms
+        assert torch.equal(y[other], y0[other])
+        y1 = s.predict(X)
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        assert torch.equal(y1, y0)
+    s.close()
