@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--extra-steps", type=int, default=20)
     ap.add_argument("--ab-steps", type=int, default=100, help="plain local-search steps of the prescreen A/B")
     ap.add_argument("--train-steps", type=int, default=2500)
-    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small", "sshape-small"], default=None,
+    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small", "sshape-small", "train-small"],
+                    default=None,
                     help="run a small case of one kernel three times (for profiler captures) and exit")
     return ap.parse_args()
 
@@ -192,8 +193,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the plan-evaluation kernels' source (the committed ncu
+    summaries name the source they were taken on)."""
     h = hashlib.sha256()
-    for name in ("k_eval.cu", "tour_core.cuh", "wh_internal.h"):
+    for name in ("k_eval.cu", "tour_core.cuh"):
         with open(os.path.join(ROOT, "paper_2110_13693_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -1168,7 +1171,18 @@ def run_case(name):
     from paper_2110_13693_gb300 import build as whbuild
     whbuild.build()
     wh.load()
-    if name == "sshape-small":
+    if name == "train-small":
+        # three training steps of 4,096 paper-scale-like feature rows
+        g = torch.Generator(device="cuda").manual_seed(0)
+        X = torch.randint(0, 3, (4096, 192), device="cuda", generator=g).to(torch.bfloat16)
+        t = torch.rand(4096, device="cuda", generator=g)
+        sg = wh.Surrogate(1)
+        for _ in range(3):
+            sg.train_step(X, t, 1e-3)
+        torch.cuda.synchronize()
+        assert sg.status() == 0
+        sg.close()
+    elif name == "sshape-small":
         # one mid-size batch (4,096 plans) under the S-shape rule alone, three calls
         inst = wh_gen.midsize(seed=2, n_plans=PLANS_PER_STEP)
         lay = wh.Layout.of(inst.layout)

@@ -39,18 +39,46 @@ namespace {
 // per order (first line << 8 | line count; count 255 marks an order that the
 // short path does not take: malformed, or 255 lines or more, so its tours go
 // to the long-tour kernel, which checks them) and one key (or SKU) per line.
+// Loads are issued STAGE_BATCH at a time before their stores, so that each
+// thread keeps that many global reads in flight.
+constexpr int STAGE_BATCH = 8;
+
 template <bool KEY16, bool SHARED_MAP>
 __device__ __forceinline__ void stage_tables(const EvalArgs& a, uint32_t* s_desc, void* s_tab, KeySrc& src,
                                              int tid, int T) {
-    for (int o = tid; o < a.n_orders; o += T) {
-        const int lb = a.order_off[o], le = a.order_off[o + 1];
-        const bool ok = lb >= 0 && le >= lb && le <= a.n_lines && le - lb < 255 && lb < (1 << 24);
-        s_desc[o] = ok ? ((uint32_t)lb << 8) | (uint32_t)(le - lb) : 0xFFu;
+    for (int o0 = tid; o0 < a.n_orders; o0 += STAGE_BATCH * T) {
+        int lbs[STAGE_BATCH], les[STAGE_BATCH];
+#pragma unroll
+        for (int u = 0; u < STAGE_BATCH; ++u) {
+            const int o = o0 + u * T;
+            lbs[u] = o < a.n_orders ? a.order_off[o] : 0;
+            les[u] = o < a.n_orders ? a.order_off[o + 1] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < STAGE_BATCH; ++u) {
+            const int o = o0 + u * T;
+            if (o >= a.n_orders) continue;
+            const int lb = lbs[u], le = les[u];
+            const bool ok = lb >= 0 && le >= lb && le <= a.n_lines && le - lb < 255 && lb < (1 << 24);
+            s_desc[o] = ok ? ((uint32_t)lb << 8) | (uint32_t)(le - lb) : 0xFFu;
+        }
     }
     if constexpr (SHARED_MAP) {
         if constexpr (KEY16) {
             uint16_t* k16 = static_cast<uint16_t*>(s_tab);
-            for (int i = tid; i < a.n_lines; i += T) k16[i] = (uint16_t)key16_of(a.line_key[i]);
+            for (int i0 = tid; i0 < a.n_lines; i0 += STAGE_BATCH * T) {
+                uint32_t k[STAGE_BATCH];
+#pragma unroll
+                for (int u = 0; u < STAGE_BATCH; ++u) {
+                    const int i = i0 + u * T;
+                    k[u] = i < a.n_lines ? a.line_key[i] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < STAGE_BATCH; ++u) {
+                    const int i = i0 + u * T;
+                    if (i < a.n_lines) k16[i] = (uint16_t)key16_of(k[u]);
+                }
+            }
         } else {
             uint32_t* k32 = static_cast<uint32_t*>(s_tab);
             for (int i = tid; i < a.n_lines; i += T) k32[i] = a.line_key[i];
@@ -147,6 +175,37 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                         if (lb < 0 || le < lb || le > a.n_lines) { flag(a.status, WH_STATUS_BAD_OFFSET); bad = true; break; }
                     }
                     if (n + (le - lb) > SHORT_MAX) { n += le - lb; break; }
+                    if constexpr (!SHARED_MAP) {
+                        // the plan's own slotting: four lines a step, their
+                        // SKUs and then their slot-map gathers (global
+                        // memory) in flight together
+                        for (int l0 = lb; l0 < le; l0 += 4) {
+                            int sk[4], loc[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) sk[j] = l0 + j < le ? src.skus[l0 + j] : 0;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                loc[j] = (l0 + j < le && (unsigned)sk[j] < (unsigned)a.n_sku) ? src.map[sk[j]] : -1;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (l0 + j >= le) continue;
+                                uint32_t k32 = KEY_BAD;
+                                if ((unsigned)sk[j] >= (unsigned)a.n_sku) flag(a.status, WH_STATUS_BAD_SKU);
+                                else if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
+                                else k32 = loc_key(a.g, loc[j]);
+                                if constexpr (KEY16) {
+                                    const uint32_t k = key16_of(k32);
+                                    kbad |= k == KEY16_BAD;
+                                    reinterpret_cast<uint16_t*>(col16 + (n >> 1) * T)[n & 1] = (uint16_t)k;
+                                } else {
+                                    kbad |= k32 == KEY_BAD;
+                                    reinterpret_cast<uint32_t*>(col32 + (n >> 1) * T)[n & 1] = k32;
+                                }
+                                ++n;
+                            }
+                        }
+                        continue;
+                    }
                     for (int l = lb; l < le; ++l, ++n) {
                         const uint32_t k = key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
                         if constexpr (KEY16) {
@@ -610,10 +669,18 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
             const int cnt = le - lb;
             const int incl = warp_inclusive_scan(cnt);
             int pos = n + incl - cnt;
-            for (int l = lb; l < le; ++l, ++pos) {
-                const uint32_t k = key_of<false, SHARED_MAP, false>(a, src, l);
-                bad |= (k == KEY_BAD);
-                if (pos < LONG_MAXL) kb[pos] = k;
+            // four lines a step: their key (or SKU and slot) loads in flight together
+            for (int l0 = lb; l0 < le; l0 += 4) {
+                uint32_t k[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) k[j] = l0 + j < le ? key_of<false, SHARED_MAP, false>(a, src, l0 + j) : 0u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (l0 + j >= le) continue;
+                    bad |= (k[j] == KEY_BAD);
+                    if (pos < LONG_MAXL) kb[pos] = k[j];
+                    ++pos;
+                }
             }
             n += __shfl_sync(0xffffffffu, incl, 31);
         }

@@ -2,13 +2,13 @@
 // sm_103a): the gradients of 0.5 * mean((y - t)^2) of the prescreen's MLP
 // (machine learning in the decision loop, Sec. 1 and Fig. 1; bf16 weights and
 // activations with fp32 accumulation).  After the tensor-core training
-// forward (k_mlp_tc.cu, which also leaves H1 transposed):
+// forward (k_mlp_tc.cu, which keeps Z1, H1, Z2, H2):
 //
 //   k_bwd_tail   32 rows per block: dy = (y - t) / n, the loss, dZ2 =
-//                bf16(dy * w3 * gelu'(Z2)) row-major and transposed, X
-//                transposed with a row of ones appended (so that the weight
-//                gradient of layer 1 also yields the bias gradient), and
-//                per-block column sums for b2, w3 and b3;
+//                bf16(dy * w3 * gelu'(Z2)) row-major and transposed, H1
+//                transposed, X transposed with a row of ones appended (so
+//                that the weight gradient of layer 1 also yields the bias
+//                gradient), and per-block column sums for b2, w3 and b3;
 //   k_mlp_dz1    dZ1 = bf16((dZ2 W2^T) * gelu'(Z1)), 128 rows per tile on
 //                tcgen05 (M 128, N 256, K 256; W2 resident in shared memory),
 //                written row-major and transposed;
@@ -42,12 +42,34 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // ------------------------------------------------------------------ tail
+// The tile s_t[col][row] (rows r0 .. r0+31) written to a transposed copy,
+// 64 bytes of each column, 16 at a time.
+__device__ __forceinline__ void write_transposed(const __nv_bfloat16 (*s_t)[BT_ROWS + 8], int cols,
+                                                 __nv_bfloat16* dst, int64_t ldt, int64_t r0, int tid) {
+    for (int c = tid; c < cols * 4; c += BT_THREADS) {
+        const int j = c >> 2, q = c & 3;
+        *reinterpret_cast<uint4*>(dst + (int64_t)j * ldt + r0 + 8 * q) = *reinterpret_cast<const uint4*>(&s_t[j][8 * q]);
+    }
+}
+
 __global__ void __launch_bounds__(BT_THREADS) k_bwd_tail(BwdArgs b) {
     __shared__ float s_dy[BT_ROWS];
     __shared__ __align__(16) __nv_bfloat16 s_t[256][BT_ROWS + 8];
     const int tid = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * BT_ROWS;
     float* part = b.part_t + (int64_t)blockIdx.x * BT_PART;
+    // H1 transposed (the forward's activations; rows past n are zero)
+    {
+        const int j = tid;
+#pragma unroll 8
+        for (int rr = 0; rr < BT_ROWS; ++rr) {
+            const int64_t r = r0 + rr;
+            s_t[j][rr] = r < b.n ? b.H1[r * 256 + j] : __float2bfloat16_rn(0.0f);
+        }
+    }
+    __syncthreads();
+    write_transposed(s_t, 256, b.H1T, b.ldt, r0, tid);
+    __syncthreads();
     if (tid < 32) {
         const int64_t r = r0 + tid;
         float d = 0.0f, l = 0.0f;
@@ -70,34 +92,41 @@ __global__ void __launch_bounds__(BT_THREADS) k_bwd_tail(BwdArgs b) {
     }
     __syncthreads();
     {
+        // dZ2 = bf16(dy * w3 * gelu'(Z2)), eight rows' loads in flight
         const int j = tid;
         const float w3j = b.P[MLP_W3_OFF + j];
         float sb2 = 0.0f, sg3 = 0.0f;
-        for (int rr = 0; rr < BT_ROWS; ++rr) {
-            const int64_t r = r0 + rr;
-            __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-            if (r < b.n) {
-                const float dyr = s_dy[rr];
-                v = __float2bfloat16_rn(dyr * w3j * gelu_grad(b.Z2[r * 256 + j]));
-                b.dZ2[r * 256 + j] = v;
-                sb2 += __bfloat162float(v);
-                sg3 += __bfloat162float(b.H2[r * 256 + j]) * dyr;
+        for (int r8 = 0; r8 < BT_ROWS; r8 += 8) {
+            float z[8], h[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t r = r0 + r8 + u;
+                z[u] = r < b.n ? b.Z2[r * 256 + j] : 0.0f;
+                h[u] = r < b.n ? __bfloat162float(b.H2[r * 256 + j]) : 0.0f;
             }
-            s_t[j][rr] = v;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t r = r0 + r8 + u;
+                __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+                if (r < b.n) {
+                    const float dyr = s_dy[r8 + u];
+                    v = __float2bfloat16_rn(dyr * w3j * gelu_grad(z[u]));
+                    b.dZ2[r * 256 + j] = v;
+                    sb2 += __bfloat162float(v);
+                    sg3 += h[u] * dyr;
+                }
+                s_t[j][r8 + u] = v;
+            }
         }
         part[j] = sb2;
         part[256 + j] = sg3;
     }
     __syncthreads();
-    // dZ2 transposed: 64 bytes of rows r0 .. r0+31 per column, 16 at a time
-    for (int c = tid; c < 256 * 4; c += BT_THREADS) {
-        const int j = c >> 2, q = c & 3;
-        *reinterpret_cast<uint4*>(b.dZ2T + (int64_t)j * b.ldt + r0 + 8 * q) =
-            *reinterpret_cast<const uint4*>(&s_t[j][8 * q]);
-    }
+    write_transposed(s_t, 256, b.dZ2T, b.ldt, r0, tid);
     __syncthreads();
     // X transposed, with row 192 = 1 for every row of the batch
     if (tid <= (int)MLP_IN) {
+#pragma unroll 8
         for (int rr = 0; rr < BT_ROWS; ++rr) {
             const int64_t r = r0 + rr;
             __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
@@ -106,11 +135,7 @@ __global__ void __launch_bounds__(BT_THREADS) k_bwd_tail(BwdArgs b) {
         }
     }
     __syncthreads();
-    for (int c = tid; c < ((int)MLP_IN + 1) * 4; c += BT_THREADS) {
-        const int j = c >> 2, q = c & 3;
-        *reinterpret_cast<uint4*>(b.XT + (int64_t)j * b.ldt + r0 + 8 * q) =
-            *reinterpret_cast<const uint4*>(&s_t[j][8 * q]);
-    }
+    write_transposed(s_t, (int)MLP_IN + 1, b.XT, b.ldt, r0, tid);
 }
 
 // ------------------------------------------------------------------- dZ1

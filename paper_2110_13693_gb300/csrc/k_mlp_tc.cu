@@ -62,8 +62,6 @@ struct MlpSave {
     __nv_bfloat16* H1;
     float* Z2;
     __nv_bfloat16* H2;
-    __nv_bfloat16* H1T;   // H1 transposed, [256][ldt] (the backward's K-major operand)
-    int64_t ldt;
 };
 
 // Test hook of the bounded waits: the producer stops before the tile
@@ -233,16 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         w[j] = pack_bf16(g0, g1);
                     }
                     const uint4 o = make_uint4(w[0], w[1], w[2], w[3]);
-                    if (save_rows) {
-                        *reinterpret_cast<uint4*>(save.H1 + row * 256 + c) = o;
-                        // transposed: the 32 lanes write 32 consecutive rows of each column
-                        uint16_t* t = reinterpret_cast<uint16_t*>(save.H1T) + (int64_t)c * save.ldt + row;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            t[(2 * j) * save.ldt] = (uint16_t)(w[j] & 0xFFFFu);
-                            t[(2 * j + 1) * save.ldt] = (uint16_t)(w[j] >> 16);
-                        }
-                    }
+                    if (save_rows) *reinterpret_cast<uint4*>(save.H1 + row * 256 + c) = o;
                     // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r % 8)
                     const int chunk = (c & 63) >> 3;
                     unsigned char* dst = smem + OFF_H + (c >> 6) * ATOM + r * 128 + ((chunk ^ (r & 7)) << 4);
@@ -323,10 +312,9 @@ cudaError_t launch_transpose_bf16(const float* p, int K, int N, void* out, cudaS
 
 cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const CUtensorMap& mw2, const float* P,
                           int64_t n, float* y, int* status, int num_sms, cudaStream_t s, float* Z1, void* H1,
-                          float* Z2, void* H2, void* H1T, int64_t ldt, int64_t skip_tile,
-                          unsigned long long wait_ns) {
+                          float* Z2, void* H2, int64_t skip_tile, unsigned long long wait_ns) {
     if (n <= 0) return cudaSuccess;
-    const bool save_acts = Z1 && H1 && Z2 && H2 && H1T && ldt >= n;
+    const bool save_acts = Z1 && H1 && Z2 && H2;
     auto kern = save_acts ? k_mlp_tc<true> : k_mlp_tc<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     if (e != cudaSuccess) return e;
@@ -337,8 +325,6 @@ cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const C
     save.H1 = static_cast<__nv_bfloat16*>(H1);
     save.Z2 = Z2;
     save.H2 = static_cast<__nv_bfloat16*>(H2);
-    save.H1T = static_cast<__nv_bfloat16*>(H1T);
-    save.ldt = ldt;
     TcFault fault;
     fault.skip_tile = skip_tile;
     fault.wait_ns = wait_ns ? wait_ns : WAIT_NS;

@@ -240,11 +240,13 @@ struct BwdArgs {
     const float* t;             // [n] targets
     const float* Z1;
     const float* Z2;
+    const __nv_bfloat16* H1;
     const __nv_bfloat16* H2;
     const __nv_bfloat16* X;     // [n][192]
     const float* P;             // fp32 master parameters
     float* dy;                  // [n] (y - t) / n
     __nv_bfloat16* dZ2;
+    __nv_bfloat16* H1T;         // [256][ldt]
     __nv_bfloat16* dZ2T;        // [256][ldt]
     __nv_bfloat16* XT;          // [193][ldt]: X transposed, row 192 = 1
     __nv_bfloat16* dZ1;
@@ -278,13 +280,13 @@ cudaError_t launch_to_bf16(const float* p, int64_t n, void* out, cudaStream_t s)
 // fused tcgen05 inference (k_mlp_tc.cu): W1t [256][192] and W2t [256][256]
 // are the transposed bf16 weights the tensor maps mw1 / mw2 describe
 cudaError_t launch_transpose_bf16(const float* p, int K, int N, void* out, cudaStream_t s);
-// Z1 / H1 / Z2 / H2 / H1T (all or none): the training forward's saved pre-
-// activations (fp32) and activations (bf16), [n][256], and H1 transposed,
-// [256][ldt] (ldt >= n)
+// Z1 / H1 / Z2 / H2 (all or none): the training forward's saved pre-
+// activations (fp32) and activations (bf16), [n][256].  skip_tile / wait_ns:
+// the bounded waits' test hook (skip_tile < 0 in normal use).
 cudaError_t launch_mlp_tc(const CUtensorMap& mx, const CUtensorMap& mw1, const CUtensorMap& mw2, const float* P,
                           int64_t n, float* y, int* status, int num_sms, cudaStream_t s, float* Z1 = nullptr,
-                          void* H1 = nullptr, float* Z2 = nullptr, void* H2 = nullptr, void* H1T = nullptr,
-                          int64_t ldt = 0, int64_t skip_tile = -1, unsigned long long wait_ns = 0);
+                          void* H1 = nullptr, float* Z2 = nullptr, void* H2 = nullptr, int64_t skip_tile = -1,
+                          unsigned long long wait_ns = 0);
 size_t mlp_tc_smem_bytes();
 
 struct Tuning {

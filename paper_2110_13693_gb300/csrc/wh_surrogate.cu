@@ -260,7 +260,7 @@ extern "C" int wh_surrogate_predict_timeout_test(wh_surrogate* s, const uint16_t
     rc = encode_map(&mx, X, (uint64_t)n, wh::MLP_IN, 128);
     if (rc != WH_OK) return rc;
     if (wh::launch_mlp_tc(mx, s->mw1, s->mw2, s->P, n, y, s->status, s->num_sms, st, nullptr, nullptr, nullptr,
-                          nullptr, nullptr, 0, skip_tile, (unsigned long long)wait_ns) != cudaSuccess)
+                          nullptr, skip_tile, (unsigned long long)wait_ns) != cudaSuccess)
         return WH_ECUDA;
     return WH_OK;
 }
@@ -283,7 +283,7 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
     const int64_t ldt = ldt_for(n);
     // forward on the tensor cores, keeping both layers' pre-activations and
-    // activations (and H1 transposed) for the backward pass
+    // activations for the backward pass
     if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return WH_EINVAL;
     rc = refresh_transposed(s, st);
     if (rc != WH_OK) return rc;
@@ -292,7 +292,7 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
         rc = encode_map(&mx, X, (uint64_t)n, wh::MLP_IN, 128);
         if (rc != WH_OK) return rc;
         if (wh::launch_mlp_tc(mx, s->mw1, s->mw2, s->P, n, s->y, s->status, s->num_sms, st, s->Z1, s->H1, s->Z2,
-                              s->H2, s->H1T, ldt) != cudaSuccess)
+                              s->H2) != cudaSuccess)
             return WH_ECUDA;
     }
     // backward on the tensor cores: dy, dZ2 and the transposed operands; dZ1;
@@ -305,7 +305,9 @@ extern "C" int wh_surrogate_train_step(wh_surrogate* s, const uint16_t* X, const
     b.t = target;
     b.Z1 = s->Z1;
     b.Z2 = s->Z2;
+    b.H1 = s->H1;
     b.H2 = s->H2;
+    b.H1T = s->H1T;
     b.X = Xb;
     b.P = s->P;
     b.dy = s->dy;
