@@ -635,94 +635,160 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b
 }
 
 // One warp per deferred tour (more than SHORT_MAX lines): keys gathered into
-// a per-warp shared-memory buffer, bitonic-sorted there, then one lane runs
-// the record scan and the DP.
+// a per-warp shared-memory buffer (lanes over orders, four lines' loads in
+// flight), bitonic-sorted there.  With record scratch (L.rec): the per-aisle
+// records are extracted in parallel (a ballot numbers the aisle runs) into
+// the warp's slice, column j for the warp's j-th tour of a group of 32, and
+// once the group is complete each lane runs the DP of one tour; a tour with
+// more than LONG_RMAX records runs its scan and DP on one lane at once.
+// Without scratch every tour's scan and DP run on one lane.
+constexpr int LONG_RMAX = 48;   // records per tour kept for the per-lane DP
+
 template <bool SHARED_MAP>
 __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
     __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
+    __shared__ int s_meta[LONG_WARPS][32][4];   // inst, tour, plan, record count (-1: done)
+    __shared__ uint32_t s_last[LONG_WARPS][32];  // largest key of the tour
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int count = min(*L.count, L.cap);
     uint32_t* kb = buf[warp];
     const bool need_rr = (L.mask & WH_ROUTE_OPTIMAL) != 0;
     const bool want_s = (L.mask & WH_ROUTE_SSHAPE) != 0;
-    for (int w = blockIdx.x * LONG_WARPS + warp; w < count; w += gridDim.x * LONG_WARPS) {
-        const int inst = L.list[3 * w], t = L.list[3 * w + 1], plan = L.list[3 * w + 2];
-        const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
-        KeySrc src = global_src(a);
-        const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];   // checked by the short kernel
-        if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
-        int n = 0;
-        bool bad = false;
-        for (int qb = q0; qb < q1; qb += 32) {
-            const int q = qb + lane;
-            int lb = 0, le = 0;
-            if (q < q1) {
-                const int o = a.order_seq[q];   // in range: checked by the short kernel
-                lb = a.order_off[o];
-                le = a.order_off[o + 1];
-                if (lb < 0 || le < lb || le > a.n_lines) {
-                    flag(a.status, WH_STATUS_BAD_OFFSET);
-                    bad = true;
-                    lb = le = 0;
+    const int gw = blockIdx.x * LONG_WARPS + warp, n_warps = gridDim.x * LONG_WARPS;
+    uint2* rec = L.rec ? L.rec + (int64_t)gw * LONG_RMAX * 32 : nullptr;   // [r][32]
+    auto commit = [&](const EvalArgs& a, int t, int plan, int cs, int cr) {
+        if (a.tour_s && want_s) a.tour_s[t] = cs;
+        if (a.tour_rr && need_rr) a.tour_rr[t] = cr;
+        if (a.plan_s && want_s) atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)cs);
+        if (a.plan_rr && need_rr)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_rr[plan]), (unsigned long long)cr);
+    };
+    // this warp's tours: gw, gw + n_warps, ..., taken 32 at a time
+    for (int w0 = gw; w0 < count; w0 += 32 * n_warps) {
+        int in_group = 0;
+        for (int j = 0; j < 32; ++j) {
+            const int w = w0 + j * n_warps;
+            if (w >= count) break;
+            in_group = j + 1;
+            const int inst = L.list[3 * w], t = L.list[3 * w + 1], plan = L.list[3 * w + 2];
+            const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
+            KeySrc src = global_src(a);
+            const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];   // checked by the short kernel
+            if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
+            int n = 0;
+            bool bad = false;
+            for (int qb = q0; qb < q1; qb += 32) {
+                const int q = qb + lane;
+                int lb = 0, le = 0;
+                if (q < q1) {
+                    const int o = a.order_seq[q];   // in range: checked by the short kernel
+                    lb = a.order_off[o];
+                    le = a.order_off[o + 1];
+                    if (lb < 0 || le < lb || le > a.n_lines) {
+                        flag(a.status, WH_STATUS_BAD_OFFSET);
+                        bad = true;
+                        lb = le = 0;
+                    }
+                }
+                const int cnt = le - lb;
+                const int incl = warp_inclusive_scan(cnt);
+                int pos = n + incl - cnt;
+                // four lines a step: their key (or SKU and slot) loads in flight together
+                for (int l0 = lb; l0 < le; l0 += 4) {
+                    uint32_t k[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) k[u] = l0 + u < le ? key_of<false, SHARED_MAP, false>(a, src, l0 + u) : 0u;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (l0 + u >= le) continue;
+                        bad |= (k[u] == KEY_BAD);
+                        if (pos < LONG_MAXL) kb[pos] = k[u];
+                        ++pos;
+                    }
+                }
+                n += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            bad = __any_sync(0xffffffffu, bad);
+            if (n > LONG_MAXL || bad) {
+                if (lane == 0) {
+                    if (n > LONG_MAXL) flag(a.status, WH_STATUS_TOUR_TOO_LONG);
+                    if (a.tour_s) a.tour_s[t] = -1;
+                    if (a.tour_rr) a.tour_rr[t] = -1;
+                    s_meta[warp][j][3] = -1;
+                }
+                __syncwarp();
+                continue;
+            }
+            warp_sort_buffer(kb, n, lane);
+            int m = 0;
+            if (rec) {
+                // per-aisle records: run r of the sorted keys -> rec[r][j]
+                for (int x0 = 0; x0 < n; x0 += 32) {
+                    const int x = x0 + lane;
+                    const bool in = x < n;
+                    const uint32_t key = in ? kb[x] : 0u;
+                    const int ai = (int)(key >> 16);
+                    const bool first = in && (x == 0 || (int)(kb[x - 1] >> 16) != ai);
+                    const bool last = in && (x == n - 1 || (int)(kb[x + 1] >> 16) != ai);
+                    const unsigned fm = __ballot_sync(0xffffffffu, first);
+                    const int r = m + __popc(fm & ((2u << lane) - 1u)) - 1;
+                    if (last && r < LONG_RMAX) {
+                        const int hi = (int)(key & 0xFFFFu);
+                        int lo = hi, gi = 0;
+                        for (int y = x; y > 0 && (int)(kb[y - 1] >> 16) == ai; --y) {
+                            const int kp = (int)(kb[y - 1] & 0xFFFFu);
+                            gi = max(gi, lo - kp);
+                            lo = kp;
+                        }
+                        rec[r * 32 + j] = make_uint2(((uint32_t)ai << 16) | (uint32_t)lo, ((uint32_t)hi << 16) | (uint32_t)gi);
+                    }
+                    m += __popc(fm);
                 }
             }
-            const int cnt = le - lb;
-            const int incl = warp_inclusive_scan(cnt);
-            int pos = n + incl - cnt;
-            // four lines a step: their key (or SKU and slot) loads in flight together
-            for (int l0 = lb; l0 < le; l0 += 4) {
-                uint32_t k[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) k[j] = l0 + j < le ? key_of<false, SHARED_MAP, false>(a, src, l0 + j) : 0u;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (l0 + j >= le) continue;
-                    bad |= (k[j] == KEY_BAD);
-                    if (pos < LONG_MAXL) kb[pos] = k[j];
-                    ++pos;
-                }
-            }
-            n += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        bad = __any_sync(0xffffffffu, bad);
-        if (n > LONG_MAXL || bad) {
             if (lane == 0) {
-                if (n > LONG_MAXL) flag(a.status, WH_STATUS_TOUR_TOO_LONG);
-                if (a.tour_s) a.tour_s[t] = -1;
-                if (a.tour_rr) a.tour_rr[t] = -1;
+                const uint32_t kl = kb[n - 1];   // rightmost aisle, its deepest slot
+                if (rec && m <= LONG_RMAX) {
+                    s_meta[warp][j][0] = inst;
+                    s_meta[warp][j][1] = t;
+                    s_meta[warp][j][2] = plan;
+                    s_meta[warp][j][3] = m;
+                    s_last[warp][j] = kl;
+                } else {
+                    // the scan and the DP on this lane
+                    DP5 v;
+                    dp_init(v);
+                    int mm = 0, pa = 0, lo = 0, prev = 0, gi = 0;
+                    for (int i = 0; i < n; ++i) {
+                        const uint32_t key = kb[i];
+                        const int ai = (int)(key >> 16), k = (int)(key & 0xFFFFu);
+                        const bool first = (i == 0) || ((int)(kb[i - 1] >> 16) != ai);
+                        const bool last = (i == n - 1) || ((int)(kb[i + 1] >> 16) != ai);
+                        gi = first ? 0 : max(gi, k - prev);
+                        lo = first ? k : lo;
+                        prev = k;
+                        if (last) {
+                            if (need_rr) dp_aisle(v, a.g, ai - pa, lo, k, gi);
+                            pa = ai;
+                            ++mm;
+                        }
+                    }
+                    commit(a, t, plan, sshape_cost(a.g, mm, (int)(kl >> 16), (int)(kl & 0xFFFFu)),
+                           need_rr ? dp_final(v) : 0);
+                    s_meta[warp][j][3] = -1;
+                }
             }
             __syncwarp();
-            continue;
         }
-        warp_sort_buffer(kb, n, lane);
-        if (lane == 0) {
-            DP5 v;
-            dp_init(v);
-            int m = 0, pa = 0, lo = 0, prev = 0, gi = 0, last_a = 0, last_hi = 0;
-            for (int i = 0; i < n; ++i) {
-                const uint32_t key = kb[i];
-                const int ai = (int)(key >> 16), k = (int)(key & 0xFFFFu);
-                const bool first = (i == 0) || ((int)(kb[i - 1] >> 16) != ai);
-                const bool last = (i == n - 1) || ((int)(kb[i + 1] >> 16) != ai);
-                gi = first ? 0 : max(gi, k - prev);
-                lo = first ? k : lo;
-                prev = k;
-                if (last) {
-                    if (need_rr) dp_aisle(v, a.g, ai - pa, lo, k, gi);
-                    pa = ai;
-                    ++m;
-                    last_a = ai;
-                    last_hi = k;
-                }
+        // the group's DPs, one tour per lane
+        if (rec && lane < in_group) {
+            const int m = s_meta[warp][lane][3];
+            if (m >= 0) {
+                const int inst = s_meta[warp][lane][0], t = s_meta[warp][lane][1], plan = s_meta[warp][lane][2];
+                const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
+                const uint32_t kl = s_last[warp][lane];
+                const int cr = need_rr ? rr_records32(a.g, rec + lane, 32, m) : 0;
+                commit(a, t, plan, sshape_cost(a.g, m, (int)(kl >> 16), (int)(kl & 0xFFFFu)), cr);
             }
-            const int cs = sshape_cost(a.g, m, last_a, last_hi);
-            const int cr = need_rr ? dp_final(v) : 0;
-            if (a.tour_s && want_s) a.tour_s[t] = cs;
-            if (a.tour_rr && need_rr) a.tour_rr[t] = cr;
-            if (a.plan_s && want_s)
-                atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)cs);
-            if (a.plan_rr && need_rr)
-                atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_rr[plan]), (unsigned long long)cr);
         }
         __syncwarp();
     }
@@ -888,12 +954,30 @@ cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int
     return sm ? launch_batch_t<false, true>(b, t, smem, num_sms, s) : launch_batch_t<false, false>(b, t, smem, num_sms, s);
 }
 
+// CTAs per SM of the long-tour kernel, the larger of its two forms: its grid
+// (and its record scratch) is sized by this
+static int long_per_sm() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_eval_long<true>, LONG_WARPS * 32, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_eval_long<false>, LONG_WARPS * 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    const int m = a > b ? a : b;
+    return m > 0 ? m : 1;
+}
+
+size_t long_rec_bytes(int num_sms) {
+    const int per_sm = long_per_sm();
+    if (per_sm < 1) return 0;
+    return sizeof(uint2) * (size_t)LONG_RMAX * 32 * LONG_WARPS * (size_t)per_sm * (size_t)num_sms;
+}
+
 cudaError_t launch_eval_long(const LongArgs& L, bool shared_map, int num_sms, cudaStream_t s) {
     auto kern = shared_map ? k_eval_long<true> : k_eval_long<false>;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LONG_WARPS * 32, 0);
-    if (e != cudaSuccess) return e;
-    kern<<<num_sms * (per_sm > 0 ? per_sm : 1), LONG_WARPS * 32, 0, s>>>(L);
+    const int per_sm = long_per_sm();
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<num_sms * per_sm, LONG_WARPS * 32, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -49,8 +49,8 @@ constexpr uint32_t OFF_H = OFF_W + TC_STAGES * W_CHUNK;
 constexpr uint32_t OFF_PAR = OFF_H + H_BYTES;     // b1, b2, w3 (fp32)
 constexpr uint32_t OFF_RED = OFF_PAR + 3 * 256 * 4;  // [2 tiles][parts 1..][128] fp32 partial sums
 constexpr uint32_t OFF_BAR = OFF_RED + 2 * (TC_PARTS - 1) * 128 * 4;
-// x_full, x_empty, w_full[], w_empty[], acc1, h1, acc2, done, red[2]
-constexpr int N_BARS = 2 + 2 * TC_STAGES + 6;
+// x_full, x_empty, w_full[], w_empty[], acc1, acc2, done, red[2], h1c[4]
+constexpr int N_BARS = 2 + 2 * TC_STAGES + 5 + 4;
 constexpr uint32_t OFF_MISC = OFF_BAR + 8 * N_BARS;  // TMEM base address, abort flag
 constexpr uint32_t TC_SMEM = OFF_MISC + 16 + 1024;   // + slack to align the base to 1024 bytes
 
@@ -87,8 +87,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t x_full = bar0, x_empty = bar0 + 8;
     auto w_full = [&](int s) { return bar0 + 16 + 8u * s; };
     auto w_empty = [&](int s) { return bar0 + 16 + 8u * (TC_STAGES + s); };
-    const uint32_t acc1_full = bar0 + 16 + 16 * TC_STAGES, h1_full = acc1_full + 8, acc2_full = acc1_full + 16,
-                   done = acc1_full + 24, red_full = acc1_full + 32;   // red_full: two barriers
+    const uint32_t acc1_full = bar0 + 16 + 16 * TC_STAGES, acc2_full = acc1_full + 8, done = acc1_full + 16,
+                   red_full = acc1_full + 24;   // red_full: two barriers
+    // h1c(c): the layer-1 activations of K-chunk c (columns 64c .. 64c+63)
+    // are in shared memory, so layer 2's MMAs on that chunk can start
+    auto h1c = [&](int c) { return acc1_full + 40 + 8u * c; };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
 
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(w_empty(s), 1);
         }
         mbar_init(acc1_full, 1);
-        mbar_init(h1_full, TC_EPI_WARPS * 32);
+        for (int c = 0; c < 4; ++c) mbar_init(h1c(c), TC_EPI_WARPS * 32);
         mbar_init(acc2_full, 1);
         mbar_init(done, 1);
         mbar_init(red_full, (TC_PARTS - 1) * 128);
@@ -176,11 +179,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!ok) break;
                 tc_commit(x_empty);
                 tc_commit(acc1_full);
-                // layer 2: acc2 = H1 W2 (K = 256 in four chunks of 64), once
-                // the epilogue has written H1
-                if (!(ok = mbar_wait(h1_full, ph, abort, status, fault.wait_ns))) break;
-                tc_fence_after();
+                // layer 2: acc2 = H1 W2 (K = 256 in four chunks of 64), each
+                // chunk as soon as the epilogue has written its columns of H1
                 for (int c = 0; ok && c < 4; ++c, ++g) {
+                    if (!(ok = mbar_wait(h1c(c), ph, abort, status, fault.wait_ns))) break;
+                    tc_fence_after();
                     const int s = (int)(g % TC_STAGES);
                     if (!(ok = mbar_wait(w_full(s), (g / TC_STAGES) & 1u, abort, status, fault.wait_ns))) break;
                     tc_fence_after();
@@ -212,13 +215,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // the TMEM loads below are warp-collective: leave together
             if (!__all_sync(0xffffffffu, mbar_wait(acc1_full, ph, abort, status, fault.wait_ns))) break;
             tc_fence_after();
+            // layer 1 in K-chunk order: every warp takes its 16 columns of
+            // chunk kc (64 kc + 16 part_id ..), then hands the chunk over
 #pragma unroll 1
-            for (int cc = 0; cc < TC_PART_COLS / 32; ++cc) {
-                const int c0 = TC_PART_COLS * part_id + 32 * cc;
-                float v[32];
-                tc_ld32(tmem + lane_addr + (uint32_t)c0, v);
+            for (int kc = 0; kc < 4; ++kc) {
+                const int c0 = 64 * kc + 16 * part_id;
+                float v[16];
+                tc_ld16(tmem + lane_addr + (uint32_t)c0, v);
 #pragma unroll
-                for (int g8 = 0; g8 < 4; ++g8) {
+                for (int g8 = 0; g8 < 2; ++g8) {
                     uint32_t w[4];
                     const int c = c0 + 8 * g8;
 #pragma unroll
@@ -237,10 +242,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     unsigned char* dst = smem + OFF_H + (c >> 6) * ATOM + r * 128 + ((chunk ^ (r & 7)) << 4);
                     *reinterpret_cast<uint4*>(dst) = o;
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(h1c(kc));
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(h1_full);
             if (!__all_sync(0xffffffffu, mbar_wait(acc2_full, ph, abort, status, fault.wait_ns))) break;
             tc_fence_after();
             uint64_t part2 = dup2(0.0f);

@@ -57,7 +57,8 @@ struct wh_batch {
     int32_t n_items = 0;
     size_t items_cap = 0;
     uint32_t* meta = nullptr;              // [0] status, [1] long count, [2] queue
-    void* scratch = nullptr;               // line keys of all instances + long list
+    void* scratch = nullptr;               // line keys of all instances + long list + long records
+    uint2* long_rec = nullptr;             // the long-tour kernel's record scratch (in scratch)
     bool key16 = true;
     int32_t max_orders = 0, max_lines = 0, max_rec = 0, max_work = 0;
     int64_t total_tours = 0;
@@ -306,12 +307,14 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
     const size_t key_bytes = shared_map && !agg ? align_up(sizeof(uint32_t) * (size_t)o.n_lines) : 0;
     const size_t agg_bytes = agg ? align_up(sizeof(uint4) * (size_t)o.n_orders) : 0;
     const size_t list_bytes = align_up(sizeof(int32_t) * 3 * ((size_t)p.n_tours + 1));
-    rc = reserve_scratch(h, key_bytes + agg_bytes + list_bytes);
+    const size_t rec_bytes = align_up(wh::long_rec_bytes(h->num_sms));
+    rc = reserve_scratch(h, key_bytes + agg_bytes + list_bytes + rec_bytes);
     if (rc != WH_OK) return rc;
     char* base = static_cast<char*>(h->scratch);
     a.line_key = shared_map && !agg && o.n_lines > 0 ? reinterpret_cast<uint32_t*>(base) : nullptr;
     a.order_agg = agg ? reinterpret_cast<uint4*>(base + key_bytes) : nullptr;
     a.long_list = reinterpret_cast<int32_t*>(base + key_bytes + agg_bytes);
+    uint2* long_rec = rec_bytes ? reinterpret_cast<uint2*>(base + key_bytes + agg_bytes + list_bytes) : nullptr;
 
     {
         LaunchTimer lt(h->timing, K_PREP, s);
@@ -331,6 +334,7 @@ extern "C" int wh_eval_plans(wh_layout* h, const wh_orders* orders, const wh_pla
         L.count = a.long_count;
         L.cap = a.long_cap;
         L.mask = routing_mask;
+        L.rec = long_rec;
         if (!lt.ok() || wh::launch_eval_long(L, shared_map, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
     }
     return WH_OK;
@@ -947,6 +951,7 @@ int launch_batch(wh_batch* b, uint32_t mask, cudaStream_t s, bool timed = false)
     L.count = B.long_count;
     L.cap = b->long_cap;
     L.mask = mask;
+    L.rec = b->long_rec;
     LaunchTimer lt(tm, KB_LONG, s);
     if (wh::launch_eval_long(L, true, b->num_sms, s) != cudaSuccess) return WH_ECUDA;
     return WH_OK;
@@ -990,8 +995,9 @@ extern "C" int wh_batch_create(const wh_instance* insts, int32_t n, wh_batch** o
     }
     b->long_cap = (int32_t)std::min<int64_t>(kBatchLongCap, b->total_tours + 1);
     const size_t list_bytes = align_up(sizeof(int32_t) * 3 * (size_t)b->long_cap);
+    const size_t rec_bytes = align_up(wh::long_rec_bytes(b->num_sms));
     if (cudaMalloc(&b->meta, kAlign) != cudaSuccess || cudaMemset(b->meta, 0, kAlign) != cudaSuccess ||
-        cudaMalloc(&b->scratch, key_bytes + list_bytes) != cudaSuccess ||
+        cudaMalloc(&b->scratch, key_bytes + list_bytes + rec_bytes) != cudaSuccess ||
         cudaMalloc(&b->d_args, sizeof(wh::EvalArgs) * n) != cudaSuccess) {
         cudaGetLastError();
         wh_batch_destroy(b);
@@ -999,6 +1005,7 @@ extern "C" int wh_batch_create(const wh_instance* insts, int32_t n, wh_batch** o
     }
     char* base = static_cast<char*>(b->scratch);
     int32_t* list = reinterpret_cast<int32_t*>(base + key_bytes);
+    b->long_rec = rec_bytes ? reinterpret_cast<uint2*>(base + key_bytes + list_bytes) : nullptr;
     size_t off = 0;
     for (int32_t i = 0; i < n; ++i) {
         wh::EvalArgs& a = b->args[i];

@@ -79,7 +79,13 @@ struct LongArgs {
     const int32_t* count;
     int32_t cap;
     uint32_t mask;
+    // per-warp record scratch (long_rec_bytes): records are extracted in
+    // parallel and the DPs of 32 tours run one per lane; NULL: each tour's
+    // scan and DP run on one lane
+    uint2* rec = nullptr;
 };
+// bytes of LongArgs::rec for a launch on num_sms SMs
+size_t long_rec_bytes(int num_sms);
 
 // Move evaluation (k_moves.cu)
 struct MoveArgs {
