@@ -224,17 +224,24 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
         const bool run = active && !bad && !is_long;
         const int nr = run ? n : 0;
         const int nmax = __reduce_max_sync(0xffffffffu, nr);
-        int cs = 0, cr = 0;
+        int cs = 0, cr = 0, m = 0;
         if constexpr (KEY16) {
-            if (nmax <= 16) tour16<8>(a, col16, T, nr, need_rr, cs, cr);
-            else if (nmax <= 32) tour16<16>(a, col16, T, nr, need_rr, cs, cr);
-            else tour16<32>(a, col16, T, nr, need_rr, cs, cr);
+            if (nmax <= 16) tour16<8>(a, col16, T, nr, need_rr, cs, cr, m);
+            else if (nmax <= 32) tour16<16>(a, col16, T, nr, need_rr, cs, cr, m);
+            else tour16<32>(a, col16, T, nr, need_rr, cs, cr, m);
         } else {
-            if (nmax <= 16) tour32<16>(a, col32, T, nr, need_rr, cs, cr);
-            else if (nmax <= 32) tour32<32>(a, col32, T, nr, need_rr, cs, cr);
-            else tour32<64>(a, col32, T, nr, need_rr, cs, cr);
+            if (nmax <= 16) tour32<16>(a, col32, T, nr, need_rr, cs, cr, m);
+            else if (nmax <= 32) tour32<32>(a, col32, T, nr, need_rr, cs, cr, m);
+            else tour32<64>(a, col32, T, nr, need_rr, cs, cr, m);
         }
-        const bool ok = run && !kbad;
+        // more pick aisles than this thread's record slots: the long-tour
+        // pass scores the tour
+        bool rec_long = run && !kbad && need_rr && m > a.max_rec;
+        if (rec_long && !defer_long(a, inst, t, plan)) {
+            rec_long = false;
+            bad = true;
+        }
+        const bool ok = run && !kbad && !rec_long && !bad;
         if (active && (bad || kbad)) {
             if (a.tour_s) a.tour_s[t] = -1;
             if (a.tour_rr) a.tour_rr[t] = -1;
@@ -855,6 +862,7 @@ bool sshape_kernel_applies(const EvalArgs& a) {
 
 
 static size_t buffer_bytes(bool k16, int max_rec, int threads) {
+    // a slot holds two keys or one record: 32 slots for 64 keys
     const size_t slots = max_rec > SHORT_MAX / 2 ? (size_t)max_rec : (size_t)(SHORT_MAX / 2);
     return (k16 ? sizeof(uint32_t) : sizeof(uint2)) * slots * (size_t)threads;
 }

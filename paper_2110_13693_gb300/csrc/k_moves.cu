@@ -422,15 +422,23 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
         }
         const int nr = run ? n : 0;
         const int nmax = __reduce_max_sync(0xffffffffu, nr);
-        int cs = 0, cr = 0;
+        int cs = 0, cr = 0, m = 0;
         if constexpr (KEY16) {
-            if (nmax <= 16) tour16<8>(a, col16, T, nr, true, cs, cr);
-            else if (nmax <= 32) tour16<16>(a, col16, T, nr, true, cs, cr);
-            else tour16<32>(a, col16, T, nr, true, cs, cr);
+            if (nmax <= 16) tour16<8>(a, col16, T, nr, true, cs, cr, m);
+            else if (nmax <= 32) tour16<16>(a, col16, T, nr, true, cs, cr, m);
+            else tour16<32>(a, col16, T, nr, true, cs, cr, m);
         } else {
-            if (nmax <= 16) tour32<16>(a, col32, T, nr, true, cs, cr);
-            else if (nmax <= 32) tour32<32>(a, col32, T, nr, true, cs, cr);
-            else tour32<64>(a, col32, T, nr, true, cs, cr);
+            if (nmax <= 16) tour32<16>(a, col32, T, nr, true, cs, cr, m);
+            else if (nmax <= 32) tour32<32>(a, col32, T, nr, true, cs, cr, m);
+            else tour32<64>(a, col32, T, nr, true, cs, cr, m);
+        }
+        // more pick aisles than this thread's record slots: the long-task
+        // pass scores the task
+        if (run && m > a.max_rec) {
+            const int slot = atomicAdd(M.long_count, 1);
+            if (slot < M.long_cap) { M.long_list[slot] = (int32_t)i; deferred = true; }
+            else { flag(a.status, WH_STATUS_LONG_OVERFLOW); M.mstatus[tk.x] = 3; }
+            run = false;
         }
         long long ds = 0, dr = 0;
         if (run) {

@@ -303,13 +303,16 @@ __device__ __forceinline__ void load16(const uint32_t* col, int T, int n, uint32
     }
 }
 
+// m: the tour's pick-aisle count; with the optimal rule, a tour of more
+// than a.max_rec pick aisles has no room for its records: cr is then not its
+// cost and the caller hands the tour to a long-tour pass.
 template <int N>
 __device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int n, bool need_rr, int& cs,
-                                       int& cr) {
+                                       int& cr, int& m) {
     uint32_t x[N];
     load32<N>(col, T, n, x);
     bitonic_sort<N>(x);
-    int m, last_a, last_hi;
+    int last_a, last_hi;
     scan32<N>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
     cs = sshape_cost(a.g, m, last_a, last_hi);
     cr = need_rr ? rr_records32(a.g, col, T, min(m, a.max_rec)) : 0;
@@ -317,11 +320,11 @@ __device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int
 
 template <int R>
 __device__ __forceinline__ void tour16(const EvalArgs& a, uint32_t* col, int T, int n, bool need_rr, int& cs,
-                                       int& cr) {
+                                       int& cr, int& m) {
     uint32_t x[R];
     load16<R>(col, T, n, x);
     sort16x2<R>(x);
-    int m, last_a, last_hi;
+    int last_a, last_hi;
     scan16<R>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
     cs = sshape_cost(a.g, m, last_a, last_hi);
     cr = need_rr ? rr_records16(a.g, col, T, min(m, a.max_rec)) : 0;

@@ -207,7 +207,10 @@ void fill_args(wh::EvalArgs& a, const wh::Geo& g, const wh_orders& o, const wh_p
     a.plan_s = out.plan_s;
     a.plan_rr = out.plan_rr;
     a.mask = mask;
-    a.max_rec = g.A < wh::SHORT_MAX ? g.A : wh::SHORT_MAX;
+    // record slots per thread: a tour of more pick aisles goes to the
+    // long-tour pass (rare: a tour of <= 64 lines rarely visits more than 32
+    // aisles), so the per-thread buffers stay at 32 slots
+    a.max_rec = g.A < wh::SHORT_MAX / 2 ? g.A : wh::SHORT_MAX / 2;
 }
 
 int device_info(int* dev, int* sms) {

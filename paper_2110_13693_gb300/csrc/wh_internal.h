@@ -40,7 +40,7 @@ struct EvalArgs {
     int64_t* plan_s;
     int64_t* plan_rr;
     uint32_t mask;
-    int32_t max_rec;            // record slots per thread = min(SHORT_MAX, A)
+    int32_t max_rec;            // record slots per thread (a tour with more pick aisles goes to the long pass)
     uint32_t* status;           // device status word
     int32_t* long_list;         // tours deferred to the long-tour kernel: (inst, tour, plan)
     int32_t* long_count;

@@ -136,7 +136,7 @@ def test_autotune_and_cache(gpu_lib, tmp_path):
     batch, items = build_batch(gpu_lib, insts)
     cache = tmp_path / "tune.json"
     th, ch, hit = batch.autotune(3, str(cache))
-    assert hit == 0 and th in (128, 256) and ch >= 1
+    assert hit == 0 and th in (128, 256, 384) and ch >= 1
     entries = json.loads(cache.read_text())
     assert len(entries) == 1 and list(entries.values())[0]["threads"] == th
     assert batch.tuning()[:2] == (th, ch)

@@ -261,3 +261,16 @@ def test_move_stats_count_the_changed_tours(gpu_lib):
                     want_t += 1
                     want_l += tl(tour_of[o])
     assert (tours, lines) == (want_t, int(want_l))
+
+
+def test_moved_tours_over_the_record_slots(gpu_lib):
+    """Moves on tours that visit more pick aisles than a thread keeps records
+    for (64 aisles, one- and two-line orders spread over them): the changed
+    tours go to the long-task pass and the deltas equal the oracle's."""
+    import test_parity_gpu as tp
+    inst = tp._wide_instance(n_plans=4)
+    rng = np.random.default_rng(1)
+    maps = np.stack([inst.slot_map if p == 0 else rng.permutation(inst.layout.n_loc)[: inst.n_sku]
+                     for p in range(4)]).astype(np.int32)
+    s, st = check(gpu_lib, inst, moves_for(inst, 3, 64), maps=maps)
+    assert st == 0 and (s == 0).sum() > 150

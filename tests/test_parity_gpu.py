@@ -378,3 +378,60 @@ def test_host_pipeline_16bit_order_ids(gpu_lib):
         assert np.array_equal(dst.cpu().numpy(), vals[off:].astype(np.int32))
     assert lay.status() == 0
     lay.close()
+
+
+def _wide_instance(n_plans=3):
+    """Tours of at most 64 lines that visit more than 32 aisles (the
+    per-thread record slots): 64 aisles, one-line orders spread over them."""
+    lay = wh_gen.Layout(64, 20)
+    rng = np.random.default_rng(40)
+    n_sku = lay.n_loc
+    slot = rng.permutation(lay.n_loc).astype(np.int32)
+    # SKU s sits at location slot[s]; order o holds SKUs of aisle o % 64
+    by_aisle = [np.nonzero(slot // (2 * lay.slots_per_side) == a)[0] for a in range(64)]
+    orders = [[int(rng.choice(by_aisle[o % 64]))] + ([int(rng.choice(by_aisle[(o * 7) % 64]))] if o % 3 == 0 else [])
+              for o in range(400)]
+    plans = []
+    for p in range(n_plans):
+        perm = rng.permutation(len(orders)).tolist()
+        sizes = [40, 33, 20, 47, 5]            # orders per tour (<= 64 lines each)
+        tours, i = [], 0
+        while i < len(perm):
+            k = sizes[len(tours) % len(sizes)]
+            tours.append(perm[i:i + k])
+            i += k
+        plans.append(tours)
+    return make_instance(lay, orders, slot, plans, n_sku)
+
+
+def test_tours_over_the_record_slots_go_to_the_long_pass(gpu_lib):
+    """Tours of <= 64 lines with more pick aisles than a thread keeps records
+    for are handed to the long-tour pass: single launch, batched launch and
+    per-plan slottings all equal the oracle."""
+    import torch
+    inst = _wide_instance()
+    want = oracle.eval_plans(inst)
+    aisles = [len({int(inst.slot_map[s]) // 40 for o in inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]
+                   for s in inst.line_sku[inst.order_off[o]:inst.order_off[o + 1]]}) for t in range(inst.n_tours)]
+    lines = inst.tour_lines()
+    assert sum(1 for a, n in zip(aisles, lines) if a > 32 and n <= 64) >= 6
+    got = gpu_eval(gpu_lib, inst)
+    assert got[4] == 0
+    assert_exact(got, want)
+    maps = np.tile(inst.slot_map, (inst.n_plans, 1)).ravel().astype(np.int32)
+    got = gpu_eval(gpu_lib, inst, slot_map=maps, stride=inst.n_sku)
+    assert got[4] == 0
+    assert_exact(got, want)
+    wh = gpu_lib
+    lay = inst.layout
+    prob = wh.to_device(inst)
+    costs = wh.alloc_costs(prob.n_tours, prob.n_plans)
+    b = wh.Batch([((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width),
+                   prob, costs)])
+    b.eval(3)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    got = (costs.tour_s[:prob.n_tours].cpu().numpy(), costs.tour_rr[:prob.n_tours].cpu().numpy(),
+           costs.plan_s[:prob.n_plans].cpu().numpy(), costs.plan_rr[:prob.n_plans].cpu().numpy())
+    assert_exact(got, want)
+    b.close()
