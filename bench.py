@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--extra-steps", type=int, default=20)
     ap.add_argument("--ab-steps", type=int, default=100, help="plain local-search steps of the prescreen A/B")
     ap.add_argument("--train-steps", type=int, default=2500)
-    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small", "sshape-small", "train-small"],
+    ap.add_argument("--case", choices=["batched-small", "moves-small", "surrogate-small", "sshape-small", "train-small",
+                                       "midsize-both"],
                     default=None,
                     help="run a small case of one kernel three times (for profiler captures) and exit")
     return ap.parse_args()
@@ -1182,14 +1183,15 @@ def run_case(name):
         torch.cuda.synchronize()
         assert sg.status() == 0
         sg.close()
-    elif name == "sshape-small":
-        # one mid-size batch (4,096 plans) under the S-shape rule alone, three calls
+    elif name in ("sshape-small", "midsize-both"):
+        # one mid-size batch (4,096 plans), three calls: the S-shape rule
+        # alone, or both rules
         inst = wh_gen.midsize(seed=2, n_plans=PLANS_PER_STEP)
         lay = wh.Layout.of(inst.layout)
         prob = wh.to_device(inst)
         costs = wh.alloc_costs(prob.n_tours, prob.n_plans)
         for _ in range(3):
-            lay.eval_plans(prob, costs, 1)
+            lay.eval_plans(prob, costs, 1 if name == "sshape-small" else 3)
         torch.cuda.synchronize()
         assert lay.status() == 0
         lay.close()
@@ -1202,6 +1204,7 @@ def run_case(name):
             items.append(((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width),
                           prob, wh.alloc_costs(prob.n_tours, prob.n_plans)))
         b = wh.Batch(items)
+        b.set_tuning(384, 16, 1)   # the headline's CTA size; items small enough to fill the GPU
         for _ in range(3):
             b.eval(3)
         torch.cuda.synchronize()
