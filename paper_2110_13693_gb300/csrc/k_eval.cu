@@ -29,6 +29,8 @@
 // without picks is crossed in one step (every class keeps to the cheapest
 // horizontal edge pattern it can use there), so the DP costs one step per
 // aisle that holds a pick instead of one per aisle up to the rightmost pick.
+#include <type_traits>
+
 #include "tour_core.cuh"
 
 namespace wh {
@@ -40,12 +42,16 @@ namespace {
 // short path does not take: malformed, or 255 lines or more, so its tours go
 // to the long-tour kernel, which checks them) and one key (or SKU) per line.
 // Loads are issued STAGE_BATCH at a time before their stores, so that each
-// thread keeps that many global reads in flight.
+// thread keeps that many global reads in flight.  Returns true when one of
+// this thread's staged keys is the bad-key marker (a line whose SKU or slot is
+// invalid) or when keys are not staged (per-plan slottings): the evaluation
+// then checks every tour's keys.
 constexpr int STAGE_BATCH = 8;
 
 template <bool KEY16, bool SHARED_MAP>
-__device__ __forceinline__ void stage_tables(const EvalArgs& a, uint32_t* s_desc, void* s_tab, KeySrc& src,
+__device__ __forceinline__ bool stage_tables(const EvalArgs& a, uint32_t* s_desc, void* s_tab, KeySrc& src,
                                              int tid, int T) {
+    bool bad = false;
     for (int o0 = tid; o0 < a.n_orders; o0 += STAGE_BATCH * T) {
         int lbs[STAGE_BATCH], les[STAGE_BATCH];
 #pragma unroll
@@ -76,20 +82,29 @@ __device__ __forceinline__ void stage_tables(const EvalArgs& a, uint32_t* s_desc
 #pragma unroll
                 for (int u = 0; u < STAGE_BATCH; ++u) {
                     const int i = i0 + u * T;
-                    if (i < a.n_lines) k16[i] = (uint16_t)key16_of(k[u]);
+                    if (i >= a.n_lines) continue;
+                    const uint32_t k16v = key16_of(k[u]);
+                    bad |= k16v == KEY16_BAD;
+                    k16[i] = (uint16_t)k16v;
                 }
             }
         } else {
             uint32_t* k32 = static_cast<uint32_t*>(s_tab);
-            for (int i = tid; i < a.n_lines; i += T) k32[i] = a.line_key[i];
+            for (int i = tid; i < a.n_lines; i += T) {
+                const uint32_t k = a.line_key[i];
+                bad |= k == KEY_BAD;
+                k32[i] = k;
+            }
         }
         src.keys = s_tab;
     } else {
         int32_t* sk = static_cast<int32_t*>(s_tab);
         for (int i = tid; i < a.n_lines; i += T) sk[i] = a.line_sku[i];
         src.skus = sk;
+        bad = true;
     }
     src.desc = s_desc;
+    return bad;
 }
 
 __device__ __forceinline__ KeySrc global_src(const EvalArgs& a) {
@@ -119,7 +134,8 @@ __device__ __forceinline__ bool defer_long(const EvalArgs& a, int inst, int t, i
 // tour per lane, and adds its plans' sums with one atomic per plan segment.
 template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
 __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint32_t mask, int inst, int c_begin,
-                                            int c_end, uint32_t* col16, uint2* col32, int T, int lane) {
+                                            int c_end, uint32_t* col16, uint2* col32, int T, int lane,
+                                            bool check_keys) {
     const bool need_rr = (mask & WH_ROUTE_OPTIMAL) != 0;
     const bool want_s = (mask & WH_ROUTE_SSHAPE) != 0;
     // plan of the first tour: largest p with plan_tour_off[p] <= t
@@ -139,9 +155,17 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
         while (plan + 1 < a.n_plans && a.plan_tour_off[plan + 1] <= t) ++plan;
         if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
         // one pass over the tour's orders: check them, count the lines and
-        // stage the first SHORT_MAX keys in this thread's buffer column
+        // stage the first SHORT_MAX keys in this thread's buffer column.
+        // Position p of the column is element (p >> 1) * 2T + (p & 1) (two
+        // keys per slot, slots T apart): the write pointer w advances by
+        // `step`, which alternates between 1 and 2T - 1, and by 2T over two
+        // positions, so no position is recomputed per line.
+        using KeyT = typename std::conditional<KEY16, uint16_t, uint32_t>::type;
+        KeyT* w = KEY16 ? reinterpret_cast<KeyT*>(col16) : reinterpret_cast<KeyT*>(col32);
+        const int two_t = 2 * T;
+        int step = 1;
         int n = 0;
-        bool bad = false, kbad = false;
+        bool bad = false;
         if (active) {
             const int q0 = __ldg(a.tour_off + t), q1 = __ldg(a.tour_off + t + 1);
             if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
@@ -175,6 +199,7 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                         if (lb < 0 || le < lb || le > a.n_lines) { flag(a.status, WH_STATUS_BAD_OFFSET); bad = true; break; }
                     }
                     if (n + (le - lb) > SHORT_MAX) { n += le - lb; break; }
+                    n += le - lb;
                     if constexpr (!SHARED_MAP) {
                         // the plan's own slotting: four lines a step, their
                         // SKUs and then their slot-map gathers (global
@@ -193,28 +218,27 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                                 if ((unsigned)sk[j] >= (unsigned)a.n_sku) flag(a.status, WH_STATUS_BAD_SKU);
                                 else if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
                                 else k32 = loc_key(a.g, loc[j]);
-                                if constexpr (KEY16) {
-                                    const uint32_t k = key16_of(k32);
-                                    kbad |= k == KEY16_BAD;
-                                    reinterpret_cast<uint16_t*>(col16 + (n >> 1) * T)[n & 1] = (uint16_t)k;
-                                } else {
-                                    kbad |= k32 == KEY_BAD;
-                                    reinterpret_cast<uint32_t*>(col32 + (n >> 1) * T)[n & 1] = k32;
-                                }
-                                ++n;
+                                *w = (KeyT)(KEY16 ? key16_of(k32) : k32);
+                                w += step;
+                                step = two_t - step;
                             }
                         }
                         continue;
                     }
-                    for (int l = lb; l < le; ++l, ++n) {
-                        const uint32_t k = key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
-                        if constexpr (KEY16) {
-                            kbad |= k == KEY16_BAD;
-                            reinterpret_cast<uint16_t*>(col16 + (n >> 1) * T)[n & 1] = (uint16_t)k;
-                        } else {
-                            kbad |= k == KEY_BAD;
-                            reinterpret_cast<uint32_t*>(col32 + (n >> 1) * T)[n & 1] = k;
-                        }
+                    // two lines a step (positions p and p + 1 sit `step`
+                    // apart), then the odd one
+                    int l = lb;
+                    for (; l + 1 < le; l += 2) {
+                        const KeyT k0 = (KeyT)key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
+                        const KeyT k1 = (KeyT)key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l + 1);
+                        w[0] = k0;
+                        w[step] = k1;
+                        w += two_t;
+                    }
+                    if (l < le) {
+                        *w = (KeyT)key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
+                        w += step;
+                        step = two_t - step;
                     }
                 }
             }
@@ -225,15 +249,17 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
         const int nr = run ? n : 0;
         const int nmax = __reduce_max_sync(0xffffffffu, nr);
         int cs = 0, cr = 0, m = 0;
+        bool kbad = false;   // a line whose SKU or slot is invalid (its key is the bad-key marker)
         if constexpr (KEY16) {
-            if (nmax <= 16) tour16<8>(a, col16, T, nr, need_rr, cs, cr, m);
-            else if (nmax <= 32) tour16<16>(a, col16, T, nr, need_rr, cs, cr, m);
-            else tour16<32>(a, col16, T, nr, need_rr, cs, cr, m);
+            if (nmax <= 16) tour16<8>(a, col16, T, nr, need_rr, cs, cr, m, check_keys, &kbad);
+            else if (nmax <= 32) tour16<16>(a, col16, T, nr, need_rr, cs, cr, m, check_keys, &kbad);
+            else tour16<32>(a, col16, T, nr, need_rr, cs, cr, m, check_keys, &kbad);
         } else {
-            if (nmax <= 16) tour32<16>(a, col32, T, nr, need_rr, cs, cr, m);
-            else if (nmax <= 32) tour32<32>(a, col32, T, nr, need_rr, cs, cr, m);
-            else tour32<64>(a, col32, T, nr, need_rr, cs, cr, m);
+            if (nmax <= 16) tour32<16>(a, col32, T, nr, need_rr, cs, cr, m, check_keys, &kbad);
+            else if (nmax <= 32) tour32<32>(a, col32, T, nr, need_rr, cs, cr, m, check_keys, &kbad);
+            else tour32<64>(a, col32, T, nr, need_rr, cs, cr, m, check_keys, &kbad);
         }
+        kbad = kbad && run;
         // more pick aisles than this thread's record slots: the long-tour
         // pass scores the tour
         bool rec_long = run && !kbad && need_rr && m > a.max_rec;
@@ -366,10 +392,8 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_short(EvalArgs a)
     unsigned char* buf_base = smem + off_b;
 
     KeySrc src = global_src(a);
-    if constexpr (SMEM_TABLES) {
-        stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T);
-        __syncthreads();
-    }
+    bool check_keys = true;   // keys read from global memory: every tour checks its own
+    if constexpr (SMEM_TABLES) check_keys = __syncthreads_or(stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T));
     // this warp's contiguous range of 32-tour chunks
     const int warps = gridDim.x * (T >> 5);
     const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
@@ -380,7 +404,7 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_short(EvalArgs a)
     if (c_begin >= c_end) return;
     eval_chunks<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, a.mask, 0, c_begin, c_end,
                                                 reinterpret_cast<uint32_t*>(buf_base) + tid,
-                                                reinterpret_cast<uint2*>(buf_base) + tid, T, lane);
+                                                reinterpret_cast<uint2*>(buf_base) + tid, T, lane, check_keys);
 }
 
 // S-shape only (routing mask = S-shape): no sort.  The S-shape length of a
@@ -406,7 +430,7 @@ __global__ void __launch_bounds__(256) k_eval_sshape(EvalArgs a) {
     const int nw = (a.g.A + 31) >> 5;
     KeySrc src = global_src(a);
     if constexpr (SMEM_TABLES) {
-        stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T);
+        stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T);   // the loop checks every key
         __syncthreads();
     }
     for (int w = 0; w < nw; ++w) bm[w * T] = 0u;
@@ -615,6 +639,7 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b
     uint32_t* col16 = reinterpret_cast<uint32_t*>(buf_base) + tid;
     uint2* col32 = reinterpret_cast<uint2*>(buf_base) + tid;
     int staged = -1;
+    bool check_keys = true;   // the staged instance has a bad key (or keys are not staged)
     KeySrc src;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(b.queue, 1);
@@ -628,15 +653,18 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b
             for (int i = tid; i < (int)(sizeof(EvalArgs) / sizeof(int)); i += T) dstw[i] = srcw[i];
             __syncthreads();
             src = global_src(s_a);
-            if constexpr (SMEM_TABLES) stage_tables<KEY16, true>(s_a, s_desc, s_tab, src, tid, T);
+            bool kb = true;
+            if constexpr (SMEM_TABLES) kb = stage_tables<KEY16, true>(s_a, s_desc, s_tab, src, tid, T);
+            check_keys = kb;
             staged = w.inst;
         }
-        __syncthreads();
+        check_keys = __syncthreads_or(check_keys);
         const int n = w.chunk_end - w.chunk_begin;
         const int per = (n + nw - 1) / nw;
         const int cb = w.chunk_begin + warp * per;
         const int ce = min(cb + per, w.chunk_end);
-        if (cb < ce) eval_chunks<KEY16, true, SMEM_TABLES>(s_a, src, b.mask, w.inst, cb, ce, col16, col32, T, lane);
+        if (cb < ce)
+            eval_chunks<KEY16, true, SMEM_TABLES>(s_a, src, b.mask, w.inst, cb, ce, col16, col32, T, lane, check_keys);
         __syncthreads();
     }
 }

@@ -305,12 +305,20 @@ __device__ __forceinline__ void load16(const uint32_t* col, int T, int n, uint32
 
 // m: the tour's pick-aisle count; with the optimal rule, a tour of more
 // than a.max_rec pick aisles has no room for its records: cr is then not its
-// cost and the caller hands the tour to a long-tour pass.
+// cost and the caller hands the tour to a long-tour pass.  With check set,
+// *kbad reports whether one of the n keys is the bad-key marker (a line whose
+// SKU or slot is invalid), tested on the loaded registers two keys at a time.
 template <int N>
 __device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int n, bool need_rr, int& cs,
-                                       int& cr, int& m) {
+                                       int& cr, int& m, bool check = false, bool* kbad = nullptr) {
     uint32_t x[N];
     load32<N>(col, T, n, x);
+    if (check) {
+        bool b = false;
+#pragma unroll
+        for (int p = 0; p < N; ++p) b |= x[p] == KEY_BAD;
+        *kbad = b;
+    }
     bitonic_sort<N>(x);
     int last_a, last_hi;
     scan32<N>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
@@ -320,9 +328,15 @@ __device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int
 
 template <int R>
 __device__ __forceinline__ void tour16(const EvalArgs& a, uint32_t* col, int T, int n, bool need_rr, int& cs,
-                                       int& cr, int& m) {
+                                       int& cr, int& m, bool check = false, bool* kbad = nullptr) {
     uint32_t x[R];
     load16<R>(col, T, n, x);
+    if (check) {
+        uint32_t acc = 0u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc |= __vcmpeq2(x[r], (KEY16_BAD << 16) | KEY16_BAD);
+        *kbad = acc != 0u;
+    }
     sort16x2<R>(x);
     int last_a, last_hi;
     scan16<R>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
