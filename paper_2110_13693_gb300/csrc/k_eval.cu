@@ -138,6 +138,12 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                                             bool check_keys) {
     const bool need_rr = (mask & WH_ROUTE_OPTIMAL) != 0;
     const bool want_s = (mask & WH_ROUTE_SSHAPE) != 0;
+    // staged order book (shared memory): descriptors and per-line keys
+    uint32_t desc_sa = 0, keys_sa = 0;
+    if constexpr (SMEM_TABLES) {
+        desc_sa = smem_addr(src.desc);
+        if constexpr (SHARED_MAP) keys_sa = smem_addr(src.keys);
+    }
     // plan of the first tour: largest p with plan_tour_off[p] <= t
     int plan = 0;
     {
@@ -157,13 +163,14 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
         // one pass over the tour's orders: check them, count the lines and
         // stage the first SHORT_MAX keys in this thread's buffer column.
         // Position p of the column is element (p >> 1) * 2T + (p & 1) (two
-        // keys per slot, slots T apart): the write pointer w advances by
-        // `step`, which alternates between 1 and 2T - 1, and by 2T over two
-        // positions, so no position is recomputed per line.
+        // keys per slot, slots T apart): the write address wa advances by
+        // stepb, which alternates between 1 and 2T - 1 elements, and by 2T
+        // elements over two positions, so no position is recomputed per line.
         using KeyT = typename std::conditional<KEY16, uint16_t, uint32_t>::type;
-        KeyT* w = KEY16 ? reinterpret_cast<KeyT*>(col16) : reinterpret_cast<KeyT*>(col32);
-        const int two_t = 2 * T;
-        int step = 1;
+        constexpr uint32_t KB = sizeof(KeyT);
+        uint32_t wa = smem_addr(KEY16 ? static_cast<void*>(col16) : static_cast<void*>(col32));
+        const uint32_t two_tb = 2u * (uint32_t)T * KB;
+        uint32_t stepb = KB;
         int n = 0;
         bool bad = false;
         if (active) {
@@ -178,14 +185,16 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                 int o1 = 0;
                 if (q0 < q1) {
                     o1 = __ldg(a.order_seq + q0);
-                    if constexpr (SMEM_TABLES) d1 = (unsigned)o1 < (unsigned)a.n_orders ? src.desc[o1] : 0xFFFFFFFFu;
+                    if constexpr (SMEM_TABLES)
+                        d1 = (unsigned)o1 < (unsigned)a.n_orders ? lds_key<uint32_t>(desc_sa + 4u * (uint32_t)o1) : 0xFFFFFFFFu;
                 }
                 for (int q = q0; q < q1; ++q) {
                     const int o = o1;
                     const uint32_t d = d1;
                     o1 = o2;
                     if constexpr (SMEM_TABLES)
-                        d1 = (q + 1 < q1 && (unsigned)o1 < (unsigned)a.n_orders) ? src.desc[o1] : 0xFFFFFFFFu;
+                        d1 = (q + 1 < q1 && (unsigned)o1 < (unsigned)a.n_orders) ? lds_key<uint32_t>(desc_sa + 4u * (uint32_t)o1)
+                                                                                  : 0xFFFFFFFFu;
                     o2 = q + 2 < q1 ? __ldg(a.order_seq + q + 2) : 0;
                     if ((unsigned)o >= (unsigned)a.n_orders) { flag(a.status, WH_STATUS_BAD_ORDER); bad = true; break; }
                     int lb, le;
@@ -218,27 +227,43 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                                 if ((unsigned)sk[j] >= (unsigned)a.n_sku) flag(a.status, WH_STATUS_BAD_SKU);
                                 else if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
                                 else k32 = loc_key(a.g, loc[j]);
-                                *w = (KeyT)(KEY16 ? key16_of(k32) : k32);
-                                w += step;
-                                step = two_t - step;
+                                sts_key<KeyT>(wa, KEY16 ? key16_of(k32) : k32);
+                                wa += stepb;
+                                stepb = two_tb - stepb;
                             }
                         }
                         continue;
                     }
-                    // two lines a step (positions p and p + 1 sit `step`
-                    // apart), then the odd one
-                    int l = lb;
-                    for (; l + 1 < le; l += 2) {
-                        const KeyT k0 = (KeyT)key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
-                        const KeyT k1 = (KeyT)key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l + 1);
-                        w[0] = k0;
-                        w[step] = k1;
-                        w += two_t;
-                    }
-                    if (l < le) {
-                        *w = (KeyT)key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
-                        w += step;
-                        step = two_t - step;
+                    // two lines a step (positions p and p + 1 sit `stepb`
+                    // bytes apart), then the odd one
+                    if constexpr (SMEM_TABLES) {
+                        uint32_t sa = keys_sa + (uint32_t)lb * KB;
+                        const uint32_t se = keys_sa + (uint32_t)le * KB;
+                        for (; sa + KB < se; sa += 2 * KB) {
+                            const uint32_t k0 = lds_key<KeyT>(sa), k1 = lds_key<KeyT>(sa + KB);
+                            sts_key<KeyT>(wa, k0);
+                            sts_key<KeyT>(wa + stepb, k1);
+                            wa += two_tb;
+                        }
+                        if (sa < se) {
+                            sts_key<KeyT>(wa, lds_key<KeyT>(sa));
+                            wa += stepb;
+                            stepb = two_tb - stepb;
+                        }
+                    } else {
+                        int l = lb;
+                        for (; l + 1 < le; l += 2) {
+                            const uint32_t k0 = key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l);
+                            const uint32_t k1 = key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l + 1);
+                            sts_key<KeyT>(wa, k0);
+                            sts_key<KeyT>(wa + stepb, k1);
+                            wa += two_tb;
+                        }
+                        if (l < le) {
+                            sts_key<KeyT>(wa, key_of<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, l));
+                            wa += stepb;
+                            stepb = two_tb - stepb;
+                        }
                     }
                 }
             }
@@ -821,7 +846,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
                 const int inst = s_meta[warp][lane][0], t = s_meta[warp][lane][1], plan = s_meta[warp][lane][2];
                 const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
                 const uint32_t kl = s_last[warp][lane];
-                const int cr = need_rr ? rr_records32(a.g, rec + lane, 32, m) : 0;
+                const int cr = need_rr ? rr_records32_mem(a.g, rec + lane, 32, m) : 0;
                 commit(a, t, plan, sshape_cost(a.g, m, (int)(kl >> 16), (int)(kl & 0xFFFFu)), cr);
             }
         }

@@ -610,7 +610,7 @@ __global__ void k_mv_long_dp(MoveArgs M) {
         if (m < 0) continue;
         const uint32_t kl = M.long_key[w];
         mv_long_commit(M, M.long_list[w], sshape_cost(M.a.g, m, (int)(kl >> 16), (int)(kl & 0xFFFFu)),
-                       rr_records32(M.a.g, M.long_rec + w, M.long_rec_cap, m));
+                       rr_records32_mem(M.a.g, M.long_rec + w, M.long_rec_cap, m));
     }
 }
 

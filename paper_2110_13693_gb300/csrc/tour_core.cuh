@@ -34,6 +34,34 @@ __device__ __forceinline__ uint32_t key16_of(uint32_t k32) {
     return ((k32 >> 8) & 0xFF00u) | (k32 & 0xFFu);
 }
 
+// 32-bit shared-window addresses for the per-line loops: one 32-bit add per
+// address step instead of generic 64-bit pointer arithmetic.  Loads and
+// stores are volatile with a memory clobber, so the compiler keeps them in
+// order with each other and with the surrounding code's memory accesses (a
+// thread's column is written, read back and rewritten in every chunk).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <typename K>
+__device__ __forceinline__ uint32_t lds_key(uint32_t addr) {
+    if constexpr (sizeof(K) == 2) {
+        unsigned short v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+        return v;
+    } else {
+        uint32_t v;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+        return v;
+    }
+}
+
+template <typename K>
+__device__ __forceinline__ void sts_key(uint32_t addr, uint32_t v) {
+    if constexpr (sizeof(K) == 2)
+        asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+    else
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 // ---------------------------------------------------------------- DP state
 // Five classes of a partial tour subgraph after an aisle, named by the degree
 // of the aisle's front end a_j and back end b_j (0: not in the subgraph, E:
@@ -81,6 +109,45 @@ __device__ __forceinline__ void dp_aisle(DP5& v, const Geo& g, int d, int lo, in
 }
 
 __device__ __forceinline__ int dp_final(const DP5& v) { return min(min(v.ee, v.e0), v.oe); }
+
+// The same step in relative form, for the record DPs of the evaluation
+// kernels: every state holds its value minus 2P * (aisle of the last step),
+// so crossing d aisle gaps adds nothing to the classes whose edge pattern
+// uses each gap twice (UU, E0, OE; EE switching to E0 / OE) and 2P * d to
+// those that use it four times (EE, E2); the caller adds 2P * (last aisle)
+// back at the end.  The vertical options are precomputed multiply-adds:
+// cB = 2(Y - y_lo), cF = 2 y_hi, and leaving out the largest gap
+// max(y_lo, gi*S, Y - y_hi) costs 2Y - 2*max(...) = min(cB, 2Y - 2 gi*S, cF).
+// Integer arithmetic throughout, so the result equals dp_aisle's exactly.
+struct DPConst {
+    int p2, s2, cb0, cf0, y, y2;   // 2P, 2S, 2(Y - h), 2h, Y, 2Y
+};
+
+__device__ __forceinline__ DPConst dp_const(const Geo& g) {
+    DPConst c;
+    c.p2 = 2 * g.P;
+    c.s2 = 2 * g.S;
+    c.cb0 = 2 * (g.Y - g.h);
+    c.cf0 = 2 * g.h;
+    c.y = g.Y;
+    c.y2 = 2 * g.Y;
+    return c;
+}
+
+__device__ __forceinline__ void dp_aisle_rel(DP5& v, const DPConst& c, int d, int lo, int hi, int gi) {
+    const int h2 = c.p2 * d;
+    const int he0 = min(v.e0, v.ee), hoe = min(v.oe, v.ee);
+    const int hee = v.ee + h2, he2 = v.e2 + h2;
+    const int cB = c.cb0 - lo * c.s2, cF = c.cf0 + hi * c.s2;
+    const int cG = __vimin3_s32(cB, c.y2 - gi * c.s2, cF);
+    const int m3 = __vimin3_s32(he0, hoe, he2);
+    const int huu = v.uu;
+    v.uu = __viaddmin_s32(huu, cG, min(m3, hee) + c.y);
+    v.ee = __viaddmin_s32(huu, c.y, __viaddmin_s32(m3, c.y2, hee + cG));
+    v.e0 = he0 + cF;
+    v.oe = hoe + cB;
+    v.e2 = m3 + cG;
+}
 
 // S-shape closed form from the number of pick aisles m, the rightmost pick
 // aisle and its deepest slot.
@@ -160,30 +227,37 @@ __device__ __forceinline__ void sort16x2(uint32_t (&x)[R]) {
 }
 
 // --------------------------------------------------------- record scans
-// Sorted keys -> per-aisle records (rec[j*stride], at most cap of them) and
-// the S-shape inputs (pick-aisle count, rightmost aisle, its deepest slot).
+// Sorted keys -> per-aisle records (at most cap of them, written from the
+// shared-memory address rec_sa on, stride_b bytes apart) and the S-shape
+// inputs (pick-aisle count, rightmost aisle, its deepest slot).  On sorted
+// keys the aisle changes between positions p and p + 1 exactly when
+// key(p + 1) > (key(p) | slot mask); the padding (all ones) and the bad-key
+// marker (all ones but the lowest bit) never satisfy that against their
+// successor, so only the final position needs the padding test.
 template <int N>
-__device__ __forceinline__ void scan32(const uint32_t (&x)[N], uint2* rec, int stride, int cap, bool write,
-                                       int& m, int& last_a, int& last_hi) {
-    int lo = 0, prev = 0, gi = 0;
-    m = 0; last_a = 0; last_hi = 0;
+__device__ __forceinline__ void scan32(const uint32_t (&x)[N], uint32_t rec_sa, uint32_t stride_b, int cap,
+                                       bool write, int& m, int& last_a, int& last_hi) {
+    const uint32_t rec_end = rec_sa + stride_b * (uint32_t)cap;
+    uint32_t lo = 0, gi = 0, last_key = 0;
+    m = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const uint32_t key = x[i];
-        const uint32_t a = key >> 16;
-        const int k = (int)(key & 0xFFFFu);
-        const bool first = (i == 0) || ((x[i - 1] >> 16) != a);
-        const bool last = (i == N - 1) || ((x[i + 1] >> 16) != a);
-        gi = first ? 0 : max(gi, k - prev);
-        lo = first ? k : lo;
-        prev = k;
-        if (key != KEY_NONE && last) {
-            if (write && m < cap) rec[m * stride] = make_uint2((a << 16) | (uint32_t)lo, ((uint32_t)k << 16) | (uint32_t)gi);
+        const bool first = (i == 0) || key > (x[i - 1] | 0xFFFFu);
+        const bool last = (i == N - 1) ? key != KEY_NONE : x[i + 1] > (key | 0xFFFFu);
+        if (i > 0) gi = first ? 0u : max(gi, key - x[i - 1]);
+        lo = first ? key : lo;
+        if (last) {
+            if (write && rec_sa < rec_end)
+                asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(rec_sa), "r"(lo), "r"((key << 16) | gi)
+                             : "memory");
+            rec_sa += stride_b;
             ++m;
-            last_a = (int)a;
-            last_hi = k;
+            last_key = key;
         }
     }
+    last_a = (int)(last_key >> 16);
+    last_hi = (int)(last_key & 0xFFFFu);
 }
 
 template <int R>
@@ -192,54 +266,74 @@ __device__ __forceinline__ uint32_t key16_at(const uint32_t (&x)[R], int p) {
 }
 
 template <int R>
-__device__ __forceinline__ void scan16(const uint32_t (&x)[R], uint32_t* rec, int stride, int cap, bool write,
-                                       int& m, int& last_a, int& last_hi) {
+__device__ __forceinline__ void scan16(const uint32_t (&x)[R], uint32_t rec_sa, uint32_t stride_b, int cap,
+                                       bool write, int& m, int& last_a, int& last_hi) {
     constexpr int N = 2 * R;
-    int lo = 0, prev = 0, gi = 0;
-    m = 0; last_a = 0; last_hi = 0;
+    const uint32_t rec_end = rec_sa + stride_b * (uint32_t)cap;
+    uint32_t lo = 0, gi = 0, last_key = 0;
+    m = 0;
 #pragma unroll
     for (int p = 0; p < N; ++p) {
         const uint32_t key = key16_at<R>(x, p);
-        const uint32_t a = key >> 8;
-        const int k = (int)(key & 0xFFu);
-        const bool first = (p == 0) || ((key16_at<R>(x, p - 1) >> 8) != a);
-        const bool last = (p == N - 1) || ((key16_at<R>(x, p + 1) >> 8) != a);
-        gi = first ? 0 : max(gi, k - prev);
-        lo = first ? k : lo;
-        prev = k;
-        if (key != KEY16_NONE && last) {
-            if (write && m < cap) rec[m * stride] = (a << 24) | ((uint32_t)lo << 16) | ((uint32_t)k << 8) | (uint32_t)gi;
+        const bool first = (p == 0) || key > (key16_at<R>(x, p - 1) | 0xFFu);
+        const bool last = (p == N - 1) ? key != KEY16_NONE : key16_at<R>(x, p + 1) > (key | 0xFFu);
+        if (p > 0) gi = first ? 0u : max(gi, key - key16_at<R>(x, p - 1));
+        lo = first ? key : lo;
+        if (last) {
+            // record: aisle << 24 | shallowest slot << 16 | deepest slot << 8 | largest gap
+            if (write && rec_sa < rec_end)
+                sts_key<uint32_t>(rec_sa, (lo << 16) | ((key & 0xFFu) << 8) | gi);
+            rec_sa += stride_b;
             ++m;
-            last_a = (int)a;
-            last_hi = k;
+            last_key = key;
         }
     }
+    last_a = (int)(last_key >> 8);
+    last_hi = (int)(last_key & 0xFFu);
 }
 
-__device__ __forceinline__ int rr_records32(const Geo& g, const uint2* rec, int64_t stride, int m) {
+// records anywhere in memory (the long-tour passes' global scratch)
+__device__ __forceinline__ int rr_records32_mem(const Geo& g, const uint2* rec, int64_t stride, int m) {
+    const DPConst c = dp_const(g);
     DP5 v;
     dp_init(v);
     int pa = 0;
     for (int j = 0; j < m; ++j) {
         const uint2 r = rec[j * stride];
         const int a = (int)(r.x >> 16);
-        dp_aisle(v, g, a - pa, (int)(r.x & 0xFFFFu), (int)(r.y >> 16), (int)(r.y & 0xFFFFu));
+        dp_aisle_rel(v, c, a - pa, (int)(r.x & 0xFFFFu), (int)(r.y >> 16), (int)(r.y & 0xFFFFu));
         pa = a;
     }
-    return dp_final(v);
+    return dp_final(v) + c.p2 * pa;
 }
 
-__device__ __forceinline__ int rr_records16(const Geo& g, const uint32_t* rec, int stride, int m) {
+__device__ __forceinline__ int rr_records32(const Geo& g, uint32_t rec_sa, uint32_t stride_b, int m) {
+    const DPConst c = dp_const(g);
     DP5 v;
     dp_init(v);
     int pa = 0;
-    for (int j = 0; j < m; ++j) {
-        const uint32_t r = rec[j * stride];
-        const int a = (int)(r >> 24);
-        dp_aisle(v, g, a - pa, (int)((r >> 16) & 0xFFu), (int)((r >> 8) & 0xFFu), (int)(r & 0xFFu));
+    for (int j = 0; j < m; ++j, rec_sa += stride_b) {
+        uint32_t rx, ry;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(rx), "=r"(ry) : "r"(rec_sa) : "memory");
+        const int a = (int)(rx >> 16);
+        dp_aisle_rel(v, c, a - pa, (int)(rx & 0xFFFFu), (int)(ry >> 16), (int)(ry & 0xFFFFu));
         pa = a;
     }
-    return dp_final(v);
+    return dp_final(v) + c.p2 * pa;
+}
+
+__device__ __forceinline__ int rr_records16(const Geo& g, uint32_t rec_sa, uint32_t stride_b, int m) {
+    const DPConst c = dp_const(g);
+    DP5 v;
+    dp_init(v);
+    int pa = 0;
+    for (int j = 0; j < m; ++j, rec_sa += stride_b) {
+        const uint32_t r = lds_key<uint32_t>(rec_sa);
+        const int a = (int)(r >> 24);
+        dp_aisle_rel(v, c, a - pa, (int)((r >> 16) & 0xFFu), (int)((r >> 8) & 0xFFu), (int)(r & 0xFFu));
+        pa = a;
+    }
+    return dp_final(v) + c.p2 * pa;
 }
 
 // Key source: with a shared slotting, keys come from the per-line table
@@ -285,19 +379,27 @@ __device__ __forceinline__ uint32_t key_of(const EvalArgs& a, const KeySrc& s, i
 // indices for the sort, and the column is then reused for the records.  The
 // gather itself is a plain loop over the tour's orders and their lines.
 template <int N>
-__device__ __forceinline__ void load32(const uint2* col, int T, int n, uint32_t (&x)[N]) {
+__device__ __forceinline__ void load32(uint32_t col_sa, uint32_t slot_b, int n, uint32_t (&x)[N]) {
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
-        const uint2 w = col[(p >> 1) * T];
-        x[p] = p < n ? ((p & 1) ? w.y : w.x) : KEY_NONE;
+    for (int p = 0; p < N; p += 2) {
+        uint32_t wx, wy;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                     : "=r"(wx), "=r"(wy)
+                     : "r"(col_sa + (uint32_t)(p >> 1) * slot_b)
+                     : "memory");
+        x[p] = p < n ? wx : KEY_NONE;
+        if (p + 1 < N) x[p + 1] = p + 1 < n ? wy : KEY_NONE;
     }
 }
 
 template <int R>
-__device__ __forceinline__ void load16(const uint32_t* col, int T, int n, uint32_t (&x)[R]) {
+__device__ __forceinline__ void load16(uint32_t col_sa, uint32_t slot_b, int n, uint32_t (&x)[R]) {
+    uint32_t wv[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) wv[j] = lds_key<uint32_t>(col_sa + (uint32_t)j * slot_b);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint32_t wl = col[(r >> 1) * T], wh = col[((r + R) >> 1) * T];
+        const uint32_t wl = wv[r >> 1], wh = wv[(r + R) >> 1];
         x[r] = __byte_perm(wl, wh, (r & 1) ? 0x7632 : 0x5410) | (r < n ? 0u : 0xFFFFu) |
                (r + R < n ? 0u : 0xFFFF0000u);
     }
@@ -311,8 +413,9 @@ __device__ __forceinline__ void load16(const uint32_t* col, int T, int n, uint32
 template <int N>
 __device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int n, bool need_rr, int& cs,
                                        int& cr, int& m, bool check = false, bool* kbad = nullptr) {
+    const uint32_t col_sa = smem_addr(col), slot_b = 8u * (uint32_t)T;
     uint32_t x[N];
-    load32<N>(col, T, n, x);
+    load32<N>(col_sa, slot_b, n, x);
     if (check) {
         bool b = false;
 #pragma unroll
@@ -321,16 +424,17 @@ __device__ __forceinline__ void tour32(const EvalArgs& a, uint2* col, int T, int
     }
     bitonic_sort<N>(x);
     int last_a, last_hi;
-    scan32<N>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
+    scan32<N>(x, col_sa, slot_b, a.max_rec, need_rr, m, last_a, last_hi);
     cs = sshape_cost(a.g, m, last_a, last_hi);
-    cr = need_rr ? rr_records32(a.g, col, T, min(m, a.max_rec)) : 0;
+    cr = need_rr ? rr_records32(a.g, col_sa, slot_b, min(m, a.max_rec)) : 0;
 }
 
 template <int R>
 __device__ __forceinline__ void tour16(const EvalArgs& a, uint32_t* col, int T, int n, bool need_rr, int& cs,
                                        int& cr, int& m, bool check = false, bool* kbad = nullptr) {
+    const uint32_t col_sa = smem_addr(col), slot_b = 4u * (uint32_t)T;
     uint32_t x[R];
-    load16<R>(col, T, n, x);
+    load16<R>(col_sa, slot_b, n, x);
     if (check) {
         uint32_t acc = 0u;
 #pragma unroll
@@ -339,9 +443,9 @@ __device__ __forceinline__ void tour16(const EvalArgs& a, uint32_t* col, int T, 
     }
     sort16x2<R>(x);
     int last_a, last_hi;
-    scan16<R>(x, col, T, a.max_rec, need_rr, m, last_a, last_hi);
+    scan16<R>(x, col_sa, slot_b, a.max_rec, need_rr, m, last_a, last_hi);
     cs = sshape_cost(a.g, m, last_a, last_hi);
-    cr = need_rr ? rr_records16(a.g, col, T, min(m, a.max_rec)) : 0;
+    cr = need_rr ? rr_records16(a.g, col_sa, slot_b, min(m, a.max_rec)) : 0;
 }
 
 // Segmented sum over the lanes of a warp whose `key` (plan id, non-decreasing
