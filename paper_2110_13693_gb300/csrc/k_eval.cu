@@ -178,6 +178,54 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
             if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
                 flag(a.status, WH_STATUS_BAD_OFFSET);
                 bad = true;
+            } else if constexpr (SMEM_TABLES && SHARED_MAP) {
+                // staged order book, shared slotting.  Software-pipelined:
+                // order ids two ahead, descriptors one ahead.  A descriptor
+                // is read at a clamped (always valid) index; an invalid id
+                // reads as count 255, so one test per order catches invalid
+                // ids, orders the short path does not take and tours over
+                // SHORT_MAX lines, and only its exit tells them apart.
+                const uint32_t o_max = (uint32_t)max(a.n_orders - 1, 0);
+                auto desc_of = [&](int o) {
+                    const uint32_t dv = lds_key<uint32_t>(desc_sa + 4u * min((uint32_t)o, o_max));
+                    return (uint32_t)o < (uint32_t)a.n_orders ? dv : 0xFFFFFFFFu;
+                };
+                const int* seq = a.order_seq;
+                int o_a = q0 < q1 ? __ldg(seq + q0) : 0;
+                int o_b = q0 + 1 < q1 ? __ldg(seq + q0 + 1) : 0;
+                uint32_t d = desc_of(o_a);
+                for (int q = q0; q < q1; ++q) {
+                    const int o = o_a;
+                    o_a = o_b;
+                    const uint32_t dn = desc_of(o_a);
+                    o_b = q + 2 < q1 ? __ldg(seq + q + 2) : 0;
+                    const int c = (int)(d & 0xFFu);
+                    if (n + c > SHORT_MAX) {
+                        if ((uint32_t)o >= (uint32_t)a.n_orders) {
+                            flag(a.status, WH_STATUS_BAD_ORDER);
+                            bad = true;
+                        } else {
+                            n += c;   // the long-tour kernel takes (and checks) it
+                        }
+                        break;
+                    }
+                    n += c;
+                    // two lines a step (positions p and p + 1 sit stepb bytes
+                    // apart), then the odd one, predicated
+                    uint32_t sa = keys_sa + (d >> 8) * KB;
+                    const uint32_t se = sa + (uint32_t)c * KB;
+                    for (; sa + KB < se; sa += 2 * KB) {
+                        const uint32_t k0 = lds_key<KeyT>(sa), k1 = lds_key<KeyT>(sa + KB);
+                        sts_key<KeyT>(wa, k0);
+                        sts_key<KeyT>(wa + stepb, k1);
+                        wa += two_tb;
+                    }
+                    const bool odd = sa < se;
+                    sts_key_if<KeyT>(odd, wa, lds_key_if<KeyT>(odd, sa));
+                    wa += odd ? stepb : 0u;
+                    stepb = odd ? two_tb - stepb : stepb;
+                    d = dn;
+                }
             } else {
                 // software-pipelined: order ids two ahead, descriptors one ahead
                 int o2 = q0 + 1 < q1 ? __ldg(a.order_seq + q0 + 1) : 0;

@@ -62,6 +62,33 @@ __device__ __forceinline__ void sts_key(uint32_t addr, uint32_t v) {
         asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+// Predicated forms (no branch around the access): the load leaves its
+// result undefined and the store writes nothing when p is false.
+template <typename K>
+__device__ __forceinline__ uint32_t lds_key_if(bool p, uint32_t addr) {
+    if constexpr (sizeof(K) == 2) {
+        unsigned short v;
+        asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q ld.shared.u16 %0, [%1]; }"
+                     : "=h"(v) : "r"(addr), "r"((uint32_t)p) : "memory");
+        return v;
+    } else {
+        uint32_t v;
+        asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q ld.shared.u32 %0, [%1]; }"
+                     : "=r"(v) : "r"(addr), "r"((uint32_t)p) : "memory");
+        return v;
+    }
+}
+
+template <typename K>
+__device__ __forceinline__ void sts_key_if(bool p, uint32_t addr, uint32_t v) {
+    if constexpr (sizeof(K) == 2)
+        asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.shared.u16 [%0], %1; }"
+                     ::"r"(addr), "h"((unsigned short)v), "r"((uint32_t)p) : "memory");
+    else
+        asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q st.shared.u32 [%0], %1; }"
+                     ::"r"(addr), "r"(v), "r"((uint32_t)p) : "memory");
+}
+
 // ---------------------------------------------------------------- DP state
 // Five classes of a partial tour subgraph after an aisle, named by the degree
 // of the aisle's front end a_j and back end b_j (0: not in the subgraph, E:
