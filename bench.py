@@ -141,6 +141,37 @@ def algorithmic_bytes_one_rule(inst):
     return 4 * lines + 4 * (inst.n_tours + 1) + 4 * inst.n_tours + 8 * inst.n_plans + 4 * inst.n_sku
 
 
+def dp_alg_ops(inst):
+    """Algorithmic integer operations of the optimal-route DP over every tour
+    of one evaluation (shared slotting): the Ratliff-Rosenthal programme in its
+    standard form steps through every aisle from the depot's to the rightmost
+    pick aisle r, 7 classes x 6 transitions + 7 x 5 per aisle, so
+    sum over tours of (r + 1) * 77 (the kernel's reduced DP steps only over
+    pick aisles; its sort, record scan and gather are not counted)."""
+    import numpy as np
+    L = inst.layout.slots_per_side
+    line_aisle = (np.asarray(inst.slot_map, np.int64) // (2 * L))[np.asarray(inst.line_sku)]
+    off = np.asarray(inst.order_off, np.int64)
+    order_max = np.full(len(off) - 1, -1, np.int64)
+    ne = np.diff(off) > 0
+    order_max[ne] = np.maximum.reduceat(line_aisle, off[:-1][ne])
+    to = np.asarray(inst.tour_off, np.int64)
+    tour_max = np.full(len(to) - 1, -1, np.int64)
+    nz = np.diff(to) > 0
+    tour_max[nz] = np.maximum.reduceat(order_max[np.asarray(inst.order_seq)], to[:-1][nz])
+    return int((tour_max + 1).sum()) * 77
+
+
+def alu_peak_tops(dev, sm_max_mhz):
+    """Integer issue limit of the GPU: one warp instruction per SM
+    sub-partition per cycle, 4 sub-partitions x 32 lanes per SM, at the
+    maximum SM clock (152 SMs x 128 x 2,070 MHz = 40.3 Tops/s on a GB300)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    return sms * 4 * 32 * mhz * 1e6 / 1e12
+
+
 def run_sshape(wh, lay, probs, batches, costs, stream, steps):
     """The streaming path: the same plan batches scored under the S-shape
     rule alone (per-order aggregates built by k_prep on every call, then the
@@ -855,18 +886,23 @@ def run_midsize(wh, dev, rank, args):
     dom_name, (dom_launches, dom_ms) = max(ktime.items(), key=lambda kv: kv[1][1])
     per_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
     alg = sum(algorithmic_bytes(batches[i % len(batches)]) for i in range(steps)) / steps
+    ops = sum(dp_alg_ops(batches[i % len(batches)]) for i in range(len(batches))) / len(batches)
     peak, peak_kind = measured_peaks()
     achieved = alg / per_launch_s / 1e9
+    alu_peak = alu_peak_tops(dev, None)
     prof = recorded_profile()
     out = {"workload": MIDSIZE_WORKLOAD, "steps": steps, "ms_per_step": ms / steps,
            "tours_per_s": n_tours / (ms / 1e3), "plans_per_s": PLANS_PER_STEP * steps / (ms / 1e3),
            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in ktime.items()},
-           "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
-                        "launch_ms": per_launch_s * 1e3,
+           "roofline": {"bound": "alu", "kernel": dom_name, "achieved": ops / per_launch_s / 1e12, "peak": alu_peak,
+                        "unit": "Tops/s", "frac": ops / per_launch_s / 1e12 / alu_peak,
+                        "peak_kind": "derived: SMs x 4 sub-partitions x 32 lanes x 2,070 MHz (issue limit)",
+                        "algorithmic_ops_per_launch": ops, "launch_ms": per_launch_s * 1e3,
                         "traffic": float(prof["dram_bytes_per_launch"]) if prof else None,
                         "issue_active_frac": prof.get("issue_active_frac") if prof else None,
-                        "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None}}
+                        "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None,
+                        "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg}}}
     out["sshape_only"] = run_sshape(wh, lay, probs, batches, costs, stream, min(steps, 200))
     # end to end from pinned host memory: 16-bit order ids widened on the device
     host = []
@@ -972,6 +1008,7 @@ def run_ours(args):
     insts = make_instances(rank)
     packed = wh.PackedInstances(insts)
     alg = sum(algorithmic_bytes(i) for i in insts)
+    ops = sum(dp_alg_ops(i) for i in insts)
     tours_step = packed.total_tours
     lines_step = sum(int(i.tour_lines().sum()) for i in insts)
     del insts
@@ -1060,6 +1097,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg / per_launch_s / 1e9
     prof, traffic = batched_profile(tours_step)
+    alu_peak = alu_peak_tops(dev, clk.get("sm_max_mhz"))
     launches_per_step = len(ktime)
     step_s = elapsed_ms / 1e3 / args.steps
 
@@ -1102,15 +1140,21 @@ def run_ours(args):
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
                         "share": round(v[1] / max(sum(x[1] for x in ktime.values()), 1e-12), 4)}
                     for k, v in ktime.items()},
-        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_s * 1e3,
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": ops / per_launch_s / 1e12, "peak": alu_peak,
+                     "unit": "Tops/s", "frac": ops / per_launch_s / 1e12 / alu_peak,
+                     "peak_kind": "derived: SMs x 4 sub-partitions x 32 lanes x max SM clock (issue limit)",
+                     "algorithmic_ops_per_launch": ops,
+                     "ops_per_tour": ops / tours_step,
+                     "launch_ms": per_launch_s * 1e3,
                      "launch_timing": f"CUDA events around each launch of {k_steps} eager steps "
                                       "(graph replays carry no per-kernel events)",
-                     "step_frac": alg / step_s / 1e9 / peak,
+                     "step_frac": ops / step_s / 1e12 / alu_peak,
                      "traffic": traffic,
                      "issue_active_frac": prof.get("issue_active_frac") if prof else None,
-                     "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None},
+                     "alu_pipe_frac": prof.get("alu_pipe_frac") if prof else None,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
+                             "step_frac": alg / step_s / 1e9 / peak}},
         "cpu_baseline": cpu,
     }
     out.update(extra)

@@ -359,6 +359,53 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
     }
 }
 
+// Per-order aggregate for the S-shape rule on <= 64 aisles: the bitmask of
+// the aisles its lines visit, its largest key (aisle << 16 | slot: the
+// rightmost aisle and that aisle's deepest pick) and flags (1: a line with an
+// invalid SKU or slot, 2: at least one valid line, 4: malformed offsets).
+__device__ __forceinline__ uint4 order_aggregate(const EvalArgs& a, int o) {
+    const int lb = a.order_off[o], le = a.order_off[o + 1];
+    uint64_t bits = 0;
+    uint32_t kmax = 0, fl = 0;
+    if (lb < 0 || le < lb || le > a.n_lines) {
+        flag(a.status, WH_STATUS_BAD_OFFSET);
+        fl = 4u;
+    } else {
+        // four lines a step: their SKU loads, then their slot loads, in
+        // flight together
+        for (int l0 = lb; l0 < le; l0 += 4) {
+            int sku[4], loc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sku[j] = l0 + j < le ? a.line_sku[l0 + j] : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                loc[j] = -1;
+                if (l0 + j >= le) continue;
+                if ((unsigned)sku[j] >= (unsigned)a.n_sku) {
+                    flag(a.status, WH_STATUS_BAD_SKU);
+                    fl |= 1u;
+                    continue;
+                }
+                loc[j] = a.slot_map[sku[j]];
+                if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) {
+                    flag(a.status, WH_STATUS_BAD_LOC);
+                    fl |= 1u;
+                    loc[j] = -1;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (loc[j] < 0) continue;
+                const uint32_t key = loc_key(a.g, loc[j]);
+                bits |= 1ull << (key >> 16);
+                kmax = max(kmax, key);
+                fl |= 2u;
+            }
+        }
+    }
+    return make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), kmax, fl);
+}
+
 // line keys of one instance, zeroed plan sums, plan offset checks
 __device__ __forceinline__ void prep_instance(const EvalArgs& a, uint32_t mask, int i0, int stride) {
     if (a.line_key) {
@@ -376,50 +423,8 @@ __device__ __forceinline__ void prep_instance(const EvalArgs& a, uint32_t mask, 
             line_key[l] = key;
         }
     }
-    if (a.order_agg) {
-        for (int o = i0; o < a.n_orders; o += stride) {
-            const int lb = a.order_off[o], le = a.order_off[o + 1];
-            uint64_t bits = 0;
-            uint32_t kmax = 0, fl = 0;
-            if (lb < 0 || le < lb || le > a.n_lines) {
-                flag(a.status, WH_STATUS_BAD_OFFSET);
-                fl = 4u;
-            } else {
-                // four lines a step: their SKU loads, then their slot loads,
-                // in flight together
-                for (int l0 = lb; l0 < le; l0 += 4) {
-                    int sku[4], loc[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) sku[j] = l0 + j < le ? a.line_sku[l0 + j] : -1;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        loc[j] = -1;
-                        if (l0 + j >= le) continue;
-                        if ((unsigned)sku[j] >= (unsigned)a.n_sku) {
-                            flag(a.status, WH_STATUS_BAD_SKU);
-                            fl |= 1u;
-                            continue;
-                        }
-                        loc[j] = a.slot_map[sku[j]];
-                        if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) {
-                            flag(a.status, WH_STATUS_BAD_LOC);
-                            fl |= 1u;
-                            loc[j] = -1;
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (loc[j] < 0) continue;
-                        const uint32_t key = loc_key(a.g, loc[j]);
-                        bits |= 1ull << (key >> 16);
-                        kmax = max(kmax, key);
-                        fl |= 2u;
-                    }
-                }
-            }
-            a.order_agg[o] = make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), kmax, fl);
-        }
-    }
+    if (a.order_agg)
+        for (int o = i0; o < a.n_orders; o += stride) a.order_agg[o] = order_aggregate(a, o);
     const bool zs = a.plan_s && (mask & WH_ROUTE_SSHAPE);
     const bool zr = a.plan_rr && (mask & WH_ROUTE_OPTIMAL);
     for (int p = i0; p < a.n_plans; p += stride) {
@@ -619,16 +624,12 @@ constexpr int SSHAPE_AGG_THREADS = 256;
 // rightmost aisle's deepest pick is the largest key over its orders, so each
 // tour merges one 16-byte record per order (no per-line work).  No shared
 // memory: full occupancy hides the order-id and record loads.
-__global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs a) {
-    const int lane = threadIdx.x & 31;
+// One warp's 32-tour chunks [c_begin, c_end): each tour merges the aggregates
+// of its orders (agg(o) -> uint4), then the S-shape closed form and the
+// segmented plan sums.
+template <typename Agg>
+__device__ __forceinline__ void sshape_agg_chunks(const EvalArgs& a, Agg agg, int c_begin, int c_end, int lane) {
     const bool vec = (reinterpret_cast<uintptr_t>(a.order_seq) & 15u) == 0;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int n_chunks = (a.n_tours + 31) >> 5;
-    const int per = (n_chunks + warps - 1) / warps;
-    const int c_begin = gw * per;
-    const int c_end = min(c_begin + per, n_chunks);
-    if (c_begin >= c_end) return;
     int plan = 0;
     {
         const int t0 = c_begin * 32;
@@ -657,7 +658,7 @@ __global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs
                         bad = true;
                         return;
                     }
-                    const uint4 r = __ldg(a.order_agg + o);
+                    const uint4 r = agg(o);
                     bits |= (uint64_t)r.x | ((uint64_t)r.y << 32);
                     kmax = (r.w & 2u) ? max(kmax, r.z) : kmax;
                     fl |= r.w;
@@ -690,6 +691,23 @@ __global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs
         if (active && (lane == 0 || prev_key != key) && a.plan_s && ss)
             atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_s[plan]), (unsigned long long)ss);
     }
+}
+
+// this warp's contiguous range of 32-tour chunks
+__device__ __forceinline__ void warp_chunk_range(const EvalArgs& a, int& c_begin, int& c_end) {
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int n_chunks = (a.n_tours + 31) >> 5;
+    const int per = (n_chunks + warps - 1) / warps;
+    c_begin = gw * per;
+    c_end = min(c_begin + per, n_chunks);
+}
+
+__global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs a) {
+    int c_begin, c_end;
+    warp_chunk_range(a, c_begin, c_end);
+    if (c_begin >= c_end) return;
+    sshape_agg_chunks(a, [&](int o) { return __ldg(a.order_agg + o); }, c_begin, c_end, threadIdx.x & 31);
 }
 
 // Persistent batch kernel: CTAs pop work items (instance, chunk range) from
