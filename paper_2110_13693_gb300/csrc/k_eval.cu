@@ -130,6 +130,38 @@ __device__ __forceinline__ bool defer_long(const EvalArgs& a, int inst, int t, i
     return true;
 }
 
+// this warp's contiguous range of 32-tour chunks: chunks split evenly over
+// all warps of the grid (each warp takes floor or ceil of chunks / warps,
+// none is left without work while another takes an extra chunk)
+__device__ __forceinline__ void warp_chunk_range(const EvalArgs& a, int& c_begin, int& c_end) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t n_chunks = ((int64_t)a.n_tours + 31) >> 5;
+    c_begin = (int)(gw * n_chunks / warps);
+    c_end = (int)((gw + 1) * n_chunks / warps);
+}
+
+// Plan of tour t0 (the largest p with plan_tour_off[p] <= t0), found by the
+// whole warp: each round probes 32 evenly spaced offsets of the remaining
+// range at once and keeps the piece between the last probe at or below t0
+// and the next, so the range shrinks 32-fold per round (3 dependent loads
+// for 4,096 plans instead of 12).  Every lane returns the same plan.
+__device__ __forceinline__ int warp_find_plan(const EvalArgs& a, int t0, int lane) {
+    int lo = 0, hi = a.n_plans - 1;
+    while (lo < hi) {
+        const int span = hi - lo;                         // candidates lo+1 .. hi
+        const int idx = lo + (int)(((int64_t)span * (lane + 1) + 31) / 32);   // in [lo+1, hi], non-decreasing
+        const bool le = a.plan_tour_off[idx] <= t0;
+        const unsigned below = __ballot_sync(0xffffffffu, le);   // a prefix of the lanes
+        const int k = __popc(below);
+        const int lo_new = k ? __shfl_sync(0xffffffffu, idx, k - 1) : lo;
+        const int hi_new = k < 32 ? __shfl_sync(0xffffffffu, idx, k < 32 ? k : 31) - 1 : hi;
+        lo = lo_new;
+        hi = hi_new;
+    }
+    return lo;
+}
+
 // One warp scores the 32-tour chunks [c_begin, c_end) of instance `a`, one
 // tour per lane, and adds its plans' sums with one atomic per plan segment.
 template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
@@ -145,16 +177,7 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
         if constexpr (SHARED_MAP) keys_sa = smem_addr(src.keys);
     }
     // plan of the first tour: largest p with plan_tour_off[p] <= t
-    int plan = 0;
-    {
-        const int t0 = c_begin * 32;
-        int lo = 0, hi = a.n_plans - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.plan_tour_off[mid] <= t0) lo = mid; else hi = mid - 1;
-        }
-        plan = lo;
-    }
+    int plan = warp_find_plan(a, c_begin * 32, lane);
     for (int c = c_begin; c < c_end; ++c) {
         const int t = c * 32 + lane;
         const bool active = t < a.n_tours;
@@ -473,12 +496,8 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_short(EvalArgs a)
     bool check_keys = true;   // keys read from global memory: every tour checks its own
     if constexpr (SMEM_TABLES) check_keys = __syncthreads_or(stage_tables<KEY16, SHARED_MAP>(a, s_desc, s_tab, src, tid, T));
     // this warp's contiguous range of 32-tour chunks
-    const int warps = gridDim.x * (T >> 5);
-    const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
-    const int n_chunks = (a.n_tours + 31) >> 5;
-    const int per = (n_chunks + warps - 1) / warps;
-    const int c_begin = gw * per;
-    const int c_end = min(c_begin + per, n_chunks);
+    int c_begin, c_end;
+    warp_chunk_range(a, c_begin, c_end);
     if (c_begin >= c_end) return;
     eval_chunks<KEY16, SHARED_MAP, SMEM_TABLES>(a, src, a.mask, 0, c_begin, c_end,
                                                 reinterpret_cast<uint32_t*>(buf_base) + tid,
@@ -512,23 +531,10 @@ __global__ void __launch_bounds__(256) k_eval_sshape(EvalArgs a) {
         __syncthreads();
     }
     for (int w = 0; w < nw; ++w) bm[w * T] = 0u;
-    const int warps = gridDim.x * (T >> 5);
-    const int gw = blockIdx.x * (T >> 5) + (tid >> 5);
-    const int n_chunks = (a.n_tours + 31) >> 5;
-    const int per = (n_chunks + warps - 1) / warps;
-    const int c_begin = gw * per;
-    const int c_end = min(c_begin + per, n_chunks);
+    int c_begin, c_end;
+    warp_chunk_range(a, c_begin, c_end);
     if (c_begin >= c_end) return;
-    int plan = 0;
-    {
-        const int t0 = c_begin * 32;
-        int lo = 0, hi = a.n_plans - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.plan_tour_off[mid] <= t0) lo = mid; else hi = mid - 1;
-        }
-        plan = lo;
-    }
+    int plan = warp_find_plan(a, c_begin * 32, lane);
     for (int c = c_begin; c < c_end; ++c) {
         const int t = c * 32 + lane;
         const bool active = t < a.n_tours;
@@ -630,16 +636,7 @@ constexpr int SSHAPE_AGG_THREADS = 256;
 template <typename Agg>
 __device__ __forceinline__ void sshape_agg_chunks(const EvalArgs& a, Agg agg, int c_begin, int c_end, int lane) {
     const bool vec = (reinterpret_cast<uintptr_t>(a.order_seq) & 15u) == 0;
-    int plan = 0;
-    {
-        const int t0 = c_begin * 32;
-        int lo = 0, hi = a.n_plans - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.plan_tour_off[mid] <= t0) lo = mid; else hi = mid - 1;
-        }
-        plan = lo;
-    }
+    int plan = warp_find_plan(a, c_begin * 32, lane);
     for (int c = c_begin; c < c_end; ++c) {
         const int t = c * 32 + lane;
         const bool active = t < a.n_tours;
@@ -693,15 +690,6 @@ __device__ __forceinline__ void sshape_agg_chunks(const EvalArgs& a, Agg agg, in
     }
 }
 
-// this warp's contiguous range of 32-tour chunks
-__device__ __forceinline__ void warp_chunk_range(const EvalArgs& a, int& c_begin, int& c_end) {
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int n_chunks = (a.n_tours + 31) >> 5;
-    const int per = (n_chunks + warps - 1) / warps;
-    c_begin = gw * per;
-    c_end = min(c_begin + per, n_chunks);
-}
 
 __global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs a) {
     int c_begin, c_end;
@@ -751,9 +739,8 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b
         }
         check_keys = __syncthreads_or(check_keys);
         const int n = w.chunk_end - w.chunk_begin;
-        const int per = (n + nw - 1) / nw;
-        const int cb = w.chunk_begin + warp * per;
-        const int ce = min(cb + per, w.chunk_end);
+        const int cb = w.chunk_begin + warp * n / nw;   // the item's chunks split evenly over the warps
+        const int ce = w.chunk_begin + (warp + 1) * n / nw;
         if (cb < ce)
             eval_chunks<KEY16, true, SMEM_TABLES>(s_a, src, b.mask, w.inst, cb, ce, col16, col32, T, lane, check_keys);
         __syncthreads();
