@@ -460,6 +460,13 @@ typedef struct wh_instance {
     wh_orders orders;
     wh_plans plans;   /* slot_map_stride must be 0 (one slotting per instance) */
     wh_costs out;
+    /* Optional (may be NULL): the plans' order ids as unsigned 16-bit values
+     * [plans.n_seq] (device memory; needs orders.n_orders <= 65,536).  When
+     * every instance of the batch sets it, the batch reads these instead of
+     * plans.order_seq (which may then be NULL): half the bytes, and host-
+     * resident plans cross the host link and are scored without a widening
+     * pass.  Setting it on some instances and not others is WH_EINVAL. */
+    const uint16_t *order_seq16;
 } wh_instance;
 
 typedef struct wh_batch wh_batch;
@@ -472,7 +479,8 @@ typedef struct wh_batch wh_batch;
  * per-plan slottings), WH_ERANGE, WH_ENOMEM or WH_ECUDA. */
 int wh_batch_create(const wh_instance *insts, int32_t n, wh_batch **out);
 
-/* Launch shape: CTA size (32..256, multiple of 32), 32-tour chunks per work
+/* Launch shape: CTA size (32..384 with 16-bit keys, layouts of <= 255 aisles
+ * and <= 256 slots per side; 32..256 otherwise; a multiple of 32), 32-tour chunks per work
  * item (>= 1) and whether order books are staged in shared memory (0/1; it
  * is turned off when the largest order book does not fit).  Rebuilds the
  * work queue and drops captured graphs.  Returns WH_OK or WH_EINVAL. */
@@ -489,9 +497,9 @@ int wh_batch_eval(wh_batch *b, uint32_t routing_mask, void *stream);
  * routing_mask captures (on a private stream) and instantiates. */
 int wh_batch_eval_graph(wh_batch *b, uint32_t routing_mask, void *stream);
 
-/* Autotuner: time candidate launch shapes (CTA size 128 or 256 x 2 to 4,096
- * chunks of 32 tours per work item) on this batch with the given mask, keep
- * the fastest and report it.  When
+/* Autotuner: time candidate launch shapes (CTA size 128, 256 or, with 16-bit
+ * keys, 384 x 2 to 4,096 chunks of 32 tours per work item) on this batch with
+ * the given mask, keep the fastest and report it.  When
  * cache_path is not NULL the choice is looked up first, and stored after, in
  * that JSON file under a key built from the batch's size bucket (key width,
  * instance count, total tours, largest order book, mask).  Synchronises

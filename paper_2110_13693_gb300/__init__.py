@@ -56,7 +56,8 @@ class wh_costs(ctypes.Structure):
 
 
 class wh_instance(ctypes.Structure):
-    _fields_ = [("layout", wh_layout_desc), ("orders", wh_orders), ("plans", wh_plans), ("out", wh_costs)]
+    _fields_ = [("layout", wh_layout_desc), ("orders", wh_orders), ("plans", wh_plans), ("out", wh_costs),
+                ("order_seq16", ctypes.c_void_p)]
 
 
 # every symbol include/wh.h declares, with its ctypes signature
@@ -323,6 +324,7 @@ class DeviceProblem:
     n_sku: int
     slot_map_stride: int = 0
     loc_used: object = None     # per-plan occupancy bits (relocation moves), see occupancy()
+    order_seq16: object = None  # the order ids as 16-bit values (batched instances; order_seq may be None)
 
     @property
     def n_plans(self) -> int:
@@ -337,7 +339,8 @@ class DeviceProblem:
                          _ptr(self.order_off), _ptr(self.line_sku))
 
     def plans(self) -> wh_plans:
-        return wh_plans(self.n_plans, self.n_tours, int(self.order_seq.shape[0]), _ptr(self.slot_map),
+        seq = self.order_seq if self.order_seq is not None else self.order_seq16
+        return wh_plans(self.n_plans, self.n_tours, int(seq.shape[0]), _ptr(self.slot_map),
                         self.slot_map_stride, _ptr(self.plan_tour_off), _ptr(self.tour_off),
                         _ptr(self.order_seq), _ptr(self.loc_used))
 
@@ -613,7 +616,8 @@ class Batch:
         self._keep = list(items)
         insts = []
         for desc, prob, costs in self._keep:
-            insts.append(wh_instance(wh_layout_desc(*desc), prob.orders(), prob.plans(), costs.c()))
+            insts.append(wh_instance(wh_layout_desc(*desc), prob.orders(), prob.plans(), costs.c(),
+                                     _ptr(prob.order_seq16)))
         self.handle = wh_batch_create(insts)
 
     def eval(self, mask: int = 3, stream=None, graph: bool = False) -> None:
@@ -656,7 +660,7 @@ class PackedInstances:
     instance's order ids as unsigned 16-bit values (each instance must have
     at most 65,536 orders).  Segments start on 16-byte boundaries (int32
     segments on multiples of 4 elements, the 16-bit order ids on multiples of
-    8, so that their int32 widening starts on 32 bytes).  ``pin()`` moves
+    8).  ``pin()`` moves
     both arrays to pinned host memory; ``device_set()`` makes a device copy
     with per-instance DeviceProblem / Costs views and a Batch over them."""
 
@@ -713,15 +717,16 @@ class PackedInstances:
 
 class PackedDeviceSet:
     """Device buffers shaped like a PackedInstances (flat int32 arrays, the
-    16-bit landing buffer and the widened int32 order ids, per-instance
-    outputs) and a Batch over per-instance views of them."""
+    16-bit order ids, per-instance outputs) and a Batch over per-instance
+    views of them; the batch reads the 16-bit order ids directly.  The
+    per-instance DeviceProblems carry no int32 order ids (order_seq None):
+    they serve this batch only."""
 
     def __init__(self, packed: PackedInstances, device="cuda"):
         import torch
         self.packed = packed
         self.flat = torch.empty(packed.flat.numel(), dtype=torch.int32, device=device)
         self.seq16 = torch.empty(packed.seq16.numel(), dtype=torch.int16, device=device)
-        self.seq = torch.empty(packed.seq16.numel(), dtype=torch.int32, device=device)
         self.tour_s = torch.empty(max(packed.total_tours, 1), dtype=torch.int32, device=device)
         self.tour_rr = torch.empty_like(self.tour_s)
         self.plan_s = torch.empty(max(packed.total_plans, 1), dtype=torch.int64, device=device)
@@ -730,7 +735,8 @@ class PackedDeviceSet:
         for i, geo in enumerate(packed.geo):
             v = [self.flat[o:o + n] for o, n in packed.offsets[i]]
             so, sn = packed.seq_off[i]
-            prob = DeviceProblem(v[0], v[1], v[2], v[3], v[4], self.seq[so:so + sn], packed.n_sku[i])
+            prob = DeviceProblem(v[0], v[1], v[2], v[3], v[4], None, packed.n_sku[i],
+                                 order_seq16=self.seq16[so:so + sn])
             nt, npl = packed.n_tours[i], packed.n_plans[i]
             costs = Costs(self.tour_s[t0:t0 + nt], self.tour_rr[t0:t0 + nt], self.plan_s[p0:p0 + npl],
                           self.plan_rr[p0:p0 + npl])
@@ -741,14 +747,12 @@ class PackedDeviceSet:
         self.batch = Batch(items)
 
     def load(self, stream=None) -> None:
-        """Copy the packed host arrays in and widen the order ids, on `stream`."""
+        """Copy the packed host arrays in (two copies), on `stream`."""
         import torch
         s = torch.cuda.current_stream() if stream is None else stream
         with torch.cuda.stream(s):
             self.flat.copy_(self.packed.flat, non_blocking=True)
             self.seq16.copy_(self.packed.seq16, non_blocking=True)
-            _check(load().wh_widen_u16(ctypes.c_void_p(_ptr(self.seq16)), ctypes.c_void_p(_ptr(self.seq)),
-                                       self.seq.numel(), _stream_ptr(s)), "wh_widen_u16")
 
     def close(self):
         self.batch.close()
@@ -757,7 +761,7 @@ class PackedDeviceSet:
 class PackedPipeline:
     """End-to-end batched scoring from pinned host memory: every submitted
     step copies all instances' inputs in (one copy of the int32 arrays, one
-    of the 16-bit order ids, widened on the device), scores them in one
+    of the 16-bit order ids, which the batch reads as they are), scores them in one
     persistent launch replayed as a CUDA graph, and copies every plan's two
     costs back to a pinned host array.  Two device sets alternate, so the
     copy of one step (copy stream) overlaps the evaluation of the previous

@@ -130,6 +130,14 @@ __device__ __forceinline__ bool defer_long(const EvalArgs& a, int inst, int t, i
     return true;
 }
 
+// Order id at sequence position q: the 16-bit copy when ID16 (batched
+// instances whose order books have at most 65,536 orders), else int32.
+template <bool ID16>
+__device__ __forceinline__ int order_id(const EvalArgs& a, int64_t q) {
+    if constexpr (ID16) return (int)__ldg(reinterpret_cast<const unsigned short*>(a.order_seq16) + q);
+    else return __ldg(a.order_seq + q);
+}
+
 // this warp's contiguous range of 32-tour chunks: chunks split evenly over
 // all warps of the grid (each warp takes floor or ceil of chunks / warps,
 // none is left without work while another takes an extra chunk)
@@ -164,7 +172,7 @@ __device__ __forceinline__ int warp_find_plan(const EvalArgs& a, int t0, int lan
 
 // One warp scores the 32-tour chunks [c_begin, c_end) of instance `a`, one
 // tour per lane, and adds its plans' sums with one atomic per plan segment.
-template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES>
+template <bool KEY16, bool SHARED_MAP, bool SMEM_TABLES, bool ID16 = false>
 __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint32_t mask, int inst, int c_begin,
                                             int c_end, uint32_t* col16, uint2* col32, int T, int lane,
                                             bool check_keys) {
@@ -213,15 +221,14 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                     const uint32_t dv = lds_key<uint32_t>(desc_sa + 4u * min((uint32_t)o, o_max));
                     return (uint32_t)o < (uint32_t)a.n_orders ? dv : 0xFFFFFFFFu;
                 };
-                const int* seq = a.order_seq;
-                int o_a = q0 < q1 ? __ldg(seq + q0) : 0;
-                int o_b = q0 + 1 < q1 ? __ldg(seq + q0 + 1) : 0;
+                int o_a = q0 < q1 ? order_id<ID16>(a, q0) : 0;
+                int o_b = q0 + 1 < q1 ? order_id<ID16>(a, q0 + 1) : 0;
                 uint32_t d = desc_of(o_a);
                 for (int q = q0; q < q1; ++q) {
                     const int o = o_a;
                     o_a = o_b;
                     const uint32_t dn = desc_of(o_a);
-                    o_b = q + 2 < q1 ? __ldg(seq + q + 2) : 0;
+                    o_b = q + 2 < q1 ? order_id<ID16>(a, q + 2) : 0;
                     const int c = (int)(d & 0xFFu);
                     if (n + c > SHORT_MAX) {
                         if ((uint32_t)o >= (uint32_t)a.n_orders) {
@@ -251,11 +258,11 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                 }
             } else {
                 // software-pipelined: order ids two ahead, descriptors one ahead
-                int o2 = q0 + 1 < q1 ? __ldg(a.order_seq + q0 + 1) : 0;
+                int o2 = q0 + 1 < q1 ? order_id<ID16>(a, q0 + 1) : 0;
                 uint32_t d1 = 0;
                 int o1 = 0;
                 if (q0 < q1) {
-                    o1 = __ldg(a.order_seq + q0);
+                    o1 = order_id<ID16>(a, q0);
                     if constexpr (SMEM_TABLES)
                         d1 = (unsigned)o1 < (unsigned)a.n_orders ? lds_key<uint32_t>(desc_sa + 4u * (uint32_t)o1) : 0xFFFFFFFFu;
                 }
@@ -266,7 +273,7 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                     if constexpr (SMEM_TABLES)
                         d1 = (q + 1 < q1 && (unsigned)o1 < (unsigned)a.n_orders) ? lds_key<uint32_t>(desc_sa + 4u * (uint32_t)o1)
                                                                                   : 0xFFFFFFFFu;
-                    o2 = q + 2 < q1 ? __ldg(a.order_seq + q + 2) : 0;
+                    o2 = q + 2 < q1 ? order_id<ID16>(a, q + 2) : 0;
                     if ((unsigned)o >= (unsigned)a.n_orders) { flag(a.status, WH_STATUS_BAD_ORDER); bad = true; break; }
                     int lb, le;
                     if constexpr (SMEM_TABLES) {
@@ -702,8 +709,9 @@ __global__ void __launch_bounds__(SSHAPE_AGG_THREADS) k_eval_sshape_agg(EvalArgs
 // a queue ordered largest first, stage that instance's order book once, and
 // split the item's chunks among their warps.
 // 16-bit keys: up to 384-thread CTAs, two per SM (85 registers a thread, as
-// k_eval_short); 32-bit keys: up to 256 threads
-template <bool KEY16, bool SMEM_TABLES>
+// k_eval_short); 32-bit keys: up to 256 threads.  ID16: the instances' order
+// ids are read as 16-bit values.
+template <bool KEY16, bool SMEM_TABLES, bool ID16>
 __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
@@ -742,7 +750,8 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b
         const int cb = w.chunk_begin + warp * n / nw;   // the item's chunks split evenly over the warps
         const int ce = w.chunk_begin + (warp + 1) * n / nw;
         if (cb < ce)
-            eval_chunks<KEY16, true, SMEM_TABLES>(s_a, src, b.mask, w.inst, cb, ce, col16, col32, T, lane, check_keys);
+            eval_chunks<KEY16, true, SMEM_TABLES, ID16>(s_a, src, b.mask, w.inst, cb, ce, col16, col32, T, lane,
+                                                        check_keys);
         __syncthreads();
     }
 }
@@ -794,7 +803,8 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
                 const int q = qb + lane;
                 int lb = 0, le = 0;
                 if (q < q1) {
-                    const int o = a.order_seq[q];   // in range: checked by the short kernel
+                    // in range: checked by the short kernel
+                    const int o = a.order_seq16 ? (int)a.order_seq16[q] : a.order_seq[q];
                     lb = a.order_off[o];
                     le = a.order_off[o + 1];
                     if (lb < 0 || le < lb || le > a.n_lines) {
@@ -948,9 +958,9 @@ cudaError_t launch_sshape_t(const EvalArgs& a, const Tuning& t, size_t smem, int
     return cudaGetLastError();
 }
 
-template <bool K16, bool SM>
+template <bool K16, bool SM, bool ID16>
 cudaError_t launch_batch_t(const BatchArgs& b, const Tuning& t, size_t smem, int num_sms, cudaStream_t s) {
-    auto kern = k_eval_batch<K16, SM>;
+    auto kern = k_eval_batch<K16, SM, ID16>;
     int grid = 0;
     cudaError_t e = grid_for(kern, t.threads, smem, num_sms, b.n_items, &grid);
     if (e != cudaSuccess) return e;
@@ -1064,8 +1074,14 @@ cudaError_t launch_eval_batch(const BatchArgs& b, const Tuning& t, bool k16, int
     if (b.n_items == 0) return cudaSuccess;
     const size_t smem = eval_batch_smem_bytes(b, t, k16);
     const bool sm = t.smem_tables != 0;
-    if (k16) return sm ? launch_batch_t<true, true>(b, t, smem, num_sms, s) : launch_batch_t<true, false>(b, t, smem, num_sms, s);
-    return sm ? launch_batch_t<false, true>(b, t, smem, num_sms, s) : launch_batch_t<false, false>(b, t, smem, num_sms, s);
+#define WH_LAUNCH(K, M, I) launch_batch_t<K, M, I>(b, t, smem, num_sms, s)
+    if (b.id16) {
+        if (k16) return sm ? WH_LAUNCH(true, true, true) : WH_LAUNCH(true, false, true);
+        return sm ? WH_LAUNCH(false, true, true) : WH_LAUNCH(false, false, true);
+    }
+    if (k16) return sm ? WH_LAUNCH(true, true, false) : WH_LAUNCH(true, false, false);
+    return sm ? WH_LAUNCH(false, true, false) : WH_LAUNCH(false, false, false);
+#undef WH_LAUNCH
 }
 
 // CTAs per SM of the long-tour kernel, the larger of its two forms: its grid

@@ -60,6 +60,7 @@ struct wh_batch {
     void* scratch = nullptr;               // line keys of all instances + long list + long records
     uint2* long_rec = nullptr;             // the long-tour kernel's record scratch (in scratch)
     bool key16 = true;
+    bool id16 = false;   // the instances' order ids are 16-bit
     int32_t max_orders = 0, max_lines = 0, max_rec = 0, max_work = 0;
     int64_t total_tours = 0;
     int32_t long_cap = 0;
@@ -927,6 +928,7 @@ wh::BatchArgs batch_args(const wh_batch* b, uint32_t mask) {
     B.max_orders = b->max_orders;
     B.max_lines = b->max_lines;
     B.max_rec = b->max_rec;
+    B.id16 = b->id16 ? 1 : 0;
     return B;
 }
 
@@ -977,17 +979,31 @@ extern "C" int wh_batch_create(const wh_instance* insts, int32_t n, wh_batch** o
     b->n_inst = n;
     b->args.resize(n);
     size_t key_bytes = 0;
+    // 16-bit order ids: every instance or none (one kernel reads them all)
+    int n16 = 0;
+    for (int32_t i = 0; i < n; ++i) n16 += insts[i].order_seq16 != nullptr;
+    b->id16 = n16 == n;
     for (int32_t i = 0; i < n; ++i) {
         wh::Geo g;
         rc = check_desc(insts[i].layout, &g);
-        if (rc == WH_OK) rc = check_problem(insts[i].orders, insts[i].plans);
-        if (rc == WH_OK && (insts[i].plans.slot_map_stride != 0 || insts[i].plans.n_plans < 1)) rc = WH_EINVAL;
+        wh_plans p = insts[i].plans;
+        if (b->id16) {
+            if (insts[i].orders.n_orders > 65536) rc = WH_EINVAL;
+            p.order_seq = reinterpret_cast<const int32_t*>(insts[i].order_seq16);   // presence check only
+        }
+        if (n16 != 0 && n16 != n) rc = WH_EINVAL;
+        if (rc == WH_OK) rc = check_problem(insts[i].orders, p);
+        if (rc == WH_OK && (p.slot_map_stride != 0 || p.n_plans < 1)) rc = WH_EINVAL;
         if (rc != WH_OK) {
             b->device = -1;
             delete b;
             return rc;
         }
         fill_args(b->args[i], g, insts[i].orders, insts[i].plans, insts[i].out, WH_ROUTE_SSHAPE | WH_ROUTE_OPTIMAL);
+        if (b->id16) {
+            b->args[i].order_seq = nullptr;
+            b->args[i].order_seq16 = insts[i].order_seq16;
+        }
         b->key16 = b->key16 && wh::key16_ok(g);
         b->max_orders = std::max(b->max_orders, insts[i].orders.n_orders);
         b->max_lines = std::max(b->max_lines, insts[i].orders.n_lines);

@@ -35,6 +35,7 @@ struct EvalArgs {
     const int32_t* plan_tour_off;
     const int32_t* tour_off;
     const int32_t* order_seq;
+    const uint16_t* order_seq16;   // the order ids as 16-bit values (batched instances), else NULL
     int32_t* tour_s;
     int32_t* tour_rr;
     int64_t* plan_s;
@@ -70,6 +71,7 @@ struct BatchArgs {
     int32_t* long_count;
     uint32_t mask;
     int32_t max_orders, max_lines, max_rec;
+    int32_t id16;               // every instance's order ids are 16-bit (order_seq16)
 };
 
 struct LongArgs {

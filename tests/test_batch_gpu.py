@@ -13,12 +13,18 @@ import wh_gen
 pytestmark = pytest.mark.gpu
 
 
-def build_batch(wh, insts, dev="cuda"):
+def build_batch(wh, insts, dev="cuda", id16=False):
+    """Batch over device copies of `insts`; with id16 each instance passes
+    its order ids only as 16-bit values (no int32 copy)."""
+    import torch
     items = []
     for inst in insts:
         lay = inst.layout
         desc = (lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width)
         prob = wh.to_device(inst, dev)
+        if id16:
+            seq16 = torch.as_tensor(np.asarray(inst.order_seq).astype(np.uint16).view(np.int16)).to(dev)
+            prob.order_seq, prob.order_seq16 = None, seq16
         costs = wh.alloc_costs(prob.n_tours, prob.n_plans, dev)
         for t in (costs.tour_s, costs.tour_rr, costs.plan_s, costs.plan_rr):
             t.fill_(-99)
@@ -130,6 +136,65 @@ def test_batch_with_long_tours_and_mixed_layouts(gpu_lib):
     batch.close()
 
 
+@pytest.mark.parametrize("shape", [(384, 16, 1), (256, 3, 0), (96, 1, 1)])
+def test_batch_16bit_order_ids(gpu_lib, shape):
+    """Order ids passed only as 16-bit values: the same results as the oracle
+    under every routing mask, with and without staged order books, with
+    16-bit and 32-bit keys and with tours that go to the long-tour kernel."""
+    import torch
+    insts = [wh_gen.paperscale(seed=8, n_plans=2), wh_gen.tiny(seed=2, n_plans=5)] + \
+            [wh_gen.batched_instance(13, i, n_plans=5) for i in range(10)]
+    want = [oracle.eval_plans(inst) for inst in insts]
+    batch, items = build_batch(gpu_lib, insts, id16=True)
+    if shape[0] > 256:
+        shape = (256,) + shape[1:]   # the paper-scale layout needs 32-bit keys: CTAs of at most 256
+    batch.set_tuning(*shape)
+    for mask in (3, 1, 2):
+        for _, _, c in items:
+            for t in (c.tour_s, c.tour_rr, c.plan_s, c.plan_rr):
+                t.fill_(-99)
+        batch.eval(mask, graph=mask == 3)
+        torch.cuda.synchronize()
+        assert batch.status() == 0
+        for i in range(len(insts)):
+            got = results(items, i)
+            if mask & 1:
+                assert np.array_equal(got[0], want[i][0]) and np.array_equal(got[2], want[i][2]), (mask, i)
+            if mask & 2:
+                assert np.array_equal(got[1], want[i][1]) and np.array_equal(got[3], want[i][3]), (mask, i)
+    batch.close()
+    # 16-bit keys only (all batched layouts), the 384-thread shape
+    b16, items16 = build_batch(gpu_lib, insts[2:], id16=True)
+    b16.set_tuning(384, 16, 1)
+    b16.eval(3)
+    torch.cuda.synchronize()
+    assert b16.status() == 0
+    for i in range(len(insts) - 2):
+        assert_same(results(items16, i), want[i + 2], f"16-bit keys instance {i}")
+    b16.close()
+
+
+def test_batch_16bit_ids_rejections(gpu_lib):
+    """16-bit ids on some instances but not all, or on an order book of more
+    than 65,536 orders, are WH_EINVAL."""
+    import torch
+    wh = gpu_lib
+    insts = [wh_gen.batched_instance(13, i, n_plans=2) for i in range(2)]
+    _, items = build_batch(wh, insts[:1], id16=True)
+    _, items32 = build_batch(wh, insts[1:])
+    with pytest.raises(wh.WhError) as e:
+        wh.Batch(items + items32)
+    assert e.value.code == wh.WH_EINVAL
+    z = lambda n: torch.zeros(n, dtype=torch.int32, device="cuda")
+    one = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    prob = wh.DeviceProblem(z(65538), z(0), z(1), one, one, None, 1,
+                            order_seq16=torch.zeros(1, dtype=torch.int16, device="cuda"))
+    costs = wh.alloc_costs(1, 1)
+    with pytest.raises(wh.WhError) as e:
+        wh.Batch([((8, 20, 3, 1, 2), prob, costs)])
+    assert e.value.code == wh.WH_EINVAL
+
+
 def test_autotune_and_cache(gpu_lib, tmp_path):
     import torch
     insts = [wh_gen.batched_instance(11, i, n_plans=16) for i in range(48)]
@@ -178,7 +243,8 @@ def test_batched_full_size_sampled(gpu_lib):
 
 def test_packed_instances_device_set_and_host_pipeline(gpu_lib):
     """The benchmark's packed layout: all instances' int32 arrays in one flat
-    buffer and the order ids as 16-bit values widened on the device.  The
+    buffer and the order ids as 16-bit values, which the batch reads
+    directly.  The
     device set scores every instance exactly as the oracle does; the host
     pipeline (two device sets, copies overlapping evaluation) returns the same
     plan costs on every submitted step; per-kernel timing counts the eager
