@@ -216,20 +216,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!__all_sync(0xffffffffu, mbar_wait(acc1_full, ph, abort, status, fault.wait_ns))) break;
             tc_fence_after();
             // layer 1 in K-chunk order: every warp takes its 16 columns of
-            // chunk kc (64 kc + 16 part_id ..), then hands the chunk over
-#pragma unroll 1
-            for (int kc = 0; kc < 4; ++kc) {
+            // chunk kc (64 kc + 16 part_id ..), then hands the chunk over; the
+            // TMEM load of the next chunk is in flight while this one is
+            // computed
+            auto e1_chunk = [&](int kc, const uint32_t (&v)[16]) {
                 const int c0 = 64 * kc + 16 * part_id;
-                float v[16];
-                tc_ld16(tmem + lane_addr + (uint32_t)c0, v);
 #pragma unroll
                 for (int g8 = 0; g8 < 2; ++g8) {
-                    uint32_t w[4];
                     const int c = c0 + 8 * g8;
+                    const ulonglong2 bA = *reinterpret_cast<const ulonglong2*>(par + c);
+                    const ulonglong2 bB = *reinterpret_cast<const ulonglong2*>(par + c + 4);
+                    const uint64_t bias[4] = {bA.x, bA.y, bB.x, bB.y};
+                    uint32_t w[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const uint64_t b = *reinterpret_cast<const uint64_t*>(par + c + 2 * j);
-                        const uint64_t z = add2(pk(v[8 * g8 + 2 * j], v[8 * g8 + 2 * j + 1]), b);
+                        const uint64_t z = add2(pk(__uint_as_float(v[8 * g8 + 2 * j]),
+                                                   __uint_as_float(v[8 * g8 + 2 * j + 1])), bias[j]);
                         if (save_rows) *reinterpret_cast<uint64_t*>(save.Z1 + row * 256 + c + 2 * j) = z;
                         float g0, g1;
                         upk(gelu2(z), g0, g1);
@@ -245,30 +247,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(h1c(kc));
+            };
+            uint32_t ta[16], tb[16];
+            tc_ld16_issue(tmem + lane_addr + (uint32_t)(16 * part_id), ta);
+            tc_wait_ld16(ta);
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                uint32_t(&cur)[16] = (kc & 1) ? tb : ta;
+                uint32_t(&nxt)[16] = (kc & 1) ? ta : tb;
+                if (kc < 3) tc_ld16_issue(tmem + lane_addr + (uint32_t)(64 * (kc + 1) + 16 * part_id), nxt);
+                e1_chunk(kc, cur);
+                if (kc < 3) tc_wait_ld16(nxt);
             }
             if (!__all_sync(0xffffffffu, mbar_wait(acc2_full, ph, abort, status, fault.wait_ns))) break;
             tc_fence_after();
+            // layer 2: this warp's TC_PART_COLS columns in steps of 16, the
+            // next step's TMEM load in flight while one is computed
             uint64_t part2 = dup2(0.0f);
-#pragma unroll 1
-            for (int cc = 0; cc < TC_PART_COLS / 32; ++cc) {
-                const int c0 = TC_PART_COLS * part_id + 32 * cc;
-                float v[32];
-                tc_ld32(tmem + lane_addr + 256u + (uint32_t)c0, v);
+            auto e2_step = [&](int c0, const uint32_t (&v)[16]) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    const uint64_t b = *reinterpret_cast<const uint64_t*>(par + 256 + c0 + j);
-                    const uint64_t z = add2(pk(v[j], v[j + 1]), b);
-                    float g0, g1;
-                    upk(gelu2(z), g0, g1);
-                    // the layer-2 activations are bf16 values
-                    const uint32_t hb = pack_bf16(g0, g1);
-                    if (save_rows) {
-                        *reinterpret_cast<uint64_t*>(save.Z2 + row * 256 + c0 + j) = z;
-                        *reinterpret_cast<uint32_t*>(save.H2 + row * 256 + c0 + j) = hb;
+                for (int j4 = 0; j4 < 16; j4 += 4) {
+                    const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(par + 256 + c0 + j4);
+                    const ulonglong2 w3 = *reinterpret_cast<const ulonglong2*>(par + 512 + c0 + j4);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = j4 + 2 * h;
+                        const uint64_t z = add2(pk(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), h ? b.y : b.x);
+                        float g0, g1;
+                        upk(gelu2(z), g0, g1);
+                        // the layer-2 activations are bf16 values
+                        const uint32_t hb = pack_bf16(g0, g1);
+                        if (save_rows) {
+                            *reinterpret_cast<uint64_t*>(save.Z2 + row * 256 + c0 + j) = z;
+                            *reinterpret_cast<uint32_t*>(save.H2 + row * 256 + c0 + j) = hb;
+                        }
+                        const uint64_t hv = pk(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u));
+                        part2 = fma2(hv, h ? w3.y : w3.x, part2);
                     }
-                    const uint64_t h = pk(__uint_as_float(hb << 16), __uint_as_float(hb & 0xFFFF0000u));
-                    part2 = fma2(h, *reinterpret_cast<const uint64_t*>(par + 512 + c0 + j), part2);
                 }
+            };
+            const uint32_t c2 = (uint32_t)(TC_PART_COLS * part_id);
+            tc_ld16_issue(tmem + lane_addr + 256u + c2, ta);
+            tc_wait_ld16(ta);
+#pragma unroll
+            for (int st = 0; st < TC_PART_COLS / 16; ++st) {
+                uint32_t(&cur)[16] = (st & 1) ? tb : ta;
+                uint32_t(&nxt)[16] = (st & 1) ? ta : tb;
+                if (st + 1 < TC_PART_COLS / 16) tc_ld16_issue(tmem + lane_addr + 256u + c2 + 16u * (st + 1), nxt);
+                e2_step((int)c2 + 16 * st, cur);
+                if (st + 1 < TC_PART_COLS / 16) tc_wait_ld16(nxt);
             }
             float pa, pb;
             upk(part2, pa, pb);

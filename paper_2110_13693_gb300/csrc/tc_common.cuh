@@ -151,6 +151,27 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Split forms of tc_ld16 for software pipelining: tc_ld16_issue starts the
+// load of 16 columns into r; tc_wait_ld16 waits for every load of the warp
+// issued so far and names r, so that no use of r is scheduled before it.
+__device__ __forceinline__ void tc_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_ld16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 // Pairs of fp32 values in one 64-bit register for the packed fp32x2
 // arithmetic of sm_100 and later (add / mul / fma .f32x2, element-wise,
 // round to nearest): the epilogue's FMA-pipe work in half the instructions.
@@ -179,33 +200,42 @@ __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
 }
 __device__ __forceinline__ uint64_t dup2(float x) { return pk(x, x); }
 
-// gelu(z) = z/2 (1 + erf(z / sqrt 2)) of both halves of z.  erf by the
+// gelu(z) = z/2 (1 + erf(z / sqrt 2)) of both halves of z, with erf by the
 // approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
 // formula 7.1.28 (after Hastings): for x >= 0,
-// erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16, |error| <= 3e-7; odd
-// in x (large x: the power overflows to inf and erf to 1).  Far below the
-// bf16 resolution (2^-8) of the activations it feeds; one reciprocal per
-// value and FMAs, all but the reciprocal on packed pairs.
+// erf(x) = 1 - P(x)^-16, P(x) = 1 + a1 x + ... + a6 x^6, |error| <= 3e-7;
+// odd in x.  Both signs of z reduce to one expression,
+//   gelu(z) = relu(z) - |z| P(|z| / sqrt 2)^-16 / 2 = relu(z) - |z| Q(|z|)^-16,
+// with Q(t) = c P(t / sqrt 2), c = 2^(1/16) (so Q^16 = 2 P^16): coefficients
+// q_k = c a_k / sqrt(2)^k, all positive.  Error of the fp32 evaluation: the
+// Horner chain over positive terms and the rounded coefficients perturb Q by
+// at most 7u relative (u = 2^-24), the four squarings make that 127u, the
+// reciprocal 129u, the product with |z| 130u of a term of at most |z|/2, and
+// the final fma adds u |z|: at most 66u |z|, plus the approximation's own
+// 1.5e-7 |z|.  Large |z|: Q^16 overflows, the reciprocal is 0 and
+// gelu = relu(z).  All but the two reciprocals on packed pairs.
+constexpr float GELU_Q0 = 1.0442737f, GELU_Q1 = 0.052075163f, GELU_Q2 = 0.022076998f,
+                GELU_Q3 = 0.0034227392f, GELU_Q4 = 3.9686136e-05f, GELU_Q5 = 5.105521e-05f,
+                GELU_Q6 = 5.6213e-06f;
+
 __device__ __forceinline__ uint64_t gelu2(uint64_t z) {
-    float x0, x1;
-    upk(mul2(z, dup2(0.70710678118654752f)), x0, x1);
-    const uint64_t ax = pk(fabsf(x0), fabsf(x1));
-    uint64_t p = fma2(dup2(0.0000430638f), ax, dup2(0.0002765672f));
-    p = fma2(p, ax, dup2(0.0001520143f));
-    p = fma2(p, ax, dup2(0.0092705272f));
-    p = fma2(p, ax, dup2(0.0422820123f));
-    p = fma2(p, ax, dup2(0.0705230784f));
-    p = fma2(p, ax, dup2(1.0f));
-    p = mul2(p, p);   // ^2
-    p = mul2(p, p);   // ^4
-    p = mul2(p, p);   // ^8
-    p = mul2(p, p);   // ^16
+    float z0, z1;
+    upk(z, z0, z1);
+    const uint64_t t = pk(fabsf(z0), fabsf(z1));
+    uint64_t q = fma2(dup2(GELU_Q6), t, dup2(GELU_Q5));
+    q = fma2(q, t, dup2(GELU_Q4));
+    q = fma2(q, t, dup2(GELU_Q3));
+    q = fma2(q, t, dup2(GELU_Q2));
+    q = fma2(q, t, dup2(GELU_Q1));
+    q = fma2(q, t, dup2(GELU_Q0));
+    q = mul2(q, q);   // ^2
+    q = mul2(q, q);   // ^4
+    q = mul2(q, q);   // ^8
+    q = mul2(q, q);   // ^16
     float p0, p1;
-    upk(p, p0, p1);
-    const float m0 = 1.0f - 1.0f / p0, m1 = 1.0f - 1.0f / p1;   // |erf|
-    const uint64_t er = pk(copysignf(m0, x0), copysignf(m1, x1));
-    const uint64_t hz = mul2(z, dup2(0.5f));
-    return fma2(hz, er, hz);
+    upk(q, p0, p1);
+    const uint64_t nr = pk(-1.0f / p0, -1.0f / p1);
+    return fma2(t, nr, pk(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f)));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
