@@ -413,6 +413,20 @@ int wh_surrogate_screen(wh_layout *layout, wh_surrogate *s, const wh_orders *ord
                         int32_t max_lines_per_tour, float *y_tour_cache, uint8_t *tour_changed, int32_t *kept,
                         void *stream);
 
+/* Diagnostics of the last wh_surrogate_screen call on `layout` (device
+ * pointers into the layout's scratch, valid until its next call; all NULL and
+ * *n_tasks = 0 when the last call was not a screen): the number of tasks (one
+ * per changed tour of a move: an order move has two, a SKU move one per order
+ * holding a moved SKU), the task list [n_tasks][4] (move index, changed tour,
+ * then order added / order removed for order moves or the order holding the
+ * SKU / a tag for SKU moves), whether each task counts ([n_tasks][2] int32:
+ * 0, 0 counted; -1, -1 not: invalid ids, or a SKU-swap task that another task
+ * of the same tour stands for) and the bf16 feature rows of the changed tours
+ * [n_tasks][192] that the screen predicted from (Sec. 1, Fig. 1).  Enqueues
+ * nothing.  Returns WH_OK or WH_EINVAL. */
+int wh_surrogate_screen_trace(wh_layout *layout, int64_t *n_tasks, const int32_t **tasks, const int32_t **counted,
+                              const uint16_t **features);
+
 void wh_surrogate_destroy(wh_surrogate *s);
 
 /* Sizes accepted by wh_eval_plans_noalloc. */

@@ -110,6 +110,9 @@ SIGNATURES = {
                                            ctypes.POINTER(wh_plans), ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_surrogate_screen_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
     "wh_surrogate_get_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "wh_surrogate_predict_timeout_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
@@ -438,6 +441,19 @@ class Layout:
                             keep, max_orders, max_lines, _ptr(kept), None if y_tour is None else _ptr(y_tour),
                             None if changed is None else _ptr(changed), stream)
         return kept[:prob.n_plans * keep]
+
+    def screen_trace(self):
+        """The last screen's tasks (int32 [n, 4]: move, changed tour, two
+        move-specific ids), counted flags (int32 [n, 2]) and feature rows
+        (bf16 [n, 192]), copied to torch tensors; None after any other call."""
+        import torch
+        n, t, c, f = wh_surrogate_screen_trace(self.handle)
+        if n == 0 or not t:
+            return None
+        tasks = torch.as_tensor(_DeviceView(t, (n, 4), "<i4"), device="cuda").clone()
+        counted = torch.as_tensor(_DeviceView(c, (n, 2), "<i4"), device="cuda").clone()
+        rows = torch.as_tensor(_DeviceView(f, (n, WH_FEATURES), "<i2"), device="cuda").clone().view(torch.bfloat16)
+        return tasks, counted, rows
 
     def batch_grow(self, prob: DeviceProblem, slot_maps, max_orders: int, max_lines: int = 0, stream=None):
         """Seed-and-grow batching of prob's orders under each slotting of
@@ -895,6 +911,25 @@ def wh_surrogate_screen(layout, s, orders: wh_orders, plans: wh_plans, moves, mo
                                       moves_per_plan, keep, max_orders, max_lines, ctypes.c_void_p(y_tour),
                                       ctypes.c_void_p(tour_changed), ctypes.c_void_p(kept), _stream_ptr(stream)),
            "wh_surrogate_screen")
+
+
+def wh_surrogate_screen_trace(layout):
+    """(n_tasks, tasks, counted, features) device pointers of the layout's last screen."""
+    n = ctypes.c_int64()
+    t, c, f = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().wh_surrogate_screen_trace(layout, ctypes.byref(n), ctypes.byref(t), ctypes.byref(c),
+                                            ctypes.byref(f)), "wh_surrogate_screen_trace")
+    return n.value, t.value, c.value, f.value
+
+
+class _DeviceView:
+    """A device buffer owned by the library seen as an array (CUDA array
+    interface), only for copying it into a torch tensor (torch takes no
+    read-only views, so it is not marked read-only)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
 
 
 def wh_surrogate_destroy(s) -> None:

@@ -69,6 +69,55 @@ __global__ void k_mv_tours(MoveArgs M) {
     }
 }
 
+// The same index built one plan per CTA (grid stride over plans): the
+// plan's order -> tour row is filled in shared memory (-1 where the plan does
+// not hold the order) and written out in one coalesced pass, so the table
+// needs no clearing pass and no tour searches for its plan.  Used when a row
+// fits MVT_MAX_ORDERS entries.
+constexpr int MVT_THREADS = 256;
+constexpr int MVT_MAX_ORDERS = 12288;   // 48 KB of shared memory
+
+__global__ void __launch_bounds__(MVT_THREADS) k_mv_tours_plan(MoveArgs M) {
+    extern __shared__ int32_t s_row[];
+    const EvalArgs& a = M.a;
+    for (int p = blockIdx.x; p < a.n_plans; p += gridDim.x) {
+        for (int o = threadIdx.x; o < a.n_orders; o += blockDim.x) s_row[o] = -1;
+        __syncthreads();
+        int t0 = a.plan_tour_off[p], t1 = a.plan_tour_off[p + 1];
+        if (t0 < 0 || t1 < t0 || t1 > a.n_tours || (p == 0 && t0 != 0) || (p == a.n_plans - 1 && t1 != a.n_tours)) {
+            if (threadIdx.x == 0) flag(a.status, WH_STATUS_BAD_OFFSET);
+            t0 = max(t0, 0);
+            t1 = min(t1, a.n_tours);
+        }
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];
+            int lines = 0;
+            if (q0 < 0 || q1 < q0 || (int64_t)q1 > a.n_seq) {
+                flag(a.status, WH_STATUS_BAD_OFFSET);
+                lines = -1;
+            } else {
+                for (int q = q0; q < q1; ++q) {
+                    const int o = a.order_seq[q];
+                    int lb, le;
+                    const int c = order_lines_checked(a, o, lb, le);
+                    if (c < 0) {
+                        flag(a.status, WH_STATUS_BAD_ORDER);
+                        lines = -1;
+                        break;
+                    }
+                    lines += c;
+                    s_row[o] = t;
+                }
+            }
+            M.tour_lines[t] = lines;
+        }
+        __syncthreads();
+        int32_t* row = M.order_tour + (int64_t)p * a.n_orders;
+        for (int o = threadIdx.x; o < a.n_orders; o += blockDim.x) row[o] = s_row[o];
+        __syncthreads();
+    }
+}
+
 __global__ void k_mv_sku_count(MoveArgs M) {
     const EvalArgs& a = M.a;
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < a.n_lines; l += gridDim.x * blockDim.x) {
@@ -645,13 +694,24 @@ __global__ void k_occupancy(const int32_t* slot_map, int64_t stride, int32_t n_p
 
 }  // namespace
 
-cudaError_t launch_moves_prepare(const MoveArgs& M, cudaStream_t s) {
+cudaError_t launch_moves_prepare(const MoveArgs& M, int num_sms, cudaStream_t s) {
     const EvalArgs& a = M.a;
-    if (cudaMemsetAsync(M.order_tour, 0xFF, sizeof(int32_t) * (size_t)a.n_plans * (size_t)a.n_orders, s) != cudaSuccess)
+    const bool per_plan = a.n_orders <= MVT_MAX_ORDERS;
+    if (!per_plan &&
+        cudaMemsetAsync(M.order_tour, 0xFF, sizeof(int32_t) * (size_t)a.n_plans * (size_t)a.n_orders, s) != cudaSuccess)
         return cudaGetLastError();
     if (cudaMemsetAsync(M.sku_cur, 0, sizeof(int32_t) * ((size_t)a.n_sku + 1), s) != cudaSuccess)
         return cudaGetLastError();
-    if (a.n_tours > 0) k_mv_tours<<<grid_of(a.n_tours, 256), 256, 0, s>>>(M);
+    if (per_plan) {
+        // tours outside every plan's range (malformed plan offsets, flagged)
+        // keep the "bad tour" line count
+        if (a.n_tours > 0 && cudaMemsetAsync(M.tour_lines, 0xFF, sizeof(int32_t) * (size_t)a.n_tours, s) != cudaSuccess)
+            return cudaGetLastError();
+        const int grid = a.n_plans < num_sms * 8 ? a.n_plans : num_sms * 8;
+        if (grid > 0) k_mv_tours_plan<<<grid, MVT_THREADS, sizeof(int32_t) * (size_t)a.n_orders, s>>>(M);
+    } else if (a.n_tours > 0) {
+        k_mv_tours<<<grid_of(a.n_tours, 256), 256, 0, s>>>(M);
+    }
     if (a.n_lines > 0) k_mv_sku_count<<<grid_of(a.n_lines, 256), 256, 0, s>>>(M);
     k_mv_sku_scan<<<1, 1024, 0, s>>>(M);
     if (a.n_orders > 0) k_mv_sku_fill<<<grid_of(a.n_orders, 256), 256, 0, s>>>(M);

@@ -44,6 +44,11 @@ struct wh_layout {
     const int64_t* last_task_off = nullptr;
     const int4* last_tasks = nullptr;
     const int2* last_task_cost = nullptr;
+    // the last wh_surrogate_screen call's task list, counted flags and rows
+    int64_t screen_n_tasks = 0;
+    const int4* screen_tasks = nullptr;
+    const int2* screen_counted = nullptr;
+    const uint16_t* screen_rows = nullptr;
     KernelTiming timing;                   // wh_set_timing
 };
 
@@ -351,6 +356,11 @@ namespace {
 int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int32_t* moves, int32_t n_moves,
                   int32_t max_orders, int32_t max_lines, int64_t* delta, int32_t* status, wh::MoveArgs& M,
                   cudaStream_t s) {
+    // the scratch is about to be reused: the last screen's trace goes stale
+    h->screen_n_tasks = 0;
+    h->screen_tasks = nullptr;
+    h->screen_counted = nullptr;
+    h->screen_rows = nullptr;
     std::memset(&M, 0, sizeof(M));
     wh_costs none;
     std::memset(&none, 0, sizeof(none));
@@ -387,7 +397,7 @@ int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int
     M.task_off = reinterpret_cast<int64_t*>(base + off[5]);
     M.scan_aux = reinterpret_cast<int64_t*>(base + off[6]);
 
-    if (wh::launch_moves_prepare(M, s) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_moves_prepare(M, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
     int64_t n_tasks = 0;
     if (cudaMemcpyAsync(&n_tasks, M.task_off + n_moves, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -563,6 +573,10 @@ extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orde
         }
     }
     if (wh::launch_task_features(M, c, X_task, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    h->screen_n_tasks = M.n_tasks;
+    h->screen_tasks = M.tasks;
+    h->screen_counted = M.task_cost;
+    h->screen_rows = X_task;
     rc = wh_surrogate_predict(sg, X_task, M.n_tasks, y_task, stream);
     if (rc != WH_OK) return rc;
     wh::ScreenArgs S;
@@ -574,6 +588,16 @@ extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orde
     S.keep = keep;
     S.kept = reinterpret_cast<int4*>(kept);
     return wh::launch_screen_select(S, s) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
+extern "C" int wh_surrogate_screen_trace(wh_layout* h, int64_t* n_tasks, const int32_t** tasks, const int32_t** counted,
+                                         const uint16_t** features) {
+    if (!h || !n_tasks || !tasks || !counted || !features) return WH_EINVAL;
+    *n_tasks = h->screen_n_tasks;
+    *tasks = reinterpret_cast<const int32_t*>(h->screen_tasks);
+    *counted = reinterpret_cast<const int32_t*>(h->screen_counted);
+    *features = h->screen_rows;
+    return WH_OK;
 }
 
 extern "C" int wh_ls_apply(wh_layout* h, const wh_orders* orders, const wh_plans* plans, const int32_t* moves,

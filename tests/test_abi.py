@@ -129,6 +129,13 @@ def test_next_row_entry_points_host_checks(lib):
     assert occ(wh.wh_plans(1, 2, 4, 48, 600, 64, 80, 96, 0)) == wh.WH_EINVAL      # no bit array
     assert occ(wh.wh_plans(0, 0, 0, 48, 600, 64, 80, 96, 0)) == wh.WH_OK          # no plans
     assert lib.wh_occupancy(None, ctypes.byref(o), ctypes.byref(p), None) == wh.WH_EINVAL
+    # screen diagnostics: nothing screened on a fresh layout
+    n_t, pt, pc, pf = ctypes.c_int64(7), ctypes.c_void_p(1), ctypes.c_void_p(1), ctypes.c_void_p(1)
+    assert lib.wh_surrogate_screen_trace(h, ctypes.byref(n_t), ctypes.byref(pt), ctypes.byref(pc),
+                                         ctypes.byref(pf)) == wh.WH_OK
+    assert n_t.value == 0 and not pt.value and not pc.value and not pf.value
+    assert lib.wh_surrogate_screen_trace(None, ctypes.byref(n_t), ctypes.byref(pt), ctypes.byref(pc),
+                                         ctypes.byref(pf)) == wh.WH_EINVAL
     # widening
     assert lib.wh_widen_u16(P(16), P(16), -1, None) == wh.WH_EINVAL
     assert lib.wh_widen_u16(None, P(16), 8, None) == wh.WH_EINVAL

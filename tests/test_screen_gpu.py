@@ -72,6 +72,50 @@ def moved_tours(inst, smap, mv):
     return [(lines(tours[t], m2), t) for t in sorted(hit)]
 
 
+@pytest.mark.parametrize("which", ["tiny", "paperscale"])
+def test_screen_task_features_bit_exact(gpu_lib, which):
+    """Every counted task's feature row (its changed tour under the move,
+    rebuilt here from the move's definition) equals the oracle's features bit
+    for bit: a tiny layout (16-bit keys, one task per thread) and paper scale
+    (32-bit keys; tasks over 64 lines go to the warp-per-task kernel)."""
+    import torch
+    wh = gpu_lib
+    tiny = which == "tiny"
+    inst = wh_gen.tiny(seed=22, n_plans=5) if tiny else wh_gen.paperscale(seed=21, n_plans=3)
+    lay, prob, costs = setup(wh, inst)
+    sg = wh.Surrogate(3)
+    M = 32 if tiny else 24
+    mv = moves_for(inst, 5, 0, M)
+    lay.screen(sg, prob, mv, M, 4, 8 if tiny else 0)
+    torch.cuda.synchronize()
+    assert lay.status() == 0
+    tasks, counted, rows = lay.screen_trace()
+    tasks, counted = tasks.cpu().numpy(), counted.cpu().numpy()
+    bits = rows.view(torch.int16).cpu().numpy()
+    mvn = mv.cpu().numpy()
+    changed, n_checked, n_long = {}, 0, 0
+    for i in range(tasks.shape[0]):
+        if counted[i, 0] != 0:
+            continue
+        m, t = int(tasks[i, 0]), int(tasks[i, 1])
+        if m not in changed:
+            changed[m] = {t_old: locs for locs, t_old in moved_tours(inst, inst.slot_map, mvn[m])}
+        locs = changed[m][t]
+        want = torch.from_numpy(oracle.bf16(oracle.features(inst.layout, locs))).to(torch.bfloat16)
+        assert np.array_equal(bits[i], want.view(torch.int16).numpy()), (which, i, m, t)
+        n_checked += 1
+        n_long += len(locs) > 64
+    assert n_checked >= 40
+    if not tiny:
+        assert n_long >= 5
+    # any other call on the layout leaves no trace
+    lay.eval_moves(prob, costs, mv)
+    torch.cuda.synchronize()
+    assert lay.screen_trace() is None
+    sg.close()
+    lay.close()
+
+
 def test_screen_keeps_lowest_predicted_deltas(gpu_lib):
     import torch
     wh = gpu_lib
