@@ -1245,7 +1245,7 @@ def run_reference(args):
 
 
 def run_case(name):
-    """Small cases for profiler captures: 128 batched instances x 64 plans,
+    """Small cases for profiler captures: 256 batched instances x 64 plans,
     paper-scale move deltas on 1,024 plans x 64 moves, or the surrogate's
     kernels (features, prescreen, tensor-core inference)."""
     import numpy as np
@@ -1279,20 +1279,18 @@ def run_case(name):
         assert lay.status() == 0
         lay.close()
     elif name == "batched-small":
-        items = []
-        for i in range(128):
-            inst = wh_gen.batched_instance(3, i, n_plans=64)
-            lay = inst.layout
-            prob = wh.to_device(inst)
-            items.append(((lay.n_aisles, lay.slots_per_side, lay.aisle_pitch, lay.slot_pitch, lay.cross_aisle_width),
-                          prob, wh.alloc_costs(prob.n_tours, prob.n_plans)))
-        b = wh.Batch(items)
-        b.set_tuning(384, 16, 1)   # the headline's CTA size; items small enough to fill the GPU
+        # 256 instances of the headline's generator x 64 plans through the
+        # same packed device set (16-bit order ids read directly) and CTA
+        # size as the headline; work items of 64 chunks fill the GPU
+        insts = [wh_gen.batched_instance(3, i, n_plans=64) for i in range(256)]
+        d = wh.PackedInstances(insts).device_set()
+        d.load()
+        d.batch.set_tuning(384, 64, 1)
         for _ in range(3):
-            b.eval(3)
+            d.batch.eval(3)
         torch.cuda.synchronize()
-        assert b.status() == 0
-        b.close()
+        assert d.batch.status() == 0
+        d.close()
     elif name == "surrogate-small":
         # features of every tour of 1,024 paper-scale plans, one prescreen of
         # 64 moves per plan, and inference on 1M feature rows (384 MB, above L2)
