@@ -20,9 +20,11 @@ constexpr int LONG_MAXL = WH_MAX_TOUR_LINES;
 
 __device__ __forceinline__ void flag(uint32_t* status, uint32_t bit) { atomicOr(status, bit); }
 
+// location (0 <= loc < n_loc) -> aisle << 16 | slot index; the division by 2L
+// is the multiply-high form set up in Geo (one multiply and one shift)
 __device__ __forceinline__ uint32_t loc_key(const Geo& g, int loc) {
     const int two_l = 2 * g.L;
-    const int a = loc / two_l;
+    const int a = (int)(__umulhi((uint32_t)loc, g.div_m) >> g.div_s);
     const int r = loc - a * two_l;          // side*L + k
     const int k = r >= g.L ? r - g.L : r;
     return ((uint32_t)a << 16) | (uint32_t)k;

@@ -174,6 +174,7 @@ int check_desc(const wh_layout_desc& d, wh::Geo* g) {
     g->h = d.cross_aisle_width / 2;
     g->Y = (int32_t)Y;
     g->n_loc = d.n_aisles * 2 * d.slots_per_side;
+    wh::geo_set_div(*g);
     return WH_OK;
 }
 

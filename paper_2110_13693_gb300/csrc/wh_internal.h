@@ -19,7 +19,22 @@ struct Geo {
     int32_t h;      // W/2: depth of slot 0
     int32_t Y;      // back cross-aisle depth
     int32_t n_loc;  // A*2*L
+    // exact division of a location (0 <= loc < 2^31) by 2L:
+    // loc / 2L = umulhi(loc, div_m) >> div_s (Granlund & Montgomery,
+    // "Division by invariant integers using multiplication", 1994: with
+    // l = ceil(log2 2L) and div_m = ceil(2^(31+l) / 2L) < 2^32 the quotient is
+    // exact for every numerator below 2^31); set by geo_set_div
+    uint32_t div_m;
+    int32_t div_s;
 };
+
+inline void geo_set_div(Geo& g) {
+    const uint64_t d = 2ull * (uint64_t)g.L;
+    int l = 0;
+    while ((1ull << l) < d) ++l;   // ceil(log2 d); d >= 2
+    g.div_m = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+    g.div_s = l - 1;
+}
 
 struct EvalArgs {
     Geo g;

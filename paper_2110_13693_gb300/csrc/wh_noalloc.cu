@@ -101,6 +101,7 @@ extern "C" int wh_eval_plans_noalloc(const wh_layout_desc* desc, const wh_orders
     a.g.h = d.cross_aisle_width / 2;
     a.g.Y = (int32_t)Y;
     a.g.n_loc = d.n_aisles * 2 * d.slots_per_side;
+    wh::geo_set_div(a.g);
     a.n_orders = o.n_orders;
     a.n_lines = o.n_lines;
     a.n_sku = o.n_sku;
