@@ -195,9 +195,10 @@ int wh_eval_moves(wh_layout *layout, const wh_orders *orders, const wh_plans *pl
  * SKU swap exchanges two entries of the plan's slotting; a relocation sets the
  * SKU's entry and, with plans->loc_used, moves its occupancy bit.  costs (may be NULL):
  * the plans' current per-tour and per-plan costs, updated in place for the
- * applied moves from the new tour costs that the wh_eval_moves call which
- * scored exactly these moves (same `moves` pointer, the last move evaluation
- * on this handle) computed -- no full re-evaluation is needed; when NULL the
+ * applied moves from the new tour costs that the wh_eval_moves (or
+ * wh_surrogate_screen_eval) call which scored exactly these moves (same
+ * `moves` pointer, the last move evaluation on this handle) computed -- no
+ * full re-evaluation is needed; when NULL the
  * costs are left stale (refresh them with wh_eval_plans).  tour_changed (device,
  * one byte per tour, may be NULL; needs costs): set to 1 for every tour an
  * applied move rewrote, for wh_surrogate_screen's prediction cache; other
@@ -412,6 +413,23 @@ int wh_surrogate_screen(wh_layout *layout, wh_surrogate *s, const wh_orders *ord
                         const int32_t *moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders_per_tour,
                         int32_t max_lines_per_tour, float *y_tour_cache, uint8_t *tour_changed, int32_t *kept,
                         void *stream);
+
+/* The prescreen of wh_surrogate_screen followed by the exact scores of the
+ * kept moves, as one call: kept [n_plans * keep][4] as wh_surrogate_screen
+ * writes it, and its move deltas kept_delta [n_plans * keep][2] (int64) and
+ * statuses kept_status [n_plans * keep] (int32) exactly as wh_eval_moves on
+ * `kept` with the current tour costs tour_s / tour_rr would give them.  The
+ * exact pass reuses the prescreen's per-plan order -> tour table and SKU ->
+ * orders index (the plans do not change inside the call) instead of building
+ * them again.  The result feeds wh_ls_apply like that wh_eval_moves call would
+ * (pass `kept` as its moves and `keep` as moves_per_plan).  Synchronises
+ * `stream` as the two calls do.  Returns as wh_surrogate_screen, WH_EINVAL also
+ * for a NULL tour_s, tour_rr, kept_delta or kept_status. */
+int wh_surrogate_screen_eval(wh_layout *layout, wh_surrogate *s, const wh_orders *orders, const wh_plans *plans,
+                             const int32_t *moves, int32_t moves_per_plan, int32_t keep,
+                             int32_t max_orders_per_tour, int32_t max_lines_per_tour, float *y_tour_cache,
+                             uint8_t *tour_changed, const int32_t *tour_s, const int32_t *tour_rr, int32_t *kept,
+                             int64_t *kept_delta, int32_t *kept_status, void *stream);
 
 /* Diagnostics of the last wh_surrogate_screen call on `layout` (device
  * pointers into the layout's scratch, valid until its next call; all NULL and

@@ -110,6 +110,11 @@ SIGNATURES = {
                                            ctypes.POINTER(wh_plans), ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "wh_surrogate_screen_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(wh_orders),
+                                                ctypes.POINTER(wh_plans), ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "wh_surrogate_screen_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                                  ctypes.POINTER(ctypes.c_void_p)]),
@@ -441,6 +446,35 @@ class Layout:
                             keep, max_orders, max_lines, _ptr(kept), None if y_tour is None else _ptr(y_tour),
                             None if changed is None else _ptr(changed), stream)
         return kept[:prob.n_plans * keep]
+
+    def screen_eval(self, surrogate: "Surrogate", prob: DeviceProblem, costs: Costs, moves, moves_per_plan: int,
+                    keep: int, max_orders: int = 0, max_lines: int = 0, stream=None, y_tour=None, changed=None):
+        """screen() and the exact scores of the kept moves in one call:
+        (kept int32 [n_plans * keep, 4], delta int64 [n, 2], status int32 [n]),
+        the scores as eval_moves(kept) gives them; pass them to apply_scored."""
+        import torch
+        mv = moves.reshape(-1, 4).contiguous()
+        n = max(prob.n_plans * keep, 1)
+        kept = torch.empty((n, 4), dtype=torch.int32, device=mv.device)
+        delta = torch.empty((n, 2), dtype=torch.int64, device=mv.device)
+        status = torch.empty(n, dtype=torch.int32, device=mv.device)
+        wh_surrogate_screen_eval(self.handle, surrogate.handle, prob.orders(), prob.plans(), _ptr(mv), moves_per_plan,
+                                 keep, max_orders, max_lines, None if y_tour is None else _ptr(y_tour),
+                                 None if changed is None else _ptr(changed), _ptr(costs.tour_s), _ptr(costs.tour_rr),
+                                 _ptr(kept), _ptr(delta), _ptr(status), stream)
+        k = prob.n_plans * keep
+        return kept[:k], delta[:k], status[:k]
+
+    def apply_scored(self, prob: DeviceProblem, costs: Costs, moves, moves_per_plan: int, delta, status,
+                     stream=None, changed=None):
+        """Apply each plan's best improving move of `moves` scored by the last
+        move evaluation on this layout (eval_moves or screen_eval of exactly
+        these moves), costs updated incrementally.  Returns applied [n_plans]."""
+        import torch
+        applied = torch.empty(max(prob.n_plans, 1), dtype=torch.int32, device=moves.device)
+        wh_ls_apply(self.handle, prob.orders(), prob.plans(), _ptr(moves), moves_per_plan, _ptr(delta), _ptr(status),
+                    _ptr(applied), costs.c(), None if changed is None else _ptr(changed), stream)
+        return applied[:prob.n_plans]
 
     def screen_trace(self):
         """The last screen's tasks (int32 [n, 4]: move, changed tour, two
@@ -911,6 +945,17 @@ def wh_surrogate_screen(layout, s, orders: wh_orders, plans: wh_plans, moves, mo
                                       moves_per_plan, keep, max_orders, max_lines, ctypes.c_void_p(y_tour),
                                       ctypes.c_void_p(tour_changed), ctypes.c_void_p(kept), _stream_ptr(stream)),
            "wh_surrogate_screen")
+
+
+def wh_surrogate_screen_eval(layout, s, orders: wh_orders, plans: wh_plans, moves, moves_per_plan: int, keep: int,
+                             max_orders: int, max_lines: int, y_tour_cache, tour_changed, tour_s, tour_rr, kept,
+                             kept_delta, kept_status, stream=None) -> None:
+    _check(load().wh_surrogate_screen_eval(layout, s, ctypes.byref(orders), ctypes.byref(plans),
+                                           ctypes.c_void_p(moves), moves_per_plan, keep, max_orders, max_lines,
+                                           ctypes.c_void_p(y_tour_cache), ctypes.c_void_p(tour_changed),
+                                           ctypes.c_void_p(tour_s), ctypes.c_void_p(tour_rr), ctypes.c_void_p(kept),
+                                           ctypes.c_void_p(kept_delta), ctypes.c_void_p(kept_status),
+                                           _stream_ptr(stream)), "wh_surrogate_screen_eval")
 
 
 def wh_surrogate_screen_trace(layout):

@@ -694,8 +694,20 @@ __global__ void k_occupancy(const int32_t* slot_map, int64_t stride, int32_t n_p
 
 }  // namespace
 
-cudaError_t launch_moves_prepare(const MoveArgs& M, int num_sms, cudaStream_t s) {
+cudaError_t launch_moves_prepare(const MoveArgs& M, int num_sms, cudaStream_t s, bool reuse_index) {
     const EvalArgs& a = M.a;
+    if (reuse_index) {
+        // the order -> tour table, the tours' line counts and the SKU ->
+        // orders index of the same plans are in place: only the moves' checks,
+        // task counts and their scan
+        k_mv_count<<<grid_of(M.n_moves, 256), 256, 0, s>>>(M);
+        const int64_t n = (int64_t)M.n_moves + 1;
+        const int nb = (int)((n + SCAN_T - 1) / SCAN_T);
+        k_scan_blocks<<<nb, SCAN_T, 0, s>>>(M.task_off, n, M.scan_aux);
+        k_scan_top<<<1, SCAN_T, 0, s>>>(M.scan_aux, nb);
+        k_scan_add<<<nb, SCAN_T, 0, s>>>(M.task_off, n, M.scan_aux);
+        return cudaGetLastError();
+    }
     const bool per_plan = a.n_orders <= MVT_MAX_ORDERS;
     if (!per_plan &&
         cudaMemsetAsync(M.order_tour, 0xFF, sizeof(int32_t) * (size_t)a.n_plans * (size_t)a.n_orders, s) != cudaSuccess)

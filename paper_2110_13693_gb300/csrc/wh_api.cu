@@ -354,9 +354,12 @@ namespace {
 
 // Scratch, index structures and the task list of a move evaluation (up to
 // and including the task fill).  Synchronises `s` once to size the list.
+// reuse_index: the order -> tour table, tour line counts and SKU -> orders
+// index that the previous preparation on this handle built for the same
+// plans and order book are used as they are (within one call only).
 int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int32_t* moves, int32_t n_moves,
                   int32_t max_orders, int32_t max_lines, int64_t* delta, int32_t* status, wh::MoveArgs& M,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool reuse_index = false) {
     // the scratch is about to be reused: the last screen's trace goes stale
     h->screen_n_tasks = 0;
     h->screen_tasks = nullptr;
@@ -387,6 +390,9 @@ int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int
         off[i] = total;
         total += align_up(sizes[i]);
     }
+    // reusing the index: the previous preparation's buffers must stay where
+    // they are (the kept set is never larger than the screened one)
+    if (reuse_index && total > h->mv_scratch_bytes) return WH_EINVAL;
     int rc = grow(&h->mv_scratch, &h->mv_scratch_bytes, total);
     if (rc != WH_OK) return rc;
     char* base = static_cast<char*>(h->mv_scratch);
@@ -398,7 +404,7 @@ int prepare_moves(wh_layout* h, const wh_orders& o, const wh_plans& p, const int
     M.task_off = reinterpret_cast<int64_t*>(base + off[5]);
     M.scan_aux = reinterpret_cast<int64_t*>(base + off[6]);
 
-    if (wh::launch_moves_prepare(M, h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    if (wh::launch_moves_prepare(M, h->num_sms, s, reuse_index) != cudaSuccess) return WH_ECUDA;
     int64_t n_tasks = 0;
     if (cudaMemcpyAsync(&n_tasks, M.task_off + n_moves, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -479,25 +485,16 @@ extern "C" int wh_eval_moves(wh_layout* h, const wh_orders* orders, const wh_pla
     return WH_OK;
 }
 
-extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orders* orders, const wh_plans* plans,
-                                   const int32_t* moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders,
-                                   int32_t max_lines, float* y_tour_cache, uint8_t* tour_changed, int32_t* kept,
-                                   void* stream) {
-    if (!h || !sg || !orders || !plans || !moves || !kept || moves_per_plan < 1 || moves_per_plan > 256 ||
-        keep < 1 || keep > moves_per_plan || max_orders < 0 || max_lines < 0 || (tour_changed && !y_tour_cache))
-        return WH_EINVAL;
-    const wh_orders o = *orders;
-    const wh_plans p = *plans;
-    int rc = check_problem(o, p);
-    if (rc != WH_OK) return rc;
-    if (h->g.L > 256) return WH_ERANGE;
-    if (p.n_plans == 0) return WH_OK;
-    const int64_t n_moves64 = (int64_t)p.n_plans * moves_per_plan;
-    if (n_moves64 > 0x7fffffff) return WH_ERANGE;
-    const int32_t n_moves = (int32_t)n_moves64;
-    rc = bind_device(h);
-    if (rc != WH_OK) return rc;
+namespace {
+
+// The prescreen of wh_surrogate_screen after its argument checks (n_plans >= 1,
+// device bound): index, task list, features, predictions, selection.
+int screen_moves(wh_layout* h, wh_surrogate* sg, const wh_orders& o, const wh_plans& p, const int32_t* moves,
+                 int32_t moves_per_plan, int32_t keep, int32_t max_orders, int32_t max_lines, float* y_tour_cache,
+                 uint8_t* tour_changed, int32_t* kept, void* stream) {
+    const int32_t n_moves = (int32_t)((int64_t)p.n_plans * moves_per_plan);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = WH_OK;
     h->last_moves = nullptr;
     // per-move status and the task list (into the screening scratch's delta/status)
     const size_t feat_row = sizeof(uint16_t) * WH_FEATURES;
@@ -589,6 +586,70 @@ extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orde
     S.keep = keep;
     S.kept = reinterpret_cast<int4*>(kept);
     return wh::launch_screen_select(S, s) == cudaSuccess ? WH_OK : WH_ECUDA;
+}
+
+int screen_args_ok(wh_layout* h, wh_surrogate* sg, const wh_orders* orders, const wh_plans* plans,
+                   const int32_t* moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders, int32_t max_lines,
+                   const float* y_tour_cache, const uint8_t* tour_changed, const int32_t* kept) {
+    if (!h || !sg || !orders || !plans || !moves || !kept || moves_per_plan < 1 || moves_per_plan > 256 ||
+        keep < 1 || keep > moves_per_plan || max_orders < 0 || max_lines < 0 || (tour_changed && !y_tour_cache))
+        return WH_EINVAL;
+    int rc = check_problem(*orders, *plans);
+    if (rc != WH_OK) return rc;
+    if (h->g.L > 256) return WH_ERANGE;
+    if ((int64_t)plans->n_plans * moves_per_plan > 0x7fffffff) return WH_ERANGE;
+    return WH_OK;
+}
+
+}  // namespace
+
+extern "C" int wh_surrogate_screen(wh_layout* h, wh_surrogate* sg, const wh_orders* orders, const wh_plans* plans,
+                                   const int32_t* moves, int32_t moves_per_plan, int32_t keep, int32_t max_orders,
+                                   int32_t max_lines, float* y_tour_cache, uint8_t* tour_changed, int32_t* kept,
+                                   void* stream) {
+    int rc = screen_args_ok(h, sg, orders, plans, moves, moves_per_plan, keep, max_orders, max_lines, y_tour_cache,
+                            tour_changed, kept);
+    if (rc != WH_OK) return rc;
+    if (plans->n_plans == 0) return WH_OK;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    return screen_moves(h, sg, *orders, *plans, moves, moves_per_plan, keep, max_orders, max_lines, y_tour_cache,
+                        tour_changed, kept, stream);
+}
+
+extern "C" int wh_surrogate_screen_eval(wh_layout* h, wh_surrogate* sg, const wh_orders* orders,
+                                        const wh_plans* plans, const int32_t* moves, int32_t moves_per_plan,
+                                        int32_t keep, int32_t max_orders, int32_t max_lines, float* y_tour_cache,
+                                        uint8_t* tour_changed, const int32_t* tour_s, const int32_t* tour_rr,
+                                        int32_t* kept, int64_t* kept_delta, int32_t* kept_status, void* stream) {
+    int rc = screen_args_ok(h, sg, orders, plans, moves, moves_per_plan, keep, max_orders, max_lines, y_tour_cache,
+                            tour_changed, kept);
+    if (rc != WH_OK) return rc;
+    if (plans->n_plans == 0) return WH_OK;
+    if (!tour_s || !tour_rr || !kept_delta || !kept_status) return WH_EINVAL;
+    rc = bind_device(h);
+    if (rc != WH_OK) return rc;
+    rc = screen_moves(h, sg, *orders, *plans, moves, moves_per_plan, keep, max_orders, max_lines, y_tour_cache,
+                      tour_changed, kept, stream);
+    if (rc != WH_OK) return rc;
+    // the kept moves scored exactly on the prescreen's index (the same plans):
+    // checks, task counts, task list, short and long tasks
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int32_t n_kept = plans->n_plans * keep;
+    wh::MoveArgs M;
+    rc = prepare_moves(h, *orders, *plans, kept, n_kept, max_orders, max_lines, kept_delta, kept_status, M, s, true);
+    if (rc != WH_OK) return rc;
+    M.tour_s_old = tour_s;
+    M.tour_rr_old = tour_rr;
+    if (wh::launch_moves_eval(M, wh::key16_ok(h->g), h->num_sms, s) != cudaSuccess) return WH_ECUDA;
+    rc = eval_long_tasks(h, M, s);
+    if (rc != WH_OK) return rc;
+    h->last_moves = kept;
+    h->last_n_moves = n_kept;
+    h->last_task_off = M.task_off;
+    h->last_tasks = M.tasks;
+    h->last_task_cost = M.task_cost;
+    return WH_OK;
 }
 
 extern "C" int wh_surrogate_screen_trace(wh_layout* h, int64_t* n_tasks, const int32_t** tasks, const int32_t** counted,

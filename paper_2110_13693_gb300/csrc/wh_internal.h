@@ -233,7 +233,10 @@ cudaError_t launch_task_features(const MoveArgs& M, const FeatConst& c, void* X,
 cudaError_t launch_screen_select(const ScreenArgs& S, cudaStream_t s);
 
 cudaError_t launch_ls_apply(const LsArgs& L, cudaStream_t s);
-cudaError_t launch_moves_prepare(const MoveArgs& M, int num_sms, cudaStream_t s);
+// the moves' index (order -> tour per plan, tour line counts, SKU -> orders),
+// checks, task counts and offsets; reuse_index: the index of the same plans
+// and order book is already in M's buffers, only the rest runs
+cudaError_t launch_moves_prepare(const MoveArgs& M, int num_sms, cudaStream_t s, bool reuse_index);
 // task fill + tasks of <= SHORT_MAX lines; the long ones are listed
 cudaError_t launch_moves_eval(const MoveArgs& M, bool k16, int num_sms, cudaStream_t s);
 // the listed long tasks (records, then their DPs) and the final status pass

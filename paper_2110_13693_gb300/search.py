@@ -23,12 +23,15 @@ def plain_step(lay, prob, costs, moves, M, max_orders=0, max_lines=0):
 
 
 def screened_step(lay, sg, prob, costs, moves, M, keep, max_orders=0, max_lines=0, cache=None):
-    """Prescreen the moves, then score the kept ones exactly and apply the best.
-    cache: (y_tour, changed) device tensors that carry the current tours'
-    predictions from step to step (only the rewritten tours are re-predicted)."""
+    """Prescreen the moves, then score the kept ones exactly and apply the best
+    (one call for the prescreen and the exact scores, which share the moves'
+    index).  cache: (y_tour, changed) device tensors that carry the current
+    tours' predictions from step to step (only the rewritten tours are
+    re-predicted)."""
     y_tour, changed = cache if cache is not None else (None, None)
-    kept = lay.screen(sg, prob, moves, M, keep, max_orders, max_lines, y_tour=y_tour, changed=changed)
-    return lay.ls_step(prob, costs, kept, keep, max_orders, max_lines, changed=changed)
+    kept, delta, status = lay.screen_eval(sg, prob, costs, moves, M, keep, max_orders, max_lines, y_tour=y_tour,
+                                          changed=changed)
+    return lay.apply_scored(prob, costs, kept, keep, delta, status, changed=changed)
 
 
 def new_cache(prob):

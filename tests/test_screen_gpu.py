@@ -116,6 +116,68 @@ def test_screen_task_features_bit_exact(gpu_lib, which):
     lay.close()
 
 
+@pytest.mark.parametrize("which", ["paperscale", "relocations"])
+def test_screen_eval_equals_screen_then_eval_moves(gpu_lib, which):
+    """The one-call prescreen and exact re-score (the exact pass on the
+    prescreen's index) gives the kept moves, deltas and statuses that the
+    prescreen followed by eval_moves on the kept moves gives, and applying them
+    leaves the same plans, costs and changed-tour flags, step after step: paper
+    scale (per-plan slottings, all order and SKU moves, tasks over 64 lines)
+    and relocations into empty locations."""
+    import torch
+    wh = gpu_lib
+    if which == "paperscale":
+        inst = wh_gen.paperscale(seed=21, n_plans=12)
+        M, max_orders = 32, 24
+        moves = lambda step: moves_for(inst, 7, step, M)
+    else:
+        base = wh_gen.tiny(seed=24, n_plans=4)
+        lay_d = wh_gen.Layout(20, 30)
+        smap = np.random.default_rng(24).permutation(lay_d.n_loc)[:base.n_sku].astype(np.int32)
+        inst = wh_gen.Instance(lay_d, base.n_sku, base.order_off, base.line_sku, smap, base.plan_tour_off,
+                               base.tour_off, base.order_seq)
+        M, max_orders = 32, 8
+
+        def moves(step):
+            mv = np.concatenate([wh_gen.gen_moves(6, step, inst, M // 2),
+                                 wh_gen.gen_relocations(7, step, inst, M // 2)], axis=1)
+            mv[..., 3] = np.arange(inst.n_plans)[:, None]
+            return torch.as_tensor(mv.reshape(-1, 4)).cuda()
+    a, b = setup(wh, inst), setup(wh, inst)
+    if which != "paperscale":
+        a[0].occupancy(a[1])
+        b[0].occupancy(b[1])
+    sg = wh.Surrogate(3)
+    keep = 4
+    ca, cb = search.new_cache(a[1]), search.new_cache(b[1])
+    for step in range(3):
+        mv = moves(step)
+        kept_a, d_a, s_a = a[0].screen_eval(sg, a[1], a[2], mv, M, keep, max_orders, y_tour=ca[0], changed=ca[1])
+        kept_b = b[0].screen(sg, b[1], mv, M, keep, max_orders, y_tour=cb[0], changed=cb[1])
+        d_b, s_b = b[0].eval_moves(b[1], b[2], kept_b, max_orders)
+        torch.cuda.synchronize()
+        assert torch.equal(kept_a, kept_b) and torch.equal(d_a, d_b) and torch.equal(s_a, s_b), step
+        assert (s_a == 0).sum() > 0
+        ra = a[0].apply_scored(a[1], a[2], kept_a, keep, d_a, s_a, changed=ca[1])
+        rb = b[0].ls_step(b[1], b[2], kept_b, keep, max_orders, changed=cb[1])
+        torch.cuda.synchronize()
+        assert torch.equal(ra, rb) and (ra >= 0).sum() > 0
+        for x, y in ((a[1].order_seq, b[1].order_seq), (a[1].tour_off, b[1].tour_off),
+                     (a[1].slot_map, b[1].slot_map), (ca[1], cb[1])):
+            assert torch.equal(x, y)
+        n_t, n_p = a[1].n_tours, a[1].n_plans
+        for x, y in ((a[2].tour_s[:n_t], b[2].tour_s[:n_t]), (a[2].tour_rr[:n_t], b[2].tour_rr[:n_t]),
+                     (a[2].plan_s[:n_p], b[2].plan_s[:n_p]), (a[2].plan_rr[:n_p], b[2].plan_rr[:n_p])):
+            assert torch.equal(x, y)
+    # the incrementally updated costs are the exact costs of the edited plans
+    fresh = wh.evaluate(a[0], a[1])
+    torch.cuda.synchronize()
+    assert torch.equal(fresh.plan_rr[:a[1].n_plans], a[2].plan_rr[:a[1].n_plans])
+    assert torch.equal(fresh.plan_s[:a[1].n_plans], a[2].plan_s[:a[1].n_plans])
+    assert a[0].status() == 0 and b[0].status() == 0
+    sg.close()
+
+
 def test_screen_keeps_lowest_predicted_deltas(gpu_lib):
     import torch
     wh = gpu_lib
