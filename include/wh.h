@@ -530,8 +530,10 @@ int wh_batch_eval(wh_batch *b, uint32_t routing_mask, void *stream);
 int wh_batch_eval_graph(wh_batch *b, uint32_t routing_mask, void *stream);
 
 /* Autotuner: time candidate launch shapes (CTA size 128, 256 or, with 16-bit
- * keys, 384 x 2 to 4,096 chunks of 32 tours per work item) on this batch with
- * the given mask, keep the fastest and report it.  When
+ * keys, 384 x 2 to 4,096 chunks of 32 tours per work item, powers of two,
+ * and for 384 threads also 12 to 1,536 chunks, multiples of its 12 warps, which
+ * split an item evenly over them) on this batch with the given mask, keep the
+ * fastest and report it.  When
  * cache_path is not NULL the choice is looked up first, and stored after, in
  * that JSON file under a key built from the batch's size bucket (key width,
  * instance count, total tours, largest order book, mask).  Synchronises

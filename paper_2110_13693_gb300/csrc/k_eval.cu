@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(KEY16 ? 384 : 256, 2) k_eval_batch(BatchArgs b
 constexpr int LONG_RMAX = 48;   // records per tour kept for the per-lane DP
 
 template <bool SHARED_MAP>
-__global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
+__global__ void __launch_bounds__(LONG_WARPS * 32, 6) k_eval_long(LongArgs L) {
     __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
     __shared__ int s_meta[LONG_WARPS][32][4];   // inst, tour, plan, record count (-1: done)
     __shared__ uint32_t s_last[LONG_WARPS][32];  // largest key of the tour
@@ -785,17 +785,48 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
         if (a.plan_rr && need_rr)
             atomicAdd(reinterpret_cast<unsigned long long*>(&a.plan_rr[plan]), (unsigned long long)cr);
     };
-    // this warp's tours: gw, gw + n_warps, ..., taken 32 at a time
+    // The warp's tours are gw, gw + n_warps, gw + 2 n_warps, ..., taken 32 at
+    // a time.  Their headers are fetched ahead, so that the chain list entry
+    // -> tour offsets -> order ids does not stall every tour: list entries
+    // two tours ahead, offsets one tour ahead (at the start of a tour) and
+    // the next tour's first 32 order ids once this tour's lines are gathered.
+    auto list_of = [&](int w, int& inst, int& t, int& plan) {
+        inst = L.list[3 * w];
+        t = L.list[3 * w + 1];
+        plan = L.list[3 * w + 2];
+    };
+    auto offs_of = [&](int inst, int t, int& q0, int& q1) {
+        const int32_t* to = L.insts ? L.insts[inst].tour_off : L.single.tour_off;
+        q0 = to[t];   // checked by the short kernel
+        q1 = to[t + 1];
+    };
+    auto id_of = [&](int inst, int q) {
+        const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
+        return a.order_seq16 ? (int)a.order_seq16[q] : a.order_seq[q];
+    };
+    int c_inst = 0, c_t = 0, c_plan = 0, c_q0 = 0, c_q1 = 0, c_o = 0;   // the next tour
+    int n_inst = 0, n_t = 0, n_plan = 0;                                 // the one after
+    if (gw < count) {
+        list_of(gw, c_inst, c_t, c_plan);
+        offs_of(c_inst, c_t, c_q0, c_q1);
+        c_o = c_q0 + lane < c_q1 ? id_of(c_inst, c_q0 + lane) : 0;
+    }
+    if (gw + n_warps < count) list_of(gw + n_warps, n_inst, n_t, n_plan);
     for (int w0 = gw; w0 < count; w0 += 32 * n_warps) {
         int in_group = 0;
         for (int j = 0; j < 32; ++j) {
             const int w = w0 + j * n_warps;
             if (w >= count) break;
             in_group = j + 1;
-            const int inst = L.list[3 * w], t = L.list[3 * w + 1], plan = L.list[3 * w + 2];
+            const int inst = c_inst, t = c_t, plan = c_plan, q0 = c_q0, q1 = c_q1, o_first = c_o;
+            const bool more1 = w + n_warps < count;
+            c_inst = n_inst;
+            c_t = n_t;
+            c_plan = n_plan;
+            if (more1) offs_of(c_inst, c_t, c_q0, c_q1);
+            if (w + 2 * n_warps < count) list_of(w + 2 * n_warps, n_inst, n_t, n_plan);
             const EvalArgs& a = L.insts ? L.insts[inst] : L.single;
             KeySrc src = global_src(a);
-            const int q0 = a.tour_off[t], q1 = a.tour_off[t + 1];   // checked by the short kernel
             if constexpr (!SHARED_MAP) src.map = a.slot_map + (int64_t)plan * a.slot_stride;
             int n = 0;
             bool bad = false;
@@ -804,7 +835,7 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
                 int lb = 0, le = 0;
                 if (q < q1) {
                     // in range: checked by the short kernel
-                    const int o = a.order_seq16 ? (int)a.order_seq16[q] : a.order_seq[q];
+                    const int o = qb == q0 ? o_first : id_of(inst, q);
                     lb = a.order_off[o];
                     le = a.order_off[o + 1];
                     if (lb < 0 || le < lb || le > a.n_lines) {
@@ -815,21 +846,35 @@ __global__ void __launch_bounds__(LONG_WARPS * 32) k_eval_long(LongArgs L) {
                 }
                 const int cnt = le - lb;
                 const int incl = warp_inclusive_scan(cnt);
+                // the lines' indices at their positions in the tour (shared
+                // stores only); their keys are gathered below
                 int pos = n + incl - cnt;
-                // four lines a step: their key (or SKU and slot) loads in flight together
-                for (int l0 = lb; l0 < le; l0 += 4) {
+                for (int l = lb; l < le; ++l, ++pos)
+                    if (pos < LONG_MAXL) kb[pos] = (uint32_t)l;
+                n += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (more1) c_o = c_q0 + lane < c_q1 ? id_of(c_inst, c_q0 + lane) : 0;
+            __syncwarp();
+            // keys: the warp's lanes over the tour's positions, four positions
+            // a lane with their SKU and slot loads in flight together
+            {
+                const int nn = min(n, LONG_MAXL);
+                for (int x0 = 0; x0 < nn; x0 += 128) {
                     uint32_t k[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) k[u] = l0 + u < le ? key_of<false, SHARED_MAP, false>(a, src, l0 + u) : 0u;
+                    for (int u = 0; u < 4; ++u) {
+                        const int x = x0 + 32 * u + lane;
+                        k[u] = x < nn ? key_of<false, SHARED_MAP, false>(a, src, (int)kb[x]) : 0u;
+                    }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        if (l0 + u >= le) continue;
-                        bad |= (k[u] == KEY_BAD);
-                        if (pos < LONG_MAXL) kb[pos] = k[u];
-                        ++pos;
+                        const int x = x0 + 32 * u + lane;
+                        if (x < nn) {
+                            bad |= (k[u] == KEY_BAD);
+                            kb[x] = k[u];
+                        }
                     }
                 }
-                n += __shfl_sync(0xffffffffu, incl, 31);
             }
             bad = __any_sync(0xffffffffu, bad);
             if (n > LONG_MAXL || bad) {

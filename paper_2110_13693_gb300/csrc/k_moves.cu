@@ -314,29 +314,64 @@ __global__ void k_scan_add(int64_t* v, int64_t n, const int64_t* block_tot) {
 
 // task = {move, tour, order, tag}: tag >= 0 or -1: order moves (tag = order
 // removed, order = order added, -1 = none); tag -2 / -3: SKU swap, `order` is
-// the order of s1's / s2's list the task came from
+// the order of s1's / s2's list the task came from.  One move per lane; a SKU
+// list longer than MVF_SERIAL orders (a popular SKU can sit in hundreds) is
+// written by the whole warp, 32 tasks a step, at the same places.
+constexpr int MVF_SERIAL = 32;
+
 __global__ void k_mv_fill(MoveArgs M) {
     const EvalArgs& a = M.a;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M.n_moves; m += gridDim.x * blockDim.x) {
-        if (M.mstatus[m] != 0) continue;
-        const int4 mv = M.moves[m];
-        const int64_t row = (int64_t)mv.w * a.n_orders;
-        int4* out = M.tasks + M.task_off[m];
-        if (mv.x == 0) {
-            const int ta = M.order_tour[row + mv.y], tb = M.order_tour[row + mv.z];
-            out[0] = make_int4(m, ta, mv.z, mv.y);
-            out[1] = make_int4(m, tb, mv.y, mv.z);
-        } else if (mv.x == 1) {
-            const int ta = M.order_tour[row + mv.y], tb = a.plan_tour_off[mv.w] + mv.z;
-            out[0] = make_int4(m, ta, -1, mv.y);
-            out[1] = make_int4(m, tb, mv.y, -1);
-        } else {
-            int k = 0;
-            for (int side = 0; side < (mv.x == 2 ? 2 : 1); ++side) {
-                const int s = side ? mv.z : mv.y;
-                for (int i = M.sku_off[s]; i < M.sku_off[s + 1]; ++i) {
-                    const int o = M.sku_orders[i];
-                    out[k++] = make_int4(m, M.order_tour[row + o], o, side ? -3 : -2);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < M.n_moves; base += stride) {
+        const int m = (int)(base + lane);
+        int lb[2] = {0, 0}, ln[2] = {0, 0}, lk[2] = {0, 0};   // a long list per side: begin, length, first task
+        int64_t row = 0, t0 = 0;
+        if (m < M.n_moves && M.mstatus[m] == 0) {
+            const int4 mv = M.moves[m];
+            row = (int64_t)mv.w * a.n_orders;
+            t0 = M.task_off[m];
+            int4* out = M.tasks + t0;
+            if (mv.x == 0) {
+                const int ta = M.order_tour[row + mv.y], tb = M.order_tour[row + mv.z];
+                out[0] = make_int4(m, ta, mv.z, mv.y);
+                out[1] = make_int4(m, tb, mv.y, mv.z);
+            } else if (mv.x == 1) {
+                const int ta = M.order_tour[row + mv.y], tb = a.plan_tour_off[mv.w] + mv.z;
+                out[0] = make_int4(m, ta, -1, mv.y);
+                out[1] = make_int4(m, tb, mv.y, -1);
+            } else {
+                int k = 0;
+                for (int side = 0; side < (mv.x == 2 ? 2 : 1); ++side) {
+                    const int sk = side ? mv.z : mv.y;
+                    const int b = M.sku_off[sk], e = M.sku_off[sk + 1];
+                    if (e - b > MVF_SERIAL) {
+                        lb[side] = b;
+                        ln[side] = e - b;
+                        lk[side] = k;
+                        k += e - b;
+                        continue;
+                    }
+                    for (int i = b; i < e; ++i) {
+                        const int o = M.sku_orders[i];
+                        out[k++] = make_int4(m, M.order_tour[row + o], o, side ? -3 : -2);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            unsigned longs = __ballot_sync(0xffffffffu, ln[side] > 0);
+            while (longs) {
+                const int src = __ffs(longs) - 1;
+                longs &= longs - 1;
+                const int b = __shfl_sync(0xffffffffu, lb[side], src), n = __shfl_sync(0xffffffffu, ln[side], src);
+                const int k0 = __shfl_sync(0xffffffffu, lk[side], src), mm = __shfl_sync(0xffffffffu, m, src);
+                const int64_t r = __shfl_sync(0xffffffffu, row, src);
+                int4* out = M.tasks + __shfl_sync(0xffffffffu, t0, src) + k0;
+                for (int i = lane; i < n; i += 32) {
+                    const int o = M.sku_orders[b + i];
+                    out[i] = make_int4(mm, M.order_tour[r + o], o, side ? -3 : -2);
                 }
             }
         }
@@ -507,10 +542,11 @@ __global__ void __launch_bounds__(MV_THREADS) k_mv_eval(MoveArgs M) {
     }
 }
 
-// Warp-parallel form of walk_task: lane j walks the changed tour's orders
-// j, j + 32, ... (the added order last) and stores its keys at positions
-// given by a warp prefix sum of the order line counts; only the first `cap`
-// keys are stored.  Returns ok and sets n and primary (all warp-uniform).
+// Warp-parallel form of walk_task: lane j takes the changed tour's orders
+// j, j + 32, ... (the added order last) and stores their line indices at
+// positions given by a warp prefix sum of the order line counts; then the
+// lanes turn positions x, x + 32, ... into keys.  Only the first `cap`
+// positions are stored.  Returns ok and sets n and primary (all warp-uniform).
 __device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk, const int4 mv, uint32_t* kb,
                                                int cap, int lane, int& n_out, bool& primary) {
     const EvalArgs& a = M.a;
@@ -523,6 +559,8 @@ __device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk,
     const int q_end = bad ? q0 : (add >= 0 ? q1 + 1 : q1);
     int hit_min = 0x7fffffff, n = 0;
     bool own_has_s1 = false;
+    // the lines' indices at their positions in the changed tour (lanes over
+    // orders; shared stores only)
     for (int qb = q0; qb < q_end; qb += 32) {
         const int q = qb + lane;
         int o = -1, lb = 0, le = 0;
@@ -534,18 +572,47 @@ __device__ __forceinline__ bool walk_task_warp(const MoveArgs& M, const int4 tk,
         const int cnt = le - lb;
         const int incl = warp_inclusive_scan(cnt);
         int pos = n + incl - cnt;
-        for (int l = lb; l < le; ++l, ++pos) {
-            const int s = a.line_sku[l];
-            if ((unsigned)s >= (unsigned)a.n_sku) { bad = true; break; }
-            if (swap && sku_hit(s, mv)) {
-                hit_min = min(hit_min, o);
-                if (o == tk.z && s == mv.y) own_has_s1 = true;
-            }
-            const int loc = task_loc(map, s, mv);
-            if ((unsigned)loc >= (unsigned)a.g.n_loc) { bad = true; break; }
-            if (pos < cap) kb[pos] = loc_key(a.g, loc);
-        }
+        for (int l = lb; l < le; ++l, ++pos)
+            if (pos < cap) kb[pos] = (uint32_t)l;
         n += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    __syncwarp();
+    // keys: lanes over positions, four a lane with their SKU and slot loads in
+    // flight together.  A line whose SKU the move changes finds its orders
+    // among the tour's (a SKU move keeps every order of the tour)
+    const int nn = bad ? 0 : min(n, cap);
+    for (int x0 = 0; x0 < nn; x0 += 128) {
+        int l[4], sk[4], loc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int x = x0 + 32 * u + lane;
+            l[u] = x < nn ? (int)kb[x] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sk[u] = l[u] >= 0 ? a.line_sku[l[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            loc[u] = (l[u] >= 0 && (unsigned)sk[u] < (unsigned)a.n_sku) ? task_loc(map, sk[u], mv) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (l[u] < 0) continue;
+            if ((unsigned)sk[u] >= (unsigned)a.n_sku || (unsigned)loc[u] >= (unsigned)a.g.n_loc) {
+                bad = true;
+                continue;
+            }
+            if (swap && sku_hit(sk[u], mv)) {
+                for (int q = q0; q < q1; ++q) {
+                    const int o = a.order_seq[q];
+                    if ((unsigned)o >= (unsigned)a.n_orders) continue;
+                    if (l[u] >= a.order_off[o] && l[u] < a.order_off[o + 1]) {
+                        hit_min = min(hit_min, o);
+                        if (o == tk.z && sk[u] == mv.y) own_has_s1 = true;
+                    }
+                }
+            }
+            kb[x0 + 32 * u + lane] = loc_key(a.g, loc[u]);
+        }
     }
     const bool ok = !__any_sync(0xffffffffu, bad);
     hit_min = __reduce_min_sync(0xffffffffu, hit_min);
@@ -571,7 +638,7 @@ __device__ __forceinline__ void mv_long_commit(const MoveArgs& M, int64_t i, int
     atomicAdd(reinterpret_cast<unsigned long long*>(&M.delta[2 * tk.x + 1]), (unsigned long long)dr);
 }
 
-__global__ void __launch_bounds__(LONG_WARPS * 32) k_mv_long_rec(MoveArgs M) {
+__global__ void __launch_bounds__(LONG_WARPS * 32, 6) k_mv_long_rec(MoveArgs M) {
     __shared__ uint32_t buf[LONG_WARPS][LONG_MAXL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int count = min(min(*M.long_count, M.long_cap), M.long_rec_cap);
@@ -1008,11 +1075,23 @@ __global__ void __launch_bounds__(TF_THREADS) k_task_features(MoveArgs M, FeatCo
 // index); unfilled places get an invalid move that scores status 3.
 __global__ void k_screen_score(ScreenArgs S) {
     const MoveArgs& M = S.M;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M.n_moves; m += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // one move per lane; a move of more than MVF_SERIAL tasks is scored by the
+    // whole warp: lanes load 32 tasks' terms at once, and every lane adds
+    // them up in task order, so the sum is the serial one
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < M.n_moves; base += stride) {
+        const int64_t m = base + lane;
         float sc = 3.0e38f;
-        if (M.mstatus[m] == 0) {
+        int64_t i0 = 0, i1 = 0;
+        if (m < M.n_moves && M.mstatus[m] == 0) {
             sc = 0.0f;
-            for (int64_t i = M.task_off[m]; i < M.task_off[m + 1]; ++i) {
+            i0 = M.task_off[m];
+            i1 = M.task_off[m + 1];
+        }
+        const bool lng = i1 - i0 > MVF_SERIAL;
+        if (!lng)
+            for (int64_t i = i0; i < i1; ++i) {
                 const int4 tk = M.tasks[i];
                 if (tk.y < 0) continue;
                 // counted task: an order move, or the first task of its tour for a SKU swap
@@ -1020,8 +1099,32 @@ __global__ void k_screen_score(ScreenArgs S) {
                 if (c.x < 0) continue;
                 sc += S.y_task[i] - S.y_tour[tk.y];
             }
+        unsigned longs = __ballot_sync(0xffffffffu, lng);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int64_t b = __shfl_sync(0xffffffffu, i0, src), e = __shfl_sync(0xffffffffu, i1, src);
+            float acc = 0.0f;
+            for (int64_t c0 = b; c0 < e; c0 += 32) {
+                const int64_t i = c0 + lane;
+                float term = 0.0f;
+                bool counted = false;
+                if (i < e) {
+                    const int4 tk = M.tasks[i];
+                    if (tk.y >= 0 && M.task_cost[i].x >= 0) {
+                        counted = true;
+                        term = S.y_task[i] - S.y_tour[tk.y];
+                    }
+                }
+                const unsigned cm = __ballot_sync(0xffffffffu, counted);
+                for (int j = 0; j < 32; ++j) {
+                    const float tj = __shfl_sync(0xffffffffu, term, j);
+                    if ((cm >> j) & 1u) acc += tj;
+                }
+            }
+            if (lane == src) sc = acc;
         }
-        S.score[m] = sc;
+        if (m < M.n_moves) S.score[m] = sc;
     }
 }
 

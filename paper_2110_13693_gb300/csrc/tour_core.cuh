@@ -327,11 +327,18 @@ __device__ __forceinline__ int rr_records32_mem(const Geo& g, const uint2* rec, 
     DP5 v;
     dp_init(v);
     int pa = 0;
-    for (int j = 0; j < m; ++j) {
-        const uint2 r = rec[j * stride];
-        const int a = (int)(r.x >> 16);
-        dp_aisle_rel(v, c, a - pa, (int)(r.x & 0xFFFFu), (int)(r.y >> 16), (int)(r.y & 0xFFFFu));
-        pa = a;
+    // four records' loads in flight ahead of their DP steps
+    for (int j0 = 0; j0 < m; j0 += 4) {
+        uint2 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = j0 + u < m ? rec[(j0 + u) * stride] : make_uint2(0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + u >= m) break;
+            const int a = (int)(r[u].x >> 16);
+            dp_aisle_rel(v, c, a - pa, (int)(r[u].x & 0xFFFFu), (int)(r[u].y >> 16), (int)(r[u].y & 0xFFFFu));
+            pa = a;
+        }
     }
     return dp_final(v) + c.p2 * pa;
 }

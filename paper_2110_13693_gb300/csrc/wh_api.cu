@@ -10,6 +10,7 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <iterator>
 
 #include "wh_internal.h"
 
@@ -1309,7 +1310,11 @@ extern "C" int wh_batch_autotune(wh_batch* b, uint32_t routing_mask, const char*
         if (from_cache) *from_cache = 0;
         const int32_t smem = b->tune.smem_tables;
         const int thread_opts[] = {128, 256, 384};
+        // powers of two, and for a warp count that is not one (384 threads:
+        // 12 warps) the multiples of the warp count that split an item's
+        // chunks evenly over the CTA's warps
         const int chunk_opts[] = {2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096};
+        const int warp_mults[] = {1, 2, 4, 8, 16, 32, 64, 128};
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess) return WH_ECUDA;
         if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1320,7 +1325,11 @@ extern "C" int wh_batch_autotune(wh_batch* b, uint32_t routing_mask, const char*
         best.ms = 1e30;
         for (int th : thread_opts) {
             if (th > 256 && !b->key16) continue;
-            for (int ch : chunk_opts) {
+            std::vector<int> chs(std::begin(chunk_opts), std::end(chunk_opts));
+            const int nw = th / 32;
+            if (nw & (nw - 1))
+                for (int m : warp_mults) chs.push_back(nw * m);
+            for (int ch : chs) {
                 rc = wh_batch_set_tuning(b, th, ch, smem);
                 if (rc != WH_OK) break;
                 rc = launch_batch(b, routing_mask, s);   // warm-up
