@@ -287,7 +287,25 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                     }
                     if (n + (le - lb) > SHORT_MAX) { n += le - lb; break; }
                     n += le - lb;
-                    if constexpr (!SHARED_MAP) {
+                    if constexpr (!SHARED_MAP && !KEY16) {
+                        // the plan's own slotting, 32-bit keys: the lines'
+                        // SKUs go to their positions here; the pass after
+                        // the order loop turns them into keys, eight
+                        // slot-map gathers in flight whatever the orders' sizes
+                        int l = lb;
+                        for (; l + 1 < le; l += 2) {
+                            const uint32_t s0 = (uint32_t)src.skus[l], s1 = (uint32_t)src.skus[l + 1];
+                            sts_key<uint32_t>(wa, s0);
+                            sts_key<uint32_t>(wa + stepb, s1);
+                            wa += two_tb;
+                        }
+                        if (l < le) {
+                            sts_key<uint32_t>(wa, (uint32_t)src.skus[l]);
+                            wa += stepb;
+                            stepb = two_tb - stepb;
+                        }
+                        continue;
+                    } else if constexpr (!SHARED_MAP) {
                         // the plan's own slotting: four lines a step, their
                         // SKUs and then their slot-map gathers (global
                         // memory) in flight together
@@ -343,6 +361,32 @@ __device__ __forceinline__ void eval_chunks(const EvalArgs& a, KeySrc src, uint3
                             stepb = two_tb - stepb;
                         }
                     }
+                }
+            }
+        }
+        if constexpr (!SHARED_MAP && !KEY16) {
+            // positions 0 .. n-1 hold SKUs: their slots, eight at a time
+            const int np = (active && !bad && n <= SHORT_MAX) ? n : 0;
+            const uint32_t cb = smem_addr(col32);
+            for (int p0 = 0; p0 < np; p0 += 8) {
+                uint32_t sk[8];
+                int loc[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int p = p0 + j;
+                    sk[j] = p < np ? lds_key<uint32_t>(cb + (uint32_t)(p >> 1) * (8u * (uint32_t)T) + 4u * (uint32_t)(p & 1)) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) loc[j] = (p0 + j < np && sk[j] < (uint32_t)a.n_sku) ? src.map[sk[j]] : -1;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int p = p0 + j;
+                    if (p >= np) continue;
+                    uint32_t k32 = KEY_BAD;
+                    if (sk[j] >= (uint32_t)a.n_sku) flag(a.status, WH_STATUS_BAD_SKU);
+                    else if ((unsigned)loc[j] >= (unsigned)a.g.n_loc) flag(a.status, WH_STATUS_BAD_LOC);
+                    else k32 = loc_key(a.g, loc[j]);
+                    sts_key<uint32_t>(cb + (uint32_t)(p >> 1) * (8u * (uint32_t)T) + 4u * (uint32_t)(p & 1), k32);
                 }
             }
         }

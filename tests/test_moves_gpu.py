@@ -274,3 +274,60 @@ def test_moved_tours_over_the_record_slots(gpu_lib):
                      for p in range(4)]).astype(np.int32)
     s, st = check(gpu_lib, inst, moves_for(inst, 3, 64), maps=maps)
     assert st == 0 and (s == 0).sum() > 150
+
+
+def test_bad_location_past_the_short_limit(gpu_lib):
+    """Three long tours of plan 0 reach a SKU whose slot-map entry is out of
+    range only after their first 64 lines (the short-task pass stops before
+    it; the long-task pass walks those tours in full).  Every move whose
+    changed tours include one of them scores status 3; every other move
+    scores as the oracle scores it on the intact slot maps."""
+    lay = wh_gen.Layout(40, 100)
+    inst = long_instance(lay, 11)
+    maps = np.tile(inst.slot_map, (inst.n_plans, 1)).astype(np.int32)
+    ol = np.diff(inst.order_off)
+    t0, t1 = inst.plan_tour_off[0], inst.plan_tour_off[1]
+    tour_of = {}
+    for t in range(t0, t1):
+        for o in inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]:
+            tour_of[int(o)] = t
+    bad_tours, bad_skus = set(), set()
+    for t in range(t0, t1):
+        orders = inst.order_seq[inst.tour_off[t]:inst.tour_off[t + 1]]
+        if ol[orders[:-1]].sum() < 65:
+            continue
+        sku = int(inst.line_sku[inst.order_off[orders[-1]]])
+        if (inst.line_sku == sku).sum() != 1:
+            continue
+        bad_tours.add(t)
+        bad_skus.add(sku)
+        if len(bad_tours) == 3:
+            break
+    assert len(bad_tours) == 3
+    mv = moves_for(inst, 12, 64)
+    keep = [m for m in range(mv.shape[0]) if not (mv[m, 0] >= 2 and (mv[m, 1] in bad_skus or mv[m, 2] in bad_skus))]
+    mv = mv[keep]
+    want_d, want_s = oracle.eval_moves(inst, mv, 0, 0, slot_map=maps.ravel(), slot_map_stride=inst.n_sku)
+    broken = maps.copy()
+    for sku in bad_skus:
+        broken[0, sku] = -1
+    d, s, _ = gpu_moves(gpu_lib, inst, mv, maps=broken)
+    line_order = np.repeat(np.arange(inst.n_orders), ol)
+    touched = 0
+    for m, (typ, a, b, p) in enumerate(mv):
+        hit = False
+        if p == 0 and want_s[m] == 0:
+            if typ == 0:
+                hit = tour_of[int(a)] in bad_tours or tour_of[int(b)] in bad_tours
+            elif typ == 1:
+                hit = tour_of[int(a)] in bad_tours or t0 + int(b) in bad_tours
+            else:
+                skus = (a, b) if typ == 2 else (a,)
+                orders = {int(line_order[l]) for l in np.nonzero(np.isin(inst.line_sku, skus))[0]}
+                hit = any(tour_of[o] in bad_tours for o in orders)
+        if hit:
+            touched += 1
+            assert s[m] == 3 and (d[m] == 0).all(), (m, mv[m], s[m], d[m])
+        else:
+            assert s[m] == want_s[m] and (d[m] == want_d[m]).all(), (m, mv[m], s[m], want_s[m], d[m], want_d[m])
+    assert touched > 0 and (s == 0).sum() > 100
