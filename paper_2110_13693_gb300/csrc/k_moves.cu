@@ -17,6 +17,7 @@
 // per (order with s1 or s2); of the tasks that land in the same tour only the
 // one of the smallest such order counts, so no de-duplication pass is needed.
 #include "tour_core.cuh"
+#include "feat_core.cuh"
 
 namespace wh {
 

@@ -6,6 +6,7 @@
 // kernel, the prediction cache's list maintenance and the bf16 copy of the
 // parameters.
 #include "tour_core.cuh"
+#include "feat_core.cuh"
 
 namespace wh {
 
