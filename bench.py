@@ -1281,11 +1281,12 @@ def run_case(name):
     elif name == "batched-small":
         # 256 instances of the headline's generator x 64 plans through the
         # same packed device set (16-bit order ids read directly) and CTA
-        # size as the headline; work items of 64 chunks fill the GPU
+        # size as the headline; work items of 120 chunks (ten for each of the
+        # CTA's 12 warps, as the headline's items split evenly) fill the GPU
         insts = [wh_gen.batched_instance(3, i, n_plans=64) for i in range(256)]
         d = wh.PackedInstances(insts).device_set()
         d.load()
-        d.batch.set_tuning(384, 64, 1)
+        d.batch.set_tuning(384, 120, 1)
         for _ in range(3):
             d.batch.eval(3)
         torch.cuda.synchronize()
